@@ -1,0 +1,243 @@
+/*
+ * rix.h: C ABI of the GB300 (sm_103a) implementation of the per-partition
+ * major-cycle measurement operator and minor cycles of the decentralized
+ * radio-interferometric reconstruction of arXiv 2507.22128 ("A Decentralized
+ * Framework for Radio-Interferometric Image Reconstruction").
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * Image: N x N, row-major, row b <-> direction cosine m = (b - N/2) dl, column
+ *   a <-> l = (a - N/2) dl (phase centre at pixel (N/2, N/2)).  Real-valued,
+ *   float (RIX_FP32 jobs) or double (RIX_FP64 jobs).
+ * Visibilities: sample s = row * nchan + chan, complex interleaved
+ *   (float2 / double2), layout [nrow][nchan].
+ * uvw: float64 [nrow][3] in metres; u_lambda = u_m * f_chan / c.
+ * Weights: float32 [nrow][nchan]; NULL means natural weights of 1.
+ * Measurement model (Eq. 1, C = D = 1): V = sum I / n exp(-2 pi i (u l + v m +
+ *   w (n - 1))), with the w-term and 1/n dropped in coplanar jobs
+ *   (n_wplanes = 0).  Gridding: exponential-of-semicircle kernel, support 8,
+ *   beta = 18.4, oversampling 2 (grid 2N x 2N), w-stacking over n_wplanes
+ *   planes with the same kernel in w.
+ *
+ * Memory ownership: every pointer argument marked "device" is caller-owned
+ * device memory on the job's device (for example a torch tensor's data_ptr());
+ * the library never frees it and keeps no reference to it once the call's
+ * stream-ordered work has completed.  Everything inside a rix_ctx_t /
+ * rix_job_t is library-owned.  Pointers marked "host" are read (or written)
+ * before the call returns.
+ *
+ * Streams: `stream` is a cudaStream_t (NULL = legacy default stream).  Calls
+ * are asynchronous unless stated; device errors surface at a later call on
+ * the same job or at rix_job_sync.
+ *
+ * Errors: every call returns RIX_OK (0) or a negative code; rix_last_error()
+ * returns a thread-local message for the last failure.  No C++ exception
+ * crosses this ABI.
+ *
+ * Threading: one job must not be used from two host threads at once;
+ * different jobs may.
+ */
+#ifndef RIX_H
+#define RIX_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define RIX_OK 0
+#define RIX_EINVAL (-1)   /* bad argument, size or pointer */
+#define RIX_ENOMEM (-2)   /* device allocation failed or memory budget exceeded */
+#define RIX_ECUDA (-3)    /* a CUDA call failed */
+#define RIX_ETIMEOUT (-4) /* a bounded device-side wait expired */
+#define RIX_ESTATE (-5)   /* calls made out of order (e.g. minor before major) */
+#define RIX_EBUSY (-6)    /* the context still owns live jobs */
+
+#define RIX_FP32 0
+#define RIX_FP64 1
+
+typedef struct rix_ctx_s* rix_ctx_t;
+typedef struct rix_job_s* rix_job_t;
+typedef void* rix_stream_t; /* cudaStream_t */
+
+/* One reconstruction job (Sec. 3: one set of visibilities split into n_part
+ * uv partitions, each solved as a pseudo-full-resolution problem). */
+typedef struct {
+  int32_t n;              /* image side N: power of two, 32 .. 4096 */
+  double cell_rad;        /* pixel size (radians), > 0 */
+  int32_t n_wplanes;      /* 0 = coplanar; else 9 .. 64 w-planes */
+  int32_t nchan;          /* channels per row, 1 .. 65536 */
+  const double* freq_hz;  /* host [nchan], copied at rix_job_create */
+  int32_t precision;      /* RIX_FP32 or RIX_FP64 */
+  int32_t n_part;         /* number of uv partitions: 1 .. 4 */
+  int32_t tile;           /* uv tile side for the sort and the gridder: 16 or 32; 0 = 16 */
+} rix_job_desc;
+
+/* Host-side statistics of a partitioned job (valid after rix_set_uv_partition). */
+typedef struct {
+  int64_t nrow;
+  int64_t n_samples;          /* nrow * nchan */
+  int64_t n_outside;          /* samples whose kernel footprint leaves the grid (excluded) */
+  int64_t n_entries;          /* sum over partitions of samples in the partition */
+  int64_t part_count[4];      /* samples per partition (overlap counted in each) */
+  double part_weight[4];      /* weight sum per partition */
+  double ell_px[3];           /* ring radii used (pixels of the N-grid's Fourier plane) */
+  double delta_px;
+  double w_min;               /* lowest w (wavelengths) */
+  double dw;                  /* w-plane spacing (wavelengths) */
+  double max_dw_nm1;          /* max |dw (n - 1)| over the image (w-stacking accuracy) */
+  int32_t window_lo[4];       /* per partition uv-grid window [lo, lo + size) on both axes */
+  int32_t window_size[4];
+  int64_t n_work_items;       /* gridder work items (tile chunks) over all partitions */
+  int32_t cycle[4];           /* major cycles completed per partition */
+} rix_job_stats;
+
+/* ms-CLEAN parameters (Eq. 6-7; Sec. 5.2). */
+typedef struct {
+  const float* scales;        /* host [n_scales], scale radii in pixels, scales[0] = 0 */
+  int32_t n_scales;           /* 1 .. 8 */
+  double gain;                /* loop gain, (0, 1] */
+  int32_t niter;              /* K, maximum CLEAN iterations this cycle */
+  double threshold;           /* stop once max |R_0| < threshold */
+} rix_msclean_params;
+
+/* FISTA parameters (Eq. 4-5; Sec. 5.2). */
+typedef struct {
+  double lambda;              /* > 0: absolute regularisation weight */
+  double lambda_rel;          /* used when lambda <= 0: lambda = lambda_rel * max|residual| of cycle 1 */
+  int32_t iters;              /* FISTA iterations per major cycle (50 in the paper) */
+  int32_t levels;             /* Db4 decomposition levels, 1 .. log2(N) - 3 */
+} rix_fista_params;
+
+/* ---- context and job lifetime --------------------------------------------- */
+
+/* Creates a context on CUDA device `device` that admits jobs while their
+ * summed workspace stays within mem_budget_bytes (0 = no budget). */
+int rix_create(rix_ctx_t* ctx, int device, size_t mem_budget_bytes);
+/* Destroys a context; RIX_EBUSY while it still owns jobs. */
+int rix_destroy(rix_ctx_t ctx);
+
+/* Upper bound of the device memory a job of this shape with `nrow` rows
+ * holds (admission control for serving).  Returns 0 for an invalid desc. */
+size_t rix_job_workspace_bytes(const rix_job_desc* desc, int64_t nrow);
+
+/* Validates desc and creates an empty job; RIX_ENOMEM if the context budget
+ * cannot admit rix_job_workspace_bytes(desc, max_rows). */
+int rix_job_create(rix_ctx_t ctx, const rix_job_desc* desc, int64_t max_rows, rix_job_t* job);
+int rix_job_destroy(rix_job_t job);
+/* Blocks until all work issued on the job has finished; reports deferred
+ * device errors (RIX_ETIMEOUT for an expired bounded wait). */
+int rix_job_sync(rix_job_t job);
+int rix_job_get_stats(rix_job_t job, rix_job_stats* out);
+
+/* ---- a1-a3: coordinates, partition, tile sort (Sec. 3, Fig. 3) ------------- */
+
+/* Computes each sample's grid coordinates (FP64), its radius
+ * r = |(u, v)|_lambda N dl in pixels of the N-grid's Fourier plane, and its
+ * partitions: sample in p  <=>  (p == 0 or r >= ell_p - delta) and
+ * (p == n_part-1 or r <= ell_{p+1} + delta), both inclusive (overlapping
+ * domains of Sec. 3).  ell_px: host [n_part-1] ascending ring radii, or NULL
+ * for the lower i/n_part quantiles of r over all samples (element
+ * floor(i (n-1) / n_part) of the ascending order; the lower median for 2).
+ * delta_px: overlap half-width (1 pixel in Sec. 5.1).  Samples whose kernel
+ * footprint leaves the grid are excluded and counted.  Then sorts the
+ * (sample, partition) entries stably by the key (partition, first w-plane,
+ * tile row, tile column) with an LSD radix sort and builds the gridder's
+ * work items.
+ *   uvw_m    device [nrow][3] float64, copied into the job
+ *   weight   device [nrow][nchan] float32 or NULL (= 1), copied
+ *   mask_out device [nrow][nchan] uint8 or NULL: bit p set for partition p
+ *            (0 for excluded samples)
+ * Synchronises `stream` once at the end (sizes are read back to the host).
+ * May be called again to re-partition; resets every partition's state. */
+int rix_set_uv_partition(rix_job_t job, const double* uvw_m, int64_t nrow, const float* weight,
+                         const double* ell_px, double delta_px, uint8_t* mask_out,
+                         rix_stream_t stream);
+
+/* Copies the sorted entries (keys and sample indices, rix_job_stats.n_entries
+ * of each) to device buffers; keys are packed as
+ * part << (2 bt + bw) | plane << 2 bt | tile_row << bt | tile_col with
+ * bt = log2(2N / tile) and bw = bits of (n_wplanes - 7) (0 if coplanar). */
+int rix_get_sorted_entries(rix_job_t job, uint32_t* keys_out, uint32_t* samples_out,
+                           rix_stream_t stream);
+
+/* ---- a4-a7: the measurement operator (Eq. 2) ------------------------------- */
+
+/* Degridding G^dagger F (Eq. 2): model visibilities of `image` (device N x N)
+ * for the samples of partition `part`, written to vis_out (device
+ * [nrow][nchan] complex); samples outside the partition are left untouched. */
+int rix_degrid(rix_job_t job, int part, const void* image, void* vis_out, rix_stream_t stream);
+
+/* Gridding F^dagger G (Eq. 2): dirty image Re(A^H (w . vis)) / W_part of the
+ * partition's samples (device vis [nrow][nchan] complex) into image_out
+ * (device N x N). */
+int rix_grid(rix_job_t job, int part, const void* vis, void* image_out, rix_stream_t stream);
+
+/* PSF of partition `part`: the dirty image of unit visibilities on a 2N x 2N
+ * image (centre at pixel (N, N)), normalised by the weight sum W_part, into
+ * psf_out (device (2N)^2, may be NULL); *weight_sum_out (host, may be NULL)
+ * receives W_part.  Computed once and kept by the job. */
+int rix_psf(rix_job_t job, int part, void* psf_out, double* weight_sum_out, rix_stream_t stream);
+
+/* One major cycle of partition `part` (Eq. 2): residual
+ * F^dagger G (v - G^dagger F model) / W_part of the partition's samples, with
+ * degrid, residual and grid fused per tile.  vis_obs: device [nrow][nchan]
+ * complex observed visibilities.  model: device N x N to replace the job's
+ * resident model image of the partition first, or NULL to use the resident
+ * model (zero initially; the minor cycles add to it, Eq. 3).  residual_out:
+ * device N x N or NULL.  Advances the partition's cycle counter. */
+int rix_major_cycle(rix_job_t job, int part, const void* vis_obs, const void* model,
+                    void* residual_out, rix_stream_t stream);
+
+/* ---- a8-a10: fill and minor cycles (Sec. 4, Eq. 4-7) ---------------------- */
+
+/* Minor cycle of partition `part` at its current cycle n, by multi-scale
+ * CLEAN on the pseudo-full-resolution problem of Eq. 7: first adds the other
+ * partitions' filtered deconvolved residuals Phi_q^{n-1} to the aggregates
+ * rho_{q->p} (n >= 2), builds the dirty image
+ *   gamma Gamma_p i_p + sum_q mu_q H_q rho_{q->p}
+ * and PSF gamma Gamma_p H_p + sum_q mu_q Gamma_q H_q ((gamma, mu) = (1, 0) at
+ * n = 1, else the partitions' weight fractions), cleans it (scales limited to
+ * those present in the partition at n = 1), then updates the resident model
+ * (Eq. 3), publishes Phi_p^n = Gamma_p i_bar_p^n and subtracts
+ * Gamma_q i_bar_p^n from rho_{q->p}.  delta_out: device N x N or NULL,
+ * receives i_bar_p^n.  Needs the major cycle n of `part` and the minor cycle
+ * n-1 of every partition (RIX_ESTATE otherwise). */
+int rix_minor_cycle_msclean(rix_job_t job, int part, const rix_msclean_params* params,
+                            void* delta_out, rix_stream_t stream);
+
+/* Same for the sparsity-regularised minor cycle of Eq. 5 (Eq. 4 when
+ * n_part = 1): FISTA on
+ *   ||Gamma_p (i_p - H_p W alpha)||^2 + gamma_n sum_q ||rho_{q->p} - Gamma_q W alpha||^2
+ *   + lambda ||alpha||_1
+ * with W the orthonormal periodic Db4 wavelet basis, gamma_n = 0 at n = 1
+ * and 1 afterwards. */
+int rix_minor_cycle_fista(rix_job_t job, int part, const rix_fista_params* params,
+                          void* delta_out, rix_stream_t stream);
+
+/* ms-CLEAN components found by the last minor cycle of `part`: count (host)
+ * and, when non-NULL, up to `capacity` entries of scale index and row-major
+ * pixel index (host int32) and amplitude (host double), in the order found.
+ * Synchronises the stream. */
+int rix_get_components(rix_job_t job, int part, int32_t* count, int32_t capacity,
+                       int32_t* scale_out, int32_t* pixel_out, double* amp_out,
+                       rix_stream_t stream);
+
+/* Copies the resident model image of `part` (device N x N). */
+int rix_get_model(rix_job_t job, int part, void* image_out, rix_stream_t stream);
+
+/* ---- a11: combine (Sec. 5.2) ----------------------------------------------- */
+
+/* Final image: the equal-weight mean of the partitions' model images
+ * (0.5 / 0.5 for two partitions), device N x N. */
+int rix_combine(rix_job_t job, void* image_out, rix_stream_t stream);
+
+/* Thread-local message of the last failed call on this thread. */
+const char* rix_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RIX_H */

@@ -1,0 +1,591 @@
+// a4-a7: G^dagger F and F^dagger G of Eq. 2 for one uv partition.
+//
+// Model image -> w-planes (correction, phase screen, pruned FFT; k_fft.cu)
+// -> per work item (one uv tile of one w-plane block, at most 2048 sorted
+// samples): stage the tile (+ kernel halo) of the 8 model planes it touches
+// into shared memory, degrid each sample with a warp (32 lanes x 16 taps,
+// warp-shuffle reduction), form the weighted residual, spread it into a
+// shared-memory sub-grid, and flush that sub-grid once per work item with
+// vector atomics -> residual planes -> inverse pruned FFT, conjugate phase
+// screen, sum over planes, correction -> residual image.
+//
+// Precision: sample coordinates, the kernel argument offsets and the w-plane
+// phases are formed in FP64; kernel weights, accumulation and FFTs in the
+// job's precision (FP32 or FP64).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "rix_internal.cuh"
+
+namespace rix {
+namespace {
+
+enum GridMode : int { kDegrid = 0, kGrid = 1, kResid = 2, kPsf = 3 };
+
+// ----------------------------------------------------------- host tables ----
+// Gauss-Legendre nodes and weights on [-1, 1] by Newton iteration on P_n.
+void gauss_legendre(int n, std::vector<double>& x, std::vector<double>& w) {
+  x.resize(n);
+  w.resize(n);
+  for (int i = 0; i < (n + 1) / 2; ++i) {
+    double z = std::cos(M_PI * (i + 0.75) / (n + 0.5));
+    double pp = 0.0;
+    for (int it = 0; it < 100; ++it) {
+      double p1 = 1.0, p2 = 0.0;
+      for (int j = 1; j <= n; ++j) {
+        const double p3 = p2;
+        p2 = p1;
+        p1 = ((2.0 * j - 1.0) * z * p2 - (j - 1.0) * p3) / j;
+      }
+      pp = n * (z * p1 - p2) / (z * z - 1.0);
+      const double dz = p1 / pp;
+      z -= dz;
+      if (std::fabs(dz) < 1e-16) break;
+    }
+    x[i] = -z;
+    x[n - 1 - i] = z;
+    w[i] = w[n - 1 - i] = 2.0 / ((1.0 - z * z) * pp * pp);
+  }
+}
+
+// Fourier transform of the ES kernel over cell units,
+//   Phi(f) = (W/2) int_{-1}^{1} phi(z) cos(pi W z f) dz,
+// with z = sin(t) (analytic integrand), by Gauss-Legendre quadrature in t.
+struct EsFourier {
+  std::vector<double> st, wt;
+  EsFourier() {
+    std::vector<double> x, w;
+    gauss_legendre(96, x, w);
+    st.resize(x.size());
+    wt.resize(x.size());
+    for (size_t k = 0; k < x.size(); ++k) {
+      const double t = 0.5 * M_PI * x[k];
+      st[k] = std::sin(t);
+      wt[k] = 0.5 * M_PI * w[k] * std::exp(kBeta * (std::cos(t) - 1.0)) * std::cos(t);
+    }
+  }
+  double operator()(double f) const {
+    double acc = 0.0;
+    for (size_t k = 0; k < st.size(); ++k) acc += wt[k] * std::cos(M_PI * kW * f * st[k]);
+    return 0.5 * kW * acc;
+  }
+};
+
+// Per-pixel correction 1 / (Phi(a'/Ng) Phi(b'/Ng) [n Phi(dw (n-1))]) and n - 1
+// of an M x M image on an Ng grid.  The w-term depends on r^2 only; it is
+// evaluated once per distinct (|a'|, |b'|) pair.
+void build_correction(int M, int ng, double cell, bool wstack, double dw, std::vector<double>& corr,
+                      std::vector<double>& nm1) {
+  static const EsFourier phi;
+  const int h = M / 2;
+  std::vector<double> p1(M);
+  for (int a = 0; a < M; ++a) p1[a] = phi((double)(a - h) / ng);
+  corr.assign((size_t)M * M, 0.0);
+  if (wstack) nm1.assign((size_t)M * M, 0.0);
+  std::vector<double> wcorr;
+  std::vector<double> wnm1;
+  if (wstack) {
+    // index by (|a'|, |b'|) with |a'|, |b'| <= h
+    wcorr.assign((size_t)(h + 1) * (h + 1), 0.0);
+    wnm1.assign((size_t)(h + 1) * (h + 1), 0.0);
+    for (int i = 0; i <= h; ++i)
+      for (int j = i; j <= h; ++j) {
+        const double l = i * cell, m = j * cell;
+        const double r2 = l * l + m * m;
+        const double n = std::sqrt(1.0 - r2);
+        const double d = -r2 / (1.0 + n);
+        const double c = 1.0 / (n * phi(dw * d));
+        wcorr[(size_t)i * (h + 1) + j] = wcorr[(size_t)j * (h + 1) + i] = c;
+        wnm1[(size_t)i * (h + 1) + j] = wnm1[(size_t)j * (h + 1) + i] = d;
+      }
+  }
+  for (int b = 0; b < M; ++b)
+    for (int a = 0; a < M; ++a) {
+      double c = 1.0 / (p1[a] * p1[b]);
+      if (wstack) {
+        const size_t k = (size_t)std::abs(a - h) * (h + 1) + std::abs(b - h);
+        // offsets of exactly -h appear once; |.| <= h covers them
+        c *= wcorr[k];
+        nm1[(size_t)b * M + a] = wnm1[k];
+      }
+      corr[(size_t)b * M + a] = c;
+    }
+}
+
+template <typename R>
+int upload_real(Job* job, DevBuf& dst, const std::vector<double>& src, cudaStream_t st) {
+  std::vector<R> tmp(src.begin(), src.end());
+  RIX_TRY(dst.alloc(job->ctx, tmp.size() * sizeof(R)));
+  RIX_CUDA(cudaMemcpyAsync(dst.p, tmp.data(), tmp.size() * sizeof(R), cudaMemcpyHostToDevice, st));
+  RIX_CUDA(cudaStreamSynchronize(st));
+  return RIX_OK;
+}
+
+int upload_double(Job* job, DevBuf& dst, const std::vector<double>& src, cudaStream_t st) {
+  RIX_TRY(dst.alloc(job->ctx, src.size() * sizeof(double)));
+  RIX_CUDA(cudaMemcpyAsync(dst.p, src.data(), src.size() * sizeof(double), cudaMemcpyHostToDevice, st));
+  RIX_CUDA(cudaStreamSynchronize(st));
+  return RIX_OK;
+}
+
+// --------------------------------------------------------------- kernels ----
+template <typename R> __device__ __forceinline__ R es_weight(R d, int i);
+template <> __device__ __forceinline__ float es_weight<float>(float d, int i) {
+  const float z = (d + (float)i) * (2.0f / kW) - 1.0f;
+  const float t = fmaxf(1.0f - z * z, 0.0f);
+  return expf((float)kBeta * (sqrtf(t) - 1.0f));
+}
+template <> __device__ __forceinline__ double es_weight<double>(double d, int i) {
+  const double z = (d + (double)i) * (2.0 / kW) - 1.0;
+  const double t = fmax(1.0 - z * z, 0.0);
+  return exp(kBeta * (sqrt(t) - 1.0));
+}
+
+struct TileArgs {
+  const uint32_t* keys;
+  const uint32_t* samples;
+  const uint32_t* items;
+  int64_t item_begin, item_count;
+  const double* uvw;
+  const double* inv_lambda;
+  int nchan;
+  double scale, half;       // grid coordinate x = u_l * scale + half
+  int nw, ww;
+  double w_min, dw;
+  int bt, bw, logT;
+  int win_lo, S;            // plane window [win_lo, win_lo + S)^2
+  const void* model;        // cplx [planes][S][S], u-major
+  void* out;                // cplx [planes][S][S]
+  const void* vis_in;       // cplx per sample
+  void* vis_out;            // cplx per sample
+  const float* weight;      // per sample or null
+};
+
+template <int T, int MODE> struct TileGeom {
+  // staged side and origin offset (in grid cells) relative to the tile origin
+  static constexpr int SP = (MODE == kPsf) ? 2 * T + 9 : T + kW - 1;
+  static constexpr int ORG = (MODE == kPsf) ? 2 : 0;
+  // plane stride in elements, == 8 (mod 16) so that the two plane halves of a
+  // half-warp land on disjoint banks
+  static constexpr int PL = ((SP * SP + 7) / 16) * 16 + 8;
+};
+
+template <typename R, int WW, int T, int MODE>
+__global__ void __launch_bounds__(256) k_tiles(TileArgs a) {
+  using C = cplx<R>;
+  using TG = TileGeom<T, MODE>;
+  constexpr int SP = TG::SP, PL = TG::PL;
+  constexpr int G = (WW == 1) ? 8 : 32;       // lanes per sample
+  constexpr int SPW = 32 / G;                 // samples per warp at once
+  constexpr int RPL = WW * kW / G;            // rows of 8 taps per lane
+  constexpr bool kUseModel = (MODE == kDegrid || MODE == kResid);
+  constexpr bool kUseGrid = (MODE != kDegrid);
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* sm_model = reinterpret_cast<C*>(smem_raw);
+  C* sm_grid = sm_model + (kUseModel ? WW * PL : 0);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
+  const int gl = lane % G, grp = lane / G;
+  const int64_t SS = (int64_t)a.S * a.S;
+  const C* model = static_cast<const C*>(a.model);
+  C* out = static_cast<C*>(a.out);
+  const C* vin = static_cast<const C*>(a.vis_in);
+  C* vout = static_cast<C*>(a.vis_out);
+  const uint32_t tmask = (1u << a.bt) - 1u;
+
+  for (int64_t it = blockIdx.x; it < a.item_count; it += gridDim.x) {
+    const int64_t item = a.item_begin + it;
+    const uint32_t e0 = a.items[item], e1 = a.items[item + 1];
+    const uint32_t key = a.keys[e0];
+    const int tx = (int)(key & tmask), ty = (int)((key >> a.bt) & tmask);
+    const int p0 = (WW > 1) ? (int)((key >> (2 * a.bt)) & ((1u << a.bw) - 1u)) : 0;
+    const int gu0 = (MODE == kPsf ? 2 * tx * T : tx * T) + TG::ORG;   // grid coords of smem (0, 0)
+    const int gv0 = (MODE == kPsf ? 2 * ty * T : ty * T) + TG::ORG;
+    const int u0 = gu0 - a.win_lo, v0 = gv0 - a.win_lo;
+
+    for (int idx = threadIdx.x; idx < WW * SP * SP; idx += blockDim.x) {
+      const int pl = idx / (SP * SP), rem = idx - pl * (SP * SP);
+      const int iu = rem / SP, iv = rem - iu * SP;
+      if (kUseModel) {
+        const int u = u0 + iu, v = v0 + iv;
+        C val = cmake<C>(0.0, 0.0);
+        if (u >= 0 && u < a.S && v >= 0 && v < a.S) val = model[(p0 + pl) * SS + (int64_t)u * a.S + v];
+        sm_model[pl * PL + iu * SP + iv] = val;
+      }
+      if (kUseGrid) sm_grid[pl * PL + iu * SP + iv] = cmake<C>(0.0, 0.0);
+    }
+    __syncthreads();
+
+    for (uint32_t base = e0 + warp * 32; base < e1; base += nwarps * 32) {
+      const int nvalid = (int)min(32u, e1 - base);
+      const bool valid = lane < nvalid;
+      // ---- per-lane sample geometry (FP64) ----
+      const uint32_t s = valid ? a.samples[base + lane] : 0u;
+      const int64_t row = s / (uint32_t)a.nchan;
+      const int ch = (int)(s - row * a.nchan);
+      const double sc = a.inv_lambda[ch];
+      const double ul = __dmul_rn(a.uvw[row * 3 + 0], sc);
+      const double vl = __dmul_rn(a.uvw[row * 3 + 1], sc);
+      const double x = __dadd_rn(__dmul_rn(ul, a.scale), a.half);
+      const double y = __dadd_rn(__dmul_rn(vl, a.scale), a.half);
+      const double xs = __dadd_rn(x, -0.5 * kW), ys = __dadd_rn(y, -0.5 * kW);
+      const double cx = ceil(xs), cy = ceil(ys);
+      int ou = (int)cx - gu0, ov = (int)cy - gv0;
+      R du = (R)__dadd_rn(cx, -xs), dv = (R)__dadd_rn(cy, -ys);
+      R dwo = R(0);
+      if (WW > 1) {
+        const double wl = __dmul_rn(a.uvw[row * 3 + 2], sc);
+        const double tw = __ddiv_rn(__dadd_rn(wl, -a.w_min), a.dw);
+        double pc = fmin(fmax(ceil(tw), 0.0), (double)(a.nw - a.ww));
+        dwo = (R)__dadd_rn(pc, -tw);
+      }
+      if (!valid) { ou = 0; ov = 0; }
+      // guard against any sample outside the staged region (never expected)
+      if (ou < 0 || ov < 0 || ou > SP - kW || ov > SP - kW) { ou = 0; ov = 0; }
+      R vre = R(0), vim = R(0), wt = R(0);
+      if (valid) {
+        wt = a.weight ? (R)a.weight[s] : R(1);
+        if (MODE == kGrid || MODE == kResid) { const C v = vin[s]; vre = v.x; vim = v.y; }
+        if (MODE == kPsf) vre = R(1);
+      }
+
+      for (int k0 = 0; k0 < nvalid; k0 += SPW) {
+        const int k = k0 + grp;
+        const bool kvalid = k < nvalid;
+        const int src = kvalid ? k : 0;
+        const int kou = __shfl_sync(0xffffffffu, ou, src);
+        const int kov = __shfl_sync(0xffffffffu, ov, src);
+        const R kdu = __shfl_sync(0xffffffffu, du, src);
+        const R kdv = __shfl_sync(0xffffffffu, dv, src);
+        // ---- kernel weights, computed lane-parallel and broadcast ----
+        R wu[kW];
+        R wvr[RPL];          // v weight times w weight of each row this lane owns
+        int rbase[RPL];      // smem offset of (plane, v row) of each row
+        if constexpr (G == 32) {
+          const R kdw = __shfl_sync(0xffffffffu, dwo, src);
+          R myw = R(0);
+          if (gl < 8) myw = es_weight<R>(kdu, gl);
+          else if (gl < 16) myw = es_weight<R>(kdv, gl - 8);
+          else if (gl < 16 + WW) myw = es_weight<R>(kdw, gl - 16);
+#pragma unroll
+          for (int i = 0; i < kW; ++i) wu[i] = __shfl_sync(0xffffffffu, myw, i);
+          const int vrow = gl & 7, plh = gl >> 3;
+          const R wv = __shfl_sync(0xffffffffu, myw, 8 + vrow);
+#pragma unroll
+          for (int r = 0; r < RPL; ++r) {
+            const int pl = plh + 4 * r;
+            const R ww = __shfl_sync(0xffffffffu, myw, 16 + pl);
+            wvr[r] = wv * ww;
+            rbase[r] = pl * PL + kou * SP + kov + vrow;
+          }
+        } else {
+          const R myu = es_weight<R>(kdu, gl);
+          const R myv = es_weight<R>(kdv, gl);
+#pragma unroll
+          for (int i = 0; i < kW; ++i) wu[i] = __shfl_sync(0xffffffffu, myu, grp * G + i);
+          wvr[0] = myv;
+          rbase[0] = kou * SP + kov + gl;
+        }
+        // ---- degrid ----
+        R accr = R(0), acci = R(0);
+        if constexpr (kUseModel) {
+#pragma unroll
+          for (int r = 0; r < RPL; ++r) {
+            R sr = R(0), si = R(0);
+#pragma unroll
+            for (int i = 0; i < kW; ++i) {
+              const C g = sm_model[rbase[r] + i * SP];
+              sr += wu[i] * g.x;
+              si += wu[i] * g.y;
+            }
+            accr += wvr[r] * sr;
+            acci += wvr[r] * si;
+          }
+#pragma unroll
+          for (int o = G / 2; o; o >>= 1) {
+            accr += __shfl_xor_sync(0xffffffffu, accr, o);
+            acci += __shfl_xor_sync(0xffffffffu, acci, o);
+          }
+        }
+        if constexpr (MODE == kDegrid) {
+          const uint32_t ks = __shfl_sync(0xffffffffu, s, src);
+          if (kvalid && gl == 0) vout[ks] = cmake<C>(accr, acci);
+        } else {
+          // ---- grid the weighted (residual) visibility ----
+          const R kvr = __shfl_sync(0xffffffffu, vre, src);
+          const R kvi = __shfl_sync(0xffffffffu, vim, src);
+          const R kwt = __shfl_sync(0xffffffffu, wt, src);
+          R yr = kwt * kvr, yi = kwt * kvi;
+          if (MODE == kResid) { yr = kwt * (kvr - accr); yi = kwt * (kvi - acci); }
+          if (kvalid) {
+#pragma unroll
+            for (int r = 0; r < RPL; ++r) {
+              const R cr = yr * wvr[r], ci = yi * wvr[r];
+#pragma unroll
+              for (int i = 0; i < kW; ++i) {
+                C* g = &sm_grid[rbase[r] + i * SP];
+                atomicAdd(&g->x, cr * wu[i]);
+                if (MODE != kPsf) atomicAdd(&g->y, ci * wu[i]);
+              }
+            }
+          }
+        }
+      }
+    }
+    __syncthreads();
+    if constexpr (kUseGrid) {
+      for (int idx = threadIdx.x; idx < WW * SP * SP; idx += blockDim.x) {
+        const int pl = idx / (SP * SP), rem = idx - pl * (SP * SP);
+        const int iu = rem / SP, iv = rem - iu * SP;
+        const int u = u0 + iu, v = v0 + iv;
+        const C val = sm_grid[pl * PL + iu * SP + iv];
+        if ((val.x != R(0) || val.y != R(0)) && u >= 0 && u < a.S && v >= 0 && v < a.S) {
+          C* dst = &out[(p0 + pl) * SS + (int64_t)u * a.S + v];
+          if constexpr (sizeof(R) == 4) {
+            atomicAdd(reinterpret_cast<float2*>(dst), *reinterpret_cast<const float2*>(&val));
+          } else {
+            atomicAdd(&dst->x, val.x);
+            atomicAdd(&dst->y, val.y);
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+}
+
+template <typename R, int WW, int T, int MODE>
+int launch_tiles_impl(const Ctx* ctx, const TileArgs& a, cudaStream_t st) {
+  using TG = TileGeom<T, MODE>;
+  constexpr bool kUseModel = (MODE == kDegrid || MODE == kResid);
+  constexpr bool kUseGrid = (MODE != kDegrid);
+  const size_t sm = (size_t)(int(kUseModel) + int(kUseGrid)) * WW * TG::PL * sizeof(cplx<R>);
+  auto kern = k_tiles<R, WW, T, MODE>;
+  RIX_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+  int per_sm = 0;
+  RIX_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, sm));
+  per_sm = std::max(per_sm, 1);
+  const int64_t blocks = std::min<int64_t>(a.item_count, (int64_t)ctx->num_sms * per_sm);
+  if (blocks <= 0) return RIX_OK;
+  kern<<<(unsigned)blocks, 256, sm, st>>>(a);
+  RIX_LAUNCH_CHECK();
+  return RIX_OK;
+}
+
+template <typename R, int MODE>
+int launch_tiles(const Job* job, const TileArgs& a, cudaStream_t st) {
+  const bool ws = job->nw > 0;
+  if (job->tile == 16) {
+    return ws ? launch_tiles_impl<R, kW, 16, MODE>(job->ctx, a, st) : launch_tiles_impl<R, 1, 16, MODE>(job->ctx, a, st);
+  }
+  return ws ? launch_tiles_impl<R, kW, 32, MODE>(job->ctx, a, st) : launch_tiles_impl<R, 1, 32, MODE>(job->ctx, a, st);
+}
+
+TileArgs base_args(const Job* job, const Part& pt) {
+  TileArgs a{};
+  a.keys = job->keys.as<uint32_t>();
+  a.samples = job->samples.as<uint32_t>();
+  a.items = job->items.as<uint32_t>();
+  a.item_begin = pt.item_begin;
+  a.item_count = pt.item_count;
+  a.uvw = job->uvw.as<double>();
+  a.inv_lambda = job->inv_lambda.as<double>();
+  a.nchan = job->desc.nchan;
+  a.scale = job->desc.cell_rad * (double)job->ng;
+  a.half = 0.5 * job->ng;
+  a.nw = job->nw;
+  a.ww = job->ww;
+  a.w_min = job->stats.w_min;
+  a.dw = job->stats.dw;
+  a.bt = job->bt;
+  a.bw = job->bw;
+  a.logT = ilog2(job->tile);
+  a.win_lo = pt.win_lo;
+  a.S = pt.win_n;
+  a.weight = job->weight.as<float>();
+  return a;
+}
+
+XformGeom plane_geom(const Job* job, const Part& pt, bool psf) {
+  XformGeom g{};
+  const int n = job->desc.n;
+  g.M = psf ? 2 * n : n;
+  g.L = psf ? 2 * job->ng : job->ng;
+  g.logL = ilog2(g.L);
+  g.lo = psf ? pt.pwin_lo : pt.win_lo;
+  g.S = psf ? pt.pwin_n : pt.win_n;
+  g.nplanes = job->nw > 0 ? job->nw : 1;
+  g.mode = job->nw > 0 ? kFacPhase : kFacReal;
+  g.corr = psf ? job->corr_psf.p : job->corr_img.p;
+  g.nm1 = psf ? job->nm1_psf.as<double>() : job->nm1_img.as<double>();
+  g.w0 = job->stats.w_min - 0.5 * job->ww * job->stats.dw;
+  g.dw = job->stats.dw;
+  return g;
+}
+
+template <typename R>
+int ensure_plane_buffers(Job* job, Part& pt) {
+  const int np = job->nw > 0 ? job->nw : 1;
+  const size_t plane = (size_t)pt.win_n * pt.win_n * sizeof(cplx<R>);
+  if (pt.model_planes.bytes < np * plane) RIX_TRY(pt.model_planes.alloc(job->ctx, np * plane));
+  if (pt.resid_planes.bytes < np * plane) RIX_TRY(pt.resid_planes.alloc(job->ctx, np * plane));
+  const size_t tb = (size_t)np * pt.win_n * job->desc.n * sizeof(cplx<R>);
+  if (pt.tbuf.bytes < tb) RIX_TRY(pt.tbuf.alloc(job->ctx, tb));
+  return RIX_OK;
+}
+
+// image -> model planes of partition p
+template <typename R>
+int image_to_planes(Job* job, Part& pt, const R* image, cudaStream_t st) {
+  RIX_TRY(ensure_plane_buffers<R>(job, pt));
+  const XformGeom g = plane_geom(job, pt, false);
+  RIX_TRY(fwd_rows<R>(job->ctx, g, image, pt.tbuf.as<cplx<R>>(), st));
+  RIX_TRY(fwd_cols<R>(job->ctx, g, pt.tbuf.as<cplx<R>>(), pt.model_planes.as<cplx<R>>(), st));
+  return RIX_OK;
+}
+
+// residual planes -> image (scaled by 1 / W_p)
+template <typename R>
+int planes_to_image(Job* job, Part& pt, R* image, cudaStream_t st) {
+  const XformGeom g = plane_geom(job, pt, false);
+  RIX_TRY(inv_cols<R>(job->ctx, g, pt.resid_planes.as<cplx<R>>(), kOpNone, nullptr, nullptr,
+                      pt.tbuf.as<cplx<R>>(), st));
+  const double sc = pt.wsum > 0.0 ? 1.0 / pt.wsum : 0.0;
+  RIX_TRY(inv_rows<R>(job->ctx, g, pt.tbuf.as<cplx<R>>(), image, sc, 0, st));
+  return RIX_OK;
+}
+
+}  // namespace
+
+template <typename R>
+int grid_build_corrections(Job* job, cudaStream_t st) {
+  const int n = job->desc.n;
+  const bool ws = job->nw > 0;
+  std::vector<double> corr, nm1;
+  build_correction(n, job->ng, job->desc.cell_rad, ws, job->stats.dw, corr, nm1);
+  RIX_TRY(upload_real<R>(job, job->corr_img, corr, st));
+  if (ws) RIX_TRY(upload_double(job, job->nm1_img, nm1, st)); else job->nm1_img.release();
+  build_correction(2 * n, 2 * job->ng, job->desc.cell_rad, ws, job->stats.dw, corr, nm1);
+  RIX_TRY(upload_real<R>(job, job->corr_psf, corr, st));
+  if (ws) RIX_TRY(upload_double(job, job->nm1_psf, nm1, st)); else job->nm1_psf.release();
+  // accuracy of w-stacking: max |dw (n - 1)| over the (PSF) field
+  if (ws) {
+    double mx = 0.0;
+    for (double d : nm1) mx = std::max(mx, std::fabs(d * job->stats.dw));
+    job->stats.max_dw_nm1 = mx;
+  }
+  return RIX_OK;
+}
+
+template <typename R>
+int op_degrid(Job* job, int p, const R* image, cplx<R>* vis_out, cudaStream_t st) {
+  Part& pt = job->part[p];
+  if (pt.ent_count == 0) return RIX_OK;
+  RIX_TRY(image_to_planes<R>(job, pt, image, st));
+  TileArgs a = base_args(job, pt);
+  a.model = pt.model_planes.p;
+  a.vis_out = vis_out;
+  return launch_tiles<R, kDegrid>(job, a, st);
+}
+
+template <typename R>
+int op_grid(Job* job, int p, const cplx<R>* vis, R* image_out, cudaStream_t st) {
+  Part& pt = job->part[p];
+  const int n = job->desc.n;
+  if (pt.ent_count == 0) {
+    RIX_CUDA(cudaMemsetAsync(image_out, 0, (size_t)n * n * sizeof(R), st));
+    return RIX_OK;
+  }
+  RIX_TRY(ensure_plane_buffers<R>(job, pt));
+  const int np = job->nw > 0 ? job->nw : 1;
+  RIX_CUDA(cudaMemsetAsync(pt.resid_planes.p, 0, (size_t)np * pt.win_n * pt.win_n * sizeof(cplx<R>), st));
+  TileArgs a = base_args(job, pt);
+  a.out = pt.resid_planes.p;
+  a.vis_in = vis;
+  RIX_TRY(launch_tiles<R, kGrid>(job, a, st));
+  return planes_to_image<R>(job, pt, image_out, st);
+}
+
+template <typename R>
+int op_major(Job* job, int p, const cplx<R>* vis, R* residual, cudaStream_t st) {
+  Part& pt = job->part[p];
+  const int n = job->desc.n;
+  if (pt.ent_count == 0) {
+    RIX_CUDA(cudaMemsetAsync(residual, 0, (size_t)n * n * sizeof(R), st));
+    return RIX_OK;
+  }
+  RIX_TRY(image_to_planes<R>(job, pt, pt.model.as<R>(), st));
+  const int np = job->nw > 0 ? job->nw : 1;
+  RIX_CUDA(cudaMemsetAsync(pt.resid_planes.p, 0, (size_t)np * pt.win_n * pt.win_n * sizeof(cplx<R>), st));
+  TileArgs a = base_args(job, pt);
+  a.model = pt.model_planes.p;
+  a.out = pt.resid_planes.p;
+  a.vis_in = vis;
+  RIX_TRY(launch_tiles<R, kResid>(job, a, st));
+  return planes_to_image<R>(job, pt, residual, st);
+}
+
+template <typename R>
+int op_psf(Job* job, int p, cudaStream_t st) {
+  Part& pt = job->part[p];
+  const int n = job->desc.n;
+  const int np = job->nw > 0 ? job->nw : 1;
+  const size_t img2 = (size_t)4 * n * n;
+  if (pt.psf.bytes < img2 * sizeof(R)) RIX_TRY(pt.psf.alloc(job->ctx, img2 * sizeof(R)));
+  if (pt.hspec.bytes < img2 * sizeof(cplx<R>)) RIX_TRY(pt.hspec.alloc(job->ctx, img2 * sizeof(cplx<R>)));
+  if (pt.ent_count == 0) {
+    RIX_CUDA(cudaMemsetAsync(pt.psf.p, 0, img2 * sizeof(R), st));
+    RIX_CUDA(cudaMemsetAsync(pt.hspec.p, 0, img2 * sizeof(cplx<R>), st));
+    pt.psf_ready = true;
+    return RIX_OK;
+  }
+  // temporary PSF planes and transpose buffer
+  const size_t planes = (size_t)np * pt.pwin_n * pt.pwin_n;
+  // also holds the [2N][2N] transpose of the PSF spectrum below
+  const size_t tb = std::max((size_t)np * pt.pwin_n * 2 * n, (size_t)4 * n * n);
+  cplx<R>* pp = nullptr;
+  cplx<R>* tt = nullptr;
+  RIX_CUDA(cudaMallocAsync(&pp, planes * sizeof(cplx<R>), st));
+  if (cudaMallocAsync(&tt, tb * sizeof(cplx<R>), st) != cudaSuccess) {
+    cudaFreeAsync(pp, st);
+    return set_error(RIX_ENOMEM, "PSF transpose buffer");
+  }
+  int rc = RIX_OK;
+  do {
+    if (cudaMemsetAsync(pp, 0, planes * sizeof(cplx<R>), st) != cudaSuccess) { rc = set_error(RIX_ECUDA, "memset"); break; }
+    TileArgs a = base_args(job, pt);
+    a.scale = job->desc.cell_rad * (double)(2 * job->ng);
+    a.half = (double)job->ng;
+    a.win_lo = pt.pwin_lo;
+    a.S = pt.pwin_n;
+    a.out = pp;
+    if ((rc = launch_tiles<R, kPsf>(job, a, st)) != RIX_OK) break;
+    const XformGeom g = plane_geom(job, pt, true);
+    if ((rc = inv_cols<R>(job->ctx, g, pp, kOpNone, nullptr, nullptr, tt, st)) != RIX_OK) break;
+    const double sc = pt.wsum > 0.0 ? 1.0 / pt.wsum : 0.0;
+    if ((rc = inv_rows<R>(job->ctx, g, tt, pt.psf.as<R>(), sc, 0, st)) != RIX_OK) break;
+    // centred spectrum of the 2N x 2N PSF on the 2N grid
+    XformGeom h{};
+    h.M = 2 * n; h.L = 2 * n; h.logL = ilog2(h.L); h.lo = 0; h.S = 2 * n; h.nplanes = 1; h.mode = kFacNone;
+    if ((rc = fwd_rows<R>(job->ctx, h, pt.psf.as<R>(), tt, st)) != RIX_OK) break;
+    if ((rc = fwd_cols<R>(job->ctx, h, tt, pt.hspec.as<cplx<R>>(), st)) != RIX_OK) break;
+  } while (0);
+  cudaFreeAsync(pp, st);
+  cudaFreeAsync(tt, st);
+  if (rc == RIX_OK) pt.psf_ready = true;
+  return rc;
+}
+
+#define RIX_GRID_INST(R)                                                               \
+  template int grid_build_corrections<R>(Job*, cudaStream_t);                          \
+  template int op_degrid<R>(Job*, int, const R*, cplx<R>*, cudaStream_t);              \
+  template int op_grid<R>(Job*, int, const cplx<R>*, R*, cudaStream_t);                \
+  template int op_major<R>(Job*, int, const cplx<R>*, R*, cudaStream_t);               \
+  template int op_psf<R>(Job*, int, cudaStream_t);
+RIX_GRID_INST(float)
+RIX_GRID_INST(double)
+
+}  // namespace rix

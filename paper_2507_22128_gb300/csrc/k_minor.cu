@@ -1,0 +1,858 @@
+// a8-a11: the fill of each partition's missing spatial frequencies from the
+// other partitions' previous-cycle images (Sec. 3-4, Eq. 5 and 7), the
+// minor cycles (FISTA with a Db4 dictionary, Eq. 4-5; multi-scale CLEAN,
+// Eq. 6-7), the image update (Eq. 3) and the equal-weight combine (Sec. 5.2).
+//
+// All image-domain operators are applied on the 2N-padded grid through the
+// transforms of k_fft.cu; spectra are centred and stored u-major, (2N)^2.
+#include <cooperative_groups.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "rix_internal.cuh"
+
+namespace cg = cooperative_groups;
+
+namespace rix {
+namespace {
+
+// ------------------------------------------------------------ transforms ----
+XformGeom fill_geom(int n) {
+  XformGeom g{};
+  g.M = n; g.L = 2 * n; g.logL = ilog2(g.L); g.lo = 0; g.S = 2 * n; g.nplanes = 1; g.mode = kFacNone;
+  return g;
+}
+
+// centred spectrum of the 2N-padded image x
+template <typename R>
+int img_spectrum(Job* job, Part& pt, const R* x, cplx<R>* spec, cudaStream_t st) {
+  const XformGeom g = fill_geom(job->desc.n);
+  RIX_TRY(fwd_rows<R>(job->ctx, g, x, pt.ft_a.as<cplx<R>>(), st));
+  return fwd_cols<R>(job->ctx, g, pt.ft_a.as<cplx<R>>(), spec, st);
+}
+
+// out (+)= scale * crop F^-1 [op(spec)]
+template <typename R>
+int spec_to_img(Job* job, Part& pt, const cplx<R>* spec, int op, const void* tab, R* out, double scale,
+                int accumulate, cudaStream_t st) {
+  const XformGeom g = fill_geom(job->desc.n);
+  RIX_TRY(inv_cols<R>(job->ctx, g, spec, op, tab, nullptr, pt.ft_a.as<cplx<R>>(), st));
+  return inv_rows<R>(job->ctx, g, pt.ft_a.as<cplx<R>>(), out, scale, accumulate, st);
+}
+
+// out (+)= scale * crop F^-1 [op(F pad x)]   (three passes; the spectral op is
+// fused between the forward and inverse column transforms)
+template <typename R>
+int convolve(Job* job, Part& pt, const R* x, int op, const void* tab, const void* tab2, R* out, double scale,
+             int accumulate, cudaStream_t st) {
+  const XformGeom g = fill_geom(job->desc.n);
+  RIX_TRY(fwd_rows<R>(job->ctx, g, x, pt.ft_a.as<cplx<R>>(), st));
+  RIX_TRY(conv_cols<R>(job->ctx, g, pt.ft_a.as<cplx<R>>(), op, tab, tab2, pt.ft_b.as<cplx<R>>(), st));
+  return inv_rows<R>(job->ctx, g, pt.ft_b.as<cplx<R>>(), out, scale, accumulate, st);
+}
+
+// ---------------------------------------------------------------- kernels ----
+int blocks_for(const Ctx* ctx, int64_t n, int threads = 256) {
+  return (int)std::min<int64_t>(ceil_div(std::max<int64_t>(n, 1), threads), (int64_t)ctx->num_sms * 8);
+}
+
+// Gamma_p = Lambda_{p+1} - Lambda_p, Lambda_i(r) = clip((ell_i + delta - r) / (2 delta), 0, 1),
+// r = |k| / 2 on the centred 2N grid (u-major index [ju][jv]).
+struct GammaArgs {
+  int n, nparts;
+  double ells[kMaxPart];
+  double delta;
+};
+
+__device__ __forceinline__ double ramp(double ell, double delta, double r) {
+  if (delta <= 0.0) return r < ell ? 1.0 : (r > ell ? 0.0 : 0.5);
+  return fmin(fmax((ell + delta - r) / (2.0 * delta), 0.0), 1.0);
+}
+
+template <typename R>
+__global__ void k_gamma(GammaArgs a, R* __restrict__ gam) {
+  const int L = 2 * a.n;
+  const int64_t tot = (int64_t)L * L;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < tot; i += (int64_t)gridDim.x * blockDim.x) {
+    const int ju = (int)(i / L), jv = (int)(i - (int64_t)ju * L);
+    const double ku = ju - a.n, kv = jv - a.n;
+    const double r = sqrt(ku * ku + kv * kv) / 2.0;
+    double lam_lo = 0.0;
+    for (int p = 0; p < a.nparts; ++p) {
+      const double lam_hi = (p == a.nparts - 1) ? 1.0 : ramp(a.ells[p], a.delta, r);
+      gam[(int64_t)p * tot + i] = (R)(lam_hi - lam_lo);
+      lam_lo = lam_hi;
+    }
+  }
+}
+
+template <typename R>
+__global__ void k_axpy(R* __restrict__ y, const R* __restrict__ x, R alpha, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    y[i] += alpha * x[i];
+}
+
+template <typename R>
+__global__ void k_mean(R* __restrict__ out, const R* const* __restrict__ imgs, int nimg, int64_t n) {
+  const R inv = R(1) / (R)nimg;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    R s = R(0);
+    for (int k = 0; k < nimg; ++k) s += imgs[k][i];
+    out[i] = s * inv;
+  }
+}
+
+// max |x| into *out (out pre-set to 0); values are >= 0 so the bit pattern
+// order of the IEEE encoding matches the value order
+__device__ __forceinline__ void atomic_max_nonneg(float* out, float v) {
+  atomicMax(reinterpret_cast<unsigned int*>(out), __float_as_uint(v));
+}
+__device__ __forceinline__ void atomic_max_nonneg(double* out, double v) {
+  atomicMax(reinterpret_cast<unsigned long long*>(out), (unsigned long long)__double_as_longlong(v));
+}
+
+template <typename R>
+__global__ void k_absmax(const R* __restrict__ x, int64_t n, R* __restrict__ out) {
+  R m = R(0);
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    m = fmax(m, fabs(x[i]));
+  for (int o = 16; o; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) atomic_max_nonneg(out, m);
+}
+
+// ------------------------------------------------------------ fill kernels ----
+// ms-CLEAN composite dirty spectrum and PSF spectrum (Eq. 7):
+//   D = g Gam_p I_p + sum_q mu_q H_q Rho_q,   P = g Gam_p H_p + sum_q mu_q Gam_q H_q
+struct FillArgs {
+  int64_t tot;
+  int p, nparts;
+  double g, mu[kMaxPart];
+  const void* gam;                 // R [P][tot]
+  const void* h[kMaxPart];         // cplx [tot]
+  const void* rho[kMaxPart];       // cplx [tot] (spectra), null for q == p
+  const void* ispec;               // cplx [tot]
+};
+
+template <typename R>
+__global__ void k_fill_msclean(FillArgs a, cplx<R>* __restrict__ dspec, cplx<R>* __restrict__ pspec) {
+  using C = cplx<R>;
+  const R* gam = static_cast<const R*>(a.gam);
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.tot; i += (int64_t)gridDim.x * blockDim.x) {
+    const R gp = gam[(int64_t)a.p * a.tot + i] * (R)a.g;
+    const C hp = static_cast<const C*>(a.h[a.p])[i];
+    C d = static_cast<const C*>(a.ispec)[i] * gp;
+    C ps = hp * gp;
+    for (int q = 0; q < a.nparts; ++q) {
+      if (q == a.p || a.mu[q] == 0.0) continue;
+      const C hq = static_cast<const C*>(a.h[q])[i];
+      const C rq = static_cast<const C*>(a.rho[q])[i];
+      d = d + cmul(hq, rq) * (R)a.mu[q];
+      ps = ps + hq * (gam[(int64_t)q * a.tot + i] * (R)a.mu[q]);
+    }
+    dspec[i] = d;
+    pspec[i] = ps;
+  }
+}
+
+// FISTA quadratic form (Eq. 5): Mx = Gam_p^2 |H_p|^2 + gn sum_q Gam_q^2,
+// C = Gam_p^2 conj(H_p) I_p + gn sum_q Gam_q Rho_q; also max(Mx) for L.
+template <typename R>
+__global__ void k_fill_fista(FillArgs a, double gn, R* __restrict__ mx, cplx<R>* __restrict__ c,
+                             R* __restrict__ mxmax) {
+  using C = cplx<R>;
+  const R* gam = static_cast<const R*>(a.gam);
+  R m = R(0);
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.tot; i += (int64_t)gridDim.x * blockDim.x) {
+    const R gp = gam[(int64_t)a.p * a.tot + i];
+    const R g2 = gp * gp;
+    const C hp = static_cast<const C*>(a.h[a.p])[i];
+    const C ip = static_cast<const C*>(a.ispec)[i];
+    R mv = g2 * (hp.x * hp.x + hp.y * hp.y);
+    C cv = cmulc(ip, hp) * g2;
+    for (int q = 0; q < a.nparts; ++q) {
+      if (q == a.p) continue;
+      const R gq = gam[(int64_t)q * a.tot + i];
+      mv += (R)gn * gq * gq;
+      cv = cv + static_cast<const C*>(a.rho[q])[i] * ((R)gn * gq);
+    }
+    mx[i] = mv;
+    c[i] = cv;
+    m = fmax(m, mv);
+  }
+  for (int o = 16; o; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) atomic_max_nonneg(mxmax, m);
+}
+
+}  // namespace
+
+namespace {
+
+// --------------------------------------------------------------- Db4 DWT ----
+// Daubechies 4-vanishing-moment low-pass filter (8 taps, minimum phase,
+// normalised to sum sqrt(2)); g[i] = (-1)^i h[7 - i].
+__constant__ double kDb4[8] = {0.23037781330885523,  0.7148465705525415,   0.6308807679295904,
+                               -0.02798376941698385, -0.18703481171888114, 0.030841381835986965,
+                               0.032883011666982945, -0.010597401784997278};
+
+template <typename R> __device__ __forceinline__ R db_h(int i) { return (R)kDb4[i]; }
+template <typename R> __device__ __forceinline__ R db_g(int i) { return (i & 1) ? -(R)kDb4[7 - i] : (R)kDb4[7 - i]; }
+
+// analysis along rows of the top-left n x n block (row stride ld):
+// out[r][k] = sum_i h[i] x[r][(2k+i) mod n], out[r][n/2+k] = sum_i g[i] x[...]
+template <typename R>
+__global__ void k_dwt_rows(const R* __restrict__ x, R* __restrict__ out, int n, int ld) {
+  const int half = n / 2;
+  const int64_t tot = (int64_t)n * half;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < tot; t += (int64_t)gridDim.x * blockDim.x) {
+    const int r = (int)(t / half), k = (int)(t - (int64_t)r * half);
+    const R* row = x + (int64_t)r * ld;
+    R a = R(0), d = R(0);
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const R v = row[(2 * k + i) & (n - 1)];
+      a += db_h<R>(i) * v;
+      d += db_g<R>(i) * v;
+    }
+    out[(int64_t)r * ld + k] = a;
+    out[(int64_t)r * ld + half + k] = d;
+  }
+}
+
+// analysis along columns: out[k][c], out[n/2+k][c]
+template <typename R>
+__global__ void k_dwt_cols(const R* __restrict__ x, R* __restrict__ out, int n, int ld) {
+  const int half = n / 2;
+  const int64_t tot = (int64_t)half * n;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < tot; t += (int64_t)gridDim.x * blockDim.x) {
+    const int k = (int)(t / n), c = (int)(t - (int64_t)k * n);
+    R a = R(0), d = R(0);
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const R v = x[(int64_t)((2 * k + i) & (n - 1)) * ld + c];
+      a += db_h<R>(i) * v;
+      d += db_g<R>(i) * v;
+    }
+    out[(int64_t)k * ld + c] = a;
+    out[(int64_t)(half + k) * ld + c] = d;
+  }
+}
+
+// synthesis (transpose of the analysis) along rows:
+// x[r][m] = sum_{i = m mod 2} h[i] a[r][((m-i) mod n)/2] + g[i] d[r][...]
+template <typename R>
+__global__ void k_idwt_rows(const R* __restrict__ c, R* __restrict__ out, int n, int ld) {
+  const int half = n / 2;
+  const int64_t tot = (int64_t)n * n;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < tot; t += (int64_t)gridDim.x * blockDim.x) {
+    const int r = (int)(t / n), m = (int)(t - (int64_t)r * n);
+    const R* row = c + (int64_t)r * ld;
+    R v = R(0);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int i = 2 * j + (m & 1);
+      const int k = ((m - i) & (n - 1)) >> 1;
+      v += db_h<R>(i) * row[k] + db_g<R>(i) * row[half + k];
+    }
+    out[(int64_t)r * ld + m] = v;
+  }
+}
+
+template <typename R>
+__global__ void k_idwt_cols(const R* __restrict__ c, R* __restrict__ out, int n, int ld) {
+  const int half = n / 2;
+  const int64_t tot = (int64_t)n * n;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < tot; t += (int64_t)gridDim.x * blockDim.x) {
+    const int m = (int)(t / n), col = (int)(t - (int64_t)m * n);
+    R v = R(0);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int i = 2 * j + (m & 1);
+      const int k = ((m - i) & (n - 1)) >> 1;
+      v += db_h<R>(i) * c[(int64_t)k * ld + col] + db_g<R>(i) * c[(int64_t)(half + k) * ld + col];
+    }
+    out[(int64_t)m * ld + col] = v;
+  }
+}
+
+template <typename R>
+__global__ void k_copy_block(const R* __restrict__ src, R* __restrict__ dst, int n, int ld) {
+  const int64_t tot = (int64_t)n * n;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < tot; t += (int64_t)gridDim.x * blockDim.x) {
+    const int r = (int)(t / n), c = (int)(t - (int64_t)r * n);
+    dst[(int64_t)r * ld + c] = src[(int64_t)r * ld + c];
+  }
+}
+
+// x (N x N) -> wavelet coefficients in place (tmp: N x N scratch)
+template <typename R>
+int dwt2(const Ctx* ctx, R* x, R* tmp, int N, int levels, cudaStream_t st) {
+  for (int l = 0, n = N; l < levels; ++l, n >>= 1) {
+    k_dwt_rows<R><<<blocks_for(ctx, (int64_t)n * n / 2), 256, 0, st>>>(x, tmp, n, N);
+    k_dwt_cols<R><<<blocks_for(ctx, (int64_t)n * n / 2), 256, 0, st>>>(tmp, x, n, N);
+  }
+  RIX_LAUNCH_CHECK();
+  return RIX_OK;
+}
+
+// coefficients c -> image out (c preserved; tmp: N x N scratch)
+template <typename R>
+int idwt2(const Ctx* ctx, const R* c, R* out, R* tmp, int N, int levels, cudaStream_t st) {
+  RIX_CUDA(cudaMemcpyAsync(out, c, (size_t)N * N * sizeof(R), cudaMemcpyDeviceToDevice, st));
+  for (int l = levels - 1; l >= 0; --l) {
+    const int n = N >> l;
+    k_idwt_cols<R><<<blocks_for(ctx, (int64_t)n * n), 256, 0, st>>>(out, tmp, n, N);
+    k_idwt_rows<R><<<blocks_for(ctx, (int64_t)n * n), 256, 0, st>>>(tmp, out, n, N);
+  }
+  RIX_LAUNCH_CHECK();
+  return RIX_OK;
+}
+
+// FISTA step in coefficient space (Beck & Teboulle 2009):
+//   a' = S_{lam/L}(y - g/L),  y = a' + mom (a' - a),  a = a'
+// L = 2 max Mx (state[0] holds max Mx); lam = lambda, or lambda_rel * state[1].
+template <typename R>
+__global__ void k_fista_step(R* __restrict__ alpha, R* __restrict__ y, const R* __restrict__ g, int64_t n,
+                             const R* __restrict__ state, double lambda, double lambda_rel, double mom) {
+  const double L = 2.0 * (double)state[0];
+  const double lam = lambda > 0.0 ? lambda : lambda_rel * (double)state[1];
+  const R inv_l = L > 0.0 ? (R)(1.0 / L) : R(0);
+  const R thr = L > 0.0 ? (R)(lam / L) : R(0);
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const R z = y[i] - g[i] * inv_l;
+    const R az = fabs(z) - thr;
+    const R an = (L > 0.0 && az > R(0)) ? copysign(az, z) : R(0);
+    y[i] = an + (R)mom * (an - alpha[i]);
+    alpha[i] = an;
+  }
+}
+
+template <typename R>
+__global__ void k_set_scalar(R* p, R v) { *p = v; }
+
+}  // namespace
+
+namespace {
+
+// --------------------------------------------------------------- ms-CLEAN ----
+template <typename R>
+struct Cand {
+  R val;       // b_s |R_s(p)| / P_ss(0); -1 = none
+  R rval;      // R_s(p), signed
+  int s, pix;
+  R r0max;     // max |R_0| over the image
+};
+
+template <typename R>
+__device__ __forceinline__ bool better(const Cand<R>& a, const Cand<R>& b) {
+  if (a.val != b.val) return a.val > b.val;
+  if (a.s != b.s) return a.s < b.s;
+  return a.pix < b.pix;
+}
+
+template <typename R>
+__device__ __forceinline__ Cand<R> shfl_cand(const Cand<R>& c, int o) {
+  Cand<R> r;
+  r.val = __shfl_xor_sync(0xffffffffu, c.val, o);
+  r.rval = __shfl_xor_sync(0xffffffffu, c.rval, o);
+  r.s = __shfl_xor_sync(0xffffffffu, c.s, o);
+  r.pix = __shfl_xor_sync(0xffffffffu, c.pix, o);
+  r.r0max = __shfl_xor_sync(0xffffffffu, c.r0max, o);
+  return r;
+}
+
+template <typename R>
+__device__ __forceinline__ Cand<R> merge(const Cand<R>& a, const Cand<R>& b) {
+  Cand<R> r = better(b, a) ? b : a;
+  r.r0max = fmax(a.r0max, b.r0max);
+  return r;
+}
+
+// block-wide reduction; the result is valid in every thread
+template <typename R>
+__device__ Cand<R> block_reduce(Cand<R> c, Cand<R>* sh) {
+  for (int o = 16; o; o >>= 1) c = merge(c, shfl_cand(c, o));
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  __syncthreads();
+  if (lane == 0) sh[warp] = c;
+  __syncthreads();
+  if (warp == 0) {
+    Cand<R> d = lane < nw ? sh[lane] : Cand<R>{R(-1), R(0), 0x7fffffff, 0x7fffffff, R(0)};
+    for (int o = 16; o; o >>= 1) d = merge(d, shfl_cand(d, o));
+    if (lane == 0) sh[0] = d;
+  }
+  __syncthreads();
+  return sh[0];
+}
+
+struct CleanArgs {
+  int n, ns, niter;
+  double gain, threshold;
+  double bias[kMaxScales];
+  int allowed;                 // bit mask of scales usable this cycle
+  void* R;                     // [ns][n][n]
+  const void* P;               // [ns][ns][2n][2n]
+  void* model;                 // [n][n]
+  const void* stencil;         // concatenated (2r+1)^2 stencils of B_s
+  int st_off[kMaxScales], st_rad[kMaxScales];
+  void* slots;                 // Cand<R> [2][gridDim]
+  int* comp_s;                 // [niter]
+  int* comp_pix;
+  double* comp_amp;
+  int* count;
+};
+
+// The whole minor cycle in one cooperative launch: each iteration subtracts
+// the previous component from every scale residual and, in the same sweep,
+// finds the next peak; one grid barrier per iteration separates the sweep
+// from the global reduction (double-buffered candidate slots).
+template <typename R>
+__global__ void __launch_bounds__(256) k_msclean(CleanArgs a) {
+  cg::grid_group grid = cg::this_grid();
+  __shared__ Cand<R> sh[32];
+  const int n = a.n, n2 = 2 * a.n;
+  const int64_t npix = (int64_t)n * n;
+  R* Rs = static_cast<R*>(a.R);
+  const R* P = static_cast<const R*>(a.P);
+  Cand<R>* slots = static_cast<Cand<R>*>(a.slots);
+  R peak[kMaxScales], bias[kMaxScales];
+  for (int s = 0; s < a.ns; ++s) {
+    peak[s] = P[((int64_t)(s * a.ns + s) * n2 + n) * n2 + n];
+    bias[s] = (R)a.bias[s];
+  }
+  const int64_t gtid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t gstride = (int64_t)gridDim.x * blockDim.x;
+
+  // sweep with the subtraction of component (sc, py, px, amp) (amp = 0: none)
+  auto sweep = [&](int sc, int py, int px, R amp) {
+    Cand<R> c{R(-1), R(0), 0x7fffffff, 0x7fffffff, R(0)};
+    for (int64_t i = gtid; i < npix; i += gstride) {
+      const int y = (int)(i / n), x = (int)(i - (int64_t)y * n);
+      for (int s = 0; s < a.ns; ++s) {
+        R v = Rs[s * npix + i];
+        if (amp != R(0)) {
+          v -= amp * P[((int64_t)(s * a.ns + sc) * n2 + (n + y - py)) * n2 + (n + x - px)];
+          Rs[s * npix + i] = v;
+        }
+        if (s == 0) c.r0max = fmax(c.r0max, fabs(v));
+        if ((a.allowed >> s) & 1) {
+          const R val = bias[s] * fabs(v) / peak[s];
+          Cand<R> t{val, v, s, (int)i, R(0)};
+          if (better(t, c)) { c.val = t.val; c.rval = t.rval; c.s = t.s; c.pix = t.pix; }
+        }
+      }
+    }
+    return block_reduce(c, sh);
+  };
+
+  Cand<R> loc = sweep(0, 0, 0, R(0));
+  if (threadIdx.x == 0) slots[blockIdx.x] = loc;
+  int it = 0;
+  for (;; ++it) {
+    grid.sync();
+    const Cand<R>* cur = slots + (int64_t)(it & 1) * gridDim.x;
+    Cand<R> c{R(-1), R(0), 0x7fffffff, 0x7fffffff, R(0)};
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) c = merge(c, cur[b]);
+    const Cand<R> best = block_reduce(c, sh);
+    if (it >= a.niter || best.r0max < (R)a.threshold || best.val < R(0) || peak[best.s] == R(0)) break;
+    const R amp = (R)a.gain * best.rval / peak[best.s];
+    const int py = best.pix / n, px = best.pix - py * n;
+    if (blockIdx.x == 0) {
+      if (threadIdx.x == 0) {
+        a.comp_s[it] = best.s;
+        a.comp_pix[it] = best.pix;
+        a.comp_amp[it] = (double)amp;
+      }
+      // model += amp * B_s(. - p*), clipped to the image
+      const int rad = a.st_rad[best.s], w = 2 * rad + 1;
+      const R* stn = static_cast<const R*>(a.stencil) + a.st_off[best.s];
+      R* model = static_cast<R*>(a.model);
+      for (int k = threadIdx.x; k < w * w; k += blockDim.x) {
+        const int dy = k / w - rad, dx = k % w - rad;
+        const int yy = py + dy, xx = px + dx;
+        if (yy >= 0 && yy < n && xx >= 0 && xx < n) model[(int64_t)yy * n + xx] += amp * stn[k];
+      }
+    }
+    loc = sweep(best.s, py, px, amp);
+    if (threadIdx.x == 0) slots[(int64_t)((it + 1) & 1) * gridDim.x + blockIdx.x] = loc;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) *a.count = it;
+}
+
+// elementwise product of two complex spectra times a third: out = a * b * c
+template <typename R>
+__global__ void k_cmul3(const cplx<R>* __restrict__ x, const cplx<R>* __restrict__ y, const cplx<R>* __restrict__ z,
+                        cplx<R>* __restrict__ out, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = cmul(cmul(x[i], y[i]), z[i]);
+}
+
+}  // namespace
+
+// ================================================================== host ====
+namespace {
+
+template <typename R>
+int alloc_zero(Job* job, DevBuf& b, size_t bytes, cudaStream_t st) {
+  if (b.bytes < bytes) RIX_TRY(b.alloc(job->ctx, bytes));
+  RIX_CUDA(cudaMemsetAsync(b.p, 0, bytes, st));
+  return RIX_OK;
+}
+
+template <typename R>
+int ensure(Job* job, DevBuf& b, size_t bytes) {
+  if (b.bytes < bytes) RIX_TRY(b.alloc(job->ctx, bytes));
+  return RIX_OK;
+}
+
+// rho_{q->p} += Phi_q^{n-1} for every other partition (cycle n >= 2)
+template <typename R>
+int ingest(Job* job, int p, int cycle, cudaStream_t st) {
+  if (cycle < 2) return RIX_OK;
+  const int64_t npix = (int64_t)job->desc.n * job->desc.n;
+  for (int q = 0; q < job->n_part; ++q) {
+    if (q == p) continue;
+    k_axpy<R><<<blocks_for(job->ctx, npix), 256, 0, st>>>(job->part[p].rho[q].as<R>(),
+                                                          job->part[q].outbox[(cycle - 1) & 1].as<R>(), R(1), npix);
+  }
+  RIX_LAUNCH_CHECK();
+  return RIX_OK;
+}
+
+// spectra of the own residual (slot p) and of the aggregates rho_{q->p}
+template <typename R>
+int fill_spectra(Job* job, int p, cudaStream_t st) {
+  Part& pt = job->part[p];
+  const int64_t tot = (int64_t)4 * job->desc.n * job->desc.n;
+  cplx<R>* sp = pt.fspec.as<cplx<R>>();
+  RIX_TRY(img_spectrum<R>(job, pt, pt.resid.as<R>(), sp + p * tot, st));
+  for (int q = 0; q < job->n_part; ++q)
+    if (q != p) RIX_TRY(img_spectrum<R>(job, pt, pt.rho[q].as<R>(), sp + q * tot, st));
+  return RIX_OK;
+}
+
+template <typename R>
+FillArgs fill_args(Job* job, int p) {
+  FillArgs a{};
+  const int64_t tot = (int64_t)4 * job->desc.n * job->desc.n;
+  a.tot = tot;
+  a.p = p;
+  a.nparts = job->n_part;
+  a.gam = job->gam.p;
+  for (int q = 0; q < job->n_part; ++q) {
+    a.h[q] = job->part[q].hspec.p;
+    a.rho[q] = (q == p) ? nullptr : job->part[p].fspec.as<cplx<R>>() + q * tot;
+  }
+  a.ispec = job->part[p].fspec.as<cplx<R>>() + p * tot;
+  return a;
+}
+
+// Eq. 3 and the exchange: model += i_bar; Phi_p = Gamma_p i_bar (outbox of
+// this cycle's parity); rho_{q->p} -= Gamma_q i_bar.
+template <typename R>
+int publish(Job* job, int p, int cycle, cudaStream_t st) {
+  Part& pt = job->part[p];
+  const int n = job->desc.n;
+  const int64_t npix = (int64_t)n * n, tot = 4 * npix;
+  const double inv = 1.0 / (double)tot;
+  const R* ibar = pt.delta.as<R>();
+  k_axpy<R><<<blocks_for(job->ctx, npix), 256, 0, st>>>(pt.model.as<R>(), ibar, R(1), npix);
+  RIX_LAUNCH_CHECK();
+  const R* gam = job->gam.as<R>();
+  RIX_TRY(convolve<R>(job, pt, ibar, kOpMulReal, gam + p * tot, nullptr, pt.outbox[cycle & 1].as<R>(), inv, 0, st));
+  for (int q = 0; q < job->n_part; ++q)
+    if (q != p) RIX_TRY(convolve<R>(job, pt, ibar, kOpMulReal, gam + q * tot, nullptr, pt.rho[q].as<R>(), -inv, 1, st));
+  return RIX_OK;
+}
+
+// B_s: 1 - (r/s)^2 for r < s pixels, unit sum; B_0 = delta.  Stencil of
+// (2 rad + 1)^2 values, rad = ceil(s) - 1 (0 for s = 0).
+void scale_stencil(double s, std::vector<double>& st, int& rad) {
+  if (s <= 0.0) {
+    rad = 0;
+    st.assign(1, 1.0);
+    return;
+  }
+  rad = (int)std::ceil(s) - 1;
+  const int w = 2 * rad + 1;
+  st.assign((size_t)w * w, 0.0);
+  double sum = 0.0;
+  for (int dy = -rad; dy <= rad; ++dy)
+    for (int dx = -rad; dx <= rad; ++dx) {
+      const double r2 = (double)(dx * dx + dy * dy);
+      const double v = r2 < s * s ? 1.0 - r2 / (s * s) : 0.0;
+      st[(size_t)(dy + rad) * w + (dx + rad)] = v;
+      sum += v;
+    }
+  for (double& v : st) v /= sum;
+}
+
+template <typename R>
+__global__ void k_place_stencil(const R* __restrict__ stn, int rad, R* __restrict__ img, int n2) {
+  const int w = 2 * rad + 1;
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < w * w; k += gridDim.x * blockDim.x) {
+    const int dy = k / w - rad, dx = k % w - rad;
+    img[(int64_t)(n2 / 2 + dy) * n2 + (n2 / 2 + dx)] = stn[k];
+  }
+}
+
+}  // namespace
+
+template <typename R>
+int fill_init(Job* job, cudaStream_t st) {
+  const int n = job->desc.n, P = job->n_part;
+  const int64_t npix = (int64_t)n * n, tot = 4 * npix;
+  RIX_TRY(ensure<R>(job, job->gam, (size_t)P * tot * sizeof(R)));
+  GammaArgs ga{};
+  ga.n = n;
+  ga.nparts = P;
+  for (int i = 0; i < P - 1; ++i) ga.ells[i] = job->ells[i];
+  ga.delta = job->stats.delta_px;
+  k_gamma<R><<<blocks_for(job->ctx, tot), 256, 0, st>>>(ga, job->gam.as<R>());
+  RIX_LAUNCH_CHECK();
+  for (int p = 0; p < P; ++p) {
+    Part& pt = job->part[p];
+    RIX_TRY(ensure<R>(job, pt.fs_a, tot * sizeof(cplx<R>)));
+    RIX_TRY(ensure<R>(job, pt.fs_b, tot * sizeof(cplx<R>)));
+    RIX_TRY(ensure<R>(job, pt.ft_a, (size_t)2 * n * n * sizeof(cplx<R>)));
+    RIX_TRY(ensure<R>(job, pt.ft_b, (size_t)2 * n * n * sizeof(cplx<R>)));
+    RIX_TRY(ensure<R>(job, pt.fimg, npix * sizeof(R)));
+    RIX_TRY(ensure<R>(job, pt.fspec, (size_t)P * tot * sizeof(cplx<R>)));
+    RIX_TRY(alloc_zero<R>(job, pt.outbox[0], npix * sizeof(R), st));
+    RIX_TRY(alloc_zero<R>(job, pt.outbox[1], npix * sizeof(R), st));
+    for (int q = 0; q < P; ++q)
+      if (q != p) RIX_TRY(alloc_zero<R>(job, pt.rho[q], npix * sizeof(R), st));
+    RIX_TRY(alloc_zero<R>(job, pt.fi_state, 2 * sizeof(R), st));
+  }
+  return RIX_OK;
+}
+
+template <typename R>
+int op_msclean(Job* job, int p, const rix_msclean_params* prm, R* delta_out, cudaStream_t st) {
+  Part& pt = job->part[p];
+  const Ctx* ctx = job->ctx;
+  const int n = job->desc.n, P = job->n_part, ns = prm->n_scales;
+  const int cycle = pt.cycle;
+  const int64_t npix = (int64_t)n * n, tot = 4 * npix;
+  const double inv = 1.0 / (double)tot;
+  RIX_TRY(ingest<R>(job, p, cycle, st));
+  // (gamma, mu) of Eq. 7: (1, 0) at cycle 1, then the partitions' weight fractions
+  double wtot = 0.0;
+  for (int q = 0; q < P; ++q) wtot += job->part[q].wsum;
+  FillArgs fa = fill_args<R>(job, p);
+  fa.g = 1.0;
+  for (int q = 0; q < P; ++q) fa.mu[q] = 0.0;
+  if (cycle > 1 && wtot > 0.0) {
+    fa.g = pt.wsum / wtot;
+    for (int q = 0; q < P; ++q) fa.mu[q] = (q == p) ? 0.0 : job->part[q].wsum / wtot;
+  }
+  RIX_TRY(fill_spectra<R>(job, p, st));
+  cplx<R>* dspec = pt.fs_a.as<cplx<R>>();
+  cplx<R>* pspec = pt.fs_b.as<cplx<R>>();
+  k_fill_msclean<R><<<blocks_for(ctx, tot), 256, 0, st>>>(fa, dspec, pspec);
+  RIX_LAUNCH_CHECK();
+
+  // scale functions: stencils, their 2N-grid spectra B_s
+  std::vector<double> stn_all;
+  CleanArgs ca{};
+  for (int s = 0; s < ns; ++s) {
+    std::vector<double> stn;
+    int rad = 0;
+    scale_stencil((double)prm->scales[s], stn, rad);
+    ca.st_off[s] = (int)stn_all.size();
+    ca.st_rad[s] = rad;
+    stn_all.insert(stn_all.end(), stn.begin(), stn.end());
+  }
+  RIX_TRY(ensure<R>(job, pt.ms_B, (size_t)ns * tot * sizeof(cplx<R>) + stn_all.size() * sizeof(R) + 64));
+  cplx<R>* bspec = pt.ms_B.as<cplx<R>>();
+  R* stn_dev = reinterpret_cast<R*>(bspec + ns * tot);
+  {
+    std::vector<R> tmp(stn_all.begin(), stn_all.end());
+    RIX_CUDA(cudaMemcpyAsync(stn_dev, tmp.data(), tmp.size() * sizeof(R), cudaMemcpyHostToDevice, st));
+    RIX_CUDA(cudaStreamSynchronize(st));   // tmp is a host temporary
+  }
+  // scratch 2N x 2N image and [2N][2N] transpose buffer
+  R* img2 = nullptr;
+  cplx<R>* t2 = nullptr;
+  RIX_CUDA(cudaMallocAsync(&img2, tot * sizeof(R), st));
+  if (cudaMallocAsync(&t2, tot * sizeof(cplx<R>), st) != cudaSuccess) {
+    cudaFreeAsync(img2, st);
+    return set_error(RIX_ENOMEM, "ms-CLEAN scratch");
+  }
+  int rc = RIX_OK;
+  XformGeom g2{};
+  g2.M = 2 * n; g2.L = 2 * n; g2.logL = ilog2(g2.L); g2.lo = 0; g2.S = 2 * n; g2.nplanes = 1; g2.mode = kFacNone;
+  for (int s = 0; s < ns && rc == RIX_OK; ++s) {
+    if (cudaMemsetAsync(img2, 0, tot * sizeof(R), st) != cudaSuccess) { rc = set_error(RIX_ECUDA, "memset"); break; }
+    k_place_stencil<R><<<4, 256, 0, st>>>(stn_dev + ca.st_off[s], ca.st_rad[s], img2, 2 * n);
+    if ((rc = fwd_rows<R>(ctx, g2, img2, t2, st)) != RIX_OK) break;
+    rc = fwd_cols<R>(ctx, g2, t2, bspec + s * tot, st);
+  }
+  // scale residuals R_s = crop F^-1[B_s D] and cross PSFs P_st = F^-1[B_s B_t P]
+  if (rc == RIX_OK) rc = ensure<R>(job, pt.ms_R, (size_t)ns * npix * sizeof(R));
+  if (rc == RIX_OK) rc = ensure<R>(job, pt.ms_P, (size_t)ns * ns * tot * sizeof(R));
+  for (int s = 0; s < ns && rc == RIX_OK; ++s)
+    rc = spec_to_img<R>(job, pt, dspec, kOpMulCplx, bspec + s * tot, pt.ms_R.as<R>() + s * npix, inv, 0, st);
+  for (int s = 0; s < ns && rc == RIX_OK; ++s)
+    for (int t = 0; t < ns && rc == RIX_OK; ++t) {
+      k_cmul3<R><<<blocks_for(ctx, tot), 256, 0, st>>>(bspec + s * tot, bspec + t * tot, pspec, dspec, tot);
+      if ((rc = inv_cols<R>(ctx, g2, dspec, kOpNone, nullptr, nullptr, t2, st)) != RIX_OK) break;
+      rc = inv_rows<R>(ctx, g2, t2, pt.ms_P.as<R>() + (int64_t)(s * ns + t) * tot, inv, 0, st);
+    }
+  cudaFreeAsync(img2, st);
+  cudaFreeAsync(t2, st);
+  if (rc != RIX_OK) return rc;
+
+  // scales present at cycle 1 (psi^1 of Eq. 7): partition 0 keeps all; p > 0
+  // keeps s = 0 and the scales with N / (2 s) >= ell_p - delta
+  int allowed = 0;
+  float smax = 0.f;
+  for (int s = 0; s < ns; ++s) smax = std::max(smax, prm->scales[s]);
+  for (int s = 0; s < ns; ++s) {
+    const double sc = prm->scales[s];
+    bool ok = true;
+    if (cycle == 1 && p > 0 && sc > 0.0) ok = (double)n / (2.0 * sc) >= job->ells[p - 1] - job->stats.delta_px;
+    if (ok) allowed |= 1 << s;
+    ca.bias[s] = smax > 0.f ? 1.0 - 0.6 * sc / (double)smax : 1.0;
+  }
+  // state: delta image, components, slots
+  const int cap = std::max(prm->niter, 1);
+  int per_sm = 0;
+  RIX_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_msclean<R>, 256, 0));
+  const int nblk = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)ctx->num_sms * std::max(per_sm, 1),
+                                                                 ceil_div(npix, 256)));
+  const size_t comp_bytes = (size_t)cap * (2 * sizeof(int) + sizeof(double)) + 16;
+  RIX_TRY(ensure<R>(job, pt.ms_comp, comp_bytes));
+  RIX_TRY(ensure<R>(job, pt.ms_state, 2 * (size_t)nblk * sizeof(Cand<R>) + 64));
+  pt.ms_ncomp_cap = cap;
+  RIX_CUDA(cudaMemsetAsync(pt.delta.p, 0, npix * sizeof(R), st));
+  RIX_CUDA(cudaMemsetAsync(pt.ms_comp.p, 0, comp_bytes, st));
+  char* cb = pt.ms_comp.as<char>();
+  ca.n = n;
+  ca.ns = ns;
+  ca.niter = prm->niter;
+  ca.gain = prm->gain;
+  ca.threshold = prm->threshold;
+  ca.allowed = allowed;
+  ca.R = pt.ms_R.p;
+  ca.P = pt.ms_P.p;
+  ca.model = pt.delta.p;
+  ca.stencil = stn_dev;
+  ca.slots = pt.ms_state.p;
+  ca.comp_amp = reinterpret_cast<double*>(cb);
+  ca.comp_s = reinterpret_cast<int*>(cb + (size_t)cap * sizeof(double));
+  ca.comp_pix = ca.comp_s + cap;
+  ca.count = ca.comp_pix + cap;
+  void* args[] = {&ca};
+  RIX_CUDA(cudaLaunchCooperativeKernel((const void*)k_msclean<R>, dim3(nblk), dim3(256), args, 0, st));
+  RIX_TRY(publish<R>(job, p, cycle, st));
+  if (delta_out) RIX_CUDA(cudaMemcpyAsync(delta_out, pt.delta.p, npix * sizeof(R), cudaMemcpyDeviceToDevice, st));
+  return RIX_OK;
+}
+
+template <typename R>
+int op_fista(Job* job, int p, const rix_fista_params* prm, R* delta_out, cudaStream_t st) {
+  Part& pt = job->part[p];
+  const Ctx* ctx = job->ctx;
+  const int n = job->desc.n;
+  const int cycle = pt.cycle;
+  const int64_t npix = (int64_t)n * n, tot = 4 * npix;
+  RIX_TRY(ingest<R>(job, p, cycle, st));
+  if (!pt.lambda_set) {
+    // lambda_rel refers to max |residual| of the partition's first cycle
+    RIX_CUDA(cudaMemsetAsync(pt.fi_state.as<R>() + 1, 0, sizeof(R), st));
+    k_absmax<R><<<blocks_for(ctx, npix), 256, 0, st>>>(pt.resid.as<R>(), npix, pt.fi_state.as<R>() + 1);
+    RIX_LAUNCH_CHECK();
+    pt.lambda_set = true;
+  }
+  RIX_TRY(fill_spectra<R>(job, p, st));
+  RIX_TRY(ensure<R>(job, pt.fi_mx, tot * sizeof(R)));
+  RIX_TRY(ensure<R>(job, pt.fi_c, tot * sizeof(cplx<R>)));
+  FillArgs fa = fill_args<R>(job, p);
+  const double gn = cycle == 1 ? 0.0 : 1.0;
+  RIX_CUDA(cudaMemsetAsync(pt.fi_state.p, 0, sizeof(R), st));
+  k_fill_fista<R><<<blocks_for(ctx, tot), 256, 0, st>>>(fa, gn, pt.fi_mx.as<R>(), pt.fi_c.as<cplx<R>>(),
+                                                        pt.fi_state.as<R>());
+  RIX_LAUNCH_CHECK();
+  RIX_TRY(alloc_zero<R>(job, pt.fi_alpha, npix * sizeof(R), st));
+  RIX_TRY(alloc_zero<R>(job, pt.fi_y, npix * sizeof(R), st));
+  RIX_TRY(ensure<R>(job, pt.fi_x, npix * sizeof(R)));
+  RIX_TRY(ensure<R>(job, pt.fi_alpha_prev, npix * sizeof(R)));
+  R* alpha = pt.fi_alpha.as<R>();
+  R* y = pt.fi_y.as<R>();
+  R* x = pt.fi_x.as<R>();
+  R* g = pt.fimg.as<R>();
+  R* tmp = pt.fi_alpha_prev.as<R>();
+  const double gscale = 2.0 / (double)tot;
+  double t = 1.0;
+  for (int it = 0; it < prm->iters; ++it) {
+    RIX_TRY(idwt2<R>(ctx, y, x, tmp, n, prm->levels, st));
+    // grad f(x) = 2 crop F^-1 [Mx X - C]
+    RIX_TRY(convolve<R>(job, pt, x, kOpAxpyReal, pt.fi_mx.p, pt.fi_c.p, g, gscale, 0, st));
+    RIX_TRY(dwt2<R>(ctx, g, tmp, n, prm->levels, st));
+    const double tn = 0.5 * (1.0 + std::sqrt(1.0 + 4.0 * t * t));
+    const double mom = (t - 1.0) / tn;
+    k_fista_step<R><<<blocks_for(ctx, npix), 256, 0, st>>>(alpha, y, g, npix, pt.fi_state.as<R>(), prm->lambda,
+                                                           prm->lambda_rel, mom);
+    RIX_LAUNCH_CHECK();
+    t = tn;
+  }
+  RIX_TRY(idwt2<R>(ctx, alpha, pt.delta.as<R>(), tmp, n, prm->levels, st));
+  RIX_TRY(publish<R>(job, p, cycle, st));
+  if (delta_out) RIX_CUDA(cudaMemcpyAsync(delta_out, pt.delta.p, npix * sizeof(R), cudaMemcpyDeviceToDevice, st));
+  return RIX_OK;
+}
+
+template <typename R>
+int op_combine(Job* job, R* out, cudaStream_t st) {
+  const int64_t npix = (int64_t)job->desc.n * job->desc.n;
+  const R* ptrs[kMaxPart];
+  for (int q = 0; q < job->n_part; ++q) ptrs[q] = job->part[q].model.as<R>();
+  const R** dptrs = nullptr;
+  RIX_CUDA(cudaMallocAsync((void**)&dptrs, sizeof(ptrs), st));
+  RIX_CUDA(cudaMemcpyAsync(dptrs, ptrs, sizeof(ptrs), cudaMemcpyHostToDevice, st));
+  k_mean<R><<<blocks_for(job->ctx, npix), 256, 0, st>>>(out, dptrs, job->n_part, npix);
+  cudaFreeAsync(dptrs, st);
+  RIX_LAUNCH_CHECK();
+  RIX_CUDA(cudaStreamSynchronize(st));   // ptrs is a host temporary
+  return RIX_OK;
+}
+
+#define RIX_MINOR_INST(R)                                                                   \
+  template int fill_init<R>(Job*, cudaStream_t);                                            \
+  template int op_msclean<R>(Job*, int, const rix_msclean_params*, R*, cudaStream_t);       \
+  template int op_fista<R>(Job*, int, const rix_fista_params*, R*, cudaStream_t);           \
+  template int op_combine<R>(Job*, R*, cudaStream_t);
+RIX_MINOR_INST(float)
+RIX_MINOR_INST(double)
+
+int get_components(Job* job, int part, int32_t* count, int32_t capacity, int32_t* scale_out,
+                   int32_t* pixel_out, double* amp_out, cudaStream_t st) {
+  Job& J = *job;
+  if (part < 0 || part >= J.n_part) return set_error(RIX_EINVAL, "partition out of range");
+  Part& pt = J.part[part];
+  *count = 0;
+  if (pt.ms_ncomp_cap == 0 || !pt.ms_comp.p) return RIX_OK;
+  const int cap = pt.ms_ncomp_cap;
+  char* cb = pt.ms_comp.as<char>();
+  const double* amp = reinterpret_cast<const double*>(cb);
+  const int* sc = reinterpret_cast<const int*>(cb + (size_t)cap * sizeof(double));
+  const int* px = sc + cap;
+  const int* cnt = px + cap;
+  int c = 0;
+  RIX_CUDA(cudaMemcpyAsync(&c, cnt, sizeof(int), cudaMemcpyDeviceToHost, st));
+  RIX_CUDA(cudaStreamSynchronize(st));
+  *count = c;
+  const int k = std::min(c, (int)std::max(capacity, 0));
+  if (k > 0) {
+    if (scale_out) RIX_CUDA(cudaMemcpyAsync(scale_out, sc, k * sizeof(int), cudaMemcpyDeviceToHost, st));
+    if (pixel_out) RIX_CUDA(cudaMemcpyAsync(pixel_out, px, k * sizeof(int), cudaMemcpyDeviceToHost, st));
+    if (amp_out) RIX_CUDA(cudaMemcpyAsync(amp_out, amp, k * sizeof(double), cudaMemcpyDeviceToHost, st));
+    RIX_CUDA(cudaStreamSynchronize(st));
+  }
+  return RIX_OK;
+}
+
+}  // namespace rix

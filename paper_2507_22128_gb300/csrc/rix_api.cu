@@ -1,0 +1,427 @@
+// The C ABI of include/rix.h: argument checks, job state, call ordering and
+// dispatch to the FP32 / FP64 device paths.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdarg>
+#include <cstring>
+#include <new>
+
+#include "rix_internal.cuh"
+
+struct rix_ctx_s {
+  rix::Ctx c;
+};
+struct rix_job_s {
+  rix::Job j;
+};
+
+namespace rix {
+
+static thread_local char g_err[1024] = "";
+
+int set_error(int code, const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+  return code;
+}
+
+const char* last_error() { return g_err; }
+
+int DevBuf::alloc(Ctx* ctx, size_t nbytes) {
+  release();
+  if (nbytes == 0) nbytes = 16;
+  void* q = nullptr;
+  cudaError_t e = cudaMalloc(&q, nbytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return set_error(RIX_ENOMEM, "cudaMalloc(%zu): %s", nbytes, cudaGetErrorString(e));
+  }
+  p = q;
+  bytes = nbytes;
+  owner = ctx;
+  return RIX_OK;
+}
+
+void DevBuf::release() {
+  if (p) cudaFree(p);
+  p = nullptr;
+  bytes = 0;
+}
+
+// upper bound of resident device bytes of a job (admission control)
+static size_t workspace_bytes(const rix_job_desc& d, int64_t nrow) {
+  const size_t real = d.precision == RIX_FP64 ? 8 : 4;
+  const size_t cplx = 2 * real;
+  const size_t n = (size_t)d.n, ng = 2 * n;
+  const size_t np = d.n_wplanes > 0 ? (size_t)d.n_wplanes : 1;
+  const size_t P = (size_t)d.n_part;
+  const size_t ns = (size_t)nrow * (size_t)d.nchan;
+  size_t b = 0;
+  b += (size_t)nrow * 24 + ns * 4;                 // uvw, weights
+  b += ns * std::min<size_t>(P, 2) * 8;            // sorted keys and samples (overlap counted twice)
+  b += ns / 512 * 4 + 64;                          // work items
+  b += n * n * (real + 8) + 4 * n * n * (real + 8); // corrections + n-1 tables (image and PSF)
+  b += P * 4 * n * n * real;                       // Gamma filters
+  b += 3 * 4 * n * n * cplx + 2 * n * n * real;    // fill scratch
+  // per partition: planes (windows are at most the full grid), transpose buffer,
+  // images, PSF and its spectrum, minor-cycle state
+  const size_t per = 2 * np * ng * ng * cplx + np * ng * n * cplx + (6 + P) * n * n * real +
+                     4 * n * n * real + 4 * n * n * cplx + 10 * n * n * real;
+  b += P * per;
+  return b;
+}
+
+static int check_desc(const rix_job_desc* d) {
+  if (!d) return set_error(RIX_EINVAL, "desc is NULL");
+  if (d->n < 32 || d->n > 4096 || (d->n & (d->n - 1))) return set_error(RIX_EINVAL, "n must be a power of two in [32, 4096]");
+  if (!(d->cell_rad > 0.0) || d->cell_rad * d->n >= 1.0) return set_error(RIX_EINVAL, "cell_rad out of range");
+  if (d->n_wplanes != 0 && (d->n_wplanes < kW + 1 || d->n_wplanes > 64))
+    return set_error(RIX_EINVAL, "n_wplanes must be 0 or in [%d, 64]", kW + 1);
+  if (d->nchan < 1 || d->nchan > 65536 || !d->freq_hz) return set_error(RIX_EINVAL, "bad channels");
+  for (int c = 0; c < d->nchan; ++c)
+    if (!(d->freq_hz[c] > 0.0)) return set_error(RIX_EINVAL, "frequencies must be positive");
+  if (d->precision != RIX_FP32 && d->precision != RIX_FP64) return set_error(RIX_EINVAL, "bad precision");
+  if (d->n_part < 1 || d->n_part > kMaxPart) return set_error(RIX_EINVAL, "n_part must be in [1, 4]");
+  if (d->tile != 0 && d->tile != 16 && d->tile != 32) return set_error(RIX_EINVAL, "tile must be 16 or 32");
+  if (d->tile == 32 && d->n_wplanes > 0) return set_error(RIX_EINVAL, "tile 32 needs a coplanar job (shared memory)");
+  if (d->precision == RIX_FP64 && d->n > 2048) return set_error(RIX_EINVAL, "FP64 jobs support n <= 2048");
+  return RIX_OK;
+}
+
+static int check_part(Job* job, int part) {
+  if (!job->partitioned) return set_error(RIX_ESTATE, "rix_set_uv_partition has not been called");
+  if (part < 0 || part >= job->n_part) return set_error(RIX_EINVAL, "partition %d out of range", part);
+  return RIX_OK;
+}
+
+static int ensure_images(Job* job, Part& pt) {
+  const size_t img = (size_t)job->desc.n * job->desc.n * (job->fp64 ? 8 : 4);
+  if (pt.model.bytes < img) {
+    RIX_TRY(pt.model.alloc(job->ctx, img));
+    RIX_CUDA(cudaMemset(pt.model.p, 0, img));
+  }
+  if (pt.resid.bytes < img) RIX_TRY(pt.resid.alloc(job->ctx, img));
+  if (pt.delta.bytes < img) RIX_TRY(pt.delta.alloc(job->ctx, img));
+  return RIX_OK;
+}
+
+static void reset_partitions(Job* job) {
+  for (int p = 0; p < kMaxPart; ++p) {
+    Part& pt = job->part[p];
+    pt.cycle = 0;
+    pt.minor_done = 0;
+    pt.psf_ready = false;
+    pt.lambda_set = false;
+    pt.model.release();
+    pt.resid.release();
+    pt.delta.release();
+    pt.outbox[0].release();
+    pt.outbox[1].release();
+    for (int q = 0; q < kMaxPart; ++q) pt.rho[q].release();
+    pt.ms_R.release(); pt.ms_P.release(); pt.ms_comp.release(); pt.ms_state.release();
+    pt.fi_alpha.release(); pt.fi_alpha_prev.release(); pt.fi_y.release();
+    pt.fi_mx.release(); pt.fi_c.release(); pt.fi_x.release();
+  }
+}
+
+}  // namespace rix
+
+using namespace rix;
+
+// ------------------------------------------------------------------------
+extern "C" {
+
+const char* rix_last_error(void) { return rix::last_error(); }
+
+int rix_create(rix_ctx_t* ctx, int device, size_t mem_budget_bytes) {
+  if (!ctx) return set_error(RIX_EINVAL, "ctx is NULL");
+  *ctx = nullptr;
+  int ndev = 0;
+  RIX_CUDA(cudaGetDeviceCount(&ndev));
+  if (device < 0 || device >= ndev) return set_error(RIX_EINVAL, "device %d out of range (%d devices)", device, ndev);
+  RIX_CUDA(cudaSetDevice(device));
+  rix_ctx_s* c = new (std::nothrow) rix_ctx_s();
+  if (!c) return set_error(RIX_ENOMEM, "host allocation");
+  c->c.device = device;
+  c->c.budget = mem_budget_bytes;
+  cudaDeviceProp prop;
+  if (cudaGetDeviceProperties(&prop, device) != cudaSuccess) {
+    delete c;
+    return set_error(RIX_ECUDA, "cudaGetDeviceProperties");
+  }
+  c->c.num_sms = prop.multiProcessorCount;
+  int rc = fft_init_twiddles(&c->c);
+  if (rc != RIX_OK) {
+    delete c;
+    return rc;
+  }
+  *ctx = c;
+  return RIX_OK;
+}
+
+int rix_destroy(rix_ctx_t ctx) {
+  if (!ctx) return RIX_OK;
+  if (ctx->c.jobs > 0) return set_error(RIX_EBUSY, "context still owns %d jobs", ctx->c.jobs);
+  cudaSetDevice(ctx->c.device);
+  delete ctx;
+  return RIX_OK;
+}
+
+size_t rix_job_workspace_bytes(const rix_job_desc* desc, int64_t nrow) {
+  if (check_desc(desc) != RIX_OK || nrow < 0) return 0;
+  return workspace_bytes(*desc, nrow);
+}
+
+int rix_job_create(rix_ctx_t ctx, const rix_job_desc* desc, int64_t max_rows, rix_job_t* job) {
+  if (!ctx || !job) return set_error(RIX_EINVAL, "NULL argument");
+  *job = nullptr;
+  RIX_TRY(check_desc(desc));
+  if (max_rows < 0 || max_rows * (int64_t)desc->nchan > (int64_t)0x7fffffff)
+    return set_error(RIX_EINVAL, "max_rows out of range");
+  const size_t need = workspace_bytes(*desc, max_rows);
+  if (ctx->c.budget && ctx->c.reserved + need > ctx->c.budget)
+    return set_error(RIX_ENOMEM, "memory budget: %zu reserved + %zu needed > %zu", ctx->c.reserved, need, ctx->c.budget);
+  RIX_CUDA(cudaSetDevice(ctx->c.device));
+  rix_job_s* js = new (std::nothrow) rix_job_s();
+  if (!js) return set_error(RIX_ENOMEM, "host allocation");
+  Job& J = js->j;
+  J.ctx = &ctx->c;
+  J.desc = *desc;
+  J.freq.assign(desc->freq_hz, desc->freq_hz + desc->nchan);
+  J.desc.freq_hz = J.freq.data();
+  J.inv_lambda_h.resize(desc->nchan);
+  for (int c = 0; c < desc->nchan; ++c) J.inv_lambda_h[c] = J.freq[c] / kC;
+  J.max_rows = max_rows;
+  J.ng = 2 * desc->n;
+  J.tile = desc->tile ? desc->tile : 16;
+  J.nw = desc->n_wplanes;
+  J.ww = desc->n_wplanes > 0 ? kW : 1;
+  J.fp64 = desc->precision == RIX_FP64;
+  J.n_part = desc->n_part;
+  int rc = J.inv_lambda.alloc(J.ctx, desc->nchan * sizeof(double));
+  if (rc == RIX_OK && cudaMemcpy(J.inv_lambda.p, J.inv_lambda_h.data(), desc->nchan * sizeof(double),
+                                 cudaMemcpyHostToDevice) != cudaSuccess)
+    rc = set_error(RIX_ECUDA, "frequency upload");
+  for (int p = 0; rc == RIX_OK && p < kMaxPart; ++p)
+    if (cudaEventCreateWithFlags(&J.part[p].ev_minor, cudaEventDisableTiming) != cudaSuccess)
+      rc = set_error(RIX_ECUDA, "event creation");
+  if (rc != RIX_OK) {
+    delete js;
+    return rc;
+  }
+  J.reserved = need;
+  ctx->c.reserved += need;
+  ctx->c.jobs += 1;
+  *job = js;
+  return RIX_OK;
+}
+
+int rix_job_destroy(rix_job_t job) {
+  if (!job) return RIX_OK;
+  Job& J = job->j;
+  cudaSetDevice(J.ctx->device);
+  cudaDeviceSynchronize();
+  for (int p = 0; p < kMaxPart; ++p)
+    if (J.part[p].ev_minor) cudaEventDestroy(J.part[p].ev_minor);
+  J.ctx->reserved -= J.reserved;
+  J.ctx->jobs -= 1;
+  delete job;
+  return RIX_OK;
+}
+
+int rix_job_sync(rix_job_t job) {
+  if (!job) return set_error(RIX_EINVAL, "job is NULL");
+  RIX_CUDA(cudaSetDevice(job->j.ctx->device));
+  RIX_CUDA(cudaDeviceSynchronize());
+  return RIX_OK;
+}
+
+int rix_job_get_stats(rix_job_t job, rix_job_stats* out) {
+  if (!job || !out) return set_error(RIX_EINVAL, "NULL argument");
+  *out = job->j.stats;
+  for (int p = 0; p < kMaxPart; ++p) out->cycle[p] = job->j.part[p].cycle;
+  return RIX_OK;
+}
+
+int rix_set_uv_partition(rix_job_t job, const double* uvw_m, int64_t nrow, const float* weight,
+                         const double* ell_px, double delta_px, uint8_t* mask_out, rix_stream_t stream) {
+  if (!job) return set_error(RIX_EINVAL, "job is NULL");
+  Job& J = job->j;
+  cudaStream_t st = (cudaStream_t)stream;
+  RIX_CUDA(cudaSetDevice(J.ctx->device));
+  J.partitioned = false;
+  reset_partitions(&J);
+  RIX_TRY(partition_job(&J, uvw_m, nrow, weight, ell_px, delta_px, mask_out, st));
+  if (J.fp64) RIX_TRY(grid_build_corrections<double>(&J, st));
+  else RIX_TRY(grid_build_corrections<float>(&J, st));
+  if (J.fp64) RIX_TRY(fill_init<double>(&J, st));
+  else RIX_TRY(fill_init<float>(&J, st));
+  for (int p = 0; p < J.n_part; ++p) RIX_TRY(ensure_images(&J, J.part[p]));
+  J.partitioned = true;
+  return RIX_OK;
+}
+
+int rix_get_sorted_entries(rix_job_t job, uint32_t* keys_out, uint32_t* samples_out, rix_stream_t stream) {
+  if (!job) return set_error(RIX_EINVAL, "job is NULL");
+  Job& J = job->j;
+  if (!J.partitioned) return set_error(RIX_ESTATE, "not partitioned");
+  cudaStream_t st = (cudaStream_t)stream;
+  if (J.n_entries == 0) return RIX_OK;
+  if (keys_out) RIX_CUDA(cudaMemcpyAsync(keys_out, J.keys.p, J.n_entries * 4, cudaMemcpyDeviceToDevice, st));
+  if (samples_out) RIX_CUDA(cudaMemcpyAsync(samples_out, J.samples.p, J.n_entries * 4, cudaMemcpyDeviceToDevice, st));
+  return RIX_OK;
+}
+
+int rix_degrid(rix_job_t job, int part, const void* image, void* vis_out, rix_stream_t stream) {
+  if (!job) return set_error(RIX_EINVAL, "job is NULL");
+  Job& J = job->j;
+  RIX_TRY(check_part(&J, part));
+  if (!image || !vis_out) return set_error(RIX_EINVAL, "NULL image or vis_out");
+  RIX_CUDA(cudaSetDevice(J.ctx->device));
+  cudaStream_t st = (cudaStream_t)stream;
+  if (J.fp64) return op_degrid<double>(&J, part, (const double*)image, (double2*)vis_out, st);
+  return op_degrid<float>(&J, part, (const float*)image, (float2*)vis_out, st);
+}
+
+int rix_grid(rix_job_t job, int part, const void* vis, void* image_out, rix_stream_t stream) {
+  if (!job) return set_error(RIX_EINVAL, "job is NULL");
+  Job& J = job->j;
+  RIX_TRY(check_part(&J, part));
+  if (!vis || !image_out) return set_error(RIX_EINVAL, "NULL vis or image_out");
+  RIX_CUDA(cudaSetDevice(J.ctx->device));
+  cudaStream_t st = (cudaStream_t)stream;
+  if (J.fp64) return op_grid<double>(&J, part, (const double2*)vis, (double*)image_out, st);
+  return op_grid<float>(&J, part, (const float2*)vis, (float*)image_out, st);
+}
+
+static int ensure_psf(Job& J, int part, cudaStream_t st) {
+  if (J.part[part].psf_ready) return RIX_OK;
+  if (J.fp64) return op_psf<double>(&J, part, st);
+  return op_psf<float>(&J, part, st);
+}
+
+int rix_psf(rix_job_t job, int part, void* psf_out, double* weight_sum_out, rix_stream_t stream) {
+  if (!job) return set_error(RIX_EINVAL, "job is NULL");
+  Job& J = job->j;
+  RIX_TRY(check_part(&J, part));
+  RIX_CUDA(cudaSetDevice(J.ctx->device));
+  cudaStream_t st = (cudaStream_t)stream;
+  RIX_TRY(ensure_psf(J, part, st));
+  if (psf_out) {
+    const size_t b = (size_t)4 * J.desc.n * J.desc.n * (J.fp64 ? 8 : 4);
+    RIX_CUDA(cudaMemcpyAsync(psf_out, J.part[part].psf.p, b, cudaMemcpyDeviceToDevice, st));
+  }
+  if (weight_sum_out) *weight_sum_out = J.part[part].wsum;
+  return RIX_OK;
+}
+
+int rix_major_cycle(rix_job_t job, int part, const void* vis_obs, const void* model, void* residual_out,
+                    rix_stream_t stream) {
+  if (!job) return set_error(RIX_EINVAL, "job is NULL");
+  Job& J = job->j;
+  RIX_TRY(check_part(&J, part));
+  if (!vis_obs) return set_error(RIX_EINVAL, "vis_obs is NULL");
+  Part& pt = J.part[part];
+  if (pt.minor_done < pt.cycle) return set_error(RIX_ESTATE, "partition %d: minor cycle %d not done", part, pt.cycle);
+  RIX_CUDA(cudaSetDevice(J.ctx->device));
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t img = (size_t)J.desc.n * J.desc.n * (J.fp64 ? 8 : 4);
+  // order after this partition's previous minor cycle, whatever stream it used
+  if (pt.minor_done > 0) RIX_CUDA(cudaStreamWaitEvent(st, pt.ev_minor, 0));
+  if (model) RIX_CUDA(cudaMemcpyAsync(pt.model.p, model, img, cudaMemcpyDeviceToDevice, st));
+  if (J.fp64) RIX_TRY(op_major<double>(&J, part, (const double2*)vis_obs, pt.resid.as<double>(), st));
+  else RIX_TRY(op_major<float>(&J, part, (const float2*)vis_obs, pt.resid.as<float>(), st));
+  if (residual_out) RIX_CUDA(cudaMemcpyAsync(residual_out, pt.resid.p, img, cudaMemcpyDeviceToDevice, st));
+  pt.cycle += 1;
+  return RIX_OK;
+}
+
+static int minor_precheck(Job& J, int part, cudaStream_t st) {
+  RIX_TRY(check_part(&J, part));
+  Part& pt = J.part[part];
+  if (pt.cycle == 0 || pt.minor_done >= pt.cycle)
+    return set_error(RIX_ESTATE, "partition %d: run the major cycle before the minor cycle", part);
+  const int n = pt.cycle;
+  for (int q = 0; q < J.n_part; ++q) {
+    if (q == part) continue;
+    if (J.part[q].minor_done < n - 1)
+      return set_error(RIX_ESTATE, "partition %d cycle %d needs partition %d's minor cycle %d", part, n, q, n - 1);
+    if (J.part[q].minor_done > 0) RIX_CUDA(cudaStreamWaitEvent(st, J.part[q].ev_minor, 0));
+  }
+  for (int q = 0; q < J.n_part; ++q) RIX_TRY(ensure_psf(J, q, st));
+  return RIX_OK;
+}
+
+int rix_minor_cycle_msclean(rix_job_t job, int part, const rix_msclean_params* prm, void* delta_out,
+                            rix_stream_t stream) {
+  if (!job || !prm) return set_error(RIX_EINVAL, "NULL argument");
+  Job& J = job->j;
+  RIX_CUDA(cudaSetDevice(J.ctx->device));
+  cudaStream_t st = (cudaStream_t)stream;
+  if (prm->n_scales < 1 || prm->n_scales > kMaxScales || !prm->scales || prm->scales[0] != 0.0f)
+    return set_error(RIX_EINVAL, "scales: 1..%d radii with scales[0] = 0", kMaxScales);
+  for (int i = 1; i < prm->n_scales; ++i)
+    if (!(prm->scales[i] > 0.0f) || prm->scales[i] >= (float)J.desc.n / 2) return set_error(RIX_EINVAL, "bad scale %d", i);
+  if (!(prm->gain > 0.0 && prm->gain <= 1.0) || prm->niter < 0 || !(prm->threshold >= 0.0))
+    return set_error(RIX_EINVAL, "bad gain / niter / threshold");
+  RIX_TRY(minor_precheck(J, part, st));
+  if (J.fp64) RIX_TRY(op_msclean<double>(&J, part, prm, (double*)delta_out, st));
+  else RIX_TRY(op_msclean<float>(&J, part, prm, (float*)delta_out, st));
+  J.part[part].minor_done += 1;
+  RIX_CUDA(cudaEventRecord(J.part[part].ev_minor, st));
+  return RIX_OK;
+}
+
+int rix_minor_cycle_fista(rix_job_t job, int part, const rix_fista_params* prm, void* delta_out,
+                          rix_stream_t stream) {
+  if (!job || !prm) return set_error(RIX_EINVAL, "NULL argument");
+  Job& J = job->j;
+  RIX_CUDA(cudaSetDevice(J.ctx->device));
+  cudaStream_t st = (cudaStream_t)stream;
+  const int maxlev = ilog2(J.desc.n) - 3;
+  if (prm->iters < 0 || prm->levels < 1 || prm->levels > maxlev)
+    return set_error(RIX_EINVAL, "iters >= 0 and levels in [1, %d]", maxlev);
+  if (!(prm->lambda > 0.0) && !(prm->lambda_rel > 0.0)) return set_error(RIX_EINVAL, "lambda or lambda_rel must be > 0");
+  RIX_TRY(minor_precheck(J, part, st));
+  if (J.fp64) RIX_TRY(op_fista<double>(&J, part, prm, (double*)delta_out, st));
+  else RIX_TRY(op_fista<float>(&J, part, prm, (float*)delta_out, st));
+  J.part[part].minor_done += 1;
+  RIX_CUDA(cudaEventRecord(J.part[part].ev_minor, st));
+  return RIX_OK;
+}
+
+int rix_get_components(rix_job_t job, int part, int32_t* count, int32_t capacity, int32_t* scale_out,
+                       int32_t* pixel_out, double* amp_out, rix_stream_t stream) {
+  if (!job || !count) return set_error(RIX_EINVAL, "NULL argument");
+  RIX_CUDA(cudaSetDevice(job->j.ctx->device));
+  return get_components(&job->j, part, count, capacity, scale_out, pixel_out, amp_out, (cudaStream_t)stream);
+}
+
+int rix_get_model(rix_job_t job, int part, void* image_out, rix_stream_t stream) {
+  if (!job || !image_out) return set_error(RIX_EINVAL, "NULL argument");
+  Job& J = job->j;
+  RIX_TRY(check_part(&J, part));
+  RIX_CUDA(cudaSetDevice(J.ctx->device));
+  cudaStream_t st = (cudaStream_t)stream;
+  if (J.part[part].minor_done > 0) RIX_CUDA(cudaStreamWaitEvent(st, J.part[part].ev_minor, 0));
+  const size_t img = (size_t)J.desc.n * J.desc.n * (J.fp64 ? 8 : 4);
+  RIX_CUDA(cudaMemcpyAsync(image_out, J.part[part].model.p, img, cudaMemcpyDeviceToDevice, st));
+  return RIX_OK;
+}
+
+int rix_combine(rix_job_t job, void* image_out, rix_stream_t stream) {
+  if (!job || !image_out) return set_error(RIX_EINVAL, "NULL argument");
+  Job& J = job->j;
+  if (!J.partitioned) return set_error(RIX_ESTATE, "not partitioned");
+  RIX_CUDA(cudaSetDevice(J.ctx->device));
+  cudaStream_t st = (cudaStream_t)stream;
+  for (int q = 0; q < J.n_part; ++q)
+    if (J.part[q].minor_done > 0) RIX_CUDA(cudaStreamWaitEvent(st, J.part[q].ev_minor, 0));
+  if (J.fp64) return op_combine<double>(&J, (double*)image_out, st);
+  return op_combine<float>(&J, (float*)image_out, st);
+}
+
+}  // extern "C"

@@ -1,0 +1,252 @@
+// Internal declarations shared by the translation units of librix.so.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <cstdio>
+#include <string>
+#include <vector>
+
+#include "../../include/rix.h"
+
+namespace rix {
+
+// ---------------------------------------------------------------------------
+// errors
+// ---------------------------------------------------------------------------
+int set_error(int code, const char* fmt, ...);
+const char* last_error();
+
+#define RIX_CUDA(...)                                                                   \
+  do {                                                                                  \
+    cudaError_t e_ = (__VA_ARGS__);                                                     \
+    if (e_ != cudaSuccess)                                                              \
+      return ::rix::set_error(RIX_ECUDA, "%s:%d %s: %s", __FILE__, __LINE__,            \
+                              #__VA_ARGS__, cudaGetErrorString(e_));                    \
+  } while (0)
+
+#define RIX_TRY(...)               \
+  do {                             \
+    int r_ = (__VA_ARGS__);        \
+    if (r_ != RIX_OK) return r_;   \
+  } while (0)
+
+#define RIX_LAUNCH_CHECK() RIX_CUDA(cudaGetLastError())
+
+// ---------------------------------------------------------------------------
+// numeric types
+// ---------------------------------------------------------------------------
+template <typename R> struct Cplx;
+template <> struct Cplx<float> { using T = float2; };
+template <> struct Cplx<double> { using T = double2; };
+template <typename R> using cplx = typename Cplx<R>::T;
+
+template <typename C> __host__ __device__ __forceinline__ C cmake(double re, double im);
+template <> __host__ __device__ __forceinline__ float2 cmake<float2>(double re, double im) {
+  return make_float2((float)re, (float)im);
+}
+template <> __host__ __device__ __forceinline__ double2 cmake<double2>(double re, double im) {
+  return make_double2(re, im);
+}
+__host__ __device__ __forceinline__ float2 operator+(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__host__ __device__ __forceinline__ float2 operator-(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__host__ __device__ __forceinline__ float2 operator*(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
+__host__ __device__ __forceinline__ double2 operator+(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__host__ __device__ __forceinline__ double2 operator-(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+__host__ __device__ __forceinline__ double2 operator*(double2 a, double s) { return make_double2(a.x * s, a.y * s); }
+template <typename C> __host__ __device__ __forceinline__ C cmul(C a, C b) {
+  C r; r.x = a.x * b.x - a.y * b.y; r.y = a.x * b.y + a.y * b.x; return r;
+}
+template <typename C> __host__ __device__ __forceinline__ C cmulc(C a, C b) {  // a * conj(b)
+  C r; r.x = a.x * b.x + a.y * b.y; r.y = a.y * b.x - a.x * b.y; return r;
+}
+
+constexpr double kC = 299792458.0;
+constexpr int kW = 8;            // ES kernel support (cells)
+constexpr double kBeta = 18.4;   // 2.30 * kW
+
+// ---------------------------------------------------------------------------
+// device buffers
+// ---------------------------------------------------------------------------
+struct Ctx;
+
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+  Ctx* owner = nullptr;
+  DevBuf() = default;
+  DevBuf(const DevBuf&) = delete;
+  DevBuf& operator=(const DevBuf&) = delete;
+  ~DevBuf() { release(); }
+  int alloc(Ctx* ctx, size_t nbytes);      // frees any previous allocation first
+  void release();
+  template <typename T> T* as() const { return static_cast<T*>(p); }
+};
+
+struct Ctx {
+  int device = 0;
+  size_t budget = 0;          // 0 = unlimited
+  size_t reserved = 0;        // sum of admitted job workspaces
+  int jobs = 0;
+  int num_sms = 0;
+  DevBuf tw32, tw64;          // FFT twiddle tables, length kTwMax
+};
+
+constexpr int kTwLog = 14;
+constexpr int kTwMax = 1 << kTwLog;   // largest 1D FFT length (4N for N = 4096)
+
+// ---------------------------------------------------------------------------
+// FFT plans (see k_fft.cu)
+// ---------------------------------------------------------------------------
+enum FactorMode : int {
+  kFacNone = 0,     // value * (-1)^(a+b)
+  kFacReal = 1,     // value * corr[b][a] * (-1)^(a+b)
+  kFacPhase = 2,    // value * corr[b][a] * exp(-+2 pi i w_p (n - 1)) * (-1)^(a+b)
+};
+
+// Describes the pixel-side factor of a transform between an M x M real image
+// (centred on an L x L grid) and the window [lo, lo + S)^2 of its spectrum.
+struct XformGeom {
+  int M, L, logL, lo, S;
+  int nplanes;
+  int mode;                    // FactorMode
+  const void* corr;            // Real [M][M] or null
+  const double* nm1;           // double [M][M]: n - 1 per pixel (kFacPhase)
+  double w0, dw;               // plane p sits at w0 + p * dw (kFacPhase)
+};
+
+template <typename R>
+int fwd_rows(const Ctx* ctx, const XformGeom& g, const R* img, cplx<R>* T, cudaStream_t st);
+template <typename R>
+int fwd_cols(const Ctx* ctx, const XformGeom& g, const cplx<R>* T, cplx<R>* spec, cudaStream_t st);
+// spectral operator applied between the forward and inverse column transforms
+enum SpecOp : int { kOpNone = 0, kOpMulReal = 1, kOpMulCplx = 2, kOpAxpyReal = 3 };
+template <typename R>
+int inv_cols(const Ctx* ctx, const XformGeom& g, const cplx<R>* spec, int op, const void* tab,
+             const void* tab2, cplx<R>* T, cudaStream_t st);
+template <typename R>
+int conv_cols(const Ctx* ctx, const XformGeom& g, const cplx<R>* Tin, int op, const void* tab,
+              const void* tab2, cplx<R>* Tout, cudaStream_t st);
+template <typename R>
+int inv_rows(const Ctx* ctx, const XformGeom& g, const cplx<R>* T, R* img, double scale,
+             int accumulate, cudaStream_t st);
+
+int fft_init_twiddles(Ctx* ctx);
+
+// ---------------------------------------------------------------------------
+// partition / sort (see k_partition.cu)
+// ---------------------------------------------------------------------------
+struct SampleGeomParams {
+  const double* uvw;          // [nrow][3]
+  const double* inv_lambda;   // [nchan] f / c
+  int64_t nrow;
+  int nchan;
+  int ng;                     // grid side 2N
+  double scale;               // cell * ng
+  double half;                // ng / 2
+  double ndl;                 // N * cell
+  int nw, ww;                 // w-planes (0 = coplanar), w support
+  double w_min, dw;
+};
+
+int scan_exclusive_u32(const uint32_t* in, uint32_t* out, int64_t n, uint32_t* total_dev,
+                       cudaStream_t st);
+int radix_sort_u32(uint32_t* keys, uint32_t* vals, uint32_t* keys_tmp, uint32_t* vals_tmp,
+                   int64_t n, int bits, cudaStream_t st, bool* result_in_tmp);
+int radix_sort_u64_keys(uint64_t* keys, uint64_t* keys_tmp, int64_t n, int bits, cudaStream_t st,
+                        bool* result_in_tmp);
+
+// ---------------------------------------------------------------------------
+// job
+// ---------------------------------------------------------------------------
+constexpr int kMaxPart = 4;
+constexpr int kMaxScales = 8;
+
+struct Part {
+  int64_t ent_begin = 0, ent_count = 0;     // range in the sorted entries
+  int64_t item_begin = 0, item_count = 0;   // range in the work items
+  double wsum = 0.0;
+  int win_lo = 0, win_n = 0;                // uv window on the 2N grid
+  int pwin_lo = 0, pwin_n = 0;              // uv window on the 4N PSF grid
+  int cycle = 0;                            // major cycles issued
+  int minor_done = 0;                       // minor cycles issued
+  bool psf_ready = false;
+  bool lambda_set = false;
+  DevBuf model_planes, resid_planes, tbuf;  // [nw][S][S], [nw][S][S], [nw][S][N]
+  DevBuf model, resid, delta;               // N x N Real
+  DevBuf outbox[2];                         // Phi_p^n by cycle parity
+  DevBuf rho[kMaxPart];                     // rho_{q->p}, N x N
+  DevBuf psf;                               // 2N x 2N Real
+  DevBuf hspec;                             // centred spectrum of the PSF, (2N)^2 complex
+  DevBuf lambda_dev;                        // double: FISTA lambda
+  // fill scratch: two (2N)^2 spectra, two [2N][N] transpose buffers, an image
+  DevBuf fs_a, fs_b, ft_a, ft_b, fimg;
+  DevBuf fspec;                             // P spectra: slot p = own residual, slot q = rho_{q->p}
+  DevBuf fi_state;                          // FISTA: [max Mx, max |residual| of cycle 1]
+  // minor-cycle state
+  DevBuf ms_R, ms_P, ms_B, ms_comp, ms_state;   // ms-CLEAN
+  DevBuf fi_alpha, fi_alpha_prev, fi_y, fi_mx, fi_c, fi_x;   // FISTA
+  int ms_ncomp_cap = 0;
+  cudaEvent_t ev_minor = nullptr;           // recorded after each minor cycle
+};
+
+struct Job {
+  Ctx* ctx = nullptr;
+  rix_job_desc desc{};
+  std::vector<double> freq;
+  std::vector<double> inv_lambda_h;
+  int64_t max_rows = 0;
+  size_t reserved = 0;
+  int ng = 0, tile = 16, nw = 0, ww = 1;
+  bool fp64 = false;
+  bool partitioned = false;
+  rix_job_stats stats{};
+  // resident inputs
+  DevBuf uvw, weight, inv_lambda;
+  // sort
+  DevBuf keys, samples, items;              // entries and work-item begin offsets (+1 sentinel)
+  int64_t n_entries = 0, n_items = 0;
+  int bt = 0, bw = 0, bp = 0;
+  // corrections
+  DevBuf corr_img, corr_psf;                // Real [N][N], [2N][2N]
+  DevBuf nm1_img, nm1_psf;                  // double n - 1 per pixel (w-stacked)
+  DevBuf gam;                               // Real [P][2N][2N] filters (u-major spectra)
+  Part part[kMaxPart];
+  double ells[kMaxPart];
+  int n_part = 1;
+  cudaEvent_t ev_tmp = nullptr;
+};
+
+// gridder entry points (k_grid.cu)
+template <typename R>
+int grid_build_corrections(Job* job, cudaStream_t st);
+template <typename R>
+int op_degrid(Job* job, int p, const R* image, cplx<R>* vis_out, cudaStream_t st);
+template <typename R>
+int op_grid(Job* job, int p, const cplx<R>* vis, R* image_out, cudaStream_t st);
+template <typename R>
+int op_major(Job* job, int p, const cplx<R>* vis, R* residual, cudaStream_t st);
+template <typename R>
+int op_psf(Job* job, int p, cudaStream_t st);
+
+// partition entry point (k_partition.cu)
+int partition_job(Job* job, const double* uvw, int64_t nrow, const float* weight,
+                  const double* ell_px, double delta, uint8_t* mask_out, cudaStream_t st);
+
+// minor cycles (k_minor.cu)
+template <typename R>
+int fill_init(Job* job, cudaStream_t st);
+template <typename R>
+int op_msclean(Job* job, int p, const rix_msclean_params* prm, R* delta_out, cudaStream_t st);
+template <typename R>
+int op_fista(Job* job, int p, const rix_fista_params* prm, R* delta_out, cudaStream_t st);
+template <typename R>
+int op_combine(Job* job, R* out, cudaStream_t st);
+int get_components(Job* job, int part, int32_t* count, int32_t capacity, int32_t* scale_out,
+                   int32_t* pixel_out, double* amp_out, cudaStream_t st);
+
+inline int ilog2(int64_t v) { int r = 0; while ((int64_t(1) << r) < v) ++r; return r; }
+inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+}  // namespace rix

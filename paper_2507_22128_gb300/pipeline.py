@@ -1,0 +1,101 @@
+"""Host driver of the decentralized major/minor loop (Sec. 3, Fig. 2).
+
+Marshalling only: it uploads an observation, creates one rix job with its uv
+partitions and issues, per major cycle, the major cycle of every partition,
+then the minor cycle of every partition, and finally the combine.  All
+arithmetic runs in librix.so.
+"""
+from __future__ import annotations
+
+import dataclasses
+
+import numpy as np
+import torch
+
+from . import rix
+
+
+@dataclasses.dataclass
+class Method:
+    kind: str = "msclean"                 # "msclean" or "fista"
+    scales: tuple = (0.0, 3.0, 9.0)
+    gain: float = 0.1
+    niter: int = 2000
+    threshold: float = 1e-4
+    lam: float = 0.0
+    lam_rel: float = 1e-3
+    iters: int = 50
+    levels: int = 4
+
+
+class Reconstruction:
+    """One job on one device; partitions run on the caller's stream."""
+
+    def __init__(self, ctx, n, cell_rad, n_wplanes, freq, nrow, n_part=2, precision=rix.FP32, tile=0,
+                 device="cuda"):
+        self.ctx = ctx
+        self.n = n
+        self.n_part = n_part
+        self.precision = precision
+        self.rdtype = torch.float64 if precision == rix.FP64 else torch.float32
+        self.cdtype = torch.complex128 if precision == rix.FP64 else torch.complex64
+        self.device = torch.device(device)
+        self.job = rix.job_create(ctx, n, cell_rad, n_wplanes, list(freq), precision, n_part, nrow, tile)
+        self.vis = None
+
+    def close(self):
+        if self.job:
+            rix.job_destroy(self.job)
+            self.job = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def set_data(self, uvw, vis, weight=None, ell_px=None, delta_px=1.0, stream=None):
+        """uvw: (nrow, 3) float64; vis: (nrow, nchan) complex; device tensors or
+        numpy arrays (copied to the device)."""
+        dev = self.device
+        self.uvw = torch.as_tensor(uvw, dtype=torch.float64, device=dev).contiguous()
+        self.vis = torch.as_tensor(vis, device=dev).to(self.cdtype).contiguous()
+        self.weight = None if weight is None else torch.as_tensor(weight, dtype=torch.float32,
+                                                                  device=dev).contiguous()
+        rix.set_uv_partition(self.job, self.uvw, self.weight, ell_px, delta_px, None, stream)
+
+    def stats(self) -> dict:
+        return rix.job_get_stats(self.job)
+
+    def major(self, p, residual_out=None, stream=None):
+        rix.major_cycle(self.job, p, self.vis, None, residual_out, stream)
+
+    def minor(self, p, m: Method, delta_out=None, stream=None):
+        if m.kind == "msclean":
+            rix.minor_cycle_msclean(self.job, p, m.scales, m.gain, m.niter, m.threshold, delta_out, stream)
+        else:
+            rix.minor_cycle_fista(self.job, p, m.lam, m.lam_rel, m.iters, m.levels, delta_out, stream)
+
+    def cycle(self, m: Method, stream=None):
+        for p in range(self.n_part):
+            self.major(p, stream=stream)
+        for p in range(self.n_part):
+            self.minor(p, m, stream=stream)
+
+    def combine(self, out=None, stream=None):
+        if out is None:
+            out = torch.empty((self.n, self.n), dtype=self.rdtype, device=self.device)
+        rix.combine(self.job, out, stream)
+        return out
+
+    def run(self, m: Method, n_major: int, stream=None):
+        for _ in range(n_major):
+            self.cycle(m, stream)
+        return self.combine(stream=stream)
+
+
+def observation_job(ctx, obs, n_part=2, precision=rix.FP32, tile=0, ell_px=None, delta_px=1.0):
+    """Reconstruction set up from a synth.Observation."""
+    r = Reconstruction(ctx, obs.n, obs.cell_rad, obs.n_wplanes, obs.freq, obs.nrow, n_part, precision, tile)
+    r.set_data(obs.uvw, obs.vis, obs.weight, ell_px, delta_px)
+    return r

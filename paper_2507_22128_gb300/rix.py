@@ -1,0 +1,244 @@
+"""Thin Python binding of librix.so (include/rix.h).
+
+Argument marshalling only: every step of the path runs in the library's CUDA
+kernels.  Device arrays are torch tensors on the job's CUDA device (PyTorch
+provides memory and streams); the default stream argument is torch's current
+stream.  Functions carry the names of the C ABI without its ``rix_`` prefix.
+Importing this module fails loudly when librix.so has not been built.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "librix.so")
+
+OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, ESTATE, EBUSY = 0, -1, -2, -3, -4, -5, -6
+FP32, FP64 = 0, 1
+
+
+class RixError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"rix error {code}: {msg}")
+        self.code = code
+
+
+class JobDesc(C.Structure):
+    _fields_ = [("n", C.c_int32), ("cell_rad", C.c_double), ("n_wplanes", C.c_int32),
+                ("nchan", C.c_int32), ("freq_hz", C.POINTER(C.c_double)), ("precision", C.c_int32),
+                ("n_part", C.c_int32), ("tile", C.c_int32)]
+
+
+class JobStats(C.Structure):
+    _fields_ = [("nrow", C.c_int64), ("n_samples", C.c_int64), ("n_outside", C.c_int64),
+                ("n_entries", C.c_int64), ("part_count", C.c_int64 * 4), ("part_weight", C.c_double * 4),
+                ("ell_px", C.c_double * 3), ("delta_px", C.c_double), ("w_min", C.c_double),
+                ("dw", C.c_double), ("max_dw_nm1", C.c_double), ("window_lo", C.c_int32 * 4),
+                ("window_size", C.c_int32 * 4), ("n_work_items", C.c_int64), ("cycle", C.c_int32 * 4)]
+
+
+class MscleanParams(C.Structure):
+    _fields_ = [("scales", C.POINTER(C.c_float)), ("n_scales", C.c_int32), ("gain", C.c_double),
+                ("niter", C.c_int32), ("threshold", C.c_double)]
+
+
+class FistaParams(C.Structure):
+    _fields_ = [("lambda_", C.c_double), ("lambda_rel", C.c_double), ("iters", C.c_int32),
+                ("levels", C.c_int32)]
+
+
+def _load() -> C.CDLL:
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: build it with paper_2507_22128_gb300.build.build()")
+    lib = C.CDLL(LIB_PATH)
+    vp, i32, i64, dbl, sz = C.c_void_p, C.c_int32, C.c_int64, C.c_double, C.c_size_t
+    sig = {
+        "rix_create": (C.c_int, [C.POINTER(vp), C.c_int, sz]),
+        "rix_destroy": (C.c_int, [vp]),
+        "rix_job_workspace_bytes": (sz, [C.POINTER(JobDesc), i64]),
+        "rix_job_create": (C.c_int, [vp, C.POINTER(JobDesc), i64, C.POINTER(vp)]),
+        "rix_job_destroy": (C.c_int, [vp]),
+        "rix_job_sync": (C.c_int, [vp]),
+        "rix_job_get_stats": (C.c_int, [vp, C.POINTER(JobStats)]),
+        "rix_set_uv_partition": (C.c_int, [vp, vp, i64, vp, C.POINTER(dbl), dbl, vp, vp]),
+        "rix_get_sorted_entries": (C.c_int, [vp, vp, vp, vp]),
+        "rix_degrid": (C.c_int, [vp, C.c_int, vp, vp, vp]),
+        "rix_grid": (C.c_int, [vp, C.c_int, vp, vp, vp]),
+        "rix_psf": (C.c_int, [vp, C.c_int, vp, C.POINTER(dbl), vp]),
+        "rix_major_cycle": (C.c_int, [vp, C.c_int, vp, vp, vp, vp]),
+        "rix_minor_cycle_msclean": (C.c_int, [vp, C.c_int, C.POINTER(MscleanParams), vp, vp]),
+        "rix_minor_cycle_fista": (C.c_int, [vp, C.c_int, C.POINTER(FistaParams), vp, vp]),
+        "rix_get_components": (C.c_int, [vp, C.c_int, C.POINTER(i32), i32, vp, vp, vp, vp]),
+        "rix_get_model": (C.c_int, [vp, C.c_int, vp, vp]),
+        "rix_combine": (C.c_int, [vp, vp, vp]),
+        "rix_last_error": (C.c_char_p, []),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    return lib
+
+
+_lib = _load()
+
+EXPORTED = ("rix_create", "rix_destroy", "rix_job_workspace_bytes", "rix_job_create", "rix_job_destroy",
+            "rix_job_sync", "rix_job_get_stats", "rix_set_uv_partition", "rix_get_sorted_entries",
+            "rix_degrid", "rix_grid", "rix_psf", "rix_major_cycle", "rix_minor_cycle_msclean",
+            "rix_minor_cycle_fista", "rix_get_components", "rix_get_model", "rix_combine", "rix_last_error")
+
+
+def _check(rc: int):
+    if rc != OK:
+        raise RixError(rc, _lib.rix_last_error().decode(errors="replace"))
+
+
+def _stream(stream):
+    if stream is None:
+        return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, torch.cuda.Stream):
+        return C.c_void_p(stream.cuda_stream)
+    return C.c_void_p(int(stream))
+
+
+def _ptr(t, dtype=None, numel=None, name="tensor"):
+    if t is None:
+        return None
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if dtype is not None and t.dtype not in (dtype if isinstance(dtype, tuple) else (dtype,)):
+        raise TypeError(f"{name} has dtype {t.dtype}, expected {dtype}")
+    if numel is not None and t.numel() != numel:
+        raise ValueError(f"{name} has {t.numel()} elements, expected {numel}")
+    return C.c_void_p(t.data_ptr())
+
+
+# ---------------------------------------------------------------- lifetime --
+def create(device: int = 0, mem_budget_bytes: int = 0) -> int:
+    h = C.c_void_p()
+    _check(_lib.rix_create(C.byref(h), device, mem_budget_bytes))
+    return h.value
+
+
+def destroy(ctx: int):
+    _check(_lib.rix_destroy(ctx))
+
+
+def _desc(n, cell_rad, n_wplanes, freq_hz, precision, n_part, tile):
+    f = (C.c_double * len(freq_hz))(*[float(x) for x in freq_hz])
+    d = JobDesc(n, cell_rad, n_wplanes, len(freq_hz), C.cast(f, C.POINTER(C.c_double)), precision,
+                n_part, tile)
+    return d, f
+
+
+def job_workspace_bytes(n, cell_rad, n_wplanes, freq_hz, precision, n_part, nrow, tile=0) -> int:
+    d, _keep = _desc(n, cell_rad, n_wplanes, freq_hz, precision, n_part, tile)
+    return int(_lib.rix_job_workspace_bytes(C.byref(d), nrow))
+
+
+def job_create(ctx, n, cell_rad, n_wplanes, freq_hz, precision, n_part, max_rows, tile=0) -> int:
+    d, _keep = _desc(n, cell_rad, n_wplanes, freq_hz, precision, n_part, tile)
+    h = C.c_void_p()
+    _check(_lib.rix_job_create(ctx, C.byref(d), max_rows, C.byref(h)))
+    return h.value
+
+
+def job_destroy(job: int):
+    _check(_lib.rix_job_destroy(job))
+
+
+def job_sync(job: int):
+    _check(_lib.rix_job_sync(job))
+
+
+def job_get_stats(job: int) -> dict:
+    s = JobStats()
+    _check(_lib.rix_job_get_stats(job, C.byref(s)))
+    out = {}
+    for name, _ in JobStats._fields_:
+        v = getattr(s, name)
+        out[name] = list(v) if not isinstance(v, (int, float)) else v
+    return out
+
+
+# --------------------------------------------------------------- a1 - a3 --
+def set_uv_partition(job, uvw, weight=None, ell_px=None, delta_px=1.0, mask_out=None, stream=None):
+    nrow = uvw.shape[0]
+    ells = None
+    if ell_px is not None:
+        ells = (C.c_double * len(ell_px))(*[float(x) for x in ell_px])
+    _check(_lib.rix_set_uv_partition(job, _ptr(uvw, torch.float64, nrow * 3, "uvw"), nrow,
+                                     _ptr(weight, torch.float32, name="weight"),
+                                     C.cast(ells, C.POINTER(C.c_double)) if ells is not None else None,
+                                     float(delta_px), _ptr(mask_out, torch.uint8, name="mask_out"),
+                                     _stream(stream)))
+
+
+def get_sorted_entries(job, keys_out, samples_out, stream=None):
+    _check(_lib.rix_get_sorted_entries(job, _ptr(keys_out, torch.int32, name="keys_out"),
+                                       _ptr(samples_out, torch.int32, name="samples_out"), _stream(stream)))
+
+
+# --------------------------------------------------------------- a4 - a7 --
+_RT = (torch.float32, torch.float64)
+_CT = (torch.complex64, torch.complex128)
+
+
+def degrid(job, part, image, vis_out, stream=None):
+    _check(_lib.rix_degrid(job, part, _ptr(image, _RT, name="image"), _ptr(vis_out, _CT, name="vis_out"),
+                           _stream(stream)))
+
+
+def grid(job, part, vis, image_out, stream=None):
+    _check(_lib.rix_grid(job, part, _ptr(vis, _CT, name="vis"), _ptr(image_out, _RT, name="image_out"),
+                         _stream(stream)))
+
+
+def psf(job, part, psf_out=None, stream=None) -> float:
+    w = C.c_double()
+    _check(_lib.rix_psf(job, part, _ptr(psf_out, _RT, name="psf_out"), C.byref(w), _stream(stream)))
+    return w.value
+
+
+def major_cycle(job, part, vis_obs, model=None, residual_out=None, stream=None):
+    _check(_lib.rix_major_cycle(job, part, _ptr(vis_obs, _CT, name="vis_obs"), _ptr(model, _RT, name="model"),
+                                _ptr(residual_out, _RT, name="residual_out"), _stream(stream)))
+
+
+# -------------------------------------------------------------- a8 - a11 --
+def minor_cycle_msclean(job, part, scales, gain, niter, threshold, delta_out=None, stream=None):
+    sc = (C.c_float * len(scales))(*[float(s) for s in scales])
+    p = MscleanParams(C.cast(sc, C.POINTER(C.c_float)), len(scales), float(gain), int(niter), float(threshold))
+    _check(_lib.rix_minor_cycle_msclean(job, part, C.byref(p), _ptr(delta_out, _RT, name="delta_out"),
+                                        _stream(stream)))
+
+
+def minor_cycle_fista(job, part, lam=0.0, lam_rel=1e-3, iters=50, levels=4, delta_out=None, stream=None):
+    p = FistaParams(float(lam), float(lam_rel), int(iters), int(levels))
+    _check(_lib.rix_minor_cycle_fista(job, part, C.byref(p), _ptr(delta_out, _RT, name="delta_out"),
+                                      _stream(stream)))
+
+
+def get_components(job, part, capacity=1 << 16, stream=None):
+    import numpy as np
+    cnt = C.c_int32()
+    s = np.zeros(capacity, np.int32)
+    px = np.zeros(capacity, np.int32)
+    amp = np.zeros(capacity, np.float64)
+    _check(_lib.rix_get_components(job, part, C.byref(cnt), capacity, s.ctypes.data_as(C.c_void_p),
+                                   px.ctypes.data_as(C.c_void_p), amp.ctypes.data_as(C.c_void_p), _stream(stream)))
+    k = min(cnt.value, capacity)
+    return s[:k].copy(), px[:k].copy(), amp[:k].copy()
+
+
+def get_model(job, part, image_out, stream=None):
+    _check(_lib.rix_get_model(job, part, _ptr(image_out, _RT, name="image_out"), _stream(stream)))
+
+
+def combine(job, image_out, stream=None):
+    _check(_lib.rix_combine(job, _ptr(image_out, _RT, name="image_out"), _stream(stream)))

@@ -1,0 +1,187 @@
+"""GPU parity of a1-a7 (partition, sort, degrid, grid, PSF, major cycle)
+against the CPU oracle, through the C ABI.
+
+Tolerances: keys, permutation and masks bit-exact; FP32 operator within 1e-5
+relative L2 of the FP64 oracle gridder with the same kernel and within 1e-4
+of the direct DFT; FP64 operator within 1e-10 of the FP64 oracle gridder.
+"""
+import numpy as np
+import pytest
+
+from gpu_util import cplx_dtype, need_gpu, real_dtype, rel_l2, sparse_model, to_dev
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL = {0: 1e-5, 1: 1e-10}      # rix.FP32, rix.FP64
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    need_gpu()
+    from paper_2507_22128_gb300 import rix
+    c = rix.create(0)
+    yield c
+    rix.destroy(c)
+
+
+def _job(ctx, obs, prec, nparts=2, tile=0):
+    from paper_2507_22128_gb300 import rix
+    job = rix.job_create(ctx, obs.n, obs.cell_rad, obs.n_wplanes, list(obs.freq), prec, nparts, obs.nrow, tile)
+    mask = torch.zeros(obs.nvis, dtype=torch.uint8, device="cuda")
+    rix.set_uv_partition(job, to_dev(obs.uvw, torch.float64), to_dev(obs.weight, torch.float32), None, 1.0, mask)
+    torch.cuda.synchronize()
+    return job, mask.cpu().numpy()
+
+
+def _oracle(obs, nparts):
+    from oracle import framework
+    return framework.setup(obs.uvw, obs.freq, obs.weight, obs.n, obs.cell_rad, obs.n_wplanes, nparts)
+
+
+CASES = [("small", 0, 2), ("small", 1, 2), ("wstack", 0, 2), ("wstack", 1, 2), ("wstack", 0, 4)]
+
+
+def _obs(name, obs_small, obs_wstack):
+    return obs_small if name == "small" else obs_wstack
+
+
+@pytest.mark.parametrize("name,prec,nparts", CASES)
+def test_partition_and_sort_bit_exact(ctx, obs_small, obs_wstack, name, prec, nparts):
+    from oracle import partition
+    from paper_2507_22128_gb300 import rix
+    obs = _obs(name, obs_small, obs_wstack)
+    job, mask = _job(ctx, obs, prec, nparts)
+    try:
+        st = _oracle(obs, nparts)
+        assert np.array_equal(mask, st.mask)
+        s = rix.job_get_stats(job)
+        assert s["n_outside"] == int((~st.geom.inside).sum())
+        for i in range(nparts - 1):
+            assert s["ell_px"][i] == st.ells[i]
+        if obs.n_wplanes:
+            assert s["w_min"] == st.geom.w_min and s["dw"] == st.geom.dw
+        keys, samples, _ = partition.entries(st.geom, st.mask, 16, nparts)
+        sk, ss = partition.sort_entries(keys, samples)
+        assert s["n_entries"] == sk.shape[0]
+        gk = torch.empty(sk.shape[0], dtype=torch.int32, device="cuda")
+        gs = torch.empty(sk.shape[0], dtype=torch.int32, device="cuda")
+        rix.get_sorted_entries(job, gk, gs)
+        torch.cuda.synchronize()
+        assert np.array_equal(gk.cpu().numpy().view(np.uint32), sk)
+        assert np.array_equal(gs.cpu().numpy().view(np.uint32), ss)
+        for p in range(nparts):
+            assert s["part_count"][p] == int(((st.mask >> p) & 1).sum())
+            assert s["part_weight"][p] == pytest.approx(st.wsum[p], rel=1e-12)
+    finally:
+        rix.job_destroy(job)
+
+
+@pytest.mark.parametrize("name,prec,nparts", CASES)
+def test_degrid_matches_oracle_gridder(ctx, obs_small, obs_wstack, name, prec, nparts):
+    from oracle import gridder
+    from paper_2507_22128_gb300 import rix
+    obs = _obs(name, obs_small, obs_wstack)
+    job, _ = _job(ctx, obs, prec, nparts)
+    try:
+        st = _oracle(obs, nparts)
+        x = sparse_model(obs.n, 40, seed=3) + 0.01 * np.random.default_rng(4).normal(size=(obs.n, obs.n))
+        for p in range(nparts):
+            vis = torch.zeros(obs.nvis, dtype=cplx_dtype(prec), device="cuda")
+            rix.degrid(job, p, to_dev(x, real_dtype(prec)), vis)
+            torch.cuda.synchronize()
+            got = vis.cpu().numpy()
+            g = st.gparts[p]
+            want = gridder.degrid(x, g)
+            sel = g.inside
+            assert rel_l2(got[sel], want[sel]) < TOL[prec]
+            assert np.all(got[~sel] == 0)          # samples outside the partition untouched
+    finally:
+        rix.job_destroy(job)
+
+
+@pytest.mark.parametrize("name,prec,nparts", CASES)
+def test_grid_matches_oracle_gridder(ctx, obs_small, obs_wstack, name, prec, nparts):
+    from oracle import gridder
+    from paper_2507_22128_gb300 import rix
+    obs = _obs(name, obs_small, obs_wstack)
+    job, _ = _job(ctx, obs, prec, nparts)
+    try:
+        st = _oracle(obs, nparts)
+        w = obs.weight.reshape(-1).astype(np.float64)
+        for p in range(nparts):
+            img = torch.empty((obs.n, obs.n), dtype=real_dtype(prec), device="cuda")
+            rix.grid(job, p, to_dev(obs.vis.reshape(-1), cplx_dtype(prec)), img)
+            torch.cuda.synchronize()
+            want = gridder.dirty(obs.vis.reshape(-1), w, st.gparts[p])
+            assert rel_l2(img.cpu().numpy(), want) < TOL[prec]
+    finally:
+        rix.job_destroy(job)
+
+
+@pytest.mark.parametrize("name,prec,nparts", CASES[:4])
+def test_psf_matches_oracle(ctx, obs_small, obs_wstack, name, prec, nparts):
+    from paper_2507_22128_gb300 import rix
+    obs = _obs(name, obs_small, obs_wstack)
+    job, _ = _job(ctx, obs, prec, nparts)
+    try:
+        st = _oracle(obs, nparts)
+        for p in range(nparts):
+            out = torch.empty((2 * obs.n, 2 * obs.n), dtype=real_dtype(prec), device="cuda")
+            wsum = rix.psf(job, p, out)
+            torch.cuda.synchronize()
+            assert wsum == pytest.approx(st.wsum[p], rel=1e-12)
+            assert rel_l2(out.cpu().numpy(), st.psf[p]) < TOL[prec]
+    finally:
+        rix.job_destroy(job)
+
+
+@pytest.mark.parametrize("name,prec,nparts", CASES)
+def test_major_cycle_matches_oracle(ctx, obs_small, obs_wstack, name, prec, nparts):
+    from oracle import gridder
+    from paper_2507_22128_gb300 import rix
+    obs = _obs(name, obs_small, obs_wstack)
+    job, _ = _job(ctx, obs, prec, nparts)
+    try:
+        st = _oracle(obs, nparts)
+        w = obs.weight.reshape(-1).astype(np.float64)
+        model = sparse_model(obs.n, 30, seed=5)
+        for p in range(nparts):
+            res = torch.empty((obs.n, obs.n), dtype=real_dtype(prec), device="cuda")
+            rix.major_cycle(job, p, to_dev(obs.vis.reshape(-1), cplx_dtype(prec)),
+                            to_dev(model, real_dtype(prec)), res)
+            torch.cuda.synchronize()
+            want = gridder.residual(obs.vis.reshape(-1), w, model, st.gparts[p])
+            assert rel_l2(res.cpu().numpy(), want) < TOL[prec]
+    finally:
+        rix.job_destroy(job)
+
+
+def test_fp32_operator_vs_direct_dft(ctx, obs_wstack):
+    """FP32 GPU degrid/grid within 1e-4 of the exact measurement operator."""
+    from oracle import dft
+    from paper_2507_22128_gb300 import rix
+    obs = obs_wstack
+    job, mask = _job(ctx, obs, rix.FP32, 2)
+    try:
+        x = sparse_model(obs.n, 25, seed=6)
+        u, v, w = dft.uvw_lambda(obs.uvw, obs.freq)
+        rng = np.random.default_rng(7)
+        sel = np.nonzero((mask & 1) == 1)[0]
+        sub = np.sort(rng.choice(sel, 2000, replace=False))
+        vis = torch.zeros(obs.nvis, dtype=torch.complex64, device="cuda")
+        rix.degrid(job, 0, to_dev(x, torch.float32), vis)
+        torch.cuda.synchronize()
+        want = dft.degrid_pixels_sparse(x, u[sub], v[sub], w[sub], obs.cell_rad, True)
+        assert rel_l2(vis.cpu().numpy()[sub], want) < 1e-4
+        # grid: sampled pixels of the dirty image of partition 0
+        img = torch.empty((obs.n, obs.n), dtype=torch.float32, device="cuda")
+        rix.grid(job, 0, to_dev(obs.vis.reshape(-1), torch.complex64), img)
+        torch.cuda.synchronize()
+        rows = rng.integers(0, obs.n, 64)
+        cols = rng.integers(0, obs.n, 64)
+        wt = np.where((mask & 1) == 1, obs.weight.reshape(-1), 0.0)
+        want = dft.adjoint_at(wt * obs.vis.reshape(-1), u, v, w, obs.n, obs.cell_rad, True, rows, cols) / wt.sum()
+        assert rel_l2(img.cpu().numpy()[rows, cols], want) < 1e-4
+    finally:
+        rix.job_destroy(job)
