@@ -1,0 +1,386 @@
+#!/usr/bin/env python
+"""Throughput benchmark of the decentralized reconstruction path on GB300.
+
+A step is one whole reconstruction job of the medium workload (1024 x 1024,
+1" cells, 64 antennas x 1000 times x 4 channels = 8.06 M visibilities, 16
+w-planes, 2 uv partitions, FISTA with Db4, lambda = 1e-3 max|dirty|, 50
+iterations, 10 major cycles, FP32): partition + sort (a1-a3), PSF (a7), ten
+major cycles of both partitions (a4-a6), the fill and FISTA minor cycles
+(a8, a10) and the combine (a11).  The metric is grid+degrid Mvis/s: the
+visibility samples the major cycles processed (overlap counted in each
+partition, ten cycles) per second of step time.  Inputs are resident in HBM
+for `value`; `e2e` adds the host->device copy of the inputs from pinned
+memory and the device->host read of the final image.
+
+Multi-GPU: independent replicas (one job per rank, no collective).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+import torch  # noqa: E402
+
+METRIC = "grid+degrid Mvis/s"
+UNIT = "Mvis/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n-times", type=int, default=1000, help="time samples (1000 = the full workload)")
+    ap.add_argument("--n", type=int, default=1024)
+    ap.add_argument("--cycles", type=int, default=10)
+    ap.add_argument("--iters", type=int, default=50)
+    ap.add_argument("--fp64", action="store_true", help="FP64 operator (comparator)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--json-out", default=None)
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", str(rank)))
+    return rank, world, local
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def flush_l2(buf):
+    buf.add_(1.0)   # a write of 512 MiB, larger than the 129 MB L2
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+# --------------------------------------------------------------------------
+def reference_arm(a, rank, world):
+    """The oracle as it stands, on the host cores, on a bounded sample of the
+    same workload (one major cycle of one partition over a row subset)."""
+    if rank != 0:
+        return 0
+    res = cpu_baseline(a, a.steps, a.warmup)
+    line = {"impl": "reference", "metric": METRIC, "value": res["value"], "unit": UNIT, "n_gpus": a.gpus,
+            "steps": a.steps, "warmup": a.warmup, "ms_per_step": res["ms_per_step"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": config_dict(a),
+            "cpu_baseline": {"value": res["value"], "unit": UNIT, "cores": res["cores"], "kind": "oracle",
+                             "sample": res["sample"]},
+            "e2e": {"value": res["value"], "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def cpu_baseline(a, steps=1, warmup=0):
+    """FP64 oracle major cycle (degrid + residual + grid, Eq. 2) of partition 0
+    on a 1/64 row subset of the workload; Mvis/s = samples / seconds."""
+    from oracle import gridder, partition
+    from paper_2507_22128_gb300 import synth
+    obs = synth.medium(seed=1, n_times=max(4, a.n_times // 64), n=a.n)
+    g = gridder.geometry(obs.uvw, obs.freq, obs.n, obs.cell_rad, W=8, nw=obs.n_wplanes)
+    r = partition.radius_px(g)
+    m = partition.masks(r, partition.ring_radii(r, 2), 1.0, 2, g.inside)
+    gp = gridder.subset(g, (m & 1) == 1)
+    w = obs.weight.reshape(-1).astype(np.float64)
+    model = np.zeros((obs.n, obs.n))
+    nsamp = int(gp.inside.sum())
+    times = []
+    for i in range(warmup + steps):
+        t0 = time.perf_counter()
+        gridder.residual(obs.vis.reshape(-1), w, model, gp)
+        dt = time.perf_counter() - t0
+        if i >= warmup:
+            times.append(dt)
+    t = statistics.median(times)
+    return {"value": nsamp / t / 1e6, "ms_per_step": t * 1e3, "cores": 1,
+            "sample": f"one FP64 major cycle of partition 0 over {obs.nrow} rows x {obs.nchan} channels "
+                      f"({nsamp} samples; 1/64 of the {a.n}^2 workload's rows), numpy, median of {steps}"}
+
+
+def config_dict(a):
+    return {"workload": f"medium: {a.n}x{a.n} 1as, 64 ant log-spiral x {a.n_times} times x 4 ch "
+                        f"(1.3-1.5 GHz), 16 w-planes, 2 uv partitions, FISTA Db4 {a.iters} it, "
+                        f"{a.cycles} major cycles",
+            "n": a.n, "n_wplanes": 16, "n_part": 2, "major_cycles": a.cycles, "fista_iters": a.iters,
+            "l2": "flushed between steps (512 MiB write)", "precision": "fp64" if a.fp64 else "fp32"}
+
+
+def main():
+    a = parse()
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if a.impl == "ours" else "gloo")
+    if a.impl == "reference":
+        return reference_arm(a, rank, world)
+
+    from paper_2507_22128_gb300 import pipeline, rix, synth
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    obs = synth.medium(seed=1 + rank, n_times=a.n_times, n=a.n)
+    prec = rix.FP64 if a.fp64 else rix.FP32
+    cdt = torch.complex128 if a.fp64 else torch.complex64
+    rdt = torch.float64 if a.fp64 else torch.float32
+    uvw_h = torch.from_numpy(obs.uvw).pin_memory()
+    vis_h = torch.from_numpy(obs.vis.astype(np.complex128 if a.fp64 else np.complex64)).pin_memory()
+    w_h = torch.from_numpy(obs.weight).pin_memory()
+    uvw_d = uvw_h.to(dev)
+    vis_d = vis_h.to(dev)
+    w_d = w_h.to(dev)
+    img_h = torch.empty((obs.n, obs.n), dtype=rdt).pin_memory()
+    ctx = rix.create(local)
+    rec = pipeline.Reconstruction(ctx, obs.n, obs.cell_rad, obs.n_wplanes, obs.freq, obs.nrow, 2, prec)
+    meth = pipeline.Method("fista", lam_rel=1e-3, iters=a.iters, levels=4)
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(128 * 1024 * 1024, dtype=torch.float32, device=dev)
+    out = torch.empty((obs.n, obs.n), dtype=rdt, device=dev)
+
+    def one_job(uvw, vis, w):
+        rec.uvw, rec.vis, rec.weight = uvw, vis, w
+        rix.set_uv_partition(rec.job, uvw, w, None, 1.0, None, stream)
+        for _ in range(a.cycles):
+            rec.cycle(meth, stream)
+        rix.combine(rec.job, out, stream)
+
+    for _ in range(a.warmup):
+        one_job(uvw_d, vis_d, w_d)
+    torch.cuda.synchronize()
+    st = rix.job_get_stats(rec.job)
+    units = a.cycles * sum(st["part_count"][:2])
+
+    # ---- timed steps: device-resident inputs ----
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(a.steps)]
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        for i in range(a.steps):
+            flush_l2(flush)
+            ev[i][0].record(stream)
+            one_job(uvw_d, vis_d, w_d)
+            ev[i][1].record(stream)
+        torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    step_ms = [s.elapsed_time(e) for s, e in ev]
+    total_ms = sum(step_ms)
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms = total_ms / a.steps
+    value = units * world / (ms * 1e-3) / 1e6
+
+    # ---- per-phase split of one job (diagnostic) ----
+    phases = phase_split(rec, rix, a, meth, stream, uvw_d, vis_d, w_d, out, flush)
+
+    # ---- end to end through the public API with host buffers ----
+    e2e = None
+    if not a.no_e2e:
+        ts = []
+        for i in range(max(2, min(a.steps, 3))):
+            flush_l2(flush)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            uvw_x = uvw_h.to(dev, non_blocking=True)
+            vis_x = vis_h.to(dev, non_blocking=True)
+            w_x = w_h.to(dev, non_blocking=True)
+            one_job(uvw_x, vis_x, w_x)
+            img_h.copy_(out, non_blocking=True)
+            torch.cuda.synchronize()
+            ts.append(time.perf_counter() - t0)
+        t = statistics.median(ts)
+        e2e = {"value": units / t / 1e6, "unit": UNIT,
+               "h2d_bytes_per_step": int(uvw_h.numel() * 8 + vis_h.numel() * vis_h.element_size() + w_h.numel() * 4),
+               "d2h_bytes_per_step": int(img_h.numel() * img_h.element_size())}
+
+    launches, top = count_launches(one_job, uvw_d, vis_d, w_d)
+    roof = roofline(top, obs, st, a)
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
+            "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64" if a.fp64 else "f32", "data": "synthetic",
+            "config": config_dict(a), "clocks": clk.summary(), "e2e": e2e, "gpu_launches": launches,
+            "roofline": roof, "phases_ms": phases,
+            "samples_per_cycle": int(sum(st["part_count"][:2])), "step_ms": step_ms}
+    if rank == 0 and not a.no_cpu_baseline:
+        cb = cpu_baseline(a)
+        line["cpu_baseline"] = {"value": cb["value"], "unit": UNIT, "cores": cb["cores"], "kind": "oracle",
+                                "sample": cb["sample"]}
+    rec.close()
+    rix.destroy(ctx)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+        if a.json_out:
+            with open(a.json_out, "w") as f:
+                json.dump(line, f, indent=1)
+    return 0
+
+
+def phase_split(rec, rix, a, meth, stream, uvw, vis, w, out, flush):
+    """Event-timed phases of one job: partition, major cycles, minor cycles."""
+    def ev():
+        e = torch.cuda.Event(enable_timing=True)
+        e.record(stream)
+        return e
+    flush_l2(flush)
+    e0 = ev()
+    rix.set_uv_partition(rec.job, uvw, w, None, 1.0, None, stream)
+    e1 = ev()
+    maj, mnr = 0.0, 0.0
+    for c in range(a.cycles):
+        s0 = ev()
+        for p in range(2):
+            rix.major_cycle(rec.job, p, vis, None, None, stream)
+        s1 = ev()
+        for p in range(2):
+            rec.minor(p, meth, stream=stream)
+        s2 = ev()
+        torch.cuda.synchronize()
+        maj += s0.elapsed_time(s1)
+        mnr += s1.elapsed_time(s2)
+    rix.combine(rec.job, out, stream)
+    torch.cuda.synchronize()
+    return {"partition_sort": e0.elapsed_time(e1), "major_cycles": maj, "minor_cycles_incl_psf": mnr}
+
+
+def count_launches(one_job, uvw, vis, w):
+    """Kernel launches of one job, and per-kernel device time, from the CUDA
+    activity trace (torch.profiler)."""
+    try:
+        from torch.profiler import ProfilerActivity, profile
+        with profile(activities=[ProfilerActivity.CUDA]) as prof:
+            one_job(uvw, vis, w)
+            torch.cuda.synchronize()
+        n = 0
+        per = {}
+        for e in prof.events():
+            if e.device_type.name == "CUDA" and "rix" in e.name and "k_" in e.name:
+                n += 1
+                key = e.name.split("(")[0]
+                t, c = per.get(key, (0.0, 0))
+                per[key] = (t + e.device_time, c + 1)
+        return n, per
+    except Exception as exc:   # profiler unavailable
+        return None, {"error": str(exc)}
+
+
+def roofline(per, obs, st, a):
+    """Roofline of the dominant kernel: algorithmic bytes or flops per launch
+    over its mean device time in one job."""
+    peaks, kind = measured_peaks()
+    if not per or "error" in per:
+        return None
+    name, (t_us, cnt) = max(per.items(), key=lambda kv: kv[1][0])
+    avg_s = t_us * 1e-6 / cnt
+    entries = sum(st["part_count"][:2])
+    if "k_tiles" in name:
+        # FP32 flops per entry: degrid 512 taps x 2 FMA (4 flops), grid 512 taps x
+        # (2 mul + 2 add) -> 4096; launches: one per partition per major cycle
+        flops = 4096.0 * entries / 2
+        sm = 152
+        clk = peaks.get("sm_max_mhz", 2070.0)
+        peak = sm * 128 * 2 * clk * 1e6 / 1e12
+        ach = flops / avg_s / 1e12
+        return {"bound": "alu", "kernel": name, "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                "frac": ach / peak, "traffic": None,
+                "peak_source": f"152 SMs x 128 FP32 lanes x 2 x {clk:.0f} MHz"}
+    # FFT / elementwise kernels are bounded by HBM: algorithmic bytes are each
+    # launch's compulsory reads + writes
+    bytes_per_launch = algorithmic_bytes(name, obs)
+    if bytes_per_launch is None:
+        return {"bound": "hbm", "kernel": name, "achieved": None, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": None, "traffic": None, "peak_source": kind}
+    ach = bytes_per_launch / avg_s / 1e9
+    return {"bound": "hbm", "kernel": name, "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+            "frac": ach / peaks["hbm_gbs"], "traffic": None, "peak_source": kind}
+
+
+def algorithmic_bytes(name, obs):
+    n = obs.n
+    c8 = 8
+    if "k_conv_cols" in name:        # read [2N][N] complex, write [2N][N] complex, tables (2N)^2 (4 + 8 B)
+        return 2 * (2 * n * n * c8) + 4 * n * n * 12
+    if "k_fwd_rows" in name:         # read N^2 real, write [2N][N] complex
+        return n * n * 4 + 2 * n * n * c8
+    if "k_inv_rows" in name:         # read [2N][N] complex, write N^2 real
+        return 2 * n * n * c8 + n * n * 4
+    return None
+
+
+if __name__ == "__main__":
+    sys.exit(main())

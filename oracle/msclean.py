@@ -49,6 +49,7 @@ class Result:
     components: list          # (scale index, row, col, amplitude)
     residuals: np.ndarray     # final R_s
     iterations: int
+    gaps: list = dataclasses.field(default_factory=list)   # (best, runner-up) per iteration
 
 
 def clean(dirty_spec: np.ndarray, psf_spec: np.ndarray, scales, gain: float, niter: int,
@@ -67,27 +68,35 @@ def clean(dirty_spec: np.ndarray, psf_spec: np.ndarray, scales, gain: float, nit
     b = bias(scales)
     model = np.zeros((n, n))
     comps = []
+    gaps = []
     it = 0
     while it < niter:
         if np.abs(R[0]).max() < threshold:
             break
         best, bs_i, bp = -1.0, -1, -1
+        second = -1.0
         for s in range(ns):
             if not allowed[s]:
                 continue
             v = (b[s] * np.abs(R[s]) / peak[s]).reshape(-1)
             p = int(np.argmax(v))
+            # runner-up over all candidates (for near-tie diagnostics only)
+            top2 = np.partition(v, -2)[-2:] if v.size > 1 else np.array([-1.0, v[0]])
             if v[p] > best:
+                second = max(best, float(top2[0]))
                 best, bs_i, bp = float(v[p]), s, p
+            else:
+                second = max(second, float(v[p]))
         py, px = divmod(bp, n)
         a = gain * R[bs_i, py, px] / peak[bs_i]
         comps.append((bs_i, py, px, float(a)))
+        gaps.append((best, second))
         # every pixel offset from p* lies in (-N, N): index the 2N-grid arrays
         model += a * bk[bs_i][n - py:2 * n - py, n - px:2 * n - px]
         for s in range(ns):
             R[s] -= a * P[s, bs_i, n - py:2 * n - py, n - px:2 * n - px]
         it += 1
-    return Result(model, comps, R, it)
+    return Result(model, comps, R, it, gaps)
 
 
 def allowed_scales(scales, n: int, p: int, cycle: int, ells, delta: float) -> np.ndarray:

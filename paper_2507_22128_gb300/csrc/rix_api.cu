@@ -31,8 +31,9 @@ int set_error(int code, const char* fmt, ...) {
 const char* last_error() { return g_err; }
 
 int DevBuf::alloc(Ctx* ctx, size_t nbytes) {
-  release();
   if (nbytes == 0) nbytes = 16;
+  if (p && bytes >= nbytes) return RIX_OK;   // reuse: re-partitioning a job keeps its buffers
+  release();
   void* q = nullptr;
   cudaError_t e = cudaMalloc(&q, nbytes);
   if (e != cudaSuccess) {
@@ -97,17 +98,16 @@ static int check_part(Job* job, int part) {
   return RIX_OK;
 }
 
-static int ensure_images(Job* job, Part& pt) {
+static int ensure_images(Job* job, Part& pt, cudaStream_t st) {
   const size_t img = (size_t)job->desc.n * job->desc.n * (job->fp64 ? 8 : 4);
-  if (pt.model.bytes < img) {
-    RIX_TRY(pt.model.alloc(job->ctx, img));
-    RIX_CUDA(cudaMemset(pt.model.p, 0, img));
-  }
-  if (pt.resid.bytes < img) RIX_TRY(pt.resid.alloc(job->ctx, img));
-  if (pt.delta.bytes < img) RIX_TRY(pt.delta.alloc(job->ctx, img));
+  RIX_TRY(pt.model.alloc(job->ctx, img));
+  RIX_CUDA(cudaMemsetAsync(pt.model.p, 0, img, st));
+  RIX_TRY(pt.resid.alloc(job->ctx, img));
+  RIX_TRY(pt.delta.alloc(job->ctx, img));
   return RIX_OK;
 }
 
+// a new partitioning restarts every partition at cycle 0 (buffers are kept)
 static void reset_partitions(Job* job) {
   for (int p = 0; p < kMaxPart; ++p) {
     Part& pt = job->part[p];
@@ -115,15 +115,7 @@ static void reset_partitions(Job* job) {
     pt.minor_done = 0;
     pt.psf_ready = false;
     pt.lambda_set = false;
-    pt.model.release();
-    pt.resid.release();
-    pt.delta.release();
-    pt.outbox[0].release();
-    pt.outbox[1].release();
-    for (int q = 0; q < kMaxPart; ++q) pt.rho[q].release();
-    pt.ms_R.release(); pt.ms_P.release(); pt.ms_comp.release(); pt.ms_state.release();
-    pt.fi_alpha.release(); pt.fi_alpha_prev.release(); pt.fi_y.release();
-    pt.fi_mx.release(); pt.fi_c.release(); pt.fi_x.release();
+    pt.ms_ncomp_cap = 0;
   }
 }
 
@@ -259,7 +251,7 @@ int rix_set_uv_partition(rix_job_t job, const double* uvw_m, int64_t nrow, const
   else RIX_TRY(grid_build_corrections<float>(&J, st));
   if (J.fp64) RIX_TRY(fill_init<double>(&J, st));
   else RIX_TRY(fill_init<float>(&J, st));
-  for (int p = 0; p < J.n_part; ++p) RIX_TRY(ensure_images(&J, J.part[p]));
+  for (int p = 0; p < J.n_part; ++p) RIX_TRY(ensure_images(&J, J.part[p], st));
   J.partitioned = true;
   return RIX_OK;
 }
