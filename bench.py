@@ -48,6 +48,7 @@ def parse():
     ap.add_argument("--fp64", action="store_true", help="FP64 operator (comparator)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-phases", action="store_true")
     ap.add_argument("--json-out", default=None)
     return ap.parse_args()
 
@@ -228,6 +229,10 @@ def main():
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
+    rix.timing_read(rix.TIME_TILES)
+    rix.timing_read(rix.TIME_FFT)
+    rix.timing_enable(True)
+    launches0 = rix.kernel_launches()
     with ClockSampler(local) as clk:
         for i in range(a.steps):
             flush_l2(flush)
@@ -235,6 +240,10 @@ def main():
             one_job(uvw_d, vis_d, w_d)
             ev[i][1].record(stream)
         torch.cuda.synchronize()
+    launches = rix.kernel_launches() - launches0
+    rix.timing_enable(False)
+    tiles_ms, tiles_n = rix.timing_read(rix.TIME_TILES)
+    fft_ms, fft_n = rix.timing_read(rix.TIME_FFT)
     if world > 1:
         torch.distributed.barrier()
     step_ms = [s.elapsed_time(e) for s, e in ev]
@@ -247,7 +256,7 @@ def main():
     value = units * world / (ms * 1e-3) / 1e6
 
     # ---- per-phase split of one job (diagnostic) ----
-    phases = phase_split(rec, rix, a, meth, stream, uvw_d, vis_d, w_d, out, flush)
+    phases = None if a.no_phases else phase_split(rec, rix, a, meth, stream, uvw_d, vis_d, w_d, out, flush)
 
     # ---- end to end through the public API with host buffers ----
     e2e = None
@@ -269,13 +278,16 @@ def main():
                "h2d_bytes_per_step": int(uvw_h.numel() * 8 + vis_h.numel() * vis_h.element_size() + w_h.numel() * 4),
                "d2h_bytes_per_step": int(img_h.numel() * img_h.element_size())}
 
-    launches, top = count_launches(one_job, uvw_d, vis_d, w_d)
-    roof = roofline(top, obs, st, a)
+    # the gridder runs once per partition per major cycle and once per
+    # partition for the PSF; the PSF launches carry (weights only) a fraction
+    # of the work, so the flop count below is a lower bound of the work timed
+    roof = roofline_tiles(tiles_ms, tiles_n, st, a, units * a.steps)
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
             "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64" if a.fp64 else "f32", "data": "synthetic",
-            "config": config_dict(a), "clocks": clk.summary(), "e2e": e2e, "gpu_launches": launches,
+            "config": config_dict(a), "clocks": clk.summary(), "e2e": e2e, "gpu_launches": int(launches),
             "roofline": roof, "phases_ms": phases,
+            "kernel_ms_per_step": {"grid_tiles": tiles_ms / a.steps, "fft_passes_outside_graphs": fft_ms / a.steps},
             "samples_per_cycle": int(sum(st["part_count"][:2])), "step_ms": step_ms}
     if rank == 0 and not a.no_cpu_baseline:
         cb = cpu_baseline(a)
@@ -318,68 +330,26 @@ def phase_split(rec, rix, a, meth, stream, uvw, vis, w, out, flush):
     return {"partition_sort": e0.elapsed_time(e1), "major_cycles": maj, "minor_cycles_incl_psf": mnr}
 
 
-def count_launches(one_job, uvw, vis, w):
-    """Kernel launches of one job, and per-kernel device time, from the CUDA
-    activity trace (torch.profiler)."""
-    try:
-        from torch.profiler import ProfilerActivity, profile
-        with profile(activities=[ProfilerActivity.CUDA]) as prof:
-            one_job(uvw, vis, w)
-            torch.cuda.synchronize()
-        n = 0
-        per = {}
-        for e in prof.events():
-            if e.device_type.name == "CUDA" and "rix" in e.name and "k_" in e.name:
-                n += 1
-                key = e.name.split("(")[0]
-                t, c = per.get(key, (0.0, 0))
-                per[key] = (t + e.device_time, c + 1)
-        return n, per
-    except Exception as exc:   # profiler unavailable
-        return None, {"error": str(exc)}
-
-
-def roofline(per, obs, st, a):
-    """Roofline of the dominant kernel: algorithmic bytes or flops per launch
-    over its mean device time in one job."""
-    peaks, kind = measured_peaks()
-    if not per or "error" in per:
+def roofline_tiles(tiles_ms, tiles_n, st, a, entries_timed):
+    """Roofline of the tiled degrid/residual/grid kernel, the gridder of the
+    major cycle: FP32 (or FP64) arithmetic over its event-timed launches.
+    Algorithmic work per (sample, partition) entry and major cycle: degrid
+    8 x 64 taps x 2 FMA (2048 flops) + grid 8 x 64 taps x (2 mul + 2 add)
+    (2048 flops) = 4096 flops; the PSF launches (weights only) are counted
+    at zero, so `achieved` is a lower bound."""
+    if not tiles_n or tiles_ms <= 0:
         return None
-    name, (t_us, cnt) = max(per.items(), key=lambda kv: kv[1][0])
-    avg_s = t_us * 1e-6 / cnt
-    entries = sum(st["part_count"][:2])
-    if "k_tiles" in name:
-        # FP32 flops per entry: degrid 512 taps x 2 FMA (4 flops), grid 512 taps x
-        # (2 mul + 2 add) -> 4096; launches: one per partition per major cycle
-        flops = 4096.0 * entries / 2
-        sm = 152
-        clk = peaks.get("sm_max_mhz", 2070.0)
-        peak = sm * 128 * 2 * clk * 1e6 / 1e12
-        ach = flops / avg_s / 1e12
-        return {"bound": "alu", "kernel": name, "achieved": ach, "peak": peak, "unit": "TFLOP/s",
-                "frac": ach / peak, "traffic": None,
-                "peak_source": f"152 SMs x 128 FP32 lanes x 2 x {clk:.0f} MHz"}
-    # FFT / elementwise kernels are bounded by HBM: algorithmic bytes are each
-    # launch's compulsory reads + writes
-    bytes_per_launch = algorithmic_bytes(name, obs)
-    if bytes_per_launch is None:
-        return {"bound": "hbm", "kernel": name, "achieved": None, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                "frac": None, "traffic": None, "peak_source": kind}
-    ach = bytes_per_launch / avg_s / 1e9
-    return {"bound": "hbm", "kernel": name, "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-            "frac": ach / peaks["hbm_gbs"], "traffic": None, "peak_source": kind}
-
-
-def algorithmic_bytes(name, obs):
-    n = obs.n
-    c8 = 8
-    if "k_conv_cols" in name:        # read [2N][N] complex, write [2N][N] complex, tables (2N)^2 (4 + 8 B)
-        return 2 * (2 * n * n * c8) + 4 * n * n * 12
-    if "k_fwd_rows" in name:         # read N^2 real, write [2N][N] complex
-        return n * n * 4 + 2 * n * n * c8
-    if "k_inv_rows" in name:         # read [2N][N] complex, write N^2 real
-        return 2 * n * n * c8 + n * n * 4
-    return None
+    peaks, kind = measured_peaks()
+    clk = float(peaks.get("sm_max_mhz", 2070.0))
+    lanes = 2 if a.fp64 else 128        # FP64 / FP32 results per SM per clock (GB300 unit counts)
+    peak = 152 * lanes * 2 * clk * 1e6 / 1e12
+    flops = 4096.0 * entries_timed
+    ach = flops / (tiles_ms * 1e-3) / 1e12
+    return {"bound": "alu", "kernel": "k_tiles (degrid + residual + grid, w-stacked, T=16)",
+            "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+            "traffic": None, "launches_timed": tiles_n, "avg_launch_ms": tiles_ms / tiles_n,
+            "peak_source": f"152 SMs x {lanes} {'FP64' if a.fp64 else 'FP32'} lanes x 2 flop x {clk:.0f} MHz "
+                           f"(max SM clock of {kind} peaks)"}
 
 
 if __name__ == "__main__":

@@ -237,6 +237,24 @@ int rix_combine(rix_job_t job, void* image_out, rix_stream_t stream);
 /* Thread-local message of the last failed call on this thread. */
 const char* rix_last_error(void);
 
+/* Number of CUDA kernels the library has run in this process, over all jobs
+ * and host threads, counting each kernel node of a replayed CUDA graph (a
+ * diagnostic: the difference across a call sequence is that sequence's
+ * kernel count). */
+uint64_t rix_kernel_launches(void);
+
+/* Opt-in device timing (a diagnostic for benchmarks): while enabled, the
+ * library records CUDA events on the launch stream around every launch of
+ * the kernel classes below (launches inside stream captures are not timed).
+ * rix_timing_read waits for the recorded events, returns the summed device
+ * time (ms) and the number of launches of one class, and clears them.
+ * Classes: 0 = tiled degrid/grid kernel, 1 = FFT passes, 2 = partition. */
+#define RIX_TIME_TILES 0
+#define RIX_TIME_FFT 1
+#define RIX_TIME_PARTITION 2
+int rix_timing_enable(int on);
+int rix_timing_read(int kernel_class, double* total_ms, int64_t* launches);
+
 #ifdef __cplusplus
 }
 #endif

@@ -539,6 +539,7 @@ int check_geom(const XformGeom& g) {
 // number of rows (or columns) to transform, `nz` the grid's y extent.
 #define RIX_FFT_LAUNCH(KERNEL, units, nz, ...)                                                   \
   do {                                                                                           \
+    timing_mark(kTimeFft, st, true);                                                             \
     if (use_inplace<R>(g.L)) {                                                                   \
       constexpr int V = Vpt<R>::kLarge;                                                          \
       const int B = batch_for<R>(ctx, V, g.L, (units), (nz));                                    \
@@ -553,6 +554,8 @@ int check_geom(const XformGeom& g) {
       RIX_TRY(set_smem(KERNEL<R, 0>, sm));                                                       \
       KERNEL<R, 0><<<dim3((unsigned)ceil_div((units), B), (nz)), kFftThreads, sm, st>>>(a, __VA_ARGS__); \
     }                                                                                            \
+    ::rix::note_launch();                                                                        \
+    timing_mark(kTimeFft, st, false);                                                            \
     RIX_LAUNCH_CHECK();                                                                          \
   } while (0)
 

@@ -74,60 +74,101 @@ struct EsFourier {
   }
 };
 
-// Per-pixel correction 1 / (Phi(a'/Ng) Phi(b'/Ng) [n Phi(dw (n-1))]) and n - 1
-// of an M x M image on an Ng grid.  The w-term depends on r^2 only; it is
-// evaluated once per distinct (|a'|, |b'|) pair.
-void build_correction(int M, int ng, double cell, bool wstack, double dw, std::vector<double>& corr,
-                      std::vector<double>& nm1) {
-  static const EsFourier phi;
-  const int h = M / 2;
-  std::vector<double> p1(M);
-  for (int a = 0; a < M; ++a) p1[a] = phi((double)(a - h) / ng);
-  corr.assign((size_t)M * M, 0.0);
-  if (wstack) nm1.assign((size_t)M * M, 0.0);
-  std::vector<double> wcorr;
-  std::vector<double> wnm1;
-  if (wstack) {
-    // index by (|a'|, |b'|) with |a'|, |b'| <= h
-    wcorr.assign((size_t)(h + 1) * (h + 1), 0.0);
-    wnm1.assign((size_t)(h + 1) * (h + 1), 0.0);
-    for (int i = 0; i <= h; ++i)
-      for (int j = i; j <= h; ++j) {
-        const double l = i * cell, m = j * cell;
-        const double r2 = l * l + m * m;
-        const double n = std::sqrt(1.0 - r2);
-        const double d = -r2 / (1.0 + n);
-        const double c = 1.0 / (n * phi(dw * d));
-        wcorr[(size_t)i * (h + 1) + j] = wcorr[(size_t)j * (h + 1) + i] = c;
-        wnm1[(size_t)i * (h + 1) + j] = wnm1[(size_t)j * (h + 1) + i] = d;
-      }
+// Chebyshev coefficients of Phi on [lo, hi] (degree kCheb - 1): Phi is entire
+// and |pi W f| <= 2 pi over the w-correction's range, so 40 terms reach
+// double precision.
+constexpr int kCheb = 40;
+void chebyshev_fit(const EsFourier& phi, double lo, double hi, double* c) {
+  const double mid = 0.5 * (lo + hi), half = 0.5 * (hi - lo);
+  double f[kCheb];
+  for (int k = 0; k < kCheb; ++k) f[k] = phi(mid + half * std::cos(M_PI * (k + 0.5) / kCheb));
+  for (int j = 0; j < kCheb; ++j) {
+    double acc = 0.0;
+    for (int k = 0; k < kCheb; ++k) acc += f[k] * std::cos(M_PI * j * (k + 0.5) / kCheb);
+    c[j] = 2.0 * acc / kCheb;
   }
-  for (int b = 0; b < M; ++b)
-    for (int a = 0; a < M; ++a) {
-      double c = 1.0 / (p1[a] * p1[b]);
-      if (wstack) {
-        const size_t k = (size_t)std::abs(a - h) * (h + 1) + std::abs(b - h);
-        // offsets of exactly -h appear once; |.| <= h covers them
-        c *= wcorr[k];
-        nm1[(size_t)b * M + a] = wnm1[k];
+  c[0] *= 0.5;
+}
+
+struct CorrArgs {
+  int M;
+  double cell;
+  const double* p1;     // Phi((a - M/2) / Ng), [M]
+  int wstack;
+  double dw, lo, hi;    // Chebyshev interval of dw (n - 1)
+  double cheb[kCheb];
+};
+
+// corr[b][a] = 1 / (Phi(a'/Ng) Phi(b'/Ng) [n Phi(dw (n-1))]),  nm1[b][a] = n - 1
+template <typename R>
+__global__ void k_corrections(CorrArgs a, R* __restrict__ corr, double* __restrict__ nm1) {
+  const int64_t tot = (int64_t)a.M * a.M;
+  const int h = a.M / 2;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < tot; i += (int64_t)gridDim.x * blockDim.x) {
+    const int b = (int)(i / a.M), c = (int)(i - (int64_t)b * a.M);
+    double v = 1.0 / (a.p1[c] * a.p1[b]);
+    if (a.wstack) {
+      const double l = (double)(c - h) * a.cell, m = (double)(b - h) * a.cell;
+      const double r2 = __dadd_rn(__dmul_rn(l, l), __dmul_rn(m, m));
+      const double n = __dsqrt_rn(1.0 - r2);
+      const double d = -r2 / (1.0 + n);
+      double phw;
+      if (a.hi > a.lo) {
+        // Clenshaw recurrence for sum_j c_j T_j(x)
+        const double x = (2.0 * a.dw * d - (a.lo + a.hi)) / (a.hi - a.lo);
+        double b1 = 0.0, b2 = 0.0;
+        for (int j = kCheb - 1; j >= 1; --j) {
+          const double t = 2.0 * x * b1 - b2 + a.cheb[j];
+          b2 = b1;
+          b1 = t;
+        }
+        phw = x * b1 - b2 + a.cheb[0];
+      } else {
+        phw = a.cheb[0];
       }
-      corr[(size_t)b * M + a] = c;
+      v /= n * phw;
+      nm1[i] = d;
     }
+    corr[i] = (R)v;
+  }
 }
 
 template <typename R>
-int upload_real(Job* job, DevBuf& dst, const std::vector<double>& src, cudaStream_t st) {
-  std::vector<R> tmp(src.begin(), src.end());
-  RIX_TRY(dst.alloc(job->ctx, tmp.size() * sizeof(R)));
-  RIX_CUDA(cudaMemcpyAsync(dst.p, tmp.data(), tmp.size() * sizeof(R), cudaMemcpyHostToDevice, st));
-  RIX_CUDA(cudaStreamSynchronize(st));
-  return RIX_OK;
-}
-
-int upload_double(Job* job, DevBuf& dst, const std::vector<double>& src, cudaStream_t st) {
-  RIX_TRY(dst.alloc(job->ctx, src.size() * sizeof(double)));
-  RIX_CUDA(cudaMemcpyAsync(dst.p, src.data(), src.size() * sizeof(double), cudaMemcpyHostToDevice, st));
-  RIX_CUDA(cudaStreamSynchronize(st));
+int build_correction(Job* job, int M, int ng, DevBuf& corr, DevBuf& nm1, cudaStream_t st) {
+  static const EsFourier phi;
+  const bool ws = job->nw > 0;
+  const double cell = job->desc.cell_rad, dw = job->stats.dw;
+  std::vector<double> p1(M);
+  for (int a = 0; a < M; ++a) p1[a] = phi((double)(a - M / 2) / ng);
+  CorrArgs ca{};
+  ca.M = M;
+  ca.cell = cell;
+  ca.wstack = ws;
+  ca.dw = dw;
+  if (ws) {
+    // the most negative dw (n - 1) is at the image corner
+    const double l = (double)(-M / 2) * cell;
+    const double r2 = 2.0 * l * l;
+    const double n = std::sqrt(1.0 - r2);
+    const double dmin = dw * (-r2 / (1.0 + n));
+    ca.lo = std::min(dmin, 0.0) * (1.0 + 1e-12);
+    ca.hi = 0.0;
+    if (ca.hi > ca.lo) chebyshev_fit(phi, ca.lo, ca.hi, ca.cheb);
+    else ca.cheb[0] = phi(0.0);
+    job->stats.max_dw_nm1 = std::max(job->stats.max_dw_nm1, std::fabs(dmin));
+  }
+  RIX_TRY(corr.alloc(job->ctx, (size_t)M * M * sizeof(R)));
+  if (ws) RIX_TRY(nm1.alloc(job->ctx, (size_t)M * M * sizeof(double)));
+  double* p1d = nullptr;
+  RIX_CUDA(cudaMallocAsync((void**)&p1d, M * sizeof(double), st));
+  RIX_CUDA(cudaMemcpyAsync(p1d, p1.data(), M * sizeof(double), cudaMemcpyHostToDevice, st));
+  ca.p1 = p1d;
+  const int64_t tot = (int64_t)M * M;
+  const int blocks = (int)std::min<int64_t>(ceil_div(tot, 256), (int64_t)job->ctx->num_sms * 16);
+  ::rix::note_launch(); k_corrections<R><<<blocks, 256, 0, st>>>(ca, corr.as<R>(), ws ? nm1.as<double>() : nullptr);
+  cudaFreeAsync(p1d, st);
+  RIX_LAUNCH_CHECK();
+  RIX_CUDA(cudaStreamSynchronize(st));   // p1 is a host temporary
   return RIX_OK;
 }
 
@@ -370,7 +411,9 @@ int launch_tiles_impl(const Ctx* ctx, const TileArgs& a, cudaStream_t st) {
   per_sm = std::max(per_sm, 1);
   const int64_t blocks = std::min<int64_t>(a.item_count, (int64_t)ctx->num_sms * per_sm);
   if (blocks <= 0) return RIX_OK;
-  kern<<<(unsigned)blocks, 256, sm, st>>>(a);
+  timing_mark(kTimeTiles, st, true);
+  ::rix::note_launch(); kern<<<(unsigned)blocks, 256, sm, st>>>(a);
+  timing_mark(kTimeTiles, st, false);
   RIX_LAUNCH_CHECK();
   return RIX_OK;
 }
@@ -463,20 +506,9 @@ int planes_to_image(Job* job, Part& pt, R* image, cudaStream_t st) {
 template <typename R>
 int grid_build_corrections(Job* job, cudaStream_t st) {
   const int n = job->desc.n;
-  const bool ws = job->nw > 0;
-  std::vector<double> corr, nm1;
-  build_correction(n, job->ng, job->desc.cell_rad, ws, job->stats.dw, corr, nm1);
-  RIX_TRY(upload_real<R>(job, job->corr_img, corr, st));
-  if (ws) RIX_TRY(upload_double(job, job->nm1_img, nm1, st)); else job->nm1_img.release();
-  build_correction(2 * n, 2 * job->ng, job->desc.cell_rad, ws, job->stats.dw, corr, nm1);
-  RIX_TRY(upload_real<R>(job, job->corr_psf, corr, st));
-  if (ws) RIX_TRY(upload_double(job, job->nm1_psf, nm1, st)); else job->nm1_psf.release();
-  // accuracy of w-stacking: max |dw (n - 1)| over the (PSF) field
-  if (ws) {
-    double mx = 0.0;
-    for (double d : nm1) mx = std::max(mx, std::fabs(d * job->stats.dw));
-    job->stats.max_dw_nm1 = mx;
-  }
+  job->stats.max_dw_nm1 = 0.0;
+  RIX_TRY(build_correction<R>(job, n, job->ng, job->corr_img, job->nm1_img, st));
+  RIX_TRY(build_correction<R>(job, 2 * n, 2 * job->ng, job->corr_psf, job->nm1_psf, st));
   return RIX_OK;
 }
 

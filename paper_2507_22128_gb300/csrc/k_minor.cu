@@ -290,8 +290,8 @@ __global__ void k_copy_block(const R* __restrict__ src, R* __restrict__ dst, int
 template <typename R>
 int dwt2(const Ctx* ctx, R* x, R* tmp, int N, int levels, cudaStream_t st) {
   for (int l = 0, n = N; l < levels; ++l, n >>= 1) {
-    k_dwt_rows<R><<<blocks_for(ctx, (int64_t)n * n / 2), 256, 0, st>>>(x, tmp, n, N);
-    k_dwt_cols<R><<<blocks_for(ctx, (int64_t)n * n / 2), 256, 0, st>>>(tmp, x, n, N);
+    ::rix::note_launch(); k_dwt_rows<R><<<blocks_for(ctx, (int64_t)n * n / 2), 256, 0, st>>>(x, tmp, n, N);
+    ::rix::note_launch(); k_dwt_cols<R><<<blocks_for(ctx, (int64_t)n * n / 2), 256, 0, st>>>(tmp, x, n, N);
   }
   RIX_LAUNCH_CHECK();
   return RIX_OK;
@@ -303,8 +303,8 @@ int idwt2(const Ctx* ctx, const R* c, R* out, R* tmp, int N, int levels, cudaStr
   RIX_CUDA(cudaMemcpyAsync(out, c, (size_t)N * N * sizeof(R), cudaMemcpyDeviceToDevice, st));
   for (int l = levels - 1; l >= 0; --l) {
     const int n = N >> l;
-    k_idwt_cols<R><<<blocks_for(ctx, (int64_t)n * n), 256, 0, st>>>(out, tmp, n, N);
-    k_idwt_rows<R><<<blocks_for(ctx, (int64_t)n * n), 256, 0, st>>>(tmp, out, n, N);
+    ::rix::note_launch(); k_idwt_cols<R><<<blocks_for(ctx, (int64_t)n * n), 256, 0, st>>>(out, tmp, n, N);
+    ::rix::note_launch(); k_idwt_rows<R><<<blocks_for(ctx, (int64_t)n * n), 256, 0, st>>>(tmp, out, n, N);
   }
   RIX_LAUNCH_CHECK();
   return RIX_OK;
@@ -514,7 +514,7 @@ int ingest(Job* job, int p, int cycle, cudaStream_t st) {
   const int64_t npix = (int64_t)job->desc.n * job->desc.n;
   for (int q = 0; q < job->n_part; ++q) {
     if (q == p) continue;
-    k_axpy<R><<<blocks_for(job->ctx, npix), 256, 0, st>>>(job->part[p].rho[q].as<R>(),
+    ::rix::note_launch(); k_axpy<R><<<blocks_for(job->ctx, npix), 256, 0, st>>>(job->part[p].rho[q].as<R>(),
                                                           job->part[q].outbox[(cycle - 1) & 1].as<R>(), R(1), npix);
   }
   RIX_LAUNCH_CHECK();
@@ -558,7 +558,7 @@ int publish(Job* job, int p, int cycle, cudaStream_t st) {
   const int64_t npix = (int64_t)n * n, tot = 4 * npix;
   const double inv = 1.0 / (double)tot;
   const R* ibar = pt.delta.as<R>();
-  k_axpy<R><<<blocks_for(job->ctx, npix), 256, 0, st>>>(pt.model.as<R>(), ibar, R(1), npix);
+  ::rix::note_launch(); k_axpy<R><<<blocks_for(job->ctx, npix), 256, 0, st>>>(pt.model.as<R>(), ibar, R(1), npix);
   RIX_LAUNCH_CHECK();
   const R* gam = job->gam.as<R>();
   RIX_TRY(convolve<R>(job, pt, ibar, kOpMulReal, gam + p * tot, nullptr, pt.outbox[cycle & 1].as<R>(), inv, 0, st));
@@ -610,7 +610,7 @@ int fill_init(Job* job, cudaStream_t st) {
   ga.nparts = P;
   for (int i = 0; i < P - 1; ++i) ga.ells[i] = job->ells[i];
   ga.delta = job->stats.delta_px;
-  k_gamma<R><<<blocks_for(job->ctx, tot), 256, 0, st>>>(ga, job->gam.as<R>());
+  ::rix::note_launch(); k_gamma<R><<<blocks_for(job->ctx, tot), 256, 0, st>>>(ga, job->gam.as<R>());
   RIX_LAUNCH_CHECK();
   for (int p = 0; p < P; ++p) {
     Part& pt = job->part[p];
@@ -651,7 +651,7 @@ int op_msclean(Job* job, int p, const rix_msclean_params* prm, R* delta_out, cud
   RIX_TRY(fill_spectra<R>(job, p, st));
   cplx<R>* dspec = pt.fs_a.as<cplx<R>>();
   cplx<R>* pspec = pt.fs_b.as<cplx<R>>();
-  k_fill_msclean<R><<<blocks_for(ctx, tot), 256, 0, st>>>(fa, dspec, pspec);
+  ::rix::note_launch(); k_fill_msclean<R><<<blocks_for(ctx, tot), 256, 0, st>>>(fa, dspec, pspec);
   RIX_LAUNCH_CHECK();
 
   // scale functions: stencils, their 2N-grid spectra B_s
@@ -686,7 +686,7 @@ int op_msclean(Job* job, int p, const rix_msclean_params* prm, R* delta_out, cud
   g2.M = 2 * n; g2.L = 2 * n; g2.logL = ilog2(g2.L); g2.lo = 0; g2.S = 2 * n; g2.nplanes = 1; g2.mode = kFacNone;
   for (int s = 0; s < ns && rc == RIX_OK; ++s) {
     if (cudaMemsetAsync(img2, 0, tot * sizeof(R), st) != cudaSuccess) { rc = set_error(RIX_ECUDA, "memset"); break; }
-    k_place_stencil<R><<<4, 256, 0, st>>>(stn_dev + ca.st_off[s], ca.st_rad[s], img2, 2 * n);
+    ::rix::note_launch(); k_place_stencil<R><<<4, 256, 0, st>>>(stn_dev + ca.st_off[s], ca.st_rad[s], img2, 2 * n);
     if ((rc = fwd_rows<R>(ctx, g2, img2, t2, st)) != RIX_OK) break;
     rc = fwd_cols<R>(ctx, g2, t2, bspec + s * tot, st);
   }
@@ -697,7 +697,7 @@ int op_msclean(Job* job, int p, const rix_msclean_params* prm, R* delta_out, cud
     rc = spec_to_img<R>(job, pt, dspec, kOpMulCplx, bspec + s * tot, pt.ms_R.as<R>() + s * npix, inv, 0, st);
   for (int s = 0; s < ns && rc == RIX_OK; ++s)
     for (int t = 0; t < ns && rc == RIX_OK; ++t) {
-      k_cmul3<R><<<blocks_for(ctx, tot), 256, 0, st>>>(bspec + s * tot, bspec + t * tot, pspec, dspec, tot);
+      ::rix::note_launch(); k_cmul3<R><<<blocks_for(ctx, tot), 256, 0, st>>>(bspec + s * tot, bspec + t * tot, pspec, dspec, tot);
       if ((rc = inv_cols<R>(ctx, g2, dspec, kOpNone, nullptr, nullptr, t2, st)) != RIX_OK) break;
       rc = inv_rows<R>(ctx, g2, t2, pt.ms_P.as<R>() + (int64_t)(s * ns + t) * tot, inv, 0, st);
     }
@@ -746,7 +746,7 @@ int op_msclean(Job* job, int p, const rix_msclean_params* prm, R* delta_out, cud
   ca.comp_pix = ca.comp_s + cap;
   ca.count = ca.comp_pix + cap;
   void* args[] = {&ca};
-  RIX_CUDA(cudaLaunchCooperativeKernel((const void*)k_msclean<R>, dim3(nblk), dim3(256), args, 0, st));
+  ::rix::note_launch(); RIX_CUDA(cudaLaunchCooperativeKernel((const void*)k_msclean<R>, dim3(nblk), dim3(256), args, 0, st));
   RIX_TRY(publish<R>(job, p, cycle, st));
   if (delta_out) RIX_CUDA(cudaMemcpyAsync(delta_out, pt.delta.p, npix * sizeof(R), cudaMemcpyDeviceToDevice, st));
   return RIX_OK;
@@ -763,7 +763,7 @@ int op_fista(Job* job, int p, const rix_fista_params* prm, R* delta_out, cudaStr
   if (!pt.lambda_set) {
     // lambda_rel refers to max |residual| of the partition's first cycle
     RIX_CUDA(cudaMemsetAsync(pt.fi_state.as<R>() + 1, 0, sizeof(R), st));
-    k_absmax<R><<<blocks_for(ctx, npix), 256, 0, st>>>(pt.resid.as<R>(), npix, pt.fi_state.as<R>() + 1);
+    ::rix::note_launch(); k_absmax<R><<<blocks_for(ctx, npix), 256, 0, st>>>(pt.resid.as<R>(), npix, pt.fi_state.as<R>() + 1);
     RIX_LAUNCH_CHECK();
     pt.lambda_set = true;
   }
@@ -773,7 +773,7 @@ int op_fista(Job* job, int p, const rix_fista_params* prm, R* delta_out, cudaStr
   FillArgs fa = fill_args<R>(job, p);
   const double gn = cycle == 1 ? 0.0 : 1.0;
   RIX_CUDA(cudaMemsetAsync(pt.fi_state.p, 0, sizeof(R), st));
-  k_fill_fista<R><<<blocks_for(ctx, tot), 256, 0, st>>>(fa, gn, pt.fi_mx.as<R>(), pt.fi_c.as<cplx<R>>(),
+  ::rix::note_launch(); k_fill_fista<R><<<blocks_for(ctx, tot), 256, 0, st>>>(fa, gn, pt.fi_mx.as<R>(), pt.fi_c.as<cplx<R>>(),
                                                         pt.fi_state.as<R>());
   RIX_LAUNCH_CHECK();
   RIX_TRY(alloc_zero<R>(job, pt.fi_alpha, npix * sizeof(R), st));
@@ -786,18 +786,49 @@ int op_fista(Job* job, int p, const rix_fista_params* prm, R* delta_out, cudaStr
   R* g = pt.fimg.as<R>();
   R* tmp = pt.fi_alpha_prev.as<R>();
   const double gscale = 2.0 / (double)tot;
-  double t = 1.0;
-  for (int it = 0; it < prm->iters; ++it) {
-    RIX_TRY(idwt2<R>(ctx, y, x, tmp, n, prm->levels, st));
-    // grad f(x) = 2 crop F^-1 [Mx X - C]
-    RIX_TRY(convolve<R>(job, pt, x, kOpAxpyReal, pt.fi_mx.p, pt.fi_c.p, g, gscale, 0, st));
-    RIX_TRY(dwt2<R>(ctx, g, tmp, n, prm->levels, st));
-    const double tn = 0.5 * (1.0 + std::sqrt(1.0 + 4.0 * t * t));
-    const double mom = (t - 1.0) / tn;
-    k_fista_step<R><<<blocks_for(ctx, npix), 256, 0, st>>>(alpha, y, g, npix, pt.fi_state.as<R>(), prm->lambda,
-                                                           prm->lambda_rel, mom);
-    RIX_LAUNCH_CHECK();
-    t = tn;
+  // The iteration sequence is fixed for a partition (buffers, momentum
+  // coefficients; lambda and L are read from device memory), so it is
+  // captured once into a CUDA graph on a private stream and replayed.
+  void* bufs[6] = {alpha, y, x, g, tmp, pt.fi_mx.p};
+  bool same = pt.fista_exec && pt.fista_iters == prm->iters && pt.fista_levels == prm->levels;
+  for (int k = 0; k < 6 && same; ++k) same = pt.fista_bufs[k] == bufs[k];
+  if (!same && prm->iters > 0) {
+    if (pt.fista_exec) { cudaGraphExecDestroy(pt.fista_exec); pt.fista_exec = nullptr; }
+    if (!job->capture_stream) RIX_CUDA(cudaStreamCreateWithFlags(&job->capture_stream, cudaStreamNonBlocking));
+    cudaStream_t cs = job->capture_stream;
+    const unsigned long long before = launch_count();
+    RIX_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+    int rc = RIX_OK;
+    double t = 1.0;
+    for (int it = 0; it < prm->iters && rc == RIX_OK; ++it) {
+      if ((rc = idwt2<R>(ctx, y, x, tmp, n, prm->levels, cs)) != RIX_OK) break;
+      // grad f(x) = 2 crop F^-1 [Mx X - C]
+      if ((rc = convolve<R>(job, pt, x, kOpAxpyReal, pt.fi_mx.p, pt.fi_c.p, g, gscale, 0, cs)) != RIX_OK) break;
+      if ((rc = dwt2<R>(ctx, g, tmp, n, prm->levels, cs)) != RIX_OK) break;
+      const double tn = 0.5 * (1.0 + std::sqrt(1.0 + 4.0 * t * t));
+      const double mom = (t - 1.0) / tn;
+      note_launch();
+      k_fista_step<R><<<blocks_for(ctx, npix), 256, 0, cs>>>(alpha, y, g, npix, pt.fi_state.as<R>(), prm->lambda,
+                                                             prm->lambda_rel, mom);
+      t = tn;
+    }
+    cudaGraph_t graph = nullptr;
+    const cudaError_t ec = cudaStreamEndCapture(cs, &graph);
+    // captured kernels run when the graph is replayed, not now
+    pt.fista_nodes = (long long)(launch_count() - before);
+    note_launch(-pt.fista_nodes);
+    if (rc != RIX_OK) { if (graph) cudaGraphDestroy(graph); return rc; }
+    if (ec != cudaSuccess) return set_error(RIX_ECUDA, "FISTA capture: %s", cudaGetErrorString(ec));
+    const cudaError_t ei = cudaGraphInstantiate(&pt.fista_exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ei != cudaSuccess) { pt.fista_exec = nullptr; return set_error(RIX_ECUDA, "FISTA graph: %s", cudaGetErrorString(ei)); }
+    pt.fista_iters = prm->iters;
+    pt.fista_levels = prm->levels;
+    for (int k = 0; k < 6; ++k) pt.fista_bufs[k] = bufs[k];
+  }
+  if (prm->iters > 0) {
+    note_launch(pt.fista_nodes);
+    RIX_CUDA(cudaGraphLaunch(pt.fista_exec, st));
   }
   RIX_TRY(idwt2<R>(ctx, alpha, pt.delta.as<R>(), tmp, n, prm->levels, st));
   RIX_TRY(publish<R>(job, p, cycle, st));
@@ -813,7 +844,7 @@ int op_combine(Job* job, R* out, cudaStream_t st) {
   const R** dptrs = nullptr;
   RIX_CUDA(cudaMallocAsync((void**)&dptrs, sizeof(ptrs), st));
   RIX_CUDA(cudaMemcpyAsync(dptrs, ptrs, sizeof(ptrs), cudaMemcpyHostToDevice, st));
-  k_mean<R><<<blocks_for(job->ctx, npix), 256, 0, st>>>(out, dptrs, job->n_part, npix);
+  ::rix::note_launch(); k_mean<R><<<blocks_for(job->ctx, npix), 256, 0, st>>>(out, dptrs, job->n_part, npix);
   cudaFreeAsync(dptrs, st);
   RIX_LAUNCH_CHECK();
   RIX_CUDA(cudaStreamSynchronize(st));   // ptrs is a host temporary

@@ -163,10 +163,10 @@ int radix_sort_impl(K* keys, uint32_t* vals, K* keys_tmp, uint32_t* vals_tmp, in
   uint32_t* va = vals; uint32_t* vb = vals_tmp;
   int rc = RIX_OK;
   for (int shift = 0; shift < bits; shift += 8) {
-    k_radix_hist<K><<<nblocks, kSortThreads, 0, st>>>(a, n, shift, hist, nblocks);
+    ::rix::note_launch(); k_radix_hist<K><<<nblocks, kSortThreads, 0, st>>>(a, n, shift, hist, nblocks);
     rc = scan_exclusive_u32(hist, hist + hn, hn, nullptr, st);
     if (rc != RIX_OK) break;
-    k_radix_scatter<K, kVals><<<nblocks, kSortThreads, 0, st>>>(a, va, b, vb, n, shift, hist + hn,
+    ::rix::note_launch(); k_radix_scatter<K, kVals><<<nblocks, kSortThreads, 0, st>>>(a, va, b, vb, n, shift, hist + hn,
                                                                  nblocks);
     std::swap(a, b);
     std::swap(va, vb);
@@ -408,17 +408,17 @@ int scan_exclusive_u32(const uint32_t* in, uint32_t* out, int64_t n, uint32_t* t
   const int64_t nb = ceil_div(n, kScanTile);
   if (nb > 0x7fffffff) return set_error(RIX_EINVAL, "scan too large");
   if (nb == 1) {
-    k_scan_block<<<1, kScanThreads, 0, st>>>(in, out, n, nullptr);
+    ::rix::note_launch(); k_scan_block<<<1, kScanThreads, 0, st>>>(in, out, n, nullptr);
   } else {
     uint32_t* sums = nullptr;
     RIX_CUDA(cudaMallocAsync(&sums, 2 * nb * sizeof(uint32_t), st));
-    k_scan_block<<<(unsigned)nb, kScanThreads, 0, st>>>(in, out, n, sums);
+    ::rix::note_launch(); k_scan_block<<<(unsigned)nb, kScanThreads, 0, st>>>(in, out, n, sums);
     int rc = scan_exclusive_u32(sums, sums + nb, nb, nullptr, st);
-    if (rc == RIX_OK) k_scan_add<<<(unsigned)nb, kScanThreads, 0, st>>>(out, n, sums + nb);
+    if (rc == RIX_OK) { ::rix::note_launch(); k_scan_add<<<(unsigned)nb, kScanThreads, 0, st>>>(out, n, sums + nb); }
     cudaFreeAsync(sums, st);
     if (rc != RIX_OK) return rc;
   }
-  if (total_dev) k_total<<<1, 1, 0, st>>>(in, out, n, total_dev);
+  if (total_dev) { ::rix::note_launch(); k_total<<<1, 1, 0, st>>>(in, out, n, total_dev); }
   RIX_LAUNCH_CHECK();
   return RIX_OK;
 }
@@ -501,7 +501,7 @@ int partition_job(Job* job, const double* uvw, int64_t nrow, const float* weight
   // --- w-plane parameters ------------------------------------------------
   double w_min = 0.0, dw = 1.0;
   if (job->nw > 0 && ns > 0) {
-    k_w_minmax<<<blocks, 256, 0, st>>>(g, ns, sm_d->wmm);
+    ::rix::note_launch(); k_w_minmax<<<blocks, 256, 0, st>>>(g, ns, sm_d->wmm);
     if (cudaGetLastError() != cudaSuccess) return fail(set_error(RIX_ECUDA, "k_w_minmax launch"));
     unsigned long long mm[2];
     if (cudaMemcpyAsync(mm, sm_d->wmm, sizeof(mm), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
@@ -530,10 +530,10 @@ int partition_job(Job* job, const double* uvw, int64_t nrow, const float* weight
       if (cudaMallocAsync(&rb, ns * sizeof(uint64_t), st) != cudaSuccess ||
           cudaMallocAsync(&rt, ns * sizeof(uint64_t), st) != cudaSuccess)
         return fail(set_error(RIX_ENOMEM, "radius sort scratch"));
-      k_radius_bits<<<blocks, 256, 0, st>>>(g, ns, rb);
+      ::rix::note_launch(); k_radius_bits<<<blocks, 256, 0, st>>>(g, ns, rb);
       bool in_tmp = false;
       int rc = radix_sort_u64_keys(rb, rt, ns, 64, st, &in_tmp);
-      if (rc == RIX_OK) k_pick<<<1, 32, 0, st>>>(in_tmp ? rt : rb, ns, P, sm_d->ells);
+      if (rc == RIX_OK) { ::rix::note_launch(); k_pick<<<1, 32, 0, st>>>(in_tmp ? rt : rb, ns, P, sm_d->ells); }
       cudaFreeAsync(rb, st);
       cudaFreeAsync(rt, st);
       if (rc != RIX_OK) return fail(rc);
@@ -557,7 +557,7 @@ int partition_job(Job* job, const double* uvw, int64_t nrow, const float* weight
     return fail(set_error(RIX_ENOMEM, "classify scratch"));
   ClassifyOut co{mask_out, counts, sm_d->win, sm_d->part_count, sm_d->wsum, &sm_d->n_outside,
                  job->weight.as<float>()};
-  if (ns > 0) k_classify<<<blocks, 256, 0, st>>>(g, ns, th, co);
+  if (ns > 0) { ::rix::note_launch(); k_classify<<<blocks, 256, 0, st>>>(g, ns, th, co); }
   int rc = scan_exclusive_u32(counts, offs, ns, &sm_d->totals[0], st);
   if (rc != RIX_OK) return fail(rc);
   if (cudaMemcpyAsync(&sm_h, sm_d, sizeof(Small), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
@@ -583,9 +583,11 @@ int partition_job(Job* job, const double* uvw, int64_t nrow, const float* weight
   if (cudaMallocAsync(&kt, std::max<int64_t>(n_ent, 1) * sizeof(uint32_t), st) != cudaSuccess ||
       cudaMallocAsync(&vt, std::max<int64_t>(n_ent, 1) * sizeof(uint32_t), st) != cudaSuccess)
     return fail(set_error(RIX_ENOMEM, "sort scratch"));
-  if (ns > 0)
+  if (ns > 0) {
+    ::rix::note_launch(); 
     k_scatter_entries<<<blocks, 256, 0, st>>>(g, ns, P, th, kl, offs, job->keys.as<uint32_t>(),
                                               job->samples.as<uint32_t>());
+  }
   bool in_tmp = false;
   rc = radix_sort_u32(job->keys.as<uint32_t>(), job->samples.as<uint32_t>(), kt, vt, n_ent, key_bits, st, &in_tmp);
   if (rc != RIX_OK) return fail(rc);
@@ -606,13 +608,13 @@ int partition_job(Job* job, const double* uvw, int64_t nrow, const float* weight
         cudaMallocAsync(&wb, n_ent * sizeof(uint32_t), st) != cudaSuccess)
       return fail(set_error(RIX_ENOMEM, "work-item scratch"));
     const int eb = grid_blocks(ctx, n_ent, 256);
-    k_seg_flags<<<eb, 256, 0, st>>>(job->keys.as<uint32_t>(), n_ent, kt);
+    ::rix::note_launch(); k_seg_flags<<<eb, 256, 0, st>>>(job->keys.as<uint32_t>(), n_ent, kt);
     rc = scan_exclusive_u32(kt, vt, n_ent, &sm_d->totals[1], st);
     if (rc != RIX_OK) return fail(rc);
     uint32_t* starts = wa;
-    k_seg_starts<<<eb, 256, 0, st>>>(kt, vt, n_ent, starts);
+    ::rix::note_launch(); k_seg_starts<<<eb, 256, 0, st>>>(kt, vt, n_ent, starts);
     uint32_t* chunks = wb;
-    k_seg_chunks<<<eb, 256, 0, st>>>(starts, &sm_d->totals[1], n_ent, chunks);
+    ::rix::note_launch(); k_seg_chunks<<<eb, 256, 0, st>>>(starts, &sm_d->totals[1], n_ent, chunks);
     // chunk offsets into kt (flags no longer needed)
     uint32_t nseg_h = 0;
     RIX_CUDA(cudaMemcpyAsync(&nseg_h, &sm_d->totals[1], sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
@@ -624,10 +626,10 @@ int partition_job(Job* job, const double* uvw, int64_t nrow, const float* weight
     RIX_CUDA(cudaStreamSynchronize(st));
     n_items = nit_h;
     RIX_TRY(job->items.alloc(ctx, (n_items + 1) * sizeof(uint32_t)));
-    k_items<<<grid_blocks(ctx, nseg_h, 256), 256, 0, st>>>(starts, &sm_d->totals[1], chunks, kt, n_ent,
+    ::rix::note_launch(); k_items<<<grid_blocks(ctx, nseg_h, 256), 256, 0, st>>>(starts, &sm_d->totals[1], chunks, kt, n_ent,
                                                          job->items.as<uint32_t>(), &sm_d->totals[2]);
     RIX_CUDA(cudaMemcpyAsync(sm_d->ent_begin, ent_begin, sizeof(ent_begin), cudaMemcpyHostToDevice, st));
-    k_item_ranges<<<1, 32, 0, st>>>(job->items.as<uint32_t>(), &sm_d->totals[2], sm_d->ent_begin, P,
+    ::rix::note_launch(); k_item_ranges<<<1, 32, 0, st>>>(job->items.as<uint32_t>(), &sm_d->totals[2], sm_d->ent_begin, P,
                                     sm_d->item_range);
   } else {
     RIX_TRY(job->items.alloc(ctx, sizeof(uint32_t)));

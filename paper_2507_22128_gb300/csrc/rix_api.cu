@@ -3,9 +3,13 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cstdarg>
 #include <cstring>
+#include <mutex>
 #include <new>
+#include <utility>
+#include <vector>
 
 #include "rix_internal.cuh"
 
@@ -29,6 +33,35 @@ int set_error(int code, const char* fmt, ...) {
 }
 
 const char* last_error() { return g_err; }
+
+static std::atomic<unsigned long long> g_launches{0};
+void note_launch(long long n) { g_launches.fetch_add((unsigned long long)n, std::memory_order_relaxed); }
+unsigned long long launch_count() { return g_launches.load(); }
+
+// ---- opt-in kernel timing ----
+static std::atomic<bool> g_timing{false};
+static std::mutex g_tmu;
+static std::vector<std::pair<cudaEvent_t, cudaEvent_t>> g_tev[kTimeClasses];
+static cudaEvent_t g_topen[kTimeClasses] = {nullptr, nullptr, nullptr};
+bool timing_on() { return g_timing.load(std::memory_order_relaxed); }
+
+void timing_mark(int cls, cudaStream_t st, bool begin) {
+  if (!timing_on()) return;
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cap) != cudaSuccess || cap != cudaStreamCaptureStatusNone) return;
+  std::lock_guard<std::mutex> lk(g_tmu);
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) return;
+  cudaEventRecord(e, st);
+  if (begin) {
+    g_topen[cls] = e;
+  } else if (g_topen[cls]) {
+    g_tev[cls].push_back({g_topen[cls], e});
+    g_topen[cls] = nullptr;
+  } else {
+    cudaEventDestroy(e);
+  }
+}
 
 int DevBuf::alloc(Ctx* ctx, size_t nbytes) {
   if (nbytes == 0) nbytes = 16;
@@ -128,6 +161,34 @@ extern "C" {
 
 const char* rix_last_error(void) { return rix::last_error(); }
 
+uint64_t rix_kernel_launches(void) { return rix::g_launches.load(); }
+
+int rix_timing_enable(int on) {
+  rix::g_timing.store(on != 0);
+  return RIX_OK;
+}
+
+int rix_timing_read(int kernel_class, double* total_ms, int64_t* launches) {
+  if (kernel_class < 0 || kernel_class >= rix::kTimeClasses || !total_ms || !launches)
+    return set_error(RIX_EINVAL, "bad timing query");
+  std::lock_guard<std::mutex> lk(rix::g_tmu);
+  double tot = 0.0;
+  int64_t n = 0;
+  for (auto& pr : rix::g_tev[kernel_class]) {
+    float ms = 0.f;
+    if (cudaEventSynchronize(pr.second) == cudaSuccess && cudaEventElapsedTime(&ms, pr.first, pr.second) == cudaSuccess) {
+      tot += ms;
+      ++n;
+    }
+    cudaEventDestroy(pr.first);
+    cudaEventDestroy(pr.second);
+  }
+  rix::g_tev[kernel_class].clear();
+  *total_ms = tot;
+  *launches = n;
+  return RIX_OK;
+}
+
 int rix_create(rix_ctx_t* ctx, int device, size_t mem_budget_bytes) {
   if (!ctx) return set_error(RIX_EINVAL, "ctx is NULL");
   *ctx = nullptr;
@@ -216,8 +277,11 @@ int rix_job_destroy(rix_job_t job) {
   Job& J = job->j;
   cudaSetDevice(J.ctx->device);
   cudaDeviceSynchronize();
-  for (int p = 0; p < kMaxPart; ++p)
+  for (int p = 0; p < kMaxPart; ++p) {
     if (J.part[p].ev_minor) cudaEventDestroy(J.part[p].ev_minor);
+    if (J.part[p].fista_exec) cudaGraphExecDestroy(J.part[p].fista_exec);
+  }
+  if (J.capture_stream) cudaStreamDestroy(J.capture_stream);
   J.ctx->reserved -= J.reserved;
   J.ctx->jobs -= 1;
   delete job;
@@ -246,12 +310,14 @@ int rix_set_uv_partition(rix_job_t job, const double* uvw_m, int64_t nrow, const
   RIX_CUDA(cudaSetDevice(J.ctx->device));
   J.partitioned = false;
   reset_partitions(&J);
+  timing_mark(kTimePartition, st, true);
   RIX_TRY(partition_job(&J, uvw_m, nrow, weight, ell_px, delta_px, mask_out, st));
   if (J.fp64) RIX_TRY(grid_build_corrections<double>(&J, st));
   else RIX_TRY(grid_build_corrections<float>(&J, st));
   if (J.fp64) RIX_TRY(fill_init<double>(&J, st));
   else RIX_TRY(fill_init<float>(&J, st));
   for (int p = 0; p < J.n_part; ++p) RIX_TRY(ensure_images(&J, J.part[p], st));
+  timing_mark(kTimePartition, st, false);
   J.partitioned = true;
   return RIX_OK;
 }

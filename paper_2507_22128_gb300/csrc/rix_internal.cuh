@@ -17,6 +17,16 @@ namespace rix {
 // ---------------------------------------------------------------------------
 int set_error(int code, const char* fmt, ...);
 const char* last_error();
+// counts the kernels the library runs (all host threads), including the
+// kernel nodes of replayed CUDA graphs
+void note_launch(long long n = 1);
+unsigned long long launch_count();
+
+// Opt-in device timing of kernel classes (CUDA events recorded on the launch
+// stream around each launch; streams under capture are skipped).
+enum TimedClass : int { kTimeTiles = 0, kTimeFft = 1, kTimePartition = 2, kTimeClasses = 3 };
+bool timing_on();
+void timing_mark(int cls, cudaStream_t st, bool begin);
 
 #define RIX_CUDA(...)                                                                   \
   do {                                                                                  \
@@ -189,6 +199,11 @@ struct Part {
   DevBuf fi_alpha, fi_alpha_prev, fi_y, fi_mx, fi_c, fi_x;   // FISTA
   int ms_ncomp_cap = 0;
   cudaEvent_t ev_minor = nullptr;           // recorded after each minor cycle
+  // captured FISTA iteration loop (replayed each minor cycle)
+  cudaGraphExec_t fista_exec = nullptr;
+  int fista_iters = -1, fista_levels = -1;
+  long long fista_nodes = 0;
+  void* fista_bufs[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
 };
 
 struct Job {
@@ -216,6 +231,7 @@ struct Job {
   double ells[kMaxPart];
   int n_part = 1;
   cudaEvent_t ev_tmp = nullptr;
+  cudaStream_t capture_stream = nullptr;    // private stream for graph capture
 };
 
 // gridder entry points (k_grid.cu)

@@ -75,6 +75,9 @@ def _load() -> C.CDLL:
         "rix_get_model": (C.c_int, [vp, C.c_int, vp, vp]),
         "rix_combine": (C.c_int, [vp, vp, vp]),
         "rix_last_error": (C.c_char_p, []),
+        "rix_kernel_launches": (C.c_uint64, []),
+        "rix_timing_enable": (C.c_int, [C.c_int]),
+        "rix_timing_read": (C.c_int, [C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -88,7 +91,8 @@ _lib = _load()
 EXPORTED = ("rix_create", "rix_destroy", "rix_job_workspace_bytes", "rix_job_create", "rix_job_destroy",
             "rix_job_sync", "rix_job_get_stats", "rix_set_uv_partition", "rix_get_sorted_entries",
             "rix_degrid", "rix_grid", "rix_psf", "rix_major_cycle", "rix_minor_cycle_msclean",
-            "rix_minor_cycle_fista", "rix_get_components", "rix_get_model", "rix_combine", "rix_last_error")
+            "rix_minor_cycle_fista", "rix_get_components", "rix_get_model", "rix_combine", "rix_last_error",
+            "rix_kernel_launches", "rix_timing_enable", "rix_timing_read")
 
 
 def _check(rc: int):
@@ -238,6 +242,25 @@ def get_components(job, part, capacity=1 << 16, stream=None):
 
 def get_model(job, part, image_out, stream=None):
     _check(_lib.rix_get_model(job, part, _ptr(image_out, _RT, name="image_out"), _stream(stream)))
+
+
+def kernel_launches() -> int:
+    return int(_lib.rix_kernel_launches())
+
+
+TIME_TILES, TIME_FFT, TIME_PARTITION = 0, 1, 2
+
+
+def timing_enable(on: bool = True):
+    _check(_lib.rix_timing_enable(1 if on else 0))
+
+
+def timing_read(kernel_class: int):
+    """(total device ms, launches) of one kernel class since the last read."""
+    ms = C.c_double()
+    n = C.c_int64()
+    _check(_lib.rix_timing_read(kernel_class, C.byref(ms), C.byref(n)))
+    return ms.value, n.value
 
 
 def combine(job, image_out, stream=None):
