@@ -186,6 +186,37 @@ __device__ void fft_rows(cplx<R>* s, int B, int logL, int stride, const cplx<R>*
   }
 }
 
+// v[r] *= w^r, w = exp(DIR 2 pi i k / (p RAD)): w, w^4 and w^8 come from the
+// FP64-accurate table, the other powers from at most three products of them
+// (a few ulp), instead of RAD - 1 dependent table loads.
+template <typename R, int DIR, int RAD>
+__device__ __forceinline__ void apply_twiddles(cplx<R>* v, const cplx<R>* __restrict__ tw, int k, int twshift) {
+  using C = cplx<R>;
+  C w[RAD];
+  auto ld = [&](int m) {
+    C t = tw[(m * k) << twshift];
+    if (DIR > 0) t.y = -t.y;
+    return t;
+  };
+  w[1] = ld(1);
+  if constexpr (RAD >= 4) {
+    w[2] = cmul(w[1], w[1]);
+    w[3] = cmul(w[2], w[1]);
+  }
+  if constexpr (RAD >= 8) {
+    w[4] = ld(4);
+#pragma unroll
+    for (int r = 5; r < 8; ++r) w[r] = cmul(w[4], w[r - 4]);
+  }
+  if constexpr (RAD >= 16) {
+    w[8] = ld(8);
+#pragma unroll
+    for (int r = 9; r < 16; ++r) w[r] = cmul(w[8], w[r - 8]);
+  }
+#pragma unroll
+  for (int r = 1; r < RAD; ++r) v[r] = cmul(v[r], w[r]);
+}
+
 // Out-of-place Stockham pass (ping-pong between two shared buffers): each
 // thread carries one radix item at a time, so register use stays low.
 template <typename R, int DIR, int RAD>
@@ -206,14 +237,7 @@ __device__ __forceinline__ void fft_pass_pp(const cplx<R>* __restrict__ src, cpl
     C v[RAD];
 #pragma unroll
     for (int r = 0; r < RAD; ++r) v[r] = rs[padi(i + r * ipr)];
-    if (k) {
-#pragma unroll
-      for (int r = 1; r < RAD; ++r) {
-        C w = tw[(r * k) << twshift];
-        if (DIR > 0) w.y = -w.y;
-        v[r] = cmul(v[r], w);
-      }
-    }
+    if (k) apply_twiddles<R, DIR, RAD>(v, tw, k, twshift);
     dft<RAD, DIR>(v);
     C* rd = dst + row * stride;
     const int o = ((i - k) << LR) + k;
@@ -287,7 +311,7 @@ struct KArgs {
 
 // ------------------------------------------------------------ row passes ----
 template <typename R, int VPT>
-__global__ void __launch_bounds__(kFftThreads) k_fwd_rows(KArgs a, const R* __restrict__ img,
+__global__ void __launch_bounds__(kFftThreads, (VPT == 0 && sizeof(R) == 4) ? 4 : 1) k_fwd_rows(KArgs a, const R* __restrict__ img,
                                                           cplx<R>* __restrict__ T,
                                                           const cplx<R>* __restrict__ tw) {
   using C = cplx<R>;
@@ -297,6 +321,7 @@ __global__ void __launch_bounds__(kFftThreads) k_fwd_rows(KArgs a, const R* __re
   const int L = a.L, M = a.M, half = M / 2;
   const R* corr = static_cast<const R*>(a.corr);
   const double wp = a.w0 + p * a.dw;
+#pragma unroll 4
   for (int idx = threadIdx.x; idx < a.B * L; idx += kFftThreads) {
     const int r = idx >> a.logL, c = idx & (L - 1);
     const int b = b0 + r;
@@ -326,7 +351,7 @@ __global__ void __launch_bounds__(kFftThreads) k_fwd_rows(KArgs a, const R* __re
 }
 
 template <typename R, int VPT>
-__global__ void __launch_bounds__(kFftThreads) k_inv_rows(KArgs a, const cplx<R>* __restrict__ T,
+__global__ void __launch_bounds__(kFftThreads, (VPT == 0 && sizeof(R) == 4) ? 4 : 1) k_inv_rows(KArgs a, const cplx<R>* __restrict__ T,
                                                           R* __restrict__ img, double scale, int accumulate,
                                                           const cplx<R>* __restrict__ tw) {
   using C = cplx<R>;
@@ -337,11 +362,13 @@ __global__ void __launch_bounds__(kFftThreads) k_inv_rows(KArgs a, const cplx<R>
   const R* corr = static_cast<const R*>(a.corr);
   for (int p = 0; p < a.nplanes; ++p) {
     const C* Tp = T + (int64_t)p * a.S * M;
-    for (int idx = threadIdx.x; idx < a.B * L; idx += kFftThreads) {
+  #pragma unroll 4
+  for (int idx = threadIdx.x; idx < a.B * L; idx += kFftThreads) {
       const int r = idx >> a.logL, c = idx & (L - 1);
       s[r * a.stride + padi(c)] = cmake<C>(0.0, 0.0);
     }
     __syncthreads();
+#pragma unroll 4
     for (int idx = threadIdx.x; idx < a.B * a.S; idx += kFftThreads) {
       const int r = idx % a.B, j = idx / a.B;
       const int b = b0 + r, col = a.lo + j;
@@ -379,6 +406,7 @@ __device__ __forceinline__ void load_column_from_T(const KArgs& a, cplx<R>* s, c
                                                    int j0) {
   using C = cplx<R>;
   const int L = a.L, M = a.M, half = M / 2;
+#pragma unroll 4
   for (int idx = threadIdx.x; idx < a.B * L; idx += kFftThreads) {
     const int r = idx >> a.logL, c = idx & (L - 1);
     const int j = j0 + r;
@@ -416,7 +444,7 @@ __device__ __forceinline__ cplx<R> spec_op(int op, cplx<R> x, const void* tab, c
 }
 
 template <typename R, int VPT>
-__global__ void __launch_bounds__(kFftThreads) k_fwd_cols(KArgs a, const cplx<R>* __restrict__ T,
+__global__ void __launch_bounds__(kFftThreads, (VPT == 0 && sizeof(R) == 4) ? 4 : 1) k_fwd_cols(KArgs a, const cplx<R>* __restrict__ T,
                                                           cplx<R>* __restrict__ spec,
                                                           const cplx<R>* __restrict__ tw) {
   using C = cplx<R>;
@@ -435,7 +463,7 @@ __global__ void __launch_bounds__(kFftThreads) k_fwd_cols(KArgs a, const cplx<R>
 }
 
 template <typename R, int VPT>
-__global__ void __launch_bounds__(kFftThreads) k_inv_cols(KArgs a, const cplx<R>* __restrict__ spec, int op,
+__global__ void __launch_bounds__(kFftThreads, (VPT == 0 && sizeof(R) == 4) ? 4 : 1) k_inv_cols(KArgs a, const cplx<R>* __restrict__ spec, int op,
                                                           const void* tab, const void* tab2,
                                                           cplx<R>* __restrict__ T,
                                                           const cplx<R>* __restrict__ tw) {
@@ -444,6 +472,7 @@ __global__ void __launch_bounds__(kFftThreads) k_inv_cols(KArgs a, const cplx<R>
   const int p = blockIdx.y;
   const int j0 = blockIdx.x * a.B;
   const C* sp = spec + (int64_t)p * a.S * a.S;
+#pragma unroll 4
   for (int idx = threadIdx.x; idx < a.B * a.L; idx += kFftThreads) {
     const int r = idx >> a.logL, c = idx & (a.L - 1);
     const int j = j0 + r, i = c - a.lo;
@@ -460,7 +489,7 @@ __global__ void __launch_bounds__(kFftThreads) k_inv_cols(KArgs a, const cplx<R>
 }
 
 template <typename R, int VPT>
-__global__ void __launch_bounds__(kFftThreads) k_conv_cols(KArgs a, const cplx<R>* __restrict__ Tin, int op,
+__global__ void __launch_bounds__(kFftThreads, (VPT == 0 && sizeof(R) == 4) ? 4 : 1) k_conv_cols(KArgs a, const cplx<R>* __restrict__ Tin, int op,
                                                            const void* tab, const void* tab2,
                                                            cplx<R>* __restrict__ Tout,
                                                            const cplx<R>* __restrict__ tw) {
@@ -470,6 +499,7 @@ __global__ void __launch_bounds__(kFftThreads) k_conv_cols(KArgs a, const cplx<R
   load_column_from_T<R>(a, s, Tin, j0);
   __syncthreads();
   C* res = fft_any<R, VPT, -1>(s, s2, a.B, a.logL, a.stride, tw);
+#pragma unroll 4
   for (int idx = threadIdx.x; idx < a.B * a.L; idx += kFftThreads) {
     const int r = idx >> a.logL, c = idx & (a.L - 1);
     const int j = j0 + r;

@@ -418,9 +418,219 @@ int launch_tiles_impl(const Ctx* ctx, const TileArgs& a, cudaStream_t st) {
   return RIX_OK;
 }
 
+// ---- w-stacked gridding without shared-memory atomics ----------------------
+// Phase A: each warp degrids 4 samples of a 32-sample batch (32 lanes x 16
+// taps, shuffle reduction) and stores per-sample records (weighted residual,
+// tap origin, the 24 kernel weights).  Phase B: warp w owns w-plane w of the
+// staged sub-grid and applies every record of the batch to it with plain
+// read-modify-writes: lane (v row = lane & 7, u taps lane >> 3 and +4) touches
+// distinct cells, warps touch distinct planes, so nothing races.
+template <int T, int MODE> struct WsGeom {
+  static constexpr int SP = (MODE == kPsf) ? 2 * T + 9 : T + kW - 1;       // staged side
+  static constexpr int ORG = (MODE == kPsf) ? 2 : 0;
+  static constexpr int SPP = (MODE == kPsf) ? SP : ((SP + 7) / 16) * 16 + 8;   // row stride, 8 mod 16
+  static constexpr int PL = ((SP * SPP + 7) / 16) * 16 + 8;                // plane stride, 8 mod 16
+};
+
+template <typename R>
+struct WsRecord {
+  R yr, yi;
+  int ou, ov;
+  R wu[kW], wv[kW], ww[kW];
+};
+
+constexpr int kWsBatch = 32;
+
+template <typename R, int T, int MODE>
+__global__ void __launch_bounds__(256) k_tiles_ws(TileArgs a) {
+  using C = cplx<R>;
+  using TG = WsGeom<T, MODE>;
+  constexpr int SP = TG::SP, SPP = TG::SPP, PL = TG::PL;
+  constexpr bool kUseModel = (MODE == kResid);
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* sm_model = reinterpret_cast<C*>(smem_raw);
+  C* sm_grid = sm_model + (kUseModel ? kW * PL : 0);
+  WsRecord<R>* rec = reinterpret_cast<WsRecord<R>*>(sm_grid + kW * PL);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
+  const int64_t SS = (int64_t)a.S * a.S;
+  const C* model = static_cast<const C*>(a.model);
+  C* out = static_cast<C*>(a.out);
+  const C* vin = static_cast<const C*>(a.vis_in);
+  const uint32_t tmask = (1u << a.bt) - 1u;
+  const int per_warp = kWsBatch / nwarps;
+
+  for (int64_t it = blockIdx.x; it < a.item_count; it += gridDim.x) {
+    const int64_t item = a.item_begin + it;
+    const uint32_t e0 = a.items[item], e1 = a.items[item + 1];
+    const uint32_t key = a.keys[e0];
+    const int tx = (int)(key & tmask), ty = (int)((key >> a.bt) & tmask);
+    const int p0 = (int)((key >> (2 * a.bt)) & ((1u << a.bw) - 1u));
+    const int gu0 = (MODE == kPsf ? 2 * tx * T : tx * T) + TG::ORG;
+    const int gv0 = (MODE == kPsf ? 2 * ty * T : ty * T) + TG::ORG;
+    const int u0 = gu0 - a.win_lo, v0 = gv0 - a.win_lo;
+
+    for (int idx = threadIdx.x; idx < kW * SP * SP; idx += blockDim.x) {
+      const int pl = idx / (SP * SP), rem = idx - pl * (SP * SP);
+      const int iu = rem / SP, iv = rem - iu * SP;
+      if (kUseModel) {
+        const int u = u0 + iu, v = v0 + iv;
+        C val = cmake<C>(0.0, 0.0);
+        if (u >= 0 && u < a.S && v >= 0 && v < a.S) val = model[(p0 + pl) * SS + (int64_t)u * a.S + v];
+        sm_model[pl * PL + iu * SPP + iv] = val;
+      }
+      sm_grid[pl * PL + iu * SPP + iv] = cmake<C>(0.0, 0.0);
+    }
+    __syncthreads();
+
+    for (uint32_t base = e0; base < e1; base += kWsBatch) {
+      const int nb = (int)min((uint32_t)kWsBatch, e1 - base);
+      // ---------------- phase A: geometry, weights, degrid, records ----------
+      {
+        const int j0 = warp * per_warp;
+        const bool valid = lane < per_warp && j0 + lane < nb;
+        const uint32_t s = valid ? a.samples[base + j0 + lane] : 0u;
+        const int64_t row = s / (uint32_t)a.nchan;
+        const int ch = (int)(s - row * a.nchan);
+        const double sc = a.inv_lambda[ch];
+        const double ul = __dmul_rn(a.uvw[row * 3 + 0], sc);
+        const double vl = __dmul_rn(a.uvw[row * 3 + 1], sc);
+        const double wl = __dmul_rn(a.uvw[row * 3 + 2], sc);
+        const double x = __dadd_rn(__dmul_rn(ul, a.scale), a.half);
+        const double y = __dadd_rn(__dmul_rn(vl, a.scale), a.half);
+        const double xs = __dadd_rn(x, -0.5 * kW), ys = __dadd_rn(y, -0.5 * kW);
+        const double cx = ceil(xs), cy = ceil(ys);
+        int ou = (int)cx - gu0, ov = (int)cy - gv0;
+        const R du = (R)__dadd_rn(cx, -xs), dv = (R)__dadd_rn(cy, -ys);
+        const double tw = __ddiv_rn(__dadd_rn(wl, -a.w_min), a.dw);
+        const double pc = fmin(fmax(ceil(tw), 0.0), (double)(a.nw - a.ww));
+        const R dwo = (R)__dadd_rn(pc, -tw);
+        if (!valid || ou < 0 || ov < 0 || ou > SP - kW || ov > SP - kW) { ou = 0; ov = 0; }
+        R vre = R(0), vim = R(0), wt = R(0);
+        if (valid) {
+          wt = a.weight ? (R)a.weight[s] : R(1);
+          if (MODE == kGrid || MODE == kResid) { const C v = vin[s]; vre = v.x; vim = v.y; }
+          if (MODE == kPsf) vre = R(1);
+        }
+        for (int j = 0; j < per_warp && j0 + j < nb; ++j) {
+          const int kou = __shfl_sync(0xffffffffu, ou, j);
+          const int kov = __shfl_sync(0xffffffffu, ov, j);
+          const R kdu = __shfl_sync(0xffffffffu, du, j);
+          const R kdv = __shfl_sync(0xffffffffu, dv, j);
+          const R kdw = __shfl_sync(0xffffffffu, dwo, j);
+          R myw = R(0);
+          if (lane < 8) myw = es_weight<R>(kdu, lane);
+          else if (lane < 16) myw = es_weight<R>(kdv, lane - 8);
+          else if (lane < 24) myw = es_weight<R>(kdw, lane - 16);
+          WsRecord<R>& rc = rec[j0 + j];
+          if (lane < 8) rc.wu[lane] = myw;
+          else if (lane < 16) rc.wv[lane - 8] = myw;
+          else if (lane < 24) rc.ww[lane - 16] = myw;
+          R accr = R(0), acci = R(0);
+          if constexpr (kUseModel) {
+            R wu[kW];
+#pragma unroll
+            for (int i = 0; i < kW; ++i) wu[i] = __shfl_sync(0xffffffffu, myw, i);
+            const int vrow = lane & 7, plh = lane >> 3;
+            const R wv = __shfl_sync(0xffffffffu, myw, 8 + vrow);
+#pragma unroll
+            for (int r = 0; r < 2; ++r) {
+              const int pl = plh + 4 * r;
+              const R wvw = wv * __shfl_sync(0xffffffffu, myw, 16 + pl);
+              const C* gp = sm_model + pl * PL + kou * SPP + kov + vrow;
+              R sr = R(0), si = R(0);
+#pragma unroll
+              for (int i = 0; i < kW; ++i) {
+                const C g = gp[i * SPP];
+                sr += wu[i] * g.x;
+                si += wu[i] * g.y;
+              }
+              accr += wvw * sr;
+              acci += wvw * si;
+            }
+#pragma unroll
+            for (int o = 16; o; o >>= 1) {
+              accr += __shfl_xor_sync(0xffffffffu, accr, o);
+              acci += __shfl_xor_sync(0xffffffffu, acci, o);
+            }
+          }
+          const R kvr = __shfl_sync(0xffffffffu, vre, j);
+          const R kvi = __shfl_sync(0xffffffffu, vim, j);
+          const R kwt = __shfl_sync(0xffffffffu, wt, j);
+          if (lane == 0) {
+            rc.yr = kwt * (kvr - accr);
+            rc.yi = kwt * (kvi - acci);
+            rc.ou = kou;
+            rc.ov = kov;
+          }
+        }
+      }
+      __syncthreads();
+      // ---------------- phase B: warp w applies the batch to plane w ----------
+      {
+        const int vrow = lane & 7, ig = lane >> 3;
+        C* gpl = sm_grid + warp * PL;
+        for (int k = 0; k < nb; ++k) {
+          const WsRecord<R>& rc = rec[k];
+          const R f = rc.ww[warp] * rc.wv[vrow];
+          const R cr = rc.yr * f, ci = rc.yi * f;
+          C* cell = gpl + (rc.ou + ig) * SPP + rc.ov + vrow;
+          const R w0 = rc.wu[ig], w1 = rc.wu[ig + 4];
+          C g0 = cell[0], g1 = cell[4 * SPP];
+          g0.x += cr * w0; g0.y += ci * w0;
+          g1.x += cr * w1; g1.y += ci * w1;
+          cell[0] = g0;
+          cell[4 * SPP] = g1;
+        }
+      }
+      __syncthreads();
+    }
+
+    for (int idx = threadIdx.x; idx < kW * SP * SP; idx += blockDim.x) {
+      const int pl = idx / (SP * SP), rem = idx - pl * (SP * SP);
+      const int iu = rem / SP, iv = rem - iu * SP;
+      const int u = u0 + iu, v = v0 + iv;
+      const C val = sm_grid[pl * PL + iu * SPP + iv];
+      if ((val.x != R(0) || val.y != R(0)) && u >= 0 && u < a.S && v >= 0 && v < a.S) {
+        C* dst = &out[(p0 + pl) * SS + (int64_t)u * a.S + v];
+        if constexpr (sizeof(R) == 4) {
+          atomicAdd(reinterpret_cast<float2*>(dst), *reinterpret_cast<const float2*>(&val));
+        } else {
+          atomicAdd(&dst->x, val.x);
+          atomicAdd(&dst->y, val.y);
+        }
+      }
+    }
+    __syncthreads();
+  }
+}
+
+template <typename R, int T, int MODE>
+int launch_tiles_ws(const Ctx* ctx, const TileArgs& a, cudaStream_t st) {
+  using TG = WsGeom<T, MODE>;
+  constexpr bool kUseModel = (MODE == kResid);
+  const size_t sm = (size_t)(int(kUseModel) + 1) * kW * TG::PL * sizeof(cplx<R>) + kWsBatch * sizeof(WsRecord<R>);
+  auto kern = k_tiles_ws<R, T, MODE>;
+  RIX_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+  int per_sm = 0;
+  RIX_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, sm));
+  per_sm = std::max(per_sm, 1);
+  const int64_t blocks = std::min<int64_t>(a.item_count, (int64_t)ctx->num_sms * per_sm);
+  if (blocks <= 0) return RIX_OK;
+  timing_mark(kTimeTiles, st, true);
+  ::rix::note_launch(); kern<<<(unsigned)blocks, 256, sm, st>>>(a);
+  timing_mark(kTimeTiles, st, false);
+  RIX_LAUNCH_CHECK();
+  return RIX_OK;
+}
+
 template <typename R, int MODE>
 int launch_tiles(const Job* job, const TileArgs& a, cudaStream_t st) {
   const bool ws = job->nw > 0;
+  if constexpr (MODE != kDegrid) {
+    // w-stacked gridding: plane-owned shared-memory sub-grid (tile 16 only)
+    if (ws) return launch_tiles_ws<R, 16, MODE>(job->ctx, a, st);
+  }
   if (job->tile == 16) {
     return ws ? launch_tiles_impl<R, kW, 16, MODE>(job->ctx, a, st) : launch_tiles_impl<R, 1, 16, MODE>(job->ctx, a, st);
   }

@@ -200,137 +200,177 @@ __constant__ double kDb4[8] = {0.23037781330885523,  0.7148465705525415,   0.630
 template <typename R> __device__ __forceinline__ R db_h(int i) { return (R)kDb4[i]; }
 template <typename R> __device__ __forceinline__ R db_g(int i) { return (i & 1) ? -(R)kDb4[7 - i] : (R)kDb4[7 - i]; }
 
-// analysis along rows of the top-left n x n block (row stride ld):
-// out[r][k] = sum_i h[i] x[r][(2k+i) mod n], out[r][n/2+k] = sum_i g[i] x[...]
+// ------------------------------------------------- fused Db4 DWT levels ----
+// One kernel per level.  Analysis: a CTA owns a kTB x kTB block of each of the
+// four subbands of an n x n block, stages the periodic (2 kTB + 6)^2 input
+// tile, filters its rows (low and high) and then its columns.  Subband layout
+// of a level: [Y][X] with Y < n/2 column-low, X < n/2 row-low.
+constexpr int kTB = 16;
+
+// FISTA step fused into the analysis of the gradient (Beck & Teboulle 2009):
+// at each final coefficient g:  a' = S_{lam/L}(y - g/L),  y = a' + mom (a' - a),  a = a'
 template <typename R>
-__global__ void k_dwt_rows(const R* __restrict__ x, R* __restrict__ out, int n, int ld) {
-  const int half = n / 2;
-  const int64_t tot = (int64_t)n * half;
-  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < tot; t += (int64_t)gridDim.x * blockDim.x) {
-    const int r = (int)(t / half), k = (int)(t - (int64_t)r * half);
-    const R* row = x + (int64_t)r * ld;
+struct StepArgs {
+  R* alpha;
+  R* y;
+  const R* state;       // [max Mx, max |residual| of cycle 1]
+  double lambda, lambda_rel, mom;
+};
+
+template <typename R>
+__device__ __forceinline__ void fista_apply(const StepArgs<R>& s, int64_t i, R g, R inv_l, R thr, bool active) {
+  const R z = s.y[i] - g * inv_l;
+  const R az = fabs(z) - thr;
+  const R an = (active && az > R(0)) ? copysign(az, z) : R(0);
+  s.y[i] = an + (R)s.mom * (an - s.alpha[i]);
+  s.alpha[i] = an;
+}
+
+// kStep = false: details -> coef (ld), LL -> ll (ld) (or coef at the last level)
+// kStep = true : details and the last LL go through the fused FISTA step
+template <typename R, bool kStep>
+__global__ void __launch_bounds__(256) k_dwt_level(const R* __restrict__ src, int lds, int n, R* __restrict__ coef,
+                                                   R* __restrict__ ll, int ld, int last, StepArgs<R> st) {
+  constexpr int TIN = 2 * kTB + 6;
+  __shared__ R tin[TIN][TIN + 1];
+  __shared__ R trow[TIN][2 * kTB + 1];     // [input row][lo x | hi x]
+  const int h = n / 2;
+  const int y0 = blockIdx.y * kTB, x0 = blockIdx.x * kTB;
+  for (int t = threadIdx.x; t < TIN * TIN; t += blockDim.x) {
+    const int r = t / TIN, c = t - r * TIN;
+    tin[r][c] = src[(int64_t)((2 * y0 + r) & (n - 1)) * lds + ((2 * x0 + c) & (n - 1))];
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < TIN * kTB; t += blockDim.x) {
+    const int r = t / kTB, x = t - r * kTB;
     R a = R(0), d = R(0);
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
-      const R v = row[(2 * k + i) & (n - 1)];
+      const R v = tin[r][2 * x + i];
       a += db_h<R>(i) * v;
       d += db_g<R>(i) * v;
     }
-    out[(int64_t)r * ld + k] = a;
-    out[(int64_t)r * ld + half + k] = d;
+    trow[r][x] = a;
+    trow[r][kTB + x] = d;
   }
-}
-
-// analysis along columns: out[k][c], out[n/2+k][c]
-template <typename R>
-__global__ void k_dwt_cols(const R* __restrict__ x, R* __restrict__ out, int n, int ld) {
-  const int half = n / 2;
-  const int64_t tot = (int64_t)half * n;
-  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < tot; t += (int64_t)gridDim.x * blockDim.x) {
-    const int k = (int)(t / n), c = (int)(t - (int64_t)k * n);
-    R a = R(0), d = R(0);
+  __syncthreads();
+  R inv_l = R(0), thr = R(0);
+  bool active = false;
+  if (kStep) {
+    const double L = 2.0 * (double)st.state[0];
+    const double lam = st.lambda > 0.0 ? st.lambda : st.lambda_rel * (double)st.state[1];
+    active = L > 0.0;
+    inv_l = active ? (R)(1.0 / L) : R(0);
+    thr = active ? (R)(lam / L) : R(0);
+  }
+  {
+    const int ty = threadIdx.x / kTB, tx = threadIdx.x - ty * kTB;   // 256 threads = kTB x kTB
+    const int y = y0 + ty, x = x0 + tx;
+    if (y < h && x < h) {
 #pragma unroll
-    for (int i = 0; i < 8; ++i) {
-      const R v = x[(int64_t)((2 * k + i) & (n - 1)) * ld + c];
-      a += db_h<R>(i) * v;
-      d += db_g<R>(i) * v;
+      for (int q = 0; q < 4; ++q) {
+        const int cy = q >> 1, cx = q & 1;
+        R v = R(0);
+#pragma unroll
+        for (int i = 0; i < 8; ++i) v += (cy ? db_g<R>(i) : db_h<R>(i)) * trow[2 * ty + i][cx * kTB + tx];
+        const int Y = cy * h + y, X = cx * h + x;
+        if (q == 0 && !last) {
+          ll[(int64_t)y * ld + x] = v;
+        } else if (kStep) {
+          fista_apply<R>(st, (int64_t)Y * ld + X, v, inv_l, thr, active);
+        } else {
+          coef[(int64_t)Y * ld + X] = v;
+        }
+      }
     }
-    out[(int64_t)k * ld + c] = a;
-    out[(int64_t)(half + k) * ld + c] = d;
   }
 }
 
-// synthesis (transpose of the analysis) along rows:
-// x[r][m] = sum_{i = m mod 2} h[i] a[r][((m-i) mod n)/2] + g[i] d[r][...]
+// Synthesis of one level: out (n x n, ld) from the LL block `llin` (ld) and
+// the detail subbands of `coef` (ld); a CTA owns a kTS x kTS output block.
+constexpr int kTS = 32;
 template <typename R>
-__global__ void k_idwt_rows(const R* __restrict__ c, R* __restrict__ out, int n, int ld) {
-  const int half = n / 2;
-  const int64_t tot = (int64_t)n * n;
-  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < tot; t += (int64_t)gridDim.x * blockDim.x) {
-    const int r = (int)(t / n), m = (int)(t - (int64_t)r * n);
-    const R* row = c + (int64_t)r * ld;
+__global__ void __launch_bounds__(256) k_idwt_level(const R* __restrict__ llin, const R* __restrict__ coef, int n,
+                                                    R* __restrict__ out, int ld) {
+  constexpr int RK = kTS / 2 + 4;
+  __shared__ R cq[4][RK][RK + 1];         // quadrant tiles: LL, row-high, col-high, HH
+  __shared__ R tr[2][RK][kTS + 1];        // after row synthesis: [column half][coef row][c]
+  const int h = n / 2;
+  const int m0 = blockIdx.y * kTS, c0 = blockIdx.x * kTS;
+  const int kb_m = (m0 >> 1) - 4, kb_c = (c0 >> 1) - 4;
+  for (int t = threadIdx.x; t < 4 * RK * RK; t += blockDim.x) {
+    const int q = t / (RK * RK), rem = t - q * RK * RK;
+    const int rk = rem / RK, ck = rem - rk * RK;
+    const int km = ((kb_m + rk) % h + h) % h, kc = ((kb_c + ck) % h + h) % h;
+    const int cy = q >> 1, cx = q & 1;
+    cq[q][rk][ck] = (q == 0) ? llin[(int64_t)km * ld + kc] : coef[(int64_t)(cy * h + km) * ld + (cx * h + kc)];
+  }
+  __syncthreads();
+  // rows: tr[cy][rk][c] = sum over the 4 taps of the parity of c
+  for (int t = threadIdx.x; t < 2 * RK * kTS; t += blockDim.x) {
+    const int cy = t / (RK * kTS), rem = t - cy * RK * kTS;
+    const int rk = rem / kTS, cl = rem - rk * kTS;
+    const int c = c0 + cl;
+    R v = R(0);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int i = 2 * j + (c & 1);
+      const int ck = ((c - i) >> 1) - kb_c;     // (c - i) even; floor division for negatives
+      v += db_h<R>(i) * cq[2 * cy][rk][ck] + db_g<R>(i) * cq[2 * cy + 1][rk][ck];
+    }
+    tr[cy][rk][cl] = v;
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < kTS * kTS; t += blockDim.x) {
+    const int ml = t / kTS, cl = t - ml * kTS;
+    const int m = m0 + ml, c = c0 + cl;
+    if (m >= n || c >= n) continue;
     R v = R(0);
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       const int i = 2 * j + (m & 1);
-      const int k = ((m - i) & (n - 1)) >> 1;
-      v += db_h<R>(i) * row[k] + db_g<R>(i) * row[half + k];
+      const int rk = ((m - i) >> 1) - kb_m;
+      v += db_h<R>(i) * tr[0][rk][cl] + db_g<R>(i) * tr[1][rk][cl];
     }
-    out[(int64_t)r * ld + m] = v;
+    out[(int64_t)m * ld + c] = v;
   }
 }
 
+// FISTA: a fused analysis of the gradient image g with the step on alpha / y.
+// la, lb: N x N scratch for the LL blocks between levels.
 template <typename R>
-__global__ void k_idwt_cols(const R* __restrict__ c, R* __restrict__ out, int n, int ld) {
-  const int half = n / 2;
-  const int64_t tot = (int64_t)n * n;
-  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < tot; t += (int64_t)gridDim.x * blockDim.x) {
-    const int m = (int)(t / n), col = (int)(t - (int64_t)m * n);
-    R v = R(0);
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const int i = 2 * j + (m & 1);
-      const int k = ((m - i) & (n - 1)) >> 1;
-      v += db_h<R>(i) * c[(int64_t)k * ld + col] + db_g<R>(i) * c[(int64_t)(half + k) * ld + col];
-    }
-    out[(int64_t)m * ld + col] = v;
-  }
-}
-
-template <typename R>
-__global__ void k_copy_block(const R* __restrict__ src, R* __restrict__ dst, int n, int ld) {
-  const int64_t tot = (int64_t)n * n;
-  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < tot; t += (int64_t)gridDim.x * blockDim.x) {
-    const int r = (int)(t / n), c = (int)(t - (int64_t)r * n);
-    dst[(int64_t)r * ld + c] = src[(int64_t)r * ld + c];
-  }
-}
-
-// x (N x N) -> wavelet coefficients in place (tmp: N x N scratch)
-template <typename R>
-int dwt2(const Ctx* ctx, R* x, R* tmp, int N, int levels, cudaStream_t st) {
-  for (int l = 0, n = N; l < levels; ++l, n >>= 1) {
-    ::rix::note_launch(); k_dwt_rows<R><<<blocks_for(ctx, (int64_t)n * n / 2), 256, 0, st>>>(x, tmp, n, N);
-    ::rix::note_launch(); k_dwt_cols<R><<<blocks_for(ctx, (int64_t)n * n / 2), 256, 0, st>>>(tmp, x, n, N);
+int dwt2_step(const Ctx* ctx, const R* g, R* la, R* lb, int N, int levels, StepArgs<R> st, cudaStream_t s) {
+  const R* src = g;
+  R* bufs[2] = {la, lb};
+  for (int l = 0; l < levels; ++l) {
+    const int n = N >> l, h = n / 2;
+    const int last = (l == levels - 1);
+    R* dst = bufs[l & 1];
+    dim3 grid((unsigned)ceil_div(h, kTB), (unsigned)ceil_div(h, kTB));
+    note_launch();
+    k_dwt_level<R, true><<<grid, 256, 0, s>>>(src, N, n, nullptr, dst, N, last, st);
+    src = dst;
   }
   RIX_LAUNCH_CHECK();
   return RIX_OK;
 }
 
-// coefficients c -> image out (c preserved; tmp: N x N scratch)
+// coefficients c (N x N) -> image out; tmp: N x N scratch.  Levels are
+// synthesised coarsest first, alternating out / tmp so the finest lands in out.
 template <typename R>
-int idwt2(const Ctx* ctx, const R* c, R* out, R* tmp, int N, int levels, cudaStream_t st) {
-  RIX_CUDA(cudaMemcpyAsync(out, c, (size_t)N * N * sizeof(R), cudaMemcpyDeviceToDevice, st));
+int idwt2(const Ctx* ctx, const R* c, R* out, R* tmp, int N, int levels, cudaStream_t s) {
+  const R* ll = c;
   for (int l = levels - 1; l >= 0; --l) {
     const int n = N >> l;
-    ::rix::note_launch(); k_idwt_cols<R><<<blocks_for(ctx, (int64_t)n * n), 256, 0, st>>>(out, tmp, n, N);
-    ::rix::note_launch(); k_idwt_rows<R><<<blocks_for(ctx, (int64_t)n * n), 256, 0, st>>>(tmp, out, n, N);
+    R* dst = ((l & 1) == 0) ? out : tmp;
+    dim3 grid((unsigned)ceil_div(n, kTS), (unsigned)ceil_div(n, kTS));
+    note_launch();
+    k_idwt_level<R><<<grid, 256, 0, s>>>(ll, c, n, dst, N);
+    ll = dst;
   }
   RIX_LAUNCH_CHECK();
   return RIX_OK;
 }
-
-// FISTA step in coefficient space (Beck & Teboulle 2009):
-//   a' = S_{lam/L}(y - g/L),  y = a' + mom (a' - a),  a = a'
-// L = 2 max Mx (state[0] holds max Mx); lam = lambda, or lambda_rel * state[1].
-template <typename R>
-__global__ void k_fista_step(R* __restrict__ alpha, R* __restrict__ y, const R* __restrict__ g, int64_t n,
-                             const R* __restrict__ state, double lambda, double lambda_rel, double mom) {
-  const double L = 2.0 * (double)state[0];
-  const double lam = lambda > 0.0 ? lambda : lambda_rel * (double)state[1];
-  const R inv_l = L > 0.0 ? (R)(1.0 / L) : R(0);
-  const R thr = L > 0.0 ? (R)(lam / L) : R(0);
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    const R z = y[i] - g[i] * inv_l;
-    const R az = fabs(z) - thr;
-    const R an = (L > 0.0 && az > R(0)) ? copysign(az, z) : R(0);
-    y[i] = an + (R)mom * (an - alpha[i]);
-    alpha[i] = an;
-  }
-}
-
-template <typename R>
-__global__ void k_set_scalar(R* p, R v) { *p = v; }
 
 }  // namespace
 
@@ -804,12 +844,10 @@ int op_fista(Job* job, int p, const rix_fista_params* prm, R* delta_out, cudaStr
       if ((rc = idwt2<R>(ctx, y, x, tmp, n, prm->levels, cs)) != RIX_OK) break;
       // grad f(x) = 2 crop F^-1 [Mx X - C]
       if ((rc = convolve<R>(job, pt, x, kOpAxpyReal, pt.fi_mx.p, pt.fi_c.p, g, gscale, 0, cs)) != RIX_OK) break;
-      if ((rc = dwt2<R>(ctx, g, tmp, n, prm->levels, cs)) != RIX_OK) break;
       const double tn = 0.5 * (1.0 + std::sqrt(1.0 + 4.0 * t * t));
-      const double mom = (t - 1.0) / tn;
-      note_launch();
-      k_fista_step<R><<<blocks_for(ctx, npix), 256, 0, cs>>>(alpha, y, g, npix, pt.fi_state.as<R>(), prm->lambda,
-                                                             prm->lambda_rel, mom);
+      StepArgs<R> sa{alpha, y, pt.fi_state.as<R>(), prm->lambda, prm->lambda_rel, (t - 1.0) / tn};
+      // W^T grad, fused with the thresholded, momentum-accelerated update
+      if ((rc = dwt2_step<R>(ctx, g, x, tmp, n, prm->levels, sa, cs)) != RIX_OK) break;
       t = tn;
     }
     cudaGraph_t graph = nullptr;
