@@ -234,6 +234,32 @@ int rix_get_model(rix_job_t job, int part, void* image_out, rix_stream_t stream)
  * (0.5 / 0.5 for two partitions), device N x N. */
 int rix_combine(rix_job_t job, void* image_out, rix_stream_t stream);
 
+/* ---- gridding without device allocation ----------------------------------- */
+
+/* rix_grid for callers that cannot allocate device memory while they grid:
+ * a host loop with a latency budget that must not stall on the allocator
+ * (cudaMalloc and cudaFree can synchronise the device), a process whose
+ * device memory another allocator has already reserved, or a host program
+ * that does not let a library own device allocations.  The paper has no
+ * counterpart; this is a deployment variant of rix_grid.
+ *
+ * Same arguments, layout and result as rix_grid (FP32 jobs only).  The
+ * partition's w-planes and transpose buffer live in one scratch area of
+ * RIX_GRID_NOALLOC_MAX_BYTES compiled into the library as a device array:
+ * every GPU that loads the library holds it until the process exits.  A
+ * partition needing more (n_wplanes * S * (S + N) * 8 bytes, S = its uv
+ * window side from rix_job_get_stats) is rejected with RIX_EINVAL.  The call
+ * allocates no device memory; it zeroes the part of the scratch it
+ * accumulates into, so each call starts clean, but all calls share the one
+ * scratch: calls whose GPU work overlaps in time (other streams, other
+ * threads, other jobs) race and corrupt each other's results.  The first
+ * call on a device looks up the scratch's device address (once per device,
+ * with that device current); make that first call before any stream
+ * capture.  The job itself (rix_job_create, rix_set_uv_partition) is set up
+ * beforehand as usual. */
+#define RIX_GRID_NOALLOC_MAX_BYTES (32u << 20)
+int rix_grid_noalloc(rix_job_t job, int part, const void* vis, void* image_out, rix_stream_t stream);
+
 /* Thread-local message of the last failed call on this thread. */
 const char* rix_last_error(void);
 

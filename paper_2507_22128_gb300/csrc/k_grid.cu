@@ -821,6 +821,36 @@ int op_psf(Job* job, int p, cudaStream_t st) {
   return rc;
 }
 
+// Gridding of partition p (as op_grid) with its w-planes and transpose buffer
+// in caller-provided device scratch instead of the job's own buffers; FP32
+// jobs.  Returns RIX_EINVAL when the scratch is too small.
+int op_grid_into_scratch(Job* job, int p, const float2* vis, float* image_out, float2* scratch,
+                         size_t scratch_elems, cudaStream_t st) {
+  Part& pt = job->part[p];
+  const int n = job->desc.n;
+  if (pt.ent_count == 0) {
+    RIX_CUDA(cudaMemsetAsync(image_out, 0, (size_t)n * n * sizeof(float), st));
+    return RIX_OK;
+  }
+  const size_t np = job->nw > 0 ? (size_t)job->nw : 1;
+  const size_t plane_elems = np * pt.win_n * pt.win_n;
+  const size_t t_elems = np * pt.win_n * n;
+  if (plane_elems + t_elems > scratch_elems)
+    return set_error(RIX_EINVAL, "partition %d needs %zu bytes of scratch, the fixed scratch holds %zu", p,
+                     (plane_elems + t_elems) * sizeof(float2), scratch_elems * sizeof(float2));
+  float2* planes = scratch;
+  float2* tbuf = scratch + plane_elems;
+  RIX_CUDA(cudaMemsetAsync(planes, 0, plane_elems * sizeof(float2), st));   // the sub-grids accumulate
+  TileArgs a = base_args(job, pt);
+  a.out = planes;
+  a.vis_in = vis;
+  RIX_TRY(launch_tiles<float, kGrid>(job, a, st));
+  const XformGeom g = plane_geom(job, pt, false);
+  RIX_TRY(inv_cols<float>(job->ctx, g, planes, kOpNone, nullptr, nullptr, tbuf, st));
+  const double sc = pt.wsum > 0.0 ? 1.0 / pt.wsum : 0.0;
+  return inv_rows<float>(job->ctx, g, tbuf, image_out, sc, 0, st);
+}
+
 #define RIX_GRID_INST(R)                                                               \
   template int grid_build_corrections<R>(Job*, cudaStream_t);                          \
   template int op_degrid<R>(Job*, int, const R*, cplx<R>*, cudaStream_t);              \

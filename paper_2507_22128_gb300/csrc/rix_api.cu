@@ -152,6 +152,8 @@ static void reset_partitions(Job* job) {
   }
 }
 
+Job* job_of(rix_job_t job) { return &job->j; }
+
 }  // namespace rix
 
 using namespace rix;

@@ -246,6 +246,9 @@ int op_major(Job* job, int p, const cplx<R>* vis, R* residual, cudaStream_t st);
 template <typename R>
 int op_psf(Job* job, int p, cudaStream_t st);
 
+int op_grid_into_scratch(Job* job, int p, const float2* vis, float* image_out, float2* scratch,
+                         size_t scratch_elems, cudaStream_t st);
+
 // partition entry point (k_partition.cu)
 int partition_job(Job* job, const double* uvw, int64_t nrow, const float* weight,
                   const double* ell_px, double delta, uint8_t* mask_out, cudaStream_t st);

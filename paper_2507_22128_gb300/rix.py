@@ -67,6 +67,7 @@ def _load() -> C.CDLL:
         "rix_get_sorted_entries": (C.c_int, [vp, vp, vp, vp]),
         "rix_degrid": (C.c_int, [vp, C.c_int, vp, vp, vp]),
         "rix_grid": (C.c_int, [vp, C.c_int, vp, vp, vp]),
+        "rix_grid_noalloc": (C.c_int, [vp, C.c_int, vp, vp, vp]),
         "rix_psf": (C.c_int, [vp, C.c_int, vp, C.POINTER(dbl), vp]),
         "rix_major_cycle": (C.c_int, [vp, C.c_int, vp, vp, vp, vp]),
         "rix_minor_cycle_msclean": (C.c_int, [vp, C.c_int, C.POINTER(MscleanParams), vp, vp]),
@@ -92,7 +93,7 @@ EXPORTED = ("rix_create", "rix_destroy", "rix_job_workspace_bytes", "rix_job_cre
             "rix_job_sync", "rix_job_get_stats", "rix_set_uv_partition", "rix_get_sorted_entries",
             "rix_degrid", "rix_grid", "rix_psf", "rix_major_cycle", "rix_minor_cycle_msclean",
             "rix_minor_cycle_fista", "rix_get_components", "rix_get_model", "rix_combine", "rix_last_error",
-            "rix_kernel_launches", "rix_timing_enable", "rix_timing_read")
+            "rix_kernel_launches", "rix_timing_enable", "rix_timing_read", "rix_grid_noalloc")
 
 
 def _check(rc: int):
@@ -201,6 +202,13 @@ def degrid(job, part, image, vis_out, stream=None):
 def grid(job, part, vis, image_out, stream=None):
     _check(_lib.rix_grid(job, part, _ptr(vis, _CT, name="vis"), _ptr(image_out, _RT, name="image_out"),
                          _stream(stream)))
+
+
+def grid_noalloc(job, part, vis, image_out, stream=None):
+    """rix_grid with its scratch in the library's fixed device array (no
+    device allocation at call time; FP32 jobs; overlapping calls race)."""
+    _check(_lib.rix_grid_noalloc(job, part, _ptr(vis, torch.complex64, name="vis"),
+                                 _ptr(image_out, torch.float32, name="image_out"), _stream(stream)))
 
 
 def psf(job, part, psf_out=None, stream=None) -> float:
