@@ -49,6 +49,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-phases", action="store_true")
+    ap.add_argument("--serve-jobs", type=int, default=24, help="arrivals in the serving experiment (0 = skip)")
+    ap.add_argument("--serve-rate", type=float, default=20.0, help="Poisson arrival rate, jobs/s")
     ap.add_argument("--json-out", default=None)
     return ap.parse_args()
 
@@ -289,6 +291,8 @@ def main():
             "roofline": roof, "phases_ms": phases,
             "kernel_ms_per_step": {"grid_tiles": tiles_ms / a.steps, "fft_passes_outside_graphs": fft_ms / a.steps},
             "samples_per_cycle": int(sum(st["part_count"][:2])), "step_ms": step_ms}
+    if a.serve_jobs > 0:
+        line["serving"] = serving_experiment(ctx, a, rank)
     if rank == 0 and not a.no_cpu_baseline:
         cb = cpu_baseline(a)
         line["cpu_baseline"] = {"value": cb["value"], "unit": UNIT, "cores": cb["cores"], "kind": "oracle",
@@ -301,6 +305,32 @@ def main():
             with open(a.json_out, "w") as f:
                 json.dump(line, f, indent=1)
     return 0
+
+
+def serving_experiment(ctx, a, rank):
+    """Continuous-batching run: Poisson arrivals of a job mix, p50/p99 latency."""
+    from paper_2507_22128_gb300 import pipeline, serve, synth
+    rng = np.random.default_rng(4 + rank)
+    kinds = [
+        ("small 128^2 coplanar ms-CLEAN 5 cycles", 0.5, synth.plain_small(seed=100),
+         pipeline.Method("msclean", (0.0, 3.0, 9.0), 0.1, 500, 1e-4), 5),
+        ("medium 1024^2 16 w-planes 2.0 M vis FISTA 10 cycles", 0.3, synth.medium(seed=101, n_times=250),
+         pipeline.Method("fista", lam_rel=1e-3, iters=50, levels=4), 10),
+        ("chunk 512^2 16 w-planes 1.0 M vis FISTA 5 cycles", 0.2, synth.medium(seed=102, n_times=125, n=512),
+         pipeline.Method("fista", lam_rel=1e-3, iters=50, levels=4), 5),
+    ]
+    probs = np.array([k[1] for k in kinds])
+    arrivals = serve.poisson_arrivals(rng, a.serve_jobs, a.serve_rate)
+    picks = rng.choice(len(kinds), a.serve_jobs, p=probs / probs.sum())
+    reqs = [serve.Request(i, kinds[k][2], kinds[k][3], kinds[k][4], arrival=float(t))
+            for i, (k, t) in enumerate(zip(picks, arrivals))]
+    torch.cuda.synchronize()
+    serve.serve(ctx, reqs, n_slots=4)
+    out = serve.summary(reqs)
+    out.update({"arrival_rate_per_s": a.serve_rate, "slots": 4,
+                "mix": {k[0]: int((picks == i).sum()) for i, k in enumerate(kinds)},
+                "offered_jobs_per_s": a.serve_jobs / float(arrivals[-1])})
+    return out
 
 
 def phase_split(rec, rix, a, meth, stream, uvw, vis, w, out, flush):

@@ -126,9 +126,12 @@ size_t rix_job_workspace_bytes(const rix_job_desc* desc, int64_t nrow);
 /* Validates desc and creates an empty job; RIX_ENOMEM if the context budget
  * cannot admit rix_job_workspace_bytes(desc, max_rows). */
 int rix_job_create(rix_ctx_t ctx, const rix_job_desc* desc, int64_t max_rows, rix_job_t* job);
+/* Waits for the work the job's calls issued (on every stream they used, not
+ * for other jobs), then releases the job's device memory without
+ * synchronising the device. */
 int rix_job_destroy(rix_job_t job);
-/* Blocks until all work issued on the job has finished; reports deferred
- * device errors (RIX_ETIMEOUT for an expired bounded wait). */
+/* Blocks until the work issued by the job's calls has finished (other jobs'
+ * work is not waited for) and reports deferred device errors. */
 int rix_job_sync(rix_job_t job);
 int rix_job_get_stats(rix_job_t job, rix_job_stats* out);
 

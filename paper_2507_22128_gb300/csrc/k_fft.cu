@@ -296,7 +296,7 @@ __device__ __forceinline__ cplx<R> wscreen(double wp, double nm1) {
 }
 
 struct KArgs {
-  int M, L, logL, lo, S, nplanes, mode, B, stride;
+  int M, L, logL, lo, S, nplanes, mode, B, stride, herm;
   const void* corr;
   const double* nm1;
   double w0, dw;
@@ -373,6 +373,19 @@ __global__ void __launch_bounds__(kFftThreads, (VPT == 0 && sizeof(R) == 4) ? 4 
       const int r = idx % a.B, j = idx / a.B;
       const int b = b0 + r, col = a.lo + j;
       if (b < M && col < L) s[r * a.stride + padi(col)] = Tp[(int64_t)j * M + b];
+    }
+    if (a.herm) {
+      // real output: the window holds k_u in [-L/2, 0] (columns 0 .. L/2);
+      // column c > L/2 (k_u > 0) is the conjugate of column L - c
+      for (int idx = threadIdx.x; idx < a.B * (L - a.S); idx += kFftThreads) {
+        const int r = idx % a.B, c = a.S + idx / a.B;
+        const int b = b0 + r;
+        if (b < M) {
+          C v = Tp[(int64_t)(L - c) * M + b];
+          v.y = -v.y;
+          s[r * a.stride + padi(c)] = v;
+        }
+      }
     }
     __syncthreads();
     const C* res = fft_any<R, VPT, +1>(s, s2, a.B, a.logL, a.stride, tw);
@@ -505,7 +518,7 @@ __global__ void __launch_bounds__(kFftThreads, (VPT == 0 && sizeof(R) == 4) ? 4 
     const int j = j0 + r;
     if (j < a.S) {
       C* e = &res[r * a.stride + padi(c)];
-      *e = spec_op<R>(op, *e, tab, tab2, (int64_t)j * a.S + c);
+      *e = spec_op<R>(op, *e, tab, tab2, (int64_t)j * a.L + c);
     }
   }
   __syncthreads();
@@ -525,7 +538,7 @@ template <typename R>
 KArgs make_args(const XformGeom& g, int B) {
   KArgs a{};
   a.M = g.M; a.L = g.L; a.logL = g.logL; a.lo = g.lo; a.S = g.S; a.nplanes = g.nplanes;
-  a.mode = g.mode; a.B = B; a.stride = padded_len(g.L);
+  a.mode = g.mode; a.B = B; a.stride = padded_len(g.L); a.herm = g.herm;
   a.corr = g.corr; a.nm1 = g.nm1; a.w0 = g.w0; a.dw = g.dw;
   return a;
 }
@@ -632,7 +645,7 @@ template <typename R>
 int conv_cols(const Ctx* ctx, const XformGeom& g, const cplx<R>* Tin, int op, const void* tab,
               const void* tab2, cplx<R>* Tout, cudaStream_t st) {
   RIX_TRY(check_geom<R>(g));
-  if (g.lo != 0 || g.S != g.L || g.nplanes != 1) return set_error(RIX_EINVAL, "conv_cols needs the full window");
+  if (g.lo != 0 || g.S > g.L || g.nplanes != 1) return set_error(RIX_EINVAL, "conv_cols needs a window starting at 0");
   RIX_FFT_LAUNCH(k_conv_cols, g.S, 1, Tin, op, tab, tab2, Tout, twiddles<R>(ctx));
   return RIX_OK;
 }

@@ -45,10 +45,16 @@ int spec_to_img(Job* job, Part& pt, const cplx<R>* spec, int op, const void* tab
 
 // out (+)= scale * crop F^-1 [op(F pad x)]   (three passes; the spectral op is
 // fused between the forward and inverse column transforms)
+// The image and the result are real and every spectral operator used here
+// preserves Hermitian symmetry, so only the columns k_u in [-N, 0] of the
+// spectrum are formed and transformed; the inverse row pass completes the
+// others by conjugation.
 template <typename R>
 int convolve(Job* job, Part& pt, const R* x, int op, const void* tab, const void* tab2, R* out, double scale,
              int accumulate, cudaStream_t st) {
-  const XformGeom g = fill_geom(job->desc.n);
+  XformGeom g = fill_geom(job->desc.n);
+  g.S = job->desc.n + 1;
+  g.herm = 1;
   RIX_TRY(fwd_rows<R>(job->ctx, g, x, pt.ft_a.as<cplx<R>>(), st));
   RIX_TRY(conv_cols<R>(job->ctx, g, pt.ft_a.as<cplx<R>>(), op, tab, tab2, pt.ft_b.as<cplx<R>>(), st));
   return inv_rows<R>(job->ctx, g, pt.ft_b.as<cplx<R>>(), out, scale, accumulate, st);

@@ -63,15 +63,19 @@ void timing_mark(int cls, cudaStream_t st, bool begin) {
   }
 }
 
+// Buffers come from the stream-ordered pool on the context's private stream:
+// allocation waits for that stream only, and release (cudaFreeAsync) never
+// synchronises the device, so tearing down one job does not stall others.
 int DevBuf::alloc(Ctx* ctx, size_t nbytes) {
   if (nbytes == 0) nbytes = 16;
   if (p && bytes >= nbytes) return RIX_OK;   // reuse: re-partitioning a job keeps its buffers
   release();
   void* q = nullptr;
-  cudaError_t e = cudaMalloc(&q, nbytes);
+  cudaError_t e = cudaMallocAsync(&q, nbytes, ctx->mem_stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->mem_stream);
   if (e != cudaSuccess) {
     cudaGetLastError();
-    return set_error(RIX_ENOMEM, "cudaMalloc(%zu): %s", nbytes, cudaGetErrorString(e));
+    return set_error(RIX_ENOMEM, "device allocation of %zu bytes: %s", nbytes, cudaGetErrorString(e));
   }
   p = q;
   bytes = nbytes;
@@ -80,9 +84,22 @@ int DevBuf::alloc(Ctx* ctx, size_t nbytes) {
 }
 
 void DevBuf::release() {
-  if (p) cudaFree(p);
+  if (p) cudaFreeAsync(p, owner->mem_stream);
   p = nullptr;
   bytes = 0;
+}
+
+int note_stream(Job* job, cudaStream_t st) {
+  for (auto& pr : job->touched)
+    if (pr.first == st) {
+      RIX_CUDA(cudaEventRecord(pr.second, st));
+      return RIX_OK;
+    }
+  cudaEvent_t ev;
+  RIX_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+  job->touched.push_back({st, ev});
+  RIX_CUDA(cudaEventRecord(ev, st));
+  return RIX_OK;
 }
 
 // upper bound of resident device bytes of a job (admission control)
@@ -208,6 +225,10 @@ int rix_create(rix_ctx_t* ctx, int device, size_t mem_budget_bytes) {
     return set_error(RIX_ECUDA, "cudaGetDeviceProperties");
   }
   c->c.num_sms = prop.multiProcessorCount;
+  if (cudaStreamCreateWithFlags(&c->c.mem_stream, cudaStreamNonBlocking) != cudaSuccess) {
+    delete c;
+    return set_error(RIX_ECUDA, "stream creation");
+  }
   int rc = fft_init_twiddles(&c->c);
   if (rc != RIX_OK) {
     delete c;
@@ -221,6 +242,10 @@ int rix_destroy(rix_ctx_t ctx) {
   if (!ctx) return RIX_OK;
   if (ctx->c.jobs > 0) return set_error(RIX_EBUSY, "context still owns %d jobs", ctx->c.jobs);
   cudaSetDevice(ctx->c.device);
+  ctx->c.tw32.release();
+  ctx->c.tw64.release();
+  cudaStreamSynchronize(ctx->c.mem_stream);
+  cudaStreamDestroy(ctx->c.mem_stream);
   delete ctx;
   return RIX_OK;
 }
@@ -278,7 +303,12 @@ int rix_job_destroy(rix_job_t job) {
   if (!job) return RIX_OK;
   Job& J = job->j;
   cudaSetDevice(J.ctx->device);
-  cudaDeviceSynchronize();
+  // wait for this job's own work only (other jobs keep running)
+  for (auto& pr : J.touched) {
+    cudaEventSynchronize(pr.second);
+    cudaEventDestroy(pr.second);
+  }
+  J.touched.clear();
   for (int p = 0; p < kMaxPart; ++p) {
     if (J.part[p].ev_minor) cudaEventDestroy(J.part[p].ev_minor);
     if (J.part[p].fista_exec) cudaGraphExecDestroy(J.part[p].fista_exec);
@@ -293,7 +323,8 @@ int rix_job_destroy(rix_job_t job) {
 int rix_job_sync(rix_job_t job) {
   if (!job) return set_error(RIX_EINVAL, "job is NULL");
   RIX_CUDA(cudaSetDevice(job->j.ctx->device));
-  RIX_CUDA(cudaDeviceSynchronize());
+  for (auto& pr : job->j.touched) RIX_CUDA(cudaEventSynchronize(pr.second));
+  RIX_CUDA(cudaGetLastError());
   return RIX_OK;
 }
 
@@ -304,7 +335,7 @@ int rix_job_get_stats(rix_job_t job, rix_job_stats* out) {
   return RIX_OK;
 }
 
-int rix_set_uv_partition(rix_job_t job, const double* uvw_m, int64_t nrow, const float* weight,
+static int rix_set_uv_partition_impl(rix_job_t job, const double* uvw_m, int64_t nrow, const float* weight,
                          const double* ell_px, double delta_px, uint8_t* mask_out, rix_stream_t stream) {
   if (!job) return set_error(RIX_EINVAL, "job is NULL");
   Job& J = job->j;
@@ -324,7 +355,7 @@ int rix_set_uv_partition(rix_job_t job, const double* uvw_m, int64_t nrow, const
   return RIX_OK;
 }
 
-int rix_get_sorted_entries(rix_job_t job, uint32_t* keys_out, uint32_t* samples_out, rix_stream_t stream) {
+static int rix_get_sorted_entries_impl(rix_job_t job, uint32_t* keys_out, uint32_t* samples_out, rix_stream_t stream) {
   if (!job) return set_error(RIX_EINVAL, "job is NULL");
   Job& J = job->j;
   if (!J.partitioned) return set_error(RIX_ESTATE, "not partitioned");
@@ -335,7 +366,7 @@ int rix_get_sorted_entries(rix_job_t job, uint32_t* keys_out, uint32_t* samples_
   return RIX_OK;
 }
 
-int rix_degrid(rix_job_t job, int part, const void* image, void* vis_out, rix_stream_t stream) {
+static int rix_degrid_impl(rix_job_t job, int part, const void* image, void* vis_out, rix_stream_t stream) {
   if (!job) return set_error(RIX_EINVAL, "job is NULL");
   Job& J = job->j;
   RIX_TRY(check_part(&J, part));
@@ -346,7 +377,7 @@ int rix_degrid(rix_job_t job, int part, const void* image, void* vis_out, rix_st
   return op_degrid<float>(&J, part, (const float*)image, (float2*)vis_out, st);
 }
 
-int rix_grid(rix_job_t job, int part, const void* vis, void* image_out, rix_stream_t stream) {
+static int rix_grid_impl(rix_job_t job, int part, const void* vis, void* image_out, rix_stream_t stream) {
   if (!job) return set_error(RIX_EINVAL, "job is NULL");
   Job& J = job->j;
   RIX_TRY(check_part(&J, part));
@@ -363,7 +394,7 @@ static int ensure_psf(Job& J, int part, cudaStream_t st) {
   return op_psf<float>(&J, part, st);
 }
 
-int rix_psf(rix_job_t job, int part, void* psf_out, double* weight_sum_out, rix_stream_t stream) {
+static int rix_psf_impl(rix_job_t job, int part, void* psf_out, double* weight_sum_out, rix_stream_t stream) {
   if (!job) return set_error(RIX_EINVAL, "job is NULL");
   Job& J = job->j;
   RIX_TRY(check_part(&J, part));
@@ -378,7 +409,7 @@ int rix_psf(rix_job_t job, int part, void* psf_out, double* weight_sum_out, rix_
   return RIX_OK;
 }
 
-int rix_major_cycle(rix_job_t job, int part, const void* vis_obs, const void* model, void* residual_out,
+static int rix_major_cycle_impl(rix_job_t job, int part, const void* vis_obs, const void* model, void* residual_out,
                     rix_stream_t stream) {
   if (!job) return set_error(RIX_EINVAL, "job is NULL");
   Job& J = job->j;
@@ -415,7 +446,7 @@ static int minor_precheck(Job& J, int part, cudaStream_t st) {
   return RIX_OK;
 }
 
-int rix_minor_cycle_msclean(rix_job_t job, int part, const rix_msclean_params* prm, void* delta_out,
+static int rix_minor_cycle_msclean_impl(rix_job_t job, int part, const rix_msclean_params* prm, void* delta_out,
                             rix_stream_t stream) {
   if (!job || !prm) return set_error(RIX_EINVAL, "NULL argument");
   Job& J = job->j;
@@ -435,7 +466,7 @@ int rix_minor_cycle_msclean(rix_job_t job, int part, const rix_msclean_params* p
   return RIX_OK;
 }
 
-int rix_minor_cycle_fista(rix_job_t job, int part, const rix_fista_params* prm, void* delta_out,
+static int rix_minor_cycle_fista_impl(rix_job_t job, int part, const rix_fista_params* prm, void* delta_out,
                           rix_stream_t stream) {
   if (!job || !prm) return set_error(RIX_EINVAL, "NULL argument");
   Job& J = job->j;
@@ -460,7 +491,7 @@ int rix_get_components(rix_job_t job, int part, int32_t* count, int32_t capacity
   return get_components(&job->j, part, count, capacity, scale_out, pixel_out, amp_out, (cudaStream_t)stream);
 }
 
-int rix_get_model(rix_job_t job, int part, void* image_out, rix_stream_t stream) {
+static int rix_get_model_impl(rix_job_t job, int part, void* image_out, rix_stream_t stream) {
   if (!job || !image_out) return set_error(RIX_EINVAL, "NULL argument");
   Job& J = job->j;
   RIX_TRY(check_part(&J, part));
@@ -472,7 +503,7 @@ int rix_get_model(rix_job_t job, int part, void* image_out, rix_stream_t stream)
   return RIX_OK;
 }
 
-int rix_combine(rix_job_t job, void* image_out, rix_stream_t stream) {
+static int rix_combine_impl(rix_job_t job, void* image_out, rix_stream_t stream) {
   if (!job || !image_out) return set_error(RIX_EINVAL, "NULL argument");
   Job& J = job->j;
   if (!J.partitioned) return set_error(RIX_ESTATE, "not partitioned");
@@ -484,4 +515,48 @@ int rix_combine(rix_job_t job, void* image_out, rix_stream_t stream) {
   return op_combine<float>(&J, (float*)image_out, st);
 }
 
+// ---- public wrappers: run the call, then note the stream the job used ----
+#define RIX_NOTE(job, stream, call)                                           \
+  do {                                                                        \
+    const int rc_ = (call);                                                   \
+    if (job && rc_ == RIX_OK) return ::rix::note_stream(&job->j, (cudaStream_t)stream); \
+    return rc_;                                                               \
+  } while (0)
+
+int rix_set_uv_partition(rix_job_t job, const double* uvw_m, int64_t nrow, const float* weight,
+                         const double* ell_px, double delta_px, uint8_t* mask_out, rix_stream_t stream) {
+  RIX_NOTE(job, stream, rix_set_uv_partition_impl(job, uvw_m, nrow, weight, ell_px, delta_px, mask_out, stream));
+}
+int rix_get_sorted_entries(rix_job_t job, uint32_t* keys_out, uint32_t* samples_out, rix_stream_t stream) {
+  RIX_NOTE(job, stream, rix_get_sorted_entries_impl(job, keys_out, samples_out, stream));
+}
+int rix_degrid(rix_job_t job, int part, const void* image, void* vis_out, rix_stream_t stream) {
+  RIX_NOTE(job, stream, rix_degrid_impl(job, part, image, vis_out, stream));
+}
+int rix_grid(rix_job_t job, int part, const void* vis, void* image_out, rix_stream_t stream) {
+  RIX_NOTE(job, stream, rix_grid_impl(job, part, vis, image_out, stream));
+}
+int rix_psf(rix_job_t job, int part, void* psf_out, double* weight_sum_out, rix_stream_t stream) {
+  RIX_NOTE(job, stream, rix_psf_impl(job, part, psf_out, weight_sum_out, stream));
+}
+int rix_major_cycle(rix_job_t job, int part, const void* vis_obs, const void* model, void* residual_out,
+                    rix_stream_t stream) {
+  RIX_NOTE(job, stream, rix_major_cycle_impl(job, part, vis_obs, model, residual_out, stream));
+}
+int rix_minor_cycle_msclean(rix_job_t job, int part, const rix_msclean_params* prm, void* delta_out,
+                            rix_stream_t stream) {
+  RIX_NOTE(job, stream, rix_minor_cycle_msclean_impl(job, part, prm, delta_out, stream));
+}
+int rix_minor_cycle_fista(rix_job_t job, int part, const rix_fista_params* prm, void* delta_out,
+                          rix_stream_t stream) {
+  RIX_NOTE(job, stream, rix_minor_cycle_fista_impl(job, part, prm, delta_out, stream));
+}
+int rix_get_model(rix_job_t job, int part, void* image_out, rix_stream_t stream) {
+  RIX_NOTE(job, stream, rix_get_model_impl(job, part, image_out, stream));
+}
+int rix_combine(rix_job_t job, void* image_out, rix_stream_t stream) {
+  RIX_NOTE(job, stream, rix_combine_impl(job, image_out, stream));
+}
+
 }  // extern "C"
+

@@ -100,6 +100,7 @@ struct Ctx {
   size_t reserved = 0;        // sum of admitted job workspaces
   int jobs = 0;
   int num_sms = 0;
+  cudaStream_t mem_stream = nullptr;   // stream-ordered allocation and release
   DevBuf tw32, tw64;          // FFT twiddle tables, length kTwMax
 };
 
@@ -124,6 +125,7 @@ struct XformGeom {
   const void* corr;            // Real [M][M] or null
   const double* nm1;           // double [M][M]: n - 1 per pixel (kFacPhase)
   double w0, dw;               // plane p sits at w0 + p * dw (kFacPhase)
+  int herm = 0;                // inverse rows: complete columns [S, L) by conjugate symmetry
 };
 
 template <typename R>
@@ -232,7 +234,12 @@ struct Job {
   int n_part = 1;
   cudaEvent_t ev_tmp = nullptr;
   cudaStream_t capture_stream = nullptr;    // private stream for graph capture
+  // streams the job's calls ran on, each with an event recorded after the call
+  std::vector<std::pair<cudaStream_t, cudaEvent_t>> touched;
 };
+
+// records that `st` carries work of `job` (for rix_job_destroy)
+int note_stream(Job* job, cudaStream_t st);
 
 // gridder entry points (k_grid.cu)
 template <typename R>
