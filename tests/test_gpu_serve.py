@@ -10,11 +10,17 @@ pytestmark = pytest.mark.gpu
 
 
 def _reqs(obs_small, obs_wstack, base_id=0, arrivals=(0.0, 0.0, 0.0, 0.0)):
-    from paper_2507_22128_gb300 import pipeline, serve
+    """Request 0: FP64 ms-CLEAN; 1: FP32 FISTA; 2, 3: FP32 jobs that share the device.
+    Greedy CLEAN can flip a near-tie under the last-bit differences of the
+    gridder's cross-tile float atomics, so its alone/mix identity is checked
+    in FP64; FISTA is continuous in its inputs and is checked in FP32."""
+    from paper_2507_22128_gb300 import pipeline, rix, serve
     ms = pipeline.Method("msclean", (0.0, 3.0, 9.0), 0.1, 200, 1e-4)
     fi = pipeline.Method("fista", lam_rel=1e-3, iters=10, levels=3)
-    kinds = [(obs_small, ms, 3), (obs_wstack, fi, 2), (obs_small, ms, 2), (obs_wstack, fi, 3)]
-    return [serve.Request(base_id + i, o, m, nm, arrival=a) for i, ((o, m, nm), a) in enumerate(zip(kinds, arrivals))]
+    kinds = [(obs_small, ms, 3, rix.FP64), (obs_wstack, fi, 2, rix.FP32), (obs_small, ms, 2, rix.FP32),
+             (obs_wstack, fi, 3, rix.FP32)]
+    return [serve.Request(base_id + i, o, m, nm, arrival=a, precision=pr)
+            for i, ((o, m, nm, pr), a) in enumerate(zip(kinds, arrivals))]
 
 
 def test_same_result_alone_and_in_the_mix(obs_small, obs_wstack):
@@ -26,7 +32,7 @@ def test_same_result_alone_and_in_the_mix(obs_small, obs_wstack):
         mix = serve.serve(ctx, _reqs(obs_small, obs_wstack, 10, arrivals=(0.0, 0.001, 0.002, 0.003)), n_slots=4)
         assert all(np.isfinite(q.image).all() for q in mix)
         # request 0 (ms-CLEAN) and 1 (FISTA) are the same jobs as the ones run alone
-        assert rel_l2(mix[0].image, alone[0]) < 1e-5
+        assert rel_l2(mix[0].image, alone[0]) < 1e-9
         assert rel_l2(mix[1].image, alone[1]) < 1e-5
         # the jobs overlapped on the device: later arrivals were admitted before earlier ones finished
         assert mix[1].t_admit < mix[0].t_done
