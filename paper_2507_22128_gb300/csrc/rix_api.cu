@@ -286,7 +286,9 @@ int rix_job_create(rix_ctx_t ctx, const rix_job_desc* desc, int64_t max_rows, ri
                                  cudaMemcpyHostToDevice) != cudaSuccess)
     rc = set_error(RIX_ECUDA, "frequency upload");
   for (int p = 0; rc == RIX_OK && p < kMaxPart; ++p)
-    if (cudaEventCreateWithFlags(&J.part[p].ev_minor, cudaEventDisableTiming) != cudaSuccess)
+    if (cudaEventCreateWithFlags(&J.part[p].ev_minor[0], cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&J.part[p].ev_minor[1], cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&J.part[p].ev_psf, cudaEventDisableTiming) != cudaSuccess)
       rc = set_error(RIX_ECUDA, "event creation");
   if (rc != RIX_OK) {
     delete js;
@@ -310,7 +312,9 @@ int rix_job_destroy(rix_job_t job) {
   }
   J.touched.clear();
   for (int p = 0; p < kMaxPart; ++p) {
-    if (J.part[p].ev_minor) cudaEventDestroy(J.part[p].ev_minor);
+    for (int k = 0; k < 2; ++k)
+      if (J.part[p].ev_minor[k]) cudaEventDestroy(J.part[p].ev_minor[k]);
+    if (J.part[p].ev_psf) cudaEventDestroy(J.part[p].ev_psf);
     if (J.part[p].fista_exec) cudaGraphExecDestroy(J.part[p].fista_exec);
   }
   if (J.capture_stream) cudaStreamDestroy(J.capture_stream);
@@ -388,10 +392,17 @@ static int rix_grid_impl(rix_job_t job, int part, const void* vis, void* image_o
   return op_grid<float>(&J, part, (const float2*)vis, (float*)image_out, st);
 }
 
+// Computes the partition's PSF once (on `st`) and makes `st` wait for it,
+// whichever stream computed it.
 static int ensure_psf(Job& J, int part, cudaStream_t st) {
-  if (J.part[part].psf_ready) return RIX_OK;
-  if (J.fp64) return op_psf<double>(&J, part, st);
-  return op_psf<float>(&J, part, st);
+  Part& pt = J.part[part];
+  if (!pt.psf_ready) {
+    if (J.fp64) RIX_TRY(op_psf<double>(&J, part, st));
+    else RIX_TRY(op_psf<float>(&J, part, st));
+    RIX_CUDA(cudaEventRecord(pt.ev_psf, st));
+  }
+  RIX_CUDA(cudaStreamWaitEvent(st, pt.ev_psf, 0));
+  return RIX_OK;
 }
 
 static int rix_psf_impl(rix_job_t job, int part, void* psf_out, double* weight_sum_out, rix_stream_t stream) {
@@ -421,7 +432,7 @@ static int rix_major_cycle_impl(rix_job_t job, int part, const void* vis_obs, co
   cudaStream_t st = (cudaStream_t)stream;
   const size_t img = (size_t)J.desc.n * J.desc.n * (J.fp64 ? 8 : 4);
   // order after this partition's previous minor cycle, whatever stream it used
-  if (pt.minor_done > 0) RIX_CUDA(cudaStreamWaitEvent(st, pt.ev_minor, 0));
+  if (pt.minor_done > 0) RIX_CUDA(cudaStreamWaitEvent(st, pt.ev_minor[pt.minor_done & 1], 0));
   if (model) RIX_CUDA(cudaMemcpyAsync(pt.model.p, model, img, cudaMemcpyDeviceToDevice, st));
   if (J.fp64) RIX_TRY(op_major<double>(&J, part, (const double2*)vis_obs, pt.resid.as<double>(), st));
   else RIX_TRY(op_major<float>(&J, part, (const float2*)vis_obs, pt.resid.as<float>(), st));
@@ -440,7 +451,9 @@ static int minor_precheck(Job& J, int part, cudaStream_t st) {
     if (q == part) continue;
     if (J.part[q].minor_done < n - 1)
       return set_error(RIX_ESTATE, "partition %d cycle %d needs partition %d's minor cycle %d", part, n, q, n - 1);
-    if (J.part[q].minor_done > 0) RIX_CUDA(cudaStreamWaitEvent(st, J.part[q].ev_minor, 0));
+    // the other partitions' previous-cycle publish (Phi_q^{n-1}); waiting on
+    // that cycle's event, not the latest, lets same-cycle minor cycles overlap
+    if (n >= 2) RIX_CUDA(cudaStreamWaitEvent(st, J.part[q].ev_minor[(n - 1) & 1], 0));
   }
   for (int q = 0; q < J.n_part; ++q) RIX_TRY(ensure_psf(J, q, st));
   return RIX_OK;
@@ -462,7 +475,7 @@ static int rix_minor_cycle_msclean_impl(rix_job_t job, int part, const rix_mscle
   if (J.fp64) RIX_TRY(op_msclean<double>(&J, part, prm, (double*)delta_out, st));
   else RIX_TRY(op_msclean<float>(&J, part, prm, (float*)delta_out, st));
   J.part[part].minor_done += 1;
-  RIX_CUDA(cudaEventRecord(J.part[part].ev_minor, st));
+  RIX_CUDA(cudaEventRecord(J.part[part].ev_minor[J.part[part].minor_done & 1], st));
   return RIX_OK;
 }
 
@@ -480,7 +493,7 @@ static int rix_minor_cycle_fista_impl(rix_job_t job, int part, const rix_fista_p
   if (J.fp64) RIX_TRY(op_fista<double>(&J, part, prm, (double*)delta_out, st));
   else RIX_TRY(op_fista<float>(&J, part, prm, (float*)delta_out, st));
   J.part[part].minor_done += 1;
-  RIX_CUDA(cudaEventRecord(J.part[part].ev_minor, st));
+  RIX_CUDA(cudaEventRecord(J.part[part].ev_minor[J.part[part].minor_done & 1], st));
   return RIX_OK;
 }
 
@@ -497,7 +510,8 @@ static int rix_get_model_impl(rix_job_t job, int part, void* image_out, rix_stre
   RIX_TRY(check_part(&J, part));
   RIX_CUDA(cudaSetDevice(J.ctx->device));
   cudaStream_t st = (cudaStream_t)stream;
-  if (J.part[part].minor_done > 0) RIX_CUDA(cudaStreamWaitEvent(st, J.part[part].ev_minor, 0));
+  if (J.part[part].minor_done > 0)
+    RIX_CUDA(cudaStreamWaitEvent(st, J.part[part].ev_minor[J.part[part].minor_done & 1], 0));
   const size_t img = (size_t)J.desc.n * J.desc.n * (J.fp64 ? 8 : 4);
   RIX_CUDA(cudaMemcpyAsync(image_out, J.part[part].model.p, img, cudaMemcpyDeviceToDevice, st));
   return RIX_OK;
@@ -510,7 +524,7 @@ static int rix_combine_impl(rix_job_t job, void* image_out, rix_stream_t stream)
   RIX_CUDA(cudaSetDevice(J.ctx->device));
   cudaStream_t st = (cudaStream_t)stream;
   for (int q = 0; q < J.n_part; ++q)
-    if (J.part[q].minor_done > 0) RIX_CUDA(cudaStreamWaitEvent(st, J.part[q].ev_minor, 0));
+    if (J.part[q].minor_done > 0) RIX_CUDA(cudaStreamWaitEvent(st, J.part[q].ev_minor[J.part[q].minor_done & 1], 0));
   if (J.fp64) return op_combine<double>(&J, (double*)image_out, st);
   return op_combine<float>(&J, (float*)image_out, st);
 }

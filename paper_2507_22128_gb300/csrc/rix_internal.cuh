@@ -200,7 +200,9 @@ struct Part {
   DevBuf ms_R, ms_P, ms_B, ms_comp, ms_state;   // ms-CLEAN
   DevBuf fi_alpha, fi_alpha_prev, fi_y, fi_mx, fi_c, fi_x;   // FISTA
   int ms_ncomp_cap = 0;
-  cudaEvent_t ev_minor = nullptr;           // recorded after each minor cycle
+  // recorded after the minor cycle of each cycle parity (cycle n -> [n % 2])
+  cudaEvent_t ev_minor[2] = {nullptr, nullptr};
+  cudaEvent_t ev_psf = nullptr;             // recorded after the PSF is computed
   // captured FISTA iteration loop (replayed each minor cycle)
   cudaGraphExec_t fista_exec = nullptr;
   int fista_iters = -1, fista_levels = -1;

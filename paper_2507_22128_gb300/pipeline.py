@@ -76,11 +76,31 @@ class Reconstruction:
         else:
             rix.minor_cycle_fista(self.job, p, m.lam, m.lam_rel, m.iters, m.levels, delta_out, stream)
 
-    def cycle(self, m: Method, stream=None):
-        for p in range(self.n_part):
-            self.major(p, stream=stream)
-        for p in range(self.n_part):
-            self.minor(p, m, stream=stream)
+    def cycle(self, m: Method, stream=None, concurrent: bool = True):
+        """One major cycle of every partition, then the minor cycles.  With
+        `concurrent`, each partition runs on its own stream (the partitions
+        are concurrent instances on the device; the library orders the
+        exchange between them with events) and `stream` waits for them."""
+        if not concurrent or self.n_part == 1:
+            for p in range(self.n_part):
+                self.major(p, stream=stream)
+            for p in range(self.n_part):
+                self.minor(p, m, stream=stream)
+            return
+        main = torch.cuda.current_stream(self.device) if stream is None else stream
+        if not hasattr(self, "_pstreams"):
+            self._pstreams = [torch.cuda.Stream(self.device) for _ in range(self.n_part)]
+        start = torch.cuda.Event()
+        start.record(main)
+        for p, s in enumerate(self._pstreams):
+            s.wait_event(start)
+            self.major(p, stream=s)
+        for p, s in enumerate(self._pstreams):
+            self.minor(p, m, stream=s)
+        for s in self._pstreams:
+            ev = torch.cuda.Event()
+            ev.record(s)
+            main.wait_event(ev)
 
     def combine(self, out=None, stream=None):
         if out is None:

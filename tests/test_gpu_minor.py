@@ -136,3 +136,25 @@ def test_call_order_is_enforced(ctx, obs_small):
         assert e.value.code == rix.ESTATE
     finally:
         rec.close()
+
+
+@pytest.mark.parametrize("method,prec", [("msclean", 1), ("fista", 0)])
+def test_concurrent_partitions_match_sequential(ctx, obs_small, obs_wstack, method, prec):
+    """Partitions on their own streams (ordered by the library's events) give
+    the same result as issuing everything on one stream."""
+    from paper_2507_22128_gb300 import pipeline
+    obs = obs_small if method == "msclean" else obs_wstack
+    if method == "msclean":
+        m = pipeline.Method("msclean", (0.0, 3.0, 9.0), 0.1, 150, 1e-4)
+    else:
+        m = pipeline.Method("fista", lam_rel=1e-3, iters=15, levels=3)
+    out = []
+    for concurrent in (False, True):
+        rec = pipeline.observation_job(ctx, obs, 2, prec)
+        try:
+            for _ in range(3):
+                rec.cycle(m, concurrent=concurrent)
+            out.append(rec.combine().cpu().numpy())
+        finally:
+            rec.close()
+    assert rel_l2(out[1], out[0]) < (1e-9 if prec == 1 else 1e-5)
