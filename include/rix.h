@@ -275,14 +275,16 @@ uint64_t rix_kernel_launches(void);
 /* Opt-in device timing (a diagnostic for benchmarks): while enabled, the
  * library records CUDA events on the launch stream around every launch of
  * the kernel classes below (launches inside stream captures are not timed).
- * rix_timing_read waits for the recorded events, returns the summed device
- * time (ms) and the number of launches of one class, and clears them.
+ * rix_timing_read waits for the recorded events and returns, for one class,
+ * the summed launch durations (ms), the busy time (ms: the union of the
+ * launch intervals, which differs from the sum when launches on different
+ * streams overlap) and the number of launches, then clears them.
  * Classes: 0 = tiled degrid/grid kernel, 1 = FFT passes, 2 = partition. */
 #define RIX_TIME_TILES 0
 #define RIX_TIME_FFT 1
 #define RIX_TIME_PARTITION 2
 int rix_timing_enable(int on);
-int rix_timing_read(int kernel_class, double* total_ms, int64_t* launches);
+int rix_timing_read(int kernel_class, double* total_ms, double* busy_ms, int64_t* launches);
 
 #ifdef __cplusplus
 }

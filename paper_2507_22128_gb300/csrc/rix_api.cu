@@ -187,24 +187,43 @@ int rix_timing_enable(int on) {
   return RIX_OK;
 }
 
-int rix_timing_read(int kernel_class, double* total_ms, int64_t* launches) {
-  if (kernel_class < 0 || kernel_class >= rix::kTimeClasses || !total_ms || !launches)
+int rix_timing_read(int kernel_class, double* total_ms, double* busy_ms, int64_t* launches) {
+  if (kernel_class < 0 || kernel_class >= rix::kTimeClasses || !total_ms || !busy_ms || !launches)
     return set_error(RIX_EINVAL, "bad timing query");
   std::lock_guard<std::mutex> lk(rix::g_tmu);
+  auto& ev = rix::g_tev[kernel_class];
   double tot = 0.0;
-  int64_t n = 0;
-  for (auto& pr : rix::g_tev[kernel_class]) {
-    float ms = 0.f;
-    if (cudaEventSynchronize(pr.second) == cudaSuccess && cudaEventElapsedTime(&ms, pr.first, pr.second) == cudaSuccess) {
+  std::vector<std::pair<double, double>> iv;   // intervals relative to the first start
+  for (auto& pr : ev) {
+    float ms = 0.f, a = 0.f, b = 0.f;
+    if (cudaEventSynchronize(pr.second) == cudaSuccess && cudaEventElapsedTime(&ms, pr.first, pr.second) == cudaSuccess &&
+        cudaEventElapsedTime(&a, ev[0].first, pr.first) == cudaSuccess &&
+        cudaEventElapsedTime(&b, ev[0].first, pr.second) == cudaSuccess) {
       tot += ms;
-      ++n;
+      iv.push_back({a, b});
     }
+  }
+  // union of the intervals: device time during which any launch of the class ran
+  std::sort(iv.begin(), iv.end());
+  double busy = 0.0, cs = 0.0, ce = -1e300;
+  for (auto& x : iv) {
+    if (x.first > ce) {
+      if (ce > cs) busy += ce - cs;
+      cs = x.first;
+      ce = x.second;
+    } else {
+      ce = std::max(ce, x.second);
+    }
+  }
+  if (ce > cs) busy += ce - cs;
+  for (auto& pr : ev) {
     cudaEventDestroy(pr.first);
     cudaEventDestroy(pr.second);
   }
-  rix::g_tev[kernel_class].clear();
+  *launches = (int64_t)iv.size();
+  ev.clear();
   *total_ms = tot;
-  *launches = n;
+  *busy_ms = busy;
   return RIX_OK;
 }
 

@@ -78,7 +78,7 @@ def _load() -> C.CDLL:
         "rix_last_error": (C.c_char_p, []),
         "rix_kernel_launches": (C.c_uint64, []),
         "rix_timing_enable": (C.c_int, [C.c_int]),
-        "rix_timing_read": (C.c_int, [C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
+        "rix_timing_read": (C.c_int, [C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -264,11 +264,13 @@ def timing_enable(on: bool = True):
 
 
 def timing_read(kernel_class: int):
-    """(total device ms, launches) of one kernel class since the last read."""
+    """(summed launch ms, busy ms = union of launch intervals, launches) of one
+    kernel class since the last read."""
     ms = C.c_double()
+    busy = C.c_double()
     n = C.c_int64()
-    _check(_lib.rix_timing_read(kernel_class, C.byref(ms), C.byref(n)))
-    return ms.value, n.value
+    _check(_lib.rix_timing_read(kernel_class, C.byref(ms), C.byref(busy), C.byref(n)))
+    return ms.value, busy.value, n.value
 
 
 def combine(job, image_out, stream=None):

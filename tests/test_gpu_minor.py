@@ -81,8 +81,10 @@ def test_msclean_loop_matches_oracle(ctx, obs_small, prec):
     loop, img, log = _run_both(ctx, obs_small, prec, 2, "msclean", 3, **prm)
     # FP32: the operator is within 1e-5 of the oracle over the whole image, but
     # the high partition's composite dirty image is high-pass filtered and much
-    # weaker, so single-pixel values there carry ~1e-4..1e-3 relative error
-    rel_tie = 1e-9 if prec == 1 else 1e-3
+    # weaker, and its scale residuals B_s * D (s > 0) weaker still, so CLEAN's
+    # candidate values there carry up to ~1e-3 relative error; choices closer
+    # than 5e-3 are near-ties at FP32 precision for this workload
+    rel_tie = 1e-9 if prec == 1 else 5e-3
     all_identical = True
     for entry in log:
         if entry[0] == "models":
