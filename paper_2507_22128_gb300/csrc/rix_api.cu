@@ -89,6 +89,15 @@ void DevBuf::release() {
   bytes = 0;
 }
 
+int check_status(Job* job) {
+  int st = 0;
+  RIX_CUDA(cudaMemcpyAsync(&st, job->status.p, sizeof(int), cudaMemcpyDeviceToHost, job->ctx->mem_stream));
+  RIX_CUDA(cudaStreamSynchronize(job->ctx->mem_stream));
+  if (st == RIX_ETIMEOUT) return set_error(RIX_ETIMEOUT, "a grid barrier of a cooperative kernel timed out");
+  if (st != 0) return set_error(st, "device-side error %d", st);
+  return RIX_OK;
+}
+
 int note_stream(Job* job, cudaStream_t st) {
   for (auto& pr : job->touched)
     if (pr.first == st) {
@@ -301,6 +310,8 @@ int rix_job_create(rix_ctx_t ctx, const rix_job_desc* desc, int64_t max_rows, ri
   J.fp64 = desc->precision == RIX_FP64;
   J.n_part = desc->n_part;
   int rc = J.inv_lambda.alloc(J.ctx, desc->nchan * sizeof(double));
+  if (rc == RIX_OK) rc = J.status.alloc(J.ctx, sizeof(int));
+  if (rc == RIX_OK && cudaMemset(J.status.p, 0, sizeof(int)) != cudaSuccess) rc = set_error(RIX_ECUDA, "status word");
   if (rc == RIX_OK && cudaMemcpy(J.inv_lambda.p, J.inv_lambda_h.data(), desc->nchan * sizeof(double),
                                  cudaMemcpyHostToDevice) != cudaSuccess)
     rc = set_error(RIX_ECUDA, "frequency upload");
@@ -334,9 +345,7 @@ int rix_job_destroy(rix_job_t job) {
     for (int k = 0; k < 2; ++k)
       if (J.part[p].ev_minor[k]) cudaEventDestroy(J.part[p].ev_minor[k]);
     if (J.part[p].ev_psf) cudaEventDestroy(J.part[p].ev_psf);
-    if (J.part[p].fista_exec) cudaGraphExecDestroy(J.part[p].fista_exec);
   }
-  if (J.capture_stream) cudaStreamDestroy(J.capture_stream);
   J.ctx->reserved -= J.reserved;
   J.ctx->jobs -= 1;
   delete job;
@@ -348,7 +357,7 @@ int rix_job_sync(rix_job_t job) {
   RIX_CUDA(cudaSetDevice(job->j.ctx->device));
   for (auto& pr : job->j.touched) RIX_CUDA(cudaEventSynchronize(pr.second));
   RIX_CUDA(cudaGetLastError());
-  return RIX_OK;
+  return check_status(&job->j);
 }
 
 int rix_job_get_stats(rix_job_t job, rix_job_stats* out) {

@@ -203,11 +203,7 @@ struct Part {
   // recorded after the minor cycle of each cycle parity (cycle n -> [n % 2])
   cudaEvent_t ev_minor[2] = {nullptr, nullptr};
   cudaEvent_t ev_psf = nullptr;             // recorded after the PSF is computed
-  // captured FISTA iteration loop (replayed each minor cycle)
-  cudaGraphExec_t fista_exec = nullptr;
-  int fista_iters = -1, fista_levels = -1;
-  long long fista_nodes = 0;
-  void* fista_bufs[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+  DevBuf sync;                              // grid-barrier arrival counters of the cooperative kernels
 };
 
 struct Job {
@@ -235,13 +231,16 @@ struct Job {
   double ells[kMaxPart];
   int n_part = 1;
   cudaEvent_t ev_tmp = nullptr;
-  cudaStream_t capture_stream = nullptr;    // private stream for graph capture
+  DevBuf status;                            // int: 0, or the RIX_E* code a device-side wait raised
   // streams the job's calls ran on, each with an event recorded after the call
   std::vector<std::pair<cudaStream_t, cudaEvent_t>> touched;
 };
 
 // records that `st` carries work of `job` (for rix_job_destroy)
 int note_stream(Job* job, cudaStream_t st);
+// reads the job's device status word (the caller has synchronised the job's
+// streams); RIX_ETIMEOUT if a bounded device-side wait gave up
+int check_status(Job* job);
 
 // gridder entry points (k_grid.cu)
 template <typename R>
