@@ -1,0 +1,312 @@
+// a10: the FISTA minor cycle (Eq. 4-5, Db4 dictionary) as one persistent
+// cooperative kernel per call, compiled for each transform length 2N.
+//
+// Every iteration is a chain of grid-wide phases separated by a bounded grid
+// barrier:
+//   synthesis   x = W y, one phase per level, coarsest first;
+//   rows        F of the rows of pad(x), two real rows per complex transform,
+//               window columns k_u in [-N, 0] written transposed (ta);
+//   columns     per window column: F, Mx X - C, F^-1, crop  (ta -> tb);
+//   rows        F^-1 of the rows (Hermitian completion, two real rows per
+//               complex transform), crop: g = 2 crop F^-1 [Mx F pad x - C];
+//   analysis    W^T g, one phase per level, with the thresholded,
+//               momentum-accelerated step fused into the final coefficients.
+// Phases hand their units (wavelet tiles, row pairs, column batches) out over
+// the CTAs.  All image-sized buffers stay in L2 between phases.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <algorithm>
+
+#include "fft_ct.cuh"
+#include "grid_sync.cuh"
+#include "wavelet_device.cuh"
+
+namespace rix {
+namespace {
+
+template <typename R, int LOGL>
+struct FistaShape {
+  static constexpr int L = 1 << LOGL;
+  static constexpr int N = L / 2;          // image side
+  static constexpr int H = N / 2;
+  static constexpr int S = N + 1;          // window columns k_u = -N .. 0
+  static constexpr int STRIDE = padded_len(L);
+  static constexpr int kVals = kPingPongVals<R> * kFftThreads;
+  // complex rows per unit: one pass of the ping-pong FFT holds kVals values;
+  // the row phases pack two real rows into each, so 2 B <= N
+  static constexpr int B0 = kVals / L > 0 ? kVals / L : 1;
+  static constexpr int B = B0 < N / 2 ? B0 : N / 2;
+  static constexpr int kRowUnits = N / (2 * B);
+  static constexpr int kColUnits = (S + B - 1) / B;
+  static constexpr size_t kFftSmem = 2 * (size_t)B * STRIDE * sizeof(cplx<R>);
+  static constexpr size_t kSmem = kFftSmem > sizeof(DwtSmem<R>)
+                                      ? (kFftSmem > sizeof(IdwtSmem<R>) ? kFftSmem : sizeof(IdwtSmem<R>))
+                                      : (sizeof(DwtSmem<R>) > sizeof(IdwtSmem<R>) ? sizeof(DwtSmem<R>)
+                                                                                 : sizeof(IdwtSmem<R>));
+};
+
+template <typename C> __device__ __forceinline__ C cpx(typename std::conditional<sizeof(C) == 8, float, double>::type re,
+                                                       typename std::conditional<sizeof(C) == 8, float, double>::type im) {
+  C r;
+  r.x = re;
+  r.y = im;
+  return r;
+}
+
+// rows b0 .. b0 + 2B of x -> window columns of their spectra, T[j][b]
+template <typename R, int LOGL>
+__device__ __forceinline__ void rows_fwd_unit(const R* __restrict__ x, cplx<R>* __restrict__ T,
+                                              const cplx<R>* __restrict__ tw, cplx<R>* s, cplx<R>* s2, int u) {
+  using C = cplx<R>;
+  using F = FistaShape<R, LOGL>;
+  constexpr int L = F::L, N = F::N, H = F::H, B = F::B, STRIDE = F::STRIDE;
+  const int b0 = u * 2 * B;
+  // complex row q = x[b0 + 2q] + i x[b0 + 2q + 1], centred: pixel a sits at
+  // grid column (a - N/2) mod L with sign (-1)^(a + b)
+  constexpr int NE = B * N;
+  constexpr int NLD = (NE + kFftThreads - 1) / kFftThreads;
+  R va[NLD], vb[NLD];
+#pragma unroll
+  for (int k = 0; k < NLD; ++k) {
+    const int e = threadIdx.x + k * kFftThreads;
+    if (NE % kFftThreads == 0 || e < NE) {
+      const int q = e / N, a = e % N;
+      const int64_t row = b0 + 2 * q;
+      va[k] = x[row * N + a];
+      vb[k] = x[(row + 1) * N + a];
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < NLD; ++k) {
+    const int e = threadIdx.x + k * kFftThreads;
+    if (NE % kFftThreads == 0 || e < NE) {
+      const int q = e / N, a = e % N;
+      const bool odd = (a + b0) & 1;               // b0 + 2q has the parity of b0
+      s[q * STRIDE + padi((a - H) & (L - 1))] = cpx<C>(odd ? -va[k] : va[k], odd ? vb[k] : -vb[k]);
+      s[q * STRIDE + padi(H + a)] = cpx<C>(R(0), R(0));   // zero padding: columns N/2 .. 3N/2 - 1
+    }
+  }
+  __syncthreads();
+  const C* res = fft_ct<R, -1, LOGL, B>(s, s2, tw);
+  // X_a[j] = (Z[j] + conj Z[-j]) / 2,  X_b[j] = (Z[j] - conj Z[-j]) / 2i
+  constexpr int NO = B * F::S;
+  for (int e = threadIdx.x; e < NO; e += kFftThreads) {
+    const int q = e % B, j = e / B;
+    const C z = res[q * STRIDE + padi(j)];
+    const C w = res[q * STRIDE + padi((L - j) & (L - 1))];
+    const R h = R(0.5);
+    C* dst = T + (int64_t)j * N + b0 + 2 * q;
+    dst[0] = cpx<C>(h * (z.x + w.x), h * (z.y - w.y));
+    dst[1] = cpx<C>(h * (z.y + w.y), h * (w.x - z.x));
+  }
+  __syncthreads();
+}
+
+// window columns j0 .. j0 + B: F, Mx X - C, F^-1, crop to the image rows
+template <typename R, int LOGL>
+__device__ __forceinline__ void cols_conv_unit(const cplx<R>* __restrict__ Tin, const R* __restrict__ mx,
+                                               const cplx<R>* __restrict__ ctab, cplx<R>* __restrict__ Tout,
+                                               const cplx<R>* __restrict__ tw, cplx<R>* s, cplx<R>* s2, int u) {
+  using C = cplx<R>;
+  using F = FistaShape<R, LOGL>;
+  constexpr int L = F::L, N = F::N, H = F::H, B = F::B, S = F::S, STRIDE = F::STRIDE;
+  const int j0 = u * B;
+  constexpr int NE = B * N;
+  constexpr int NLD = (NE + kFftThreads - 1) / kFftThreads;
+  C v[NLD];
+#pragma unroll
+  for (int k = 0; k < NLD; ++k) {
+    const int e = threadIdx.x + k * kFftThreads;
+    const int q = e / N, b = e % N;
+    const int j = j0 + q;
+    v[k] = cpx<C>(R(0), R(0));
+    if ((NE % kFftThreads == 0 || e < NE) && j < S) v[k] = Tin[(int64_t)j * N + b];
+  }
+#pragma unroll
+  for (int k = 0; k < NLD; ++k) {
+    const int e = threadIdx.x + k * kFftThreads;
+    if (NE % kFftThreads == 0 || e < NE) {
+      const int q = e / N, b = e % N;
+      s[q * STRIDE + padi((b - H) & (L - 1))] = v[k];
+      s[q * STRIDE + padi(H + b)] = cpx<C>(R(0), R(0));
+    }
+  }
+  __syncthreads();
+  C* res = fft_ct<R, -1, LOGL, B>(s, s2, tw);
+  // Mx X - C on the window columns (the tables are read here rather than
+  // prefetched into registers: that would cost the co-residency of two loops)
+  constexpr int NT = (B * L) / kFftThreads;
+#pragma unroll 4
+  for (int k = 0; k < NT; ++k) {
+    const int e = threadIdx.x + k * kFftThreads;
+    const int q = e >> LOGL, c = e & (L - 1);
+    const int j = j0 + q;
+    if (j < S) {
+      C* p = &res[q * STRIDE + padi(c)];
+      const C z = *p;
+      const R m = mx[(int64_t)j * L + c];
+      const C cc = ctab[(int64_t)j * L + c];
+      *p = cpx<C>(z.x * m - cc.x, z.y * m - cc.y);
+    }
+  }
+  __syncthreads();
+  C* other = (res == s) ? s2 : s;
+  const C* out = fft_ct<R, +1, LOGL, B>(res, other, tw);
+  for (int e = threadIdx.x; e < NE; e += kFftThreads) {
+    const int q = e / N, b = e % N;
+    const int j = j0 + q;
+    if (j < S) Tout[(int64_t)j * N + b] = out[q * STRIDE + padi((b - H) & (L - 1))];
+  }
+  __syncthreads();
+}
+
+// rows b0 .. b0 + 2B of g = scale * crop F^-1 [spectrum], the spectrum given
+// by its window columns k_u in [-N, 0] (T[j][b]) and Hermitian symmetry
+template <typename R, int LOGL>
+__device__ __forceinline__ void rows_inv_unit(const cplx<R>* __restrict__ T, R* __restrict__ g, R scale,
+                                              const cplx<R>* __restrict__ tw, cplx<R>* s, cplx<R>* s2, int u) {
+  using C = cplx<R>;
+  using F = FistaShape<R, LOGL>;
+  constexpr int L = F::L, N = F::N, H = F::H, B = F::B, S = F::S, STRIDE = F::STRIDE;
+  const int b0 = u * 2 * B;
+  // Z = Y_a + i Y_b over all columns: Z[c] from window column c and
+  // Z[L - c] = conj Y_a[c] + i conj Y_b[c]; the self-conjugate columns 0 and
+  // N keep their real parts (the imaginary parts only feed Im F^-1 Y)
+  constexpr int NE = B * S;
+  constexpr int NLD = (NE + kFftThreads - 1) / kFftThreads;
+  C ya[NLD], yb[NLD];
+#pragma unroll
+  for (int k = 0; k < NLD; ++k) {
+    const int e = threadIdx.x + k * kFftThreads;
+    if (e < NE) {
+      const int q = e % B, c = e / B;
+      const C* src = T + (int64_t)c * N + b0 + 2 * q;
+      ya[k] = src[0];
+      yb[k] = src[1];
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < NLD; ++k) {
+    const int e = threadIdx.x + k * kFftThreads;
+    if (e < NE) {
+      const int q = e % B, c = e / B;
+      C a = ya[k], b = yb[k];
+      if (c == 0 || c == N) { a.y = R(0); b.y = R(0); }
+      s[q * STRIDE + padi(c)] = cpx<C>(a.x - b.y, a.y + b.x);
+      if (c != 0 && c != N) s[q * STRIDE + padi(L - c)] = cpx<C>(a.x + b.y, b.x - a.y);
+    }
+  }
+  __syncthreads();
+  const C* res = fft_ct<R, +1, LOGL, B>(s, s2, tw);
+  constexpr int NO = B * N;
+  for (int e = threadIdx.x; e < NO; e += kFftThreads) {
+    const int q = e / N, a = e % N;
+    const C z = res[q * STRIDE + padi((a - H) & (L - 1))];
+    const int64_t row = b0 + 2 * q;
+    const bool odd = (a + b0) & 1;
+    const R va = z.x * scale, vb = z.y * scale;
+    g[row * N + a] = odd ? -va : va;
+    g[(row + 1) * N + a] = odd ? vb : -vb;
+  }
+  __syncthreads();
+}
+
+template <typename R>
+struct FistaArgs {
+  FistaLoop<R> f;
+  R gscale;
+};
+
+template <typename R, int LOGL>
+__global__ void __launch_bounds__(kFftThreads, sizeof(R) == 4 && LOGL <= 12 ? 2 : 1)
+    k_fista_loop(FistaArgs<R> a) {
+  using C = cplx<R>;
+  using F = FistaShape<R, LOGL>;
+  constexpr int N = F::N;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* s = reinterpret_cast<C*>(smem_raw);
+  C* s2 = s + F::B * F::STRIDE;
+  DwtSmem<R>& dsm = *reinterpret_cast<DwtSmem<R>*>(smem_raw);
+  IdwtSmem<R>& ism = *reinterpret_cast<IdwtSmem<R>*>(smem_raw);
+  const FistaLoop<R>& f = a.f;
+  GridBarrier bar{f.barrier, f.status, 0u};
+  // L = 2 max Mx and lambda (absolute, or relative to max |residual| of the
+  // first cycle) are fixed during the minor cycle
+  const double lip = 2.0 * (double)f.state[0];
+  const double lam = f.lambda > 0.0 ? f.lambda : f.lambda_rel * (double)f.state[1];
+  const bool active = lip > 0.0;
+  const R inv_l = active ? (R)(1.0 / lip) : R(0);
+  const R thr = active ? (R)(lam / lip) : R(0);
+  double t = 1.0;
+  for (int it = 0; it < f.iters; ++it) {
+    // x = W y; level l lands in x for even l and in tmp for odd l
+    const R* ll = f.y;
+    for (int l = f.levels - 1; l >= 0; --l) {
+      const int n = N >> l, nt = (n + kTS - 1) / kTS;
+      R* dst = (l & 1) ? f.tmp : f.x;
+      for (int u = blockIdx.x; u < nt * nt; u += gridDim.x) idwt_tile<R>(ll, f.y, n, dst, N, u % nt, u / nt, ism);
+      if (!grid_barrier(bar)) return;
+      ll = dst;
+    }
+    for (int u = blockIdx.x; u < F::kRowUnits; u += gridDim.x) rows_fwd_unit<R, LOGL>(f.x, f.ta, f.tw, s, s2, u);
+    if (!grid_barrier(bar)) return;
+    for (int u = blockIdx.x; u < F::kColUnits; u += gridDim.x)
+      cols_conv_unit<R, LOGL>(f.ta, f.mx, f.c, f.tb, f.tw, s, s2, u);
+    if (!grid_barrier(bar)) return;
+    for (int u = blockIdx.x; u < F::kRowUnits; u += gridDim.x) rows_inv_unit<R, LOGL>(f.tb, f.g, a.gscale, f.tw, s, s2, u);
+    if (!grid_barrier(bar)) return;
+    // t_{k+1} = (1 + sqrt(1 + 4 t_k^2)) / 2, momentum (t_k - 1) / t_{k+1}, each
+    // operation rounded on its own
+    const double tn = __dmul_rn(0.5, __dadd_rn(1.0, __dsqrt_rn(__dadd_rn(1.0, __dmul_rn(__dmul_rn(4.0, t), t)))));
+    const StepArgs<R> sa{f.alpha, f.y, inv_l, thr, active, (R)__ddiv_rn(__dadd_rn(t, -1.0), tn)};
+    const R* src = f.g;
+    for (int l = 0; l < f.levels; ++l) {
+      const int n = N >> l, nt = (n / 2 + kTB - 1) / kTB;
+      R* dst = (l & 1) ? f.tmp : f.x;
+      for (int u = blockIdx.x; u < nt * nt; u += gridDim.x)
+        dwt_tile<R, true>(src, N, n, nullptr, dst, N, l == f.levels - 1, sa, u % nt, u / nt, dsm);
+      if (!grid_barrier(bar)) return;
+      src = dst;
+    }
+    t = tn;
+  }
+}
+
+template <typename R, int LOGL>
+int launch_fista_loop(const Ctx* ctx, const FistaLoop<R>& f, cudaStream_t st) {
+  using F = FistaShape<R, LOGL>;
+  auto kern = k_fista_loop<R, LOGL>;
+  const size_t smem = F::kSmem;
+  RIX_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  int per_sm = 0;
+  RIX_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kFftThreads, smem));
+  if (per_sm < 1) return set_error(RIX_EINVAL, "FISTA loop does not fit on an SM (%zu B shared)", smem);
+  // one CTA per SM: the loop of another partition or job fits beside it
+  const int nblk = ctx->num_sms;
+  FistaArgs<R> args{f, (R)(2.0 / (4.0 * (double)F::N * (double)F::N))};
+  RIX_CUDA(cudaMemsetAsync(f.barrier, 0, sizeof(unsigned int), st));
+  void* params[] = {&args};
+  ::rix::note_launch();
+  RIX_CUDA(cudaLaunchCooperativeKernel((const void*)kern, dim3(nblk), dim3(kFftThreads), params, smem, st));
+  return RIX_OK;
+}
+
+// dispatch on the transform length 2N (N a power of two in [32, KMAXN])
+template <typename R, int LOGL, int LOGL_MAX>
+int fista_loop_dispatch(const Ctx* ctx, const FistaLoop<R>& f, int logl, cudaStream_t st) {
+  if (logl == LOGL) return launch_fista_loop<R, LOGL>(ctx, f, st);
+  if constexpr (LOGL < LOGL_MAX) return fista_loop_dispatch<R, LOGL + 1, LOGL_MAX>(ctx, f, logl, st);
+  return set_error(RIX_EINVAL, "FISTA loop: image side %d not supported", f.n);
+}
+
+}  // namespace
+
+template <typename R>
+int fista_loop(const Ctx* ctx, const FistaLoop<R>& f, cudaStream_t st) {
+  constexpr int kMaxLogL = std::is_same<R, float>::value ? 13 : 12;   // N <= 4096 (FP32), 2048 (FP64)
+  return fista_loop_dispatch<R, 6, kMaxLogL>(ctx, f, ilog2(2 * (int64_t)f.n), st);
+}
+
+}  // namespace rix

@@ -14,7 +14,7 @@
 
 #include "rix_internal.cuh"
 #include "fft_device.cuh"
-#include "grid_sync.cuh"
+#include "wavelet_device.cuh"
 
 namespace cg = cooperative_groups;
 
@@ -198,204 +198,6 @@ __global__ void k_fill_fista(FillArgs a, double gn, R* __restrict__ mx, cplx<R>*
 
 namespace {
 
-// --------------------------------------------------------------- Db4 DWT ----
-// Daubechies 4-vanishing-moment low-pass filter (8 taps, minimum phase,
-// normalised to sum sqrt(2)); g[i] = (-1)^i h[7 - i].
-// Compile-time constants: every use below has a compile-time tap index, so the
-// taps fold into immediates (no constant-bank loads or FP64 conversions).
-__device__ constexpr double kDb4[8] = {0.23037781330885523,  0.7148465705525415,   0.6308807679295904,
-                                       -0.02798376941698385, -0.18703481171888114, 0.030841381835986965,
-                                       0.032883011666982945, -0.010597401784997278};
-
-template <typename R> __device__ __forceinline__ constexpr R db_h(int i) { return (R)kDb4[i]; }
-template <typename R> __device__ __forceinline__ constexpr R db_g(int i) {
-  return (i & 1) ? -(R)kDb4[7 - i] : (R)kDb4[7 - i];
-}
-
-// ------------------------------------------------- fused Db4 DWT levels ----
-// Analysis of one level: a CTA owns a kTB x kTB block of each of the four
-// subbands of an n x n block (n a power of two), stages the periodic
-// (2 kTB + 6)^2 input tile, filters its rows (low and high) and then its
-// columns.  Subband layout of a level: [Y][X] with Y < n/2 column-low,
-// X < n/2 row-low.  Every global load of a tile is issued before the first
-// one is used.
-constexpr int kTB = 16;
-constexpr int kTin = 2 * kTB + 6;
-
-// FISTA step fused into the analysis of the gradient (Beck & Teboulle 2009):
-// at each final coefficient g:  a' = S_{lam/L}(y - g/L),  y = a' + mom (a' - a),  a = a'
-template <typename R>
-struct StepArgs {
-  R* alpha;
-  R* y;
-  R inv_l, thr;         // 1 / L and lambda / L (both 0 when L = 0: the step is a no-op)
-  bool active;
-  R mom;
-};
-
-template <typename R>
-struct DwtSmem {
-  R tin[kTin][kTin + 1];
-  R trow[kTin][2 * kTB + 1];     // [input row][lo x | hi x]
-};
-
-// one kTB x kTB output block (bx, by) of each subband; 256 threads
-template <typename R, bool kStep>
-__device__ __forceinline__ void dwt_tile(const R* __restrict__ src, int lds, int n, R* __restrict__ coef,
-                                         R* __restrict__ ll, int ld, int last, const StepArgs<R>& st, int bx, int by,
-                                         DwtSmem<R>& sm) {
-  constexpr int TIN = kTin;
-  constexpr int NLD = (TIN * TIN + 255) / 256;
-  auto& tin = sm.tin;
-  auto& trow = sm.trow;
-  const int h = n / 2;
-  const int y0 = by * kTB, x0 = bx * kTB;
-  const int ty = threadIdx.x / kTB, tx = threadIdx.x - ty * kTB;   // 256 threads = kTB x kTB
-  const int y = y0 + ty, x = x0 + tx;
-  const bool own = y < h && x < h;
-  // the coefficients this thread updates: quadrants 1-3, and 0 at the last level
-  R yq[4], aq[4];
-  if (kStep && own) {
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      if (q == 0 && !last) continue;
-      const int64_t i = (int64_t)((q >> 1) * h + y) * ld + (q & 1) * h + x;
-      yq[q] = st.y[i];
-      aq[q] = st.alpha[i];
-    }
-  }
-  R v[NLD];
-#pragma unroll
-  for (int k = 0; k < NLD; ++k) {
-    const int t = threadIdx.x + 256 * k;
-    if (t < TIN * TIN) {
-      const int r = t / TIN, c = t - r * TIN;
-      v[k] = src[(int64_t)((2 * y0 + r) & (n - 1)) * lds + ((2 * x0 + c) & (n - 1))];
-    }
-  }
-#pragma unroll
-  for (int k = 0; k < NLD; ++k) {
-    const int t = threadIdx.x + 256 * k;
-    if (t < TIN * TIN) {
-      const int r = t / TIN, c = t - r * TIN;
-      tin[r][c] = v[k];
-    }
-  }
-  __syncthreads();
-  for (int t = threadIdx.x; t < TIN * kTB; t += blockDim.x) {
-    const int r = t / kTB, xx = t - r * kTB;
-    R a = R(0), d = R(0);
-#pragma unroll
-    for (int i = 0; i < 8; ++i) {
-      const R w = tin[r][2 * xx + i];
-      a += db_h<R>(i) * w;
-      d += db_g<R>(i) * w;
-    }
-    trow[r][xx] = a;
-    trow[r][kTB + xx] = d;
-  }
-  __syncthreads();
-  if (own) {
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int cy = q >> 1, cx = q & 1;
-      R g = R(0);
-#pragma unroll
-      for (int i = 0; i < 8; ++i) g += (cy ? db_g<R>(i) : db_h<R>(i)) * trow[2 * ty + i][cx * kTB + tx];
-      const int64_t idx = (int64_t)(cy * h + y) * ld + cx * h + x;
-      if (q == 0 && !last) {
-        ll[(int64_t)y * ld + x] = g;
-      } else if (kStep) {
-        const R z = yq[q] - g * st.inv_l;
-        const R az = fabs(z) - st.thr;
-        const R an = (st.active && az > R(0)) ? copysign(az, z) : R(0);
-        st.y[idx] = an + st.mom * (an - aq[q]);
-        st.alpha[idx] = an;
-      } else {
-        coef[idx] = g;
-      }
-    }
-  }
-  __syncthreads();
-}
-
-// Synthesis of one level: out (n x n, ld) from the LL block `llin` (ld) and
-// the detail subbands of `coef` (ld); a CTA owns a kTS x kTS output block.
-constexpr int kTS = 32;
-constexpr int kRK = kTS / 2 + 4;
-template <typename R>
-struct IdwtSmem {
-  R cq[4][kRK][kRK + 1];         // quadrant tiles: LL, row-high, col-high, HH
-  R tr[2][kRK][kTS + 1];         // after row synthesis: [column half][coef row][c]
-};
-
-template <typename R>
-__device__ __forceinline__ void idwt_tile(const R* __restrict__ llin, const R* __restrict__ coef, int n,
-                                          R* __restrict__ out, int ld, int bx, int by, IdwtSmem<R>& sm) {
-  constexpr int RK = kRK;
-  auto& cq = sm.cq;
-  auto& tr = sm.tr;
-  const int h = n / 2;
-  const int m0 = by * kTS, c0 = bx * kTS;
-  const int kb_m = (m0 >> 1) - 4, kb_c = (c0 >> 1) - 4;
-  constexpr int NLD = (4 * RK * RK + 255) / 256;
-  R v[NLD];
-#pragma unroll
-  for (int k = 0; k < NLD; ++k) {
-    const int t = threadIdx.x + 256 * k;
-    if (t < 4 * RK * RK) {
-      const int q = t / (RK * RK), rem = t - q * RK * RK;
-      const int rk = rem / RK, ck = rem - rk * RK;
-      const int km = (kb_m + rk) & (h - 1), kc = (kb_c + ck) & (h - 1);   // periodic; h a power of two
-      const int cy = q >> 1, cx = q & 1;
-      v[k] = (q == 0) ? llin[(int64_t)km * ld + kc] : coef[(int64_t)(cy * h + km) * ld + (cx * h + kc)];
-    }
-  }
-#pragma unroll
-  for (int k = 0; k < NLD; ++k) {
-    const int t = threadIdx.x + 256 * k;
-    if (t < 4 * RK * RK) {
-      const int q = t / (RK * RK), rem = t - q * RK * RK;
-      const int rk = rem / RK, ck = rem - rk * RK;
-      cq[q][rk][ck] = v[k];
-    }
-  }
-  __syncthreads();
-  // rows: tr[cy][rk][c] = sum over the 4 taps of the parity of c
-  for (int t = threadIdx.x; t < 2 * RK * kTS; t += blockDim.x) {
-    const int cy = t / (RK * kTS), rem = t - cy * RK * kTS;
-    const int rk = rem / kTS, cl = rem - rk * kTS;
-    const int c = c0 + cl;
-    const bool odd = c & 1;
-    const int kc = (c >> 1) - kb_c;             // tap i = 2 j + (c & 1) reads coefficient (c - i) / 2
-    R v = R(0);
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const R hh = odd ? db_h<R>(2 * j + 1) : db_h<R>(2 * j);
-      const R gg = odd ? db_g<R>(2 * j + 1) : db_g<R>(2 * j);
-      v += hh * cq[2 * cy][rk][kc - j] + gg * cq[2 * cy + 1][rk][kc - j];
-    }
-    tr[cy][rk][cl] = v;
-  }
-  __syncthreads();
-  for (int t = threadIdx.x; t < kTS * kTS; t += blockDim.x) {
-    const int ml = t / kTS, cl = t - ml * kTS;
-    const int m = m0 + ml, c = c0 + cl;
-    if (m >= n || c >= n) continue;
-    const bool odd = m & 1;
-    const int km = (m >> 1) - kb_m;
-    R v = R(0);
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const R hh = odd ? db_h<R>(2 * j + 1) : db_h<R>(2 * j);
-      const R gg = odd ? db_g<R>(2 * j + 1) : db_g<R>(2 * j);
-      v += hh * tr[0][km - j][cl] + gg * tr[1][km - j][cl];
-    }
-    out[(int64_t)m * ld + c] = v;
-  }
-  __syncthreads();
-}
-
 template <typename R>
 __global__ void __launch_bounds__(256) k_idwt_level(const R* __restrict__ llin, const R* __restrict__ coef, int n,
                                                     R* __restrict__ out, int ld) {
@@ -423,106 +225,6 @@ int idwt2(const Ctx* ctx, const R* c, R* out, R* tmp, int N, int levels, cudaStr
 }  // namespace
 
 namespace {
-
-// ------------------------------------------------ persistent FISTA loop ----
-// All iterations of one FISTA minor cycle in one cooperative launch.  Every
-// iteration is a chain of grid-wide phases: the synthesis levels x = W y
-// (coarsest first), the three passes of the Hermitian-half convolution that
-// form the gradient g = 2 crop F^-1 [Mx F pad x - C], and the analysis levels
-// of g with the thresholded, momentum-accelerated step fused into the last
-// stage.  Each phase hands its units (wavelet tiles, batches of FFT rows or
-// columns) out over the CTAs; a bounded grid barrier separates the phases.
-// The image-sized buffers (x, g, y, alpha, two (N+1) x N transposes) stay in
-// L2 between phases; the barrier replaces the kernel boundary of the
-// launch-per-phase schedule.
-template <typename R>
-struct FistaLoopArgs {
-  KArgs k;                     // Hermitian-half convolution on the 2N grid
-  const cplx<R>* tw;
-  R* alpha;
-  R* y;
-  R* x;
-  R* g;
-  R* tmp;
-  cplx<R>* ta;
-  cplx<R>* tb;
-  const R* mx;
-  const cplx<R>* c;
-  const R* state;
-  double lambda, lambda_rel, gscale;
-  int N, levels, iters;
-  GridBarrier bar;
-};
-
-template <typename R, int VPT>
-__global__ void __launch_bounds__(kFftThreads, (VPT == 0 && sizeof(R) == 4) ? 2 : 1) k_fista_loop(FistaLoopArgs<R> a) {
-  using C = cplx<R>;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  C* s = reinterpret_cast<C*>(smem_raw);
-  C* s2 = s + (VPT == 0 ? a.k.B * a.k.stride : 0);
-  DwtSmem<R>& dsm = *reinterpret_cast<DwtSmem<R>*>(smem_raw);
-  IdwtSmem<R>& ism = *reinterpret_cast<IdwtSmem<R>*>(smem_raw);
-  GridBarrier bar = a.bar;
-  const int N = a.N;
-  const int nrow = (a.k.M + a.k.B - 1) / a.k.B, ncol = (a.k.S + a.k.B - 1) / a.k.B;
-  // L = 2 max Mx and lambda (absolute, or relative to max |residual| of the
-  // first cycle) are fixed during the minor cycle
-  const double lip = 2.0 * (double)a.state[0];
-  const double lam = a.lambda > 0.0 ? a.lambda : a.lambda_rel * (double)a.state[1];
-  const bool active = lip > 0.0;
-  const R inv_l = active ? (R)(1.0 / lip) : R(0);
-  const R thr = active ? (R)(lam / lip) : R(0);
-  double t = 1.0;
-  for (int it = 0; it < a.iters; ++it) {
-    // x = W y; level l lands in x for even l and in tmp for odd l
-    const R* ll = a.y;
-    for (int l = a.levels - 1; l >= 0; --l) {
-      const int n = N >> l, nt = (n + kTS - 1) / kTS;
-      R* dst = (l & 1) ? a.tmp : a.x;
-      for (int u = blockIdx.x; u < nt * nt; u += gridDim.x) idwt_tile<R>(ll, a.y, n, dst, N, u % nt, u / nt, ism);
-      if (!grid_barrier(bar)) return;
-      ll = dst;
-    }
-    for (int u = blockIdx.x; u < nrow; u += gridDim.x) fwd_rows_block<R, VPT>(a.k, a.x, a.ta, a.tw, s, s2, u, 0);
-    if (!grid_barrier(bar)) return;
-    for (int u = blockIdx.x; u < ncol; u += gridDim.x)
-      conv_cols_block<R, VPT>(a.k, a.ta, kOpAxpyReal, a.mx, a.c, a.tb, a.tw, s, s2, u, 0);
-    if (!grid_barrier(bar)) return;
-    for (int u = blockIdx.x; u < nrow; u += gridDim.x)
-      inv_rows_block<R, VPT>(a.k, a.tb, a.g, a.gscale, 0, a.tw, s, s2, u, 0);
-    if (!grid_barrier(bar)) return;
-    // t_{k+1} = (1 + sqrt(1 + 4 t_k^2)) / 2, momentum (t_k - 1) / t_{k+1}, each
-    // operation rounded on its own
-    const double tn = __dmul_rn(0.5, __dadd_rn(1.0, __dsqrt_rn(__dadd_rn(1.0, __dmul_rn(__dmul_rn(4.0, t), t)))));
-    const StepArgs<R> sa{a.alpha, a.y, inv_l, thr, active, (R)__ddiv_rn(__dadd_rn(t, -1.0), tn)};
-    const R* src = a.g;
-    for (int l = 0; l < a.levels; ++l) {
-      const int n = N >> l, nt = (n / 2 + kTB - 1) / kTB;
-      R* dst = (l & 1) ? a.tmp : a.x;
-      for (int u = blockIdx.x; u < nt * nt; u += gridDim.x)
-        dwt_tile<R, true>(src, N, n, nullptr, dst, N, l == a.levels - 1, sa, u % nt, u / nt, dsm);
-      if (!grid_barrier(bar)) return;
-      src = dst;
-    }
-    t = tn;
-  }
-}
-
-template <typename R, int VPT>
-int launch_fista_loop(const Ctx* ctx, FistaLoopArgs<R> a, cudaStream_t st) {
-  auto kern = k_fista_loop<R, VPT>;
-  const size_t fft = (size_t)(VPT == 0 ? 2 : 1) * a.k.B * a.k.stride * sizeof(cplx<R>);
-  const size_t smem = std::max({fft, sizeof(DwtSmem<R>), sizeof(IdwtSmem<R>)});
-  RIX_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  int per_sm = 0;
-  RIX_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kFftThreads, smem));
-  if (per_sm < 1) return set_error(RIX_EINVAL, "FISTA loop does not fit on an SM (%zu B shared)", smem);
-  const int nblk = ctx->num_sms * std::min(per_sm, 2);
-  void* args[] = {&a};
-  ::rix::note_launch();
-  RIX_CUDA(cudaLaunchCooperativeKernel((const void*)kern, dim3(nblk), dim3(kFftThreads), args, smem, st));
-  return RIX_OK;
-}
 
 // --------------------------------------------------------------- ms-CLEAN ----
 template <typename R>
@@ -974,33 +676,24 @@ int op_fista(Job* job, int p, const rix_fista_params* prm, R* delta_out, cudaStr
   R* g = pt.fimg.as<R>();
   R* tmp = pt.fi_alpha_prev.as<R>();
   if (prm->iters > 0) {
-    // gradient of ||M x - C||^2 on the 2N grid: 2 crop F^-1 [Mx F pad x - C],
-    // the 1 / (2N)^2 of the inverse transform folded into the scale
-    XformGeom cg_ = fill_geom(n);
-    cg_.S = n + 1;
-    cg_.herm = 1;
-    FistaLoopArgs<R> fa{};
-    const bool inplace = use_inplace<R>(cg_.L);
-    const int vpt = inplace ? Vpt<R>::kLarge : kPingPongVals<R>;
-    fa.k = make_args<R>(cg_, std::max(1, kFftThreads * vpt / cg_.L));
-    fa.tw = twiddles<R>(ctx);
-    fa.alpha = alpha; fa.y = y; fa.x = x; fa.g = g; fa.tmp = tmp;
-    fa.ta = pt.ft_a.as<cplx<R>>();
-    fa.tb = pt.ft_b.as<cplx<R>>();
-    fa.mx = pt.fi_mx.as<R>();
-    fa.c = pt.fi_c.as<cplx<R>>();
-    fa.state = pt.fi_state.as<R>();
-    fa.lambda = prm->lambda;
-    fa.lambda_rel = prm->lambda_rel;
-    fa.gscale = 2.0 / (double)tot;
-    fa.N = n;
-    fa.levels = prm->levels;
-    fa.iters = prm->iters;
+    // gradient of ||M x - C||^2 on the 2N grid: 2 crop F^-1 [Mx F pad x - C]
     RIX_TRY(ensure<R>(job, pt.sync, 16));
-    RIX_CUDA(cudaMemsetAsync(pt.sync.p, 0, sizeof(unsigned int), st));
-    fa.bar = GridBarrier{pt.sync.as<unsigned int>(), job->status.as<int>(), 0u};
-    if (inplace) RIX_TRY((launch_fista_loop<R, Vpt<R>::kLarge>(ctx, fa, st)));
-    else RIX_TRY((launch_fista_loop<R, 0>(ctx, fa, st)));
+    FistaLoop<R> f{};
+    f.alpha = alpha; f.y = y; f.x = x; f.g = g; f.tmp = tmp;
+    f.ta = pt.ft_a.as<cplx<R>>();
+    f.tb = pt.ft_b.as<cplx<R>>();
+    f.mx = pt.fi_mx.as<R>();
+    f.c = pt.fi_c.as<cplx<R>>();
+    f.state = pt.fi_state.as<R>();
+    f.tw = twiddles<R>(ctx);
+    f.barrier = pt.sync.as<unsigned int>();
+    f.status = job->status.as<int>();
+    f.lambda = prm->lambda;
+    f.lambda_rel = prm->lambda_rel;
+    f.n = n;
+    f.levels = prm->levels;
+    f.iters = prm->iters;
+    RIX_TRY(fista_loop<R>(ctx, f, st));
   }
   RIX_TRY(idwt2<R>(ctx, alpha, pt.delta.as<R>(), tmp, n, prm->levels, st));
   RIX_TRY(publish<R>(job, p, cycle, st));

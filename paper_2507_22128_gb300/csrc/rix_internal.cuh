@@ -270,6 +270,30 @@ template <typename R>
 int op_fista(Job* job, int p, const rix_fista_params* prm, R* delta_out, cudaStream_t st);
 template <typename R>
 int op_combine(Job* job, R* out, cudaStream_t st);
+
+// persistent FISTA iteration loop (k_fista*.cu): all `iters` iterations of
+// one minor cycle in one cooperative launch.  Images are N x N, the
+// transposes (N+1) x N complex, mx / c the u-major (2N)^2 fill tables.
+template <typename R>
+struct FistaLoop {
+  R* alpha;
+  R* y;
+  R* x;
+  R* g;
+  R* tmp;
+  cplx<R>* ta;
+  cplx<R>* tb;
+  const R* mx;
+  const cplx<R>* c;
+  const R* state;          // [max Mx, max |residual| of cycle 1]
+  const cplx<R>* tw;       // twiddle table, length kTwMax
+  unsigned int* barrier;   // arrival counter (zeroed by the call, stream-ordered)
+  int* status;             // the job's status word
+  double lambda, lambda_rel;
+  int n, levels, iters;
+};
+template <typename R>
+int fista_loop(const Ctx* ctx, const FistaLoop<R>& f, cudaStream_t st);
 int get_components(Job* job, int part, int32_t* count, int32_t capacity, int32_t* scale_out,
                    int32_t* pixel_out, double* amp_out, cudaStream_t st);
 
