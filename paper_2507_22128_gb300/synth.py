@@ -221,15 +221,19 @@ def _visibilities(uvw_m: np.ndarray, freq: np.ndarray, sky: Sky,
 
 def _observe(name, rng_layout, rng_sky, rng_noise, enu, n_times, ha_span_h,
              freq, n, cell_arcsec, n_wplanes, n_pts, n_gauss, pts_flux, sigma,
-             dec_deg=-30.0, lat_deg=-30.0) -> Observation:
+             dec_deg=-30.0, lat_deg=-30.0, with_vis=True) -> Observation:
     freq = np.asarray(freq, dtype=np.float64)
     ha = np.linspace(-0.5 * ha_span_h, 0.5 * ha_span_h, n_times) * (15.0 * DEG)
     uvw = uvw_tracks(enu, lat_deg * DEG, dec_deg * DEG, ha)
     cell = cell_arcsec * ARCSEC
     sky = make_sky(rng_sky, n, n_pts, n_gauss, pts_flux)
-    vis = _visibilities(uvw, freq, sky, cell, wterm=n_wplanes > 0)
-    noise = rng_noise.normal(0.0, sigma, vis.shape) + 1j * rng_noise.normal(0.0, sigma, vis.shape)
-    vis = vis + noise
+    if with_vis:
+        vis = _visibilities(uvw, freq, sky, cell, wterm=n_wplanes > 0)
+        noise = rng_noise.normal(0.0, sigma, vis.shape) + 1j * rng_noise.normal(0.0, sigma, vis.shape)
+        vis = vis + noise
+    else:
+        # geometry only (operator tests that bring their own visibilities)
+        vis = np.zeros((uvw.shape[0], freq.shape[0]), dtype=np.complex128)
     weight = np.ones(vis.shape, dtype=np.float32)
     return Observation(name, n, cell, n_wplanes, uvw, freq,
                        vis, weight, sky, sigma)
@@ -254,7 +258,7 @@ def plain_small(seed: int = 0) -> Observation:
 
 
 def medium(seed: int = 1, n_times: int = 1000, n: int = 1024, n_wplanes: int = 16,
-           n_ant: int = 64, n_chan: int = 4) -> Observation:
+           n_ant: int = 64, n_chan: int = 4, with_vis: bool = True) -> Observation:
     """1024x1024 at 1", 64 antennas on a 3-arm log spiral 50 m - 5 km (2016
     baselines) x 1000 times x 4 channels over 1.3-1.5 GHz = 8.06 M
     visibilities, 16 w-planes; 200 points (power-law counts) + 20 Gaussians;
@@ -265,7 +269,7 @@ def medium(seed: int = 1, n_times: int = 1000, n: int = 1024, n_wplanes: int = 1
     freq = np.linspace(1.3e9, 1.5e9, n_chan)
     cell = 1.0
     return _observe(f"medium_{n}", rl, rs, rn, enu, n_times, 4.0, freq, n, cell, n_wplanes,
-                    200, 20, "powerlaw", 1e-3)
+                    200, 20, "powerlaw", 1e-3, with_vis=with_vis)
 
 
 def large(seed: int = 3, n_times: int = 4000, n: int = 4096, n_wplanes: int = 32,

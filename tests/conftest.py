@@ -21,7 +21,15 @@ def obs_small():
 
 @pytest.fixture(scope="session")
 def obs_wstack():
-    """Reduced medium recipe: 256x256 at 4", 16 w-planes, 24 antennas x 40
+    """Reduced medium recipe: 256x256 at 1", 16 w-planes, 24 antennas x 40
     times x 2 channels (w-stacked parity case)."""
     from paper_2507_22128_gb300 import synth
     return synth.medium(seed=11, n_times=40, n=256, n_wplanes=16, n_ant=24, n_chan=2)
+
+
+@pytest.fixture(scope="session")
+def obs_large():
+    """Reduced large recipe: 256x256 at 0.5", 32 w-planes, 128 antennas on a
+    10 km spiral x 6 times x 1 channel (P = 4 parity case)."""
+    from paper_2507_22128_gb300 import synth
+    return synth.large(seed=3, n_times=6, n=256, n_chan=1)

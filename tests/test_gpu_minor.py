@@ -160,3 +160,23 @@ def test_concurrent_partitions_match_sequential(ctx, obs_small, obs_wstack, meth
         finally:
             rec.close()
     assert rel_l2(out[1], out[0]) < (1e-9 if prec == 1 else 1e-5)
+
+
+def test_msclean_four_partitions_large_recipe(ctx, obs_large):
+    """P = 4 rings and the scale set {0, 4, 16, 32} of the 4096^2 recipe, at
+    reduced size, FP64: component lists up to the first near-tie, then images."""
+    prm = dict(scales=[0.0, 4.0, 16.0, 32.0], gain=0.1, niter=200, threshold=1e-4)
+    loop, img, log = _run_both(ctx, obs_large, 1, 4, "msclean", 3, **prm)
+    all_identical = True
+    for entry in log:
+        if entry[0] == "models":
+            continue
+        c, p, res, gpu = entry
+        k, same = _compare_components(res, gpu, 1e-9)
+        all_identical &= same and len(gpu[0]) == res.iterations
+    if all_identical:
+        for entry in log:
+            if entry[0] == "models":
+                for g, o in zip(entry[2], entry[3]):
+                    assert rel_l2(g, o) < 1e-9
+        assert rel_l2(img, loop.combine()) < 1e-9
