@@ -216,8 +216,7 @@ def main():
     def one_job(uvw, vis, w):
         rec.uvw, rec.vis, rec.weight = uvw, vis, w
         rix.set_uv_partition(rec.job, uvw, w, None, 1.0, None, stream)
-        for _ in range(a.cycles):
-            rec.cycle(meth, stream)
+        rec.cycles(meth, a.cycles, stream)
         rix.combine(rec.job, out, stream)
 
     for _ in range(max(a.warmup, 1)):
@@ -361,6 +360,27 @@ def phase_split(rec, rix, a, meth, stream, uvw, vis, w, out, flush):
     return {"partition_sort": e0.elapsed_time(e1), "major_cycles": maj, "minor_cycles_incl_psf": mnr}
 
 
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per k_tiles_ws
+# launch at the default 1024^2 workload, from a one-pass ncu capture of one
+# timed job (profiles/k_tiles_ws_medium_dram.md): residual launches of
+# partitions 0 and 1, PSF launches of partitions 0 and 1.  Reported only for
+# that workload and while k_grid.cu is the source the counters were taken on.
+TILES_TRAFFIC = {"k_grid_sha1": "f00709e1c5bbc07f0b29a43cec683a0dd2474bb2",
+                 "resid": (134.10e6, 271.75e6), "psf": (85.59e6, 221.12e6)}
+
+
+def tiles_traffic(a):
+    import hashlib
+    src = os.path.join(ROOT, "paper_2507_22128_gb300", "csrc", "k_grid.cu")
+    with open(src, "rb") as f:
+        sha = hashlib.sha1(f.read()).hexdigest()
+    if sha != TILES_TRAFFIC["k_grid_sha1"] or a.fp64 or a.n != 1024 or a.n_times != 1000:
+        return None
+    # a step: `cycles` residual launches per partition and one PSF launch each
+    tot = a.cycles * sum(TILES_TRAFFIC["resid"]) + sum(TILES_TRAFFIC["psf"])
+    return tot / (2 * a.cycles + 2)
+
+
 def roofline_tiles(tiles_ms, tiles_n, st, a, entries_timed):
     """Roofline of the tiled degrid/residual/grid kernel, the gridder of the
     major cycle: FP32 (or FP64) arithmetic over its event-timed launches
@@ -379,7 +399,8 @@ def roofline_tiles(tiles_ms, tiles_n, st, a, entries_timed):
     ach = flops / (tiles_ms * 1e-3) / 1e12
     return {"bound": "alu", "kernel": "k_tiles (degrid + residual + grid, w-stacked, T=16)",
             "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
-            "traffic": None, "launches_timed": tiles_n, "busy_ms_per_launch": tiles_ms / tiles_n,
+            "traffic": tiles_traffic(a), "traffic_unit": "B per launch",
+            "launches_timed": tiles_n, "busy_ms_per_launch": tiles_ms / tiles_n,
             "peak_source": f"152 SMs x {lanes} {'FP64' if a.fp64 else 'FP32'} lanes x 2 flop x {clk:.0f} MHz "
                            f"(max SM clock of {kind} peaks)"}
 

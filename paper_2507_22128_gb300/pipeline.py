@@ -102,6 +102,32 @@ class Reconstruction:
             ev.record(s)
             main.wait_event(ev)
 
+    def cycles(self, m: Method, n_major: int, stream=None):
+        """`n_major` major+minor cycles with each partition on its own stream
+        and no join between cycles: a partition starts its next major cycle as
+        soon as its own minor cycle is done, while the library's events order
+        the exchange with the other partitions.  `stream` waits for all."""
+        if self.n_part == 1:
+            for _ in range(n_major):
+                self.cycle(m, stream)
+            return
+        main = torch.cuda.current_stream(self.device) if stream is None else stream
+        if not hasattr(self, "_pstreams"):
+            self._pstreams = [torch.cuda.Stream(self.device) for _ in range(self.n_part)]
+        start = torch.cuda.Event()
+        start.record(main)
+        for s in self._pstreams:
+            s.wait_event(start)
+        for _ in range(n_major):
+            for p, s in enumerate(self._pstreams):
+                self.major(p, stream=s)
+            for p, s in enumerate(self._pstreams):
+                self.minor(p, m, stream=s)
+        for s in self._pstreams:
+            ev = torch.cuda.Event()
+            ev.record(s)
+            main.wait_event(ev)
+
     def combine(self, out=None, stream=None):
         if out is None:
             out = torch.empty((self.n, self.n), dtype=self.rdtype, device=self.device)
@@ -109,8 +135,7 @@ class Reconstruction:
         return out
 
     def run(self, m: Method, n_major: int, stream=None):
-        for _ in range(n_major):
-            self.cycle(m, stream)
+        self.cycles(m, n_major, stream)
         return self.combine(stream=stream)
 
 

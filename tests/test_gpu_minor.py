@@ -142,8 +142,9 @@ def test_call_order_is_enforced(ctx, obs_small):
 
 @pytest.mark.parametrize("method,prec", [("msclean", 1), ("fista", 0)])
 def test_concurrent_partitions_match_sequential(ctx, obs_small, obs_wstack, method, prec):
-    """Partitions on their own streams (ordered by the library's events) give
-    the same result as issuing everything on one stream."""
+    """Partitions on their own streams (ordered by the library's events), with
+    or without a join after every cycle, give the same result as issuing
+    everything on one stream."""
     from paper_2507_22128_gb300 import pipeline
     obs = obs_small if method == "msclean" else obs_wstack
     if method == "msclean":
@@ -151,15 +152,19 @@ def test_concurrent_partitions_match_sequential(ctx, obs_small, obs_wstack, meth
     else:
         m = pipeline.Method("fista", lam_rel=1e-3, iters=15, levels=3)
     out = []
-    for concurrent in (False, True):
+    for mode in ("sequential", "per-cycle join", "no join"):
         rec = pipeline.observation_job(ctx, obs, 2, prec)
         try:
-            for _ in range(3):
-                rec.cycle(m, concurrent=concurrent)
+            if mode == "no join":
+                rec.cycles(m, 3)
+            else:
+                for _ in range(3):
+                    rec.cycle(m, concurrent=(mode != "sequential"))
             out.append(rec.combine().cpu().numpy())
         finally:
             rec.close()
-    assert rel_l2(out[1], out[0]) < (1e-9 if prec == 1 else 1e-5)
+    for o in out[1:]:
+        assert rel_l2(o, out[0]) < (1e-9 if prec == 1 else 1e-5)
 
 
 def test_msclean_four_partitions_large_recipe(ctx, obs_large):
