@@ -286,6 +286,18 @@ uint64_t rix_kernel_launches(void);
 int rix_timing_enable(int on);
 int rix_timing_read(int kernel_class, double* total_ms, double* busy_ms, int64_t* launches);
 
+/* Self-test of the failure-detection path (a diagnostic; the paper has no
+ * counterpart).  Launches, on the context's device, a cooperative kernel of
+ * one CTA per SM whose first CTA never arrives at the library's bounded grid
+ * barrier: every other CTA's wait runs out (after about 2 s), the first one
+ * to give up stores RIX_ETIMEOUT in a status word, all of them return, and
+ * the call synchronises.  *status_out receives the status word (RIX_ETIMEOUT
+ * when detection works) and *gave_up_out the number of CTAs that left the
+ * barrier without it completing (all but one).  Returns RIX_OK when the
+ * kernel ran to completion, whatever the status; the context stays usable.
+ * Blocks the calling thread for the length of the wait. */
+int rix_selftest_barrier_timeout(rix_ctx_t ctx, int* status_out, int* gave_up_out);
+
 #ifdef __cplusplus
 }
 #endif

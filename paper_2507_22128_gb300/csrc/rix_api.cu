@@ -360,6 +360,12 @@ int rix_job_sync(rix_job_t job) {
   return check_status(&job->j);
 }
 
+int rix_selftest_barrier_timeout(rix_ctx_t ctx, int* status_out, int* gave_up_out) {
+  if (!ctx || !status_out || !gave_up_out) return set_error(RIX_EINVAL, "NULL argument");
+  RIX_CUDA(cudaSetDevice(ctx->c.device));
+  return selftest_barrier(&ctx->c, status_out, gave_up_out);
+}
+
 int rix_job_get_stats(rix_job_t job, rix_job_stats* out) {
   if (!job || !out) return set_error(RIX_EINVAL, "NULL argument");
   *out = job->j.stats;

@@ -241,6 +241,8 @@ int note_stream(Job* job, cudaStream_t st);
 // reads the job's device status word (the caller has synchronised the job's
 // streams); RIX_ETIMEOUT if a bounded device-side wait gave up
 int check_status(Job* job);
+// k_selftest.cu: bounded-barrier timeout self-test (rix_selftest_barrier_timeout)
+int selftest_barrier(Ctx* ctx, int* status_out, int* gave_up_out);
 
 // gridder entry points (k_grid.cu)
 template <typename R>

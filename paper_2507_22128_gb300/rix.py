@@ -79,6 +79,7 @@ def _load() -> C.CDLL:
         "rix_kernel_launches": (C.c_uint64, []),
         "rix_timing_enable": (C.c_int, [C.c_int]),
         "rix_timing_read": (C.c_int, [C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
+        "rix_selftest_barrier_timeout": (C.c_int, [vp, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -93,7 +94,8 @@ EXPORTED = ("rix_create", "rix_destroy", "rix_job_workspace_bytes", "rix_job_cre
             "rix_job_sync", "rix_job_get_stats", "rix_set_uv_partition", "rix_get_sorted_entries",
             "rix_degrid", "rix_grid", "rix_psf", "rix_major_cycle", "rix_minor_cycle_msclean",
             "rix_minor_cycle_fista", "rix_get_components", "rix_get_model", "rix_combine", "rix_last_error",
-            "rix_kernel_launches", "rix_timing_enable", "rix_timing_read", "rix_grid_noalloc")
+            "rix_kernel_launches", "rix_timing_enable", "rix_timing_read", "rix_grid_noalloc",
+            "rix_selftest_barrier_timeout")
 
 
 def _check(rc: int):
@@ -275,3 +277,10 @@ def timing_read(kernel_class: int):
 
 def combine(job, image_out, stream=None):
     _check(_lib.rix_combine(job, _ptr(image_out, _RT, name="image_out"), _stream(stream)))
+
+
+def selftest_barrier_timeout(ctx):
+    """Runs the bounded-barrier self-test; returns (status word, CTAs that gave up)."""
+    status, gave_up = C.c_int(), C.c_int()
+    _check(_lib.rix_selftest_barrier_timeout(ctx, C.byref(status), C.byref(gave_up)))
+    return status.value, gave_up.value
