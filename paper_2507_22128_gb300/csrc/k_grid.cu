@@ -203,6 +203,18 @@ struct TileArgs {
   const void* vis_in;       // cplx per sample
   void* vis_out;            // cplx per sample
   const float* weight;      // per sample or null
+  const void* geom;         // EntryGeom<R> per sorted entry (image-grid modes), null for the PSF
+};
+
+// Per sorted entry, fixed for the job: the kernel offsets du = ceil(xs) - xs,
+// dv, dw (rounded once from FP64 to the job's precision) and the first tap
+// relative to the entry's tile origin (ou | ov << 8).  Computed once at
+// partition time with the FP64 arithmetic the kernels used to repeat every
+// major cycle (GB300 runs FP64 at 1/64 of the FP32 rate).
+template <typename R>
+struct alignas(4 * sizeof(R)) EntryGeom {
+  R du, dv, dw;
+  uint32_t ouv;
 };
 
 template <int T, int MODE> struct TileGeom {
@@ -213,6 +225,40 @@ template <int T, int MODE> struct TileGeom {
   // half-warp land on disjoint banks
   static constexpr int PL = ((SP * SP + 7) / 16) * 16 + 8;
 };
+
+template <typename R>
+__global__ void k_entry_geom(TileArgs a, int64_t n, int T, EntryGeom<R>* __restrict__ out) {
+  const uint32_t tmask = (1u << a.bt) - 1u;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+    const uint32_t key = a.keys[e];
+    const int gu0 = (int)(key & tmask) * T, gv0 = (int)((key >> a.bt) & tmask) * T;
+    const uint32_t s = a.samples[e];
+    const int64_t row = s / (uint32_t)a.nchan;
+    const int ch = (int)(s - row * a.nchan);
+    const double sc = a.inv_lambda[ch];
+    const double ul = __dmul_rn(a.uvw[row * 3 + 0], sc);
+    const double vl = __dmul_rn(a.uvw[row * 3 + 1], sc);
+    const double x = __dadd_rn(__dmul_rn(ul, a.scale), a.half);
+    const double y = __dadd_rn(__dmul_rn(vl, a.scale), a.half);
+    const double xs = __dadd_rn(x, -0.5 * kW), ys = __dadd_rn(y, -0.5 * kW);
+    const double cx = ceil(xs), cy = ceil(ys);
+    int ou = (int)cx - gu0, ov = (int)cy - gv0;
+    EntryGeom<R> g;
+    g.du = (R)__dadd_rn(cx, -xs);
+    g.dv = (R)__dadd_rn(cy, -ys);
+    g.dw = R(0);
+    if (a.nw > 0) {
+      const double wl = __dmul_rn(a.uvw[row * 3 + 2], sc);
+      const double tw = __ddiv_rn(__dadd_rn(wl, -a.w_min), a.dw);
+      const double pc = fmin(fmax(ceil(tw), 0.0), (double)(a.nw - a.ww));
+      g.dw = (R)__dadd_rn(pc, -tw);
+    }
+    // the first tap lies in the entry's tile by construction of the key
+    if (ou < 0 || ov < 0 || ou >= T || ov >= T) { ou = 0; ov = 0; }
+    g.ouv = (uint32_t)ou | ((uint32_t)ov << 8);
+    out[e] = g;
+  }
+}
 
 template <typename R, int WW, int T, int MODE>
 __global__ void __launch_bounds__(256) k_tiles(TileArgs a) {
@@ -263,25 +309,37 @@ __global__ void __launch_bounds__(256) k_tiles(TileArgs a) {
     for (uint32_t base = e0 + warp * 32; base < e1; base += nwarps * 32) {
       const int nvalid = (int)min(32u, e1 - base);
       const bool valid = lane < nvalid;
-      // ---- per-lane sample geometry (FP64) ----
+      // ---- per-lane sample geometry ----
       const uint32_t s = valid ? a.samples[base + lane] : 0u;
-      const int64_t row = s / (uint32_t)a.nchan;
-      const int ch = (int)(s - row * a.nchan);
-      const double sc = a.inv_lambda[ch];
-      const double ul = __dmul_rn(a.uvw[row * 3 + 0], sc);
-      const double vl = __dmul_rn(a.uvw[row * 3 + 1], sc);
-      const double x = __dadd_rn(__dmul_rn(ul, a.scale), a.half);
-      const double y = __dadd_rn(__dmul_rn(vl, a.scale), a.half);
-      const double xs = __dadd_rn(x, -0.5 * kW), ys = __dadd_rn(y, -0.5 * kW);
-      const double cx = ceil(xs), cy = ceil(ys);
-      int ou = (int)cx - gu0, ov = (int)cy - gv0;
-      R du = (R)__dadd_rn(cx, -xs), dv = (R)__dadd_rn(cy, -ys);
-      R dwo = R(0);
-      if (WW > 1) {
-        const double wl = __dmul_rn(a.uvw[row * 3 + 2], sc);
-        const double tw = __ddiv_rn(__dadd_rn(wl, -a.w_min), a.dw);
-        double pc = fmin(fmax(ceil(tw), 0.0), (double)(a.nw - a.ww));
-        dwo = (R)__dadd_rn(pc, -tw);
+      int ou = 0, ov = 0;
+      R du = R(0), dv = R(0), dwo = R(0);
+      if constexpr (MODE != kPsf) {
+        // precomputed per entry at partition time
+        if (valid) {
+          const EntryGeom<R> g = static_cast<const EntryGeom<R>*>(a.geom)[base + lane];
+          ou = (int)(g.ouv & 0xffu);
+          ov = (int)(g.ouv >> 8);
+          du = g.du; dv = g.dv; dwo = g.dw;
+        }
+      } else {
+        // PSF: the 2N grid's geometry, in FP64 (once per partition and job)
+        const int64_t row = s / (uint32_t)a.nchan;
+        const int ch = (int)(s - row * a.nchan);
+        const double sc = a.inv_lambda[ch];
+        const double ul = __dmul_rn(a.uvw[row * 3 + 0], sc);
+        const double vl = __dmul_rn(a.uvw[row * 3 + 1], sc);
+        const double x = __dadd_rn(__dmul_rn(ul, a.scale), a.half);
+        const double y = __dadd_rn(__dmul_rn(vl, a.scale), a.half);
+        const double xs = __dadd_rn(x, -0.5 * kW), ys = __dadd_rn(y, -0.5 * kW);
+        const double cx = ceil(xs), cy = ceil(ys);
+        ou = (int)cx - gu0; ov = (int)cy - gv0;
+        du = (R)__dadd_rn(cx, -xs); dv = (R)__dadd_rn(cy, -ys);
+        if (WW > 1) {
+          const double wl = __dmul_rn(a.uvw[row * 3 + 2], sc);
+          const double tw = __ddiv_rn(__dadd_rn(wl, -a.w_min), a.dw);
+          double pc = fmin(fmax(ceil(tw), 0.0), (double)(a.nw - a.ww));
+          dwo = (R)__dadd_rn(pc, -tw);
+        }
       }
       if (!valid) { ou = 0; ov = 0; }
       // guard against any sample outside the staged region (never expected)
@@ -307,10 +365,9 @@ __global__ void __launch_bounds__(256) k_tiles(TileArgs a) {
         int rbase[RPL];      // smem offset of (plane, v row) of each row
         if constexpr (G == 32) {
           const R kdw = __shfl_sync(0xffffffffu, dwo, src);
-          R myw = R(0);
-          if (gl < 8) myw = es_weight<R>(kdu, gl);
-          else if (gl < 16) myw = es_weight<R>(kdv, gl - 8);
-          else if (gl < 16 + WW) myw = es_weight<R>(kdw, gl - 16);
+          // lanes 0-7: u weights, 8-15: v weights, 16 .. 16 + WW - 1: w weights
+          const R kd = gl < 8 ? kdu : (gl < 16 ? kdv : kdw);
+          const R myw = gl < 16 + WW ? es_weight<R>(kd, gl & 7) : R(0);
 #pragma unroll
           for (int i = 0; i < kW; ++i) wu[i] = __shfl_sync(0xffffffffu, myw, i);
           const int vrow = gl & 7, plh = gl >> 3;
@@ -436,7 +493,7 @@ template <typename R>
 struct WsRecord {
   R yr, yi;
   int ou, ov;
-  R wu[kW], wv[kW], ww[kW];
+  R w[3 * kW];          // u weights, v weights, w weights
 };
 
 constexpr int kWsBatch = 32;
@@ -490,21 +547,34 @@ __global__ void __launch_bounds__(256) k_tiles_ws(TileArgs a) {
         const int j0 = warp * per_warp;
         const bool valid = lane < per_warp && j0 + lane < nb;
         const uint32_t s = valid ? a.samples[base + j0 + lane] : 0u;
-        const int64_t row = s / (uint32_t)a.nchan;
-        const int ch = (int)(s - row * a.nchan);
-        const double sc = a.inv_lambda[ch];
-        const double ul = __dmul_rn(a.uvw[row * 3 + 0], sc);
-        const double vl = __dmul_rn(a.uvw[row * 3 + 1], sc);
-        const double wl = __dmul_rn(a.uvw[row * 3 + 2], sc);
-        const double x = __dadd_rn(__dmul_rn(ul, a.scale), a.half);
-        const double y = __dadd_rn(__dmul_rn(vl, a.scale), a.half);
-        const double xs = __dadd_rn(x, -0.5 * kW), ys = __dadd_rn(y, -0.5 * kW);
-        const double cx = ceil(xs), cy = ceil(ys);
-        int ou = (int)cx - gu0, ov = (int)cy - gv0;
-        const R du = (R)__dadd_rn(cx, -xs), dv = (R)__dadd_rn(cy, -ys);
-        const double tw = __ddiv_rn(__dadd_rn(wl, -a.w_min), a.dw);
-        const double pc = fmin(fmax(ceil(tw), 0.0), (double)(a.nw - a.ww));
-        const R dwo = (R)__dadd_rn(pc, -tw);
+        int ou = 0, ov = 0;
+        R du = R(0), dv = R(0), dwo = R(0);
+        if constexpr (MODE != kPsf) {
+          // precomputed per entry at partition time
+          if (valid) {
+            const EntryGeom<R> g = static_cast<const EntryGeom<R>*>(a.geom)[base + j0 + lane];
+            ou = (int)(g.ouv & 0xffu);
+            ov = (int)(g.ouv >> 8);
+            du = g.du; dv = g.dv; dwo = g.dw;
+          }
+        } else if (valid) {
+          // PSF: the 2N grid's geometry, in FP64 (once per partition and job)
+          const int64_t row = s / (uint32_t)a.nchan;
+          const int ch = (int)(s - row * a.nchan);
+          const double sc = a.inv_lambda[ch];
+          const double ul = __dmul_rn(a.uvw[row * 3 + 0], sc);
+          const double vl = __dmul_rn(a.uvw[row * 3 + 1], sc);
+          const double wl = __dmul_rn(a.uvw[row * 3 + 2], sc);
+          const double x = __dadd_rn(__dmul_rn(ul, a.scale), a.half);
+          const double y = __dadd_rn(__dmul_rn(vl, a.scale), a.half);
+          const double xs = __dadd_rn(x, -0.5 * kW), ys = __dadd_rn(y, -0.5 * kW);
+          const double cx = ceil(xs), cy = ceil(ys);
+          ou = (int)cx - gu0; ov = (int)cy - gv0;
+          du = (R)__dadd_rn(cx, -xs); dv = (R)__dadd_rn(cy, -ys);
+          const double tw = __ddiv_rn(__dadd_rn(wl, -a.w_min), a.dw);
+          const double pc = fmin(fmax(ceil(tw), 0.0), (double)(a.nw - a.ww));
+          dwo = (R)__dadd_rn(pc, -tw);
+        }
         if (!valid || ou < 0 || ov < 0 || ou > SP - kW || ov > SP - kW) { ou = 0; ov = 0; }
         R vre = R(0), vim = R(0), wt = R(0);
         if (valid) {
@@ -518,14 +588,11 @@ __global__ void __launch_bounds__(256) k_tiles_ws(TileArgs a) {
           const R kdu = __shfl_sync(0xffffffffu, du, j);
           const R kdv = __shfl_sync(0xffffffffu, dv, j);
           const R kdw = __shfl_sync(0xffffffffu, dwo, j);
-          R myw = R(0);
-          if (lane < 8) myw = es_weight<R>(kdu, lane);
-          else if (lane < 16) myw = es_weight<R>(kdv, lane - 8);
-          else if (lane < 24) myw = es_weight<R>(kdw, lane - 16);
+          // lanes 0-7: u weights, 8-15: v weights, 16-23: w weights
+          const R kd = lane < 8 ? kdu : (lane < 16 ? kdv : kdw);
+          const R myw = lane < 24 ? es_weight<R>(kd, lane & 7) : R(0);
           WsRecord<R>& rc = rec[j0 + j];
-          if (lane < 8) rc.wu[lane] = myw;
-          else if (lane < 16) rc.wv[lane - 8] = myw;
-          else if (lane < 24) rc.ww[lane - 16] = myw;
+          if (lane < 24) rc.w[lane] = myw;
           R accr = R(0), acci = R(0);
           if constexpr (kUseModel) {
             R wu[kW];
@@ -572,10 +639,10 @@ __global__ void __launch_bounds__(256) k_tiles_ws(TileArgs a) {
         C* gpl = sm_grid + warp * PL;
         for (int k = 0; k < nb; ++k) {
           const WsRecord<R>& rc = rec[k];
-          const R f = rc.ww[warp] * rc.wv[vrow];
+          const R f = rc.w[2 * kW + warp] * rc.w[kW + vrow];
           const R cr = rc.yr * f, ci = rc.yi * f;
           C* cell = gpl + (rc.ou + ig) * SPP + rc.ov + vrow;
-          const R w0 = rc.wu[ig], w1 = rc.wu[ig + 4];
+          const R w0 = rc.w[ig], w1 = rc.w[ig + 4];
           C g0 = cell[0], g1 = cell[4 * SPP];
           g0.x += cr * w0; g0.y += ci * w0;
           g1.x += cr * w1; g1.y += ci * w1;
@@ -659,6 +726,7 @@ TileArgs base_args(const Job* job, const Part& pt) {
   a.win_lo = pt.win_lo;
   a.S = pt.win_n;
   a.weight = job->weight.as<float>();
+  a.geom = job->egeom.p;
   return a;
 }
 
@@ -801,6 +869,7 @@ int op_psf(Job* job, int p, cudaStream_t st) {
     TileArgs a = base_args(job, pt);
     a.scale = job->desc.cell_rad * (double)(2 * job->ng);
     a.half = (double)job->ng;
+    a.geom = nullptr;
     a.win_lo = pt.pwin_lo;
     a.S = pt.pwin_n;
     a.out = pp;
@@ -851,8 +920,22 @@ int op_grid_into_scratch(Job* job, int p, const float2* vis, float* image_out, f
   return inv_rows<float>(job->ctx, g, tbuf, image_out, sc, 0, st);
 }
 
+template <typename R>
+int grid_entry_geometry(Job* job, cudaStream_t st) {
+  const int64_t n = job->n_entries;
+  RIX_TRY(job->egeom.alloc(job->ctx, (size_t)std::max<int64_t>(n, 1) * sizeof(EntryGeom<R>)));
+  if (n == 0) return RIX_OK;
+  const TileArgs a = base_args(job, job->part[0]);   // job-level fields only
+  const int blocks = (int)std::min<int64_t>(ceil_div(n, 256), (int64_t)job->ctx->num_sms * 16);
+  ::rix::note_launch();
+  k_entry_geom<R><<<blocks, 256, 0, st>>>(a, n, job->tile, job->egeom.as<EntryGeom<R>>());
+  RIX_LAUNCH_CHECK();
+  return RIX_OK;
+}
+
 #define RIX_GRID_INST(R)                                                               \
   template int grid_build_corrections<R>(Job*, cudaStream_t);                          \
+  template int grid_entry_geometry<R>(Job*, cudaStream_t);                             \
   template int op_degrid<R>(Job*, int, const R*, cplx<R>*, cudaStream_t);              \
   template int op_grid<R>(Job*, int, const cplx<R>*, R*, cudaStream_t);                \
   template int op_major<R>(Job*, int, const cplx<R>*, R*, cudaStream_t);               \

@@ -122,6 +122,7 @@ static size_t workspace_bytes(const rix_job_desc& d, int64_t nrow) {
   size_t b = 0;
   b += (size_t)nrow * 24 + ns * 4;                 // uvw, weights
   b += ns * std::min<size_t>(P, 2) * 8;            // sorted keys and samples (overlap counted twice)
+  b += ns * std::min<size_t>(P, 2) * 4 * real;     // per-entry kernel geometry
   b += ns / 512 * 4 + 64;                          // work items
   b += n * n * (real + 8) + 4 * n * n * (real + 8); // corrections + n-1 tables (image and PSF)
   b += P * 4 * n * n * real;                       // Gamma filters
@@ -385,6 +386,8 @@ static int rix_set_uv_partition_impl(rix_job_t job, const double* uvw_m, int64_t
   RIX_TRY(partition_job(&J, uvw_m, nrow, weight, ell_px, delta_px, mask_out, st));
   if (J.fp64) RIX_TRY(grid_build_corrections<double>(&J, st));
   else RIX_TRY(grid_build_corrections<float>(&J, st));
+  if (J.fp64) RIX_TRY(grid_entry_geometry<double>(&J, st));
+  else RIX_TRY(grid_entry_geometry<float>(&J, st));
   if (J.fp64) RIX_TRY(fill_init<double>(&J, st));
   else RIX_TRY(fill_init<float>(&J, st));
   for (int p = 0; p < J.n_part; ++p) RIX_TRY(ensure_images(&J, J.part[p], st));

@@ -221,6 +221,7 @@ struct Job {
   DevBuf uvw, weight, inv_lambda;
   // sort
   DevBuf keys, samples, items;              // entries and work-item begin offsets (+1 sentinel)
+  DevBuf egeom;                             // per sorted entry: kernel offsets and tap origin (see k_grid.cu)
   int64_t n_entries = 0, n_items = 0;
   int bt = 0, bw = 0, bp = 0;
   // corrections
@@ -247,6 +248,8 @@ int selftest_barrier(Ctx* ctx, int* status_out, int* gave_up_out);
 // gridder entry points (k_grid.cu)
 template <typename R>
 int grid_build_corrections(Job* job, cudaStream_t st);
+template <typename R>
+int grid_entry_geometry(Job* job, cudaStream_t st);
 template <typename R>
 int op_degrid(Job* job, int p, const R* image, cplx<R>* vis_out, cudaStream_t st);
 template <typename R>
