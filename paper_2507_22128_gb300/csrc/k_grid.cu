@@ -15,6 +15,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstddef>
 #include <cmath>
 #include <vector>
 
@@ -270,7 +271,7 @@ __global__ void __launch_bounds__(256) k_tiles(TileArgs a) {
   constexpr int RPL = WW * kW / G;            // rows of 8 taps per lane
   constexpr bool kUseModel = (MODE == kDegrid || MODE == kResid);
   constexpr bool kUseGrid = (MODE != kDegrid);
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+  extern __shared__ __align__(32) unsigned char smem_raw[];
   C* sm_model = reinterpret_cast<C*>(smem_raw);
   C* sm_grid = sm_model + (kUseModel ? WW * PL : 0);
 
@@ -490,11 +491,28 @@ template <int T, int MODE> struct WsGeom {
 };
 
 template <typename R>
-struct WsRecord {
+struct alignas(4 * sizeof(R)) WsRecord {
+  // header, one vector load: weighted residual and the tap origin (ou | ov << 8)
   R yr, yi;
-  int ou, ov;
-  R w[3 * kW];          // u weights, v weights, w weights
+  uint32_t ouv;
+  uint32_t pad[sizeof(R) == 8 ? 3 : 1];   // the weights start on a 4 sizeof(R) boundary
+  // u weights in pairs (u_i, u_{i+4}) at [2i, 2i + 1] for i < 4, then the 8
+  // v weights and the 8 w weights
+  R w[3 * kW];
 };
+
+// header of a record as loaded by phase B
+static_assert(offsetof(WsRecord<float>, w) == 16 && sizeof(WsRecord<float>) % 16 == 0, "record layout");
+static_assert(offsetof(WsRecord<double>, w) == 32 && sizeof(WsRecord<double>) % 32 == 0, "record layout");
+template <typename R> struct WsHead { R yr, yi; uint32_t ouv; };
+__device__ __forceinline__ WsHead<float> ws_head(const WsRecord<float>& r) {
+  const float4 h = *reinterpret_cast<const float4*>(&r);
+  return {h.x, h.y, __float_as_uint(h.z)};
+}
+__device__ __forceinline__ WsHead<double> ws_head(const WsRecord<double>& r) {
+  const double2 h = *reinterpret_cast<const double2*>(&r);
+  return {h.x, h.y, r.ouv};
+}
 
 constexpr int kWsBatch = 32;
 
@@ -504,10 +522,11 @@ __global__ void __launch_bounds__(256) k_tiles_ws(TileArgs a) {
   using TG = WsGeom<T, MODE>;
   constexpr int SP = TG::SP, SPP = TG::SPP, PL = TG::PL;
   constexpr bool kUseModel = (MODE == kResid);
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+  extern __shared__ __align__(32) unsigned char smem_raw[];
   C* sm_model = reinterpret_cast<C*>(smem_raw);
   C* sm_grid = sm_model + (kUseModel ? kW * PL : 0);
   WsRecord<R>* rec = reinterpret_cast<WsRecord<R>*>(sm_grid + kW * PL);
+  EntryGeom<R>* psf_geo = reinterpret_cast<EntryGeom<R>*>(rec + kWsBatch);   // PSF only
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
   const int64_t SS = (int64_t)a.S * a.S;
@@ -542,23 +561,11 @@ __global__ void __launch_bounds__(256) k_tiles_ws(TileArgs a) {
 
     for (uint32_t base = e0; base < e1; base += kWsBatch) {
       const int nb = (int)min((uint32_t)kWsBatch, e1 - base);
-      // ---------------- phase A: geometry, weights, degrid, records ----------
-      {
-        const int j0 = warp * per_warp;
-        const bool valid = lane < per_warp && j0 + lane < nb;
-        const uint32_t s = valid ? a.samples[base + j0 + lane] : 0u;
-        int ou = 0, ov = 0;
-        R du = R(0), dv = R(0), dwo = R(0);
-        if constexpr (MODE != kPsf) {
-          // precomputed per entry at partition time
-          if (valid) {
-            const EntryGeom<R> g = static_cast<const EntryGeom<R>*>(a.geom)[base + j0 + lane];
-            ou = (int)(g.ouv & 0xffu);
-            ov = (int)(g.ouv >> 8);
-            du = g.du; dv = g.dv; dwo = g.dw;
-          }
-        } else if (valid) {
-          // PSF: the 2N grid's geometry, in FP64 (once per partition and job)
+      if constexpr (MODE == kPsf) {
+        // the 2N grid's geometry of the batch, in FP64, one sample per lane of
+        // warp 0 (once per partition and job)
+        if (warp == 0 && lane < nb) {
+          const uint32_t s = a.samples[base + lane];
           const int64_t row = s / (uint32_t)a.nchan;
           const int ch = (int)(s - row * a.nchan);
           const double sc = a.inv_lambda[ch];
@@ -569,11 +576,34 @@ __global__ void __launch_bounds__(256) k_tiles_ws(TileArgs a) {
           const double y = __dadd_rn(__dmul_rn(vl, a.scale), a.half);
           const double xs = __dadd_rn(x, -0.5 * kW), ys = __dadd_rn(y, -0.5 * kW);
           const double cx = ceil(xs), cy = ceil(ys);
-          ou = (int)cx - gu0; ov = (int)cy - gv0;
-          du = (R)__dadd_rn(cx, -xs); dv = (R)__dadd_rn(cy, -ys);
+          int ou = (int)cx - gu0, ov = (int)cy - gv0;
+          if (ou < 0 || ov < 0 || ou > SP - kW || ov > SP - kW) { ou = 0; ov = 0; }
           const double tw = __ddiv_rn(__dadd_rn(wl, -a.w_min), a.dw);
           const double pc = fmin(fmax(ceil(tw), 0.0), (double)(a.nw - a.ww));
-          dwo = (R)__dadd_rn(pc, -tw);
+          EntryGeom<R> g;
+          g.du = (R)__dadd_rn(cx, -xs);
+          g.dv = (R)__dadd_rn(cy, -ys);
+          g.dw = (R)__dadd_rn(pc, -tw);
+          g.ouv = (uint32_t)ou | ((uint32_t)ov << 8);
+          psf_geo[lane] = g;
+        }
+        __syncthreads();
+      }
+      // ---------------- phase A: weights, degrid, records ----------------------
+      {
+        const int j0 = warp * per_warp;
+        const bool valid = lane < per_warp && j0 + lane < nb;
+        const uint32_t s = valid ? a.samples[base + j0 + lane] : 0u;
+        int ou = 0, ov = 0;
+        R du = R(0), dv = R(0), dwo = R(0);
+        if (valid) {
+          // image grid: precomputed per entry at partition time; PSF: formed
+          // for the batch by warp 0 above
+          const EntryGeom<R> g = (MODE == kPsf) ? psf_geo[j0 + lane]
+                                                : static_cast<const EntryGeom<R>*>(a.geom)[base + j0 + lane];
+          ou = (int)(g.ouv & 0xffu);
+          ov = (int)(g.ouv >> 8);
+          du = g.du; dv = g.dv; dwo = g.dw;
         }
         if (!valid || ou < 0 || ov < 0 || ou > SP - kW || ov > SP - kW) { ou = 0; ov = 0; }
         R vre = R(0), vim = R(0), wt = R(0);
@@ -592,7 +622,7 @@ __global__ void __launch_bounds__(256) k_tiles_ws(TileArgs a) {
           const R kd = lane < 8 ? kdu : (lane < 16 ? kdv : kdw);
           const R myw = lane < 24 ? es_weight<R>(kd, lane & 7) : R(0);
           WsRecord<R>& rc = rec[j0 + j];
-          if (lane < 24) rc.w[lane] = myw;
+          if (lane < 24) rc.w[lane < 8 ? 2 * (lane & 3) + (lane >> 2) : lane] = myw;
           R accr = R(0), acci = R(0);
           if constexpr (kUseModel) {
             R wu[kW];
@@ -627,8 +657,7 @@ __global__ void __launch_bounds__(256) k_tiles_ws(TileArgs a) {
           if (lane == 0) {
             rc.yr = kwt * (kvr - accr);
             rc.yi = kwt * (kvi - acci);
-            rc.ou = kou;
-            rc.ov = kov;
+            rc.ouv = (uint32_t)kou | ((uint32_t)kov << 8);
           }
         }
       }
@@ -639,10 +668,13 @@ __global__ void __launch_bounds__(256) k_tiles_ws(TileArgs a) {
         C* gpl = sm_grid + warp * PL;
         for (int k = 0; k < nb; ++k) {
           const WsRecord<R>& rc = rec[k];
+          const WsHead<R> hd = ws_head(rc);
           const R f = rc.w[2 * kW + warp] * rc.w[kW + vrow];
-          const R cr = rc.yr * f, ci = rc.yi * f;
-          C* cell = gpl + (rc.ou + ig) * SPP + rc.ov + vrow;
-          const R w0 = rc.w[ig], w1 = rc.w[ig + 4];
+          const R cr = hd.yr * f, ci = hd.yi * f;
+          C* cell = gpl + ((int)(hd.ouv & 0xffu) + ig) * SPP + (int)(hd.ouv >> 8) + vrow;
+          using R2 = cplx<R>;
+          const R2 wp = *reinterpret_cast<const R2*>(&rc.w[2 * ig]);
+          const R w0 = wp.x, w1 = wp.y;
           C g0 = cell[0], g1 = cell[4 * SPP];
           g0.x += cr * w0; g0.y += ci * w0;
           g1.x += cr * w1; g1.y += ci * w1;
@@ -676,7 +708,8 @@ template <typename R, int T, int MODE>
 int launch_tiles_ws(const Ctx* ctx, const TileArgs& a, cudaStream_t st) {
   using TG = WsGeom<T, MODE>;
   constexpr bool kUseModel = (MODE == kResid);
-  const size_t sm = (size_t)(int(kUseModel) + 1) * kW * TG::PL * sizeof(cplx<R>) + kWsBatch * sizeof(WsRecord<R>);
+  const size_t sm = (size_t)(int(kUseModel) + 1) * kW * TG::PL * sizeof(cplx<R>) + kWsBatch * sizeof(WsRecord<R>) +
+                    (MODE == kPsf ? kWsBatch * sizeof(EntryGeom<R>) : 0);
   auto kern = k_tiles_ws<R, T, MODE>;
   RIX_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
   int per_sm = 0;
