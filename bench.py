@@ -397,8 +397,20 @@ def roofline_tiles(tiles_ms, tiles_n, st, a, entries_timed):
     peak = 152 * lanes * 2 * clk * 1e6 / 1e12
     flops = 4096.0 * entries_timed
     ach = flops / (tiles_ms * 1e-3) / 1e12
+    # secondary: HBM against the measured copy bandwidth, with the algorithmic
+    # bytes of the residual launches (per entry: uvw 24/nchan + visibility 8 +
+    # weight 4 + index 4 B; per w-plane of the partition's uv window: model
+    # read + residual write, 2 x 8 B per cell)
+    nchan = 4
+    ent_b = (24.0 / nchan + 8 + 4 + 4) * entries_timed
+    win = st["window_size"][:2]
+    plane_b = a.steps * a.cycles * sum(2 * 8.0 * 16 * w * w for w in win)
+    hbm = (ent_b + plane_b) / (tiles_ms * 1e-3) / 1e9
+    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
     return {"bound": "alu", "kernel": "k_tiles (degrid + residual + grid, w-stacked, T=16)",
             "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+            "hbm": {"achieved_gbs": hbm, "peak_gbs": hbm_peak, "frac": hbm / hbm_peak,
+                    "algorithmic_bytes_per_launch": (ent_b + plane_b) / tiles_n, "peak_source": kind},
             "traffic": tiles_traffic(a), "traffic_unit": "B per launch",
             "launches_timed": tiles_n, "busy_ms_per_launch": tiles_ms / tiles_n,
             "peak_source": f"152 SMs x {lanes} {'FP64' if a.fp64 else 'FP32'} lanes x 2 flop x {clk:.0f} MHz "
