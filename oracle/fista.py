@@ -70,15 +70,25 @@ def soft(x: np.ndarray, t: float) -> np.ndarray:
     return np.sign(x) * np.maximum(np.abs(x) - t, 0.0)
 
 
-def solve(prob: Problem, lam: float, n_iter: int, levels: int, accelerate: bool = True):
-    """Returns (i_bar, alpha)."""
+def _operators(levels: int, dictionary):
+    """(W, W^T, coefficient shape) of the Db4 basis (dictionary None) or of a
+    wavelet.Concatenation."""
+    if dictionary is None:
+        return (lambda c: wavelet.idwt2(c, levels)), (lambda x: wavelet.dwt2(x, levels)), (lambda n: (n, n))
+    return dictionary.synthesis, dictionary.analysis, dictionary.shape
+
+
+def solve(prob: Problem, lam: float, n_iter: int, levels: int, accelerate: bool = True, dictionary=None):
+    """Returns (i_bar, alpha).  ``dictionary``: None for the Db4 basis, or a
+    wavelet.Concatenation (the tight frame keeps L = 2 max Mx a bound)."""
     n = prob.n
     L = prob.lipschitz
-    alpha = np.zeros((n, n))
+    W, WT, shape = _operators(levels, dictionary)
+    alpha = np.zeros(shape(n))
     y = alpha.copy()
     t = 1.0
     for _ in range(n_iter):
-        g = wavelet.dwt2(prob.grad(wavelet.idwt2(y, levels)), levels)
+        g = WT(prob.grad(W(y)))
         alpha_new = soft(y - g / L, lam / L)
         if accelerate:
             t_new = 0.5 * (1.0 + np.sqrt(1.0 + 4.0 * t * t))
@@ -87,8 +97,9 @@ def solve(prob: Problem, lam: float, n_iter: int, levels: int, accelerate: bool 
         else:
             y = alpha_new
         alpha = alpha_new
-    return wavelet.idwt2(alpha, levels), alpha
+    return W(alpha), alpha
 
 
-def objective(prob: Problem, alpha: np.ndarray, lam: float, levels: int) -> float:
-    return prob.data_term(wavelet.idwt2(alpha, levels)) + lam * float(np.abs(alpha).sum())
+def objective(prob: Problem, alpha: np.ndarray, lam: float, levels: int, dictionary=None) -> float:
+    W, _, _ = _operators(levels, dictionary)
+    return prob.data_term(W(alpha)) + lam * float(np.abs(alpha).sum())

@@ -23,7 +23,7 @@ import dataclasses
 
 import numpy as np
 
-from . import filters, fista, gridder, msclean, partition
+from . import filters, fista, gridder, msclean, partition, wavelet
 
 
 @dataclasses.dataclass
@@ -127,14 +127,24 @@ class Loop:
         self._publish(p, cycle, res.model)
         return res
 
-    def minor_fista(self, p: int, cycle: int, lam_rel=1e-3, lam=None, n_iter=50, levels=4):
+    def minor_fista(self, p: int, cycle: int, lam_rel=1e-3, lam=None, n_iter=50, levels=4, dictionary="db4",
+                    schedule=None):
+        """lambda: ``lam`` if given; else with ``schedule`` = (a, b) the paper's
+        lambda_n = a ||i_p^n||_2 b^n (Sec. 5.2; i_p^n the partition's residual
+        image of this cycle, n the cycle number from 1); else lam_rel times
+        max |i_p^1| of the partition's first residual.  ``dictionary``: "db4"
+        or "sara" (db1 .. db8 concatenated)."""
         self._ingest(p, cycle)
+        if lam is None and schedule is not None:
+            a, b = schedule
+            lam = a * float(np.linalg.norm(self.residual[p])) * b ** cycle
         if lam is None:
             if self.lam[p] is None:
                 self.lam[p] = lam_rel * float(np.abs(self.residual[p]).max())
             lam = self.lam[p]
         prob = self.fista_problem(p, cycle)
-        ibar, alpha = fista.solve(prob, lam, n_iter, levels)
+        dic = None if dictionary == "db4" else wavelet.Concatenation(levels)
+        ibar, alpha = fista.solve(prob, lam, n_iter, levels, dictionary=dic)
         self._publish(p, cycle, ibar)
         return ibar
 

@@ -1,13 +1,16 @@
-"""Daubechies-4 wavelet (8 taps, 4 vanishing moments) and the periodic
-orthonormal 2D DWT used as the dictionary W of Eq. 4-5.
+"""Daubechies wavelets and the periodic orthonormal 2D DWT used as the
+dictionary W of Eq. 4-5.
 
-The paper's dictionary is a concatenation of the first 8 Daubechies wavelets
-(Sec. 5.2); the hot path uses the Db4 member alone (a single orthonormal
-basis, so W^T W = I).
+Two dictionaries: the Db4 member alone (8 taps, 4 vanishing moments; a single
+orthonormal basis, W^T W = I), and the paper's concatenation of the first 8
+Daubechies wavelets (Sec. 5.2): W = [Psi_1 ... Psi_8] / sqrt(8) with Psi_p the
+orthonormal periodic DWT of db_p (2p taps, p vanishing moments), a tight frame
+(W W^T = I, so ||W|| = 1 and the Lipschitz bound of the FISTA problem is
+unchanged).  Each basis is transformed independently (Sec. 5.3).
 
 Filter: Daubechies' construction.  With y = sin^2(w/2), the squared modulus
 of the low-pass response is cos^{2N}(w/2) P(y), P(y) = sum_{k<N}
-binom(N-1+k, k) y^k, N = 4.  Substituting y = (2 - z - 1/z)/4 makes z^{N-1}
+binom(N-1+k, k) y^k for N vanishing moments.  Substituting y = (2 - z - 1/z)/4 makes z^{N-1}
 P a degree-2(N-1) polynomial whose roots come in pairs (r, 1/r); keeping the
 roots inside the unit circle (spectral factorisation) and multiplying by
 (1 + z)^N gives the filter, normalised to sum sqrt(2).  Coefficients are
@@ -48,8 +51,17 @@ def daubechies(nvm: int = 4) -> np.ndarray:
     return h.copy()
 
 
+def highpass(h: np.ndarray) -> np.ndarray:
+    """g[i] = (-1)^i h[K - 1 - i]."""
+    k = h.shape[0]
+    return np.array([(-1) ** i * h[k - 1 - i] for i in range(k)])
+
+
 H_DB4 = daubechies(4)
-G_DB4 = np.array([(-1) ** i * H_DB4[len(H_DB4) - 1 - i] for i in range(len(H_DB4))])
+G_DB4 = highpass(H_DB4)
+
+# db1 .. db8, the members of the concatenated dictionary (Sec. 5.2)
+SARA_ORDERS = tuple(range(1, 9))
 
 
 def _analysis_last_axis(x: np.ndarray, h: np.ndarray, g: np.ndarray):
@@ -92,3 +104,27 @@ def idwt2(c: np.ndarray, levels: int, h: np.ndarray = H_DB4, g: np.ndarray = G_D
         rows = _synthesis_last_axis(cols[:, :n // 2], cols[:, n // 2:], h, g)
         x[:n, :n] = rows
     return x
+
+
+class Concatenation:
+    """W = [Psi_p1 ... Psi_pm] / sqrt(m): coefficients of shape (m, n, n), one
+    orthonormal periodic DWT (``levels`` levels) per member filter."""
+
+    def __init__(self, levels: int, orders=SARA_ORDERS):
+        self.levels = levels
+        self.filters = [(h, highpass(h)) for h in (daubechies(p) for p in orders)]
+        self.scale = 1.0 / np.sqrt(len(self.filters))
+
+    def shape(self, n: int) -> tuple:
+        return (len(self.filters), n, n)
+
+    def synthesis(self, c: np.ndarray) -> np.ndarray:
+        """x = W c = sum_p Psi_p c_p / sqrt(m)."""
+        x = np.zeros(c.shape[1:])
+        for k, (h, g) in enumerate(self.filters):
+            x += idwt2(c[k], self.levels, h, g)
+        return self.scale * x
+
+    def analysis(self, x: np.ndarray) -> np.ndarray:
+        """W^T x = [Psi_p^T x] / sqrt(m)."""
+        return self.scale * np.stack([dwt2(x, self.levels, h, g) for h, g in self.filters])

@@ -77,3 +77,37 @@ def test_fista_beats_ista_after_50():
     _, a_f = fista.solve(prob, lam, 50, 2, accelerate=True)
     _, a_i = fista.solve(prob, lam, 50, 2, accelerate=False)
     assert fista.objective(prob, a_f, lam, 2) <= fista.objective(prob, a_i, lam, 2)
+
+
+def test_kkt_with_the_concatenated_dictionary():
+    prob, n = _problem(seed=6, n=8)
+    d = wavelet.Concatenation(2)
+    lam = 0.3 * float(np.abs(d.analysis(prob.grad(np.zeros((n, n))))).max())
+    _, alpha = fista.solve(prob, lam, 2000, 2, dictionary=d)
+    g = d.analysis(prob.grad(d.synthesis(alpha)))
+    zero = alpha == 0
+    assert zero.any() and (~zero).any()
+    assert np.all(np.abs(g[zero]) <= lam * (1 + 1e-6))
+    assert np.allclose(g[~zero], -lam * np.sign(alpha[~zero]), atol=1e-5 * lam)
+
+
+def test_fista_beats_ista_with_the_concatenated_dictionary():
+    prob, n = _problem(seed=8)
+    d = wavelet.Concatenation(2)
+    lam = 0.2
+    _, a_f = fista.solve(prob, lam, 50, 2, dictionary=d)
+    _, a_i = fista.solve(prob, lam, 50, 2, accelerate=False, dictionary=d)
+    assert fista.objective(prob, a_f, lam, 2, d) <= fista.objective(prob, a_i, lam, 2, d)
+
+
+def test_lambda_at_the_kkt_threshold_gives_the_zero_solution():
+    """alpha = 0 is optimal iff lambda >= max |W^T grad f(0)|; FISTA from 0
+    stays at 0 above the threshold and moves below it (both dictionaries)."""
+    prob, n = _problem(seed=9)
+    for d in (None, wavelet.Concatenation(2)):
+        W, WT, _ = fista._operators(2, d)
+        thr = float(np.abs(WT(prob.grad(np.zeros((n, n))))).max())
+        above, _ = fista.solve(prob, 1.001 * thr, 20, 2, dictionary=d)
+        below, _ = fista.solve(prob, 0.99 * thr, 20, 2, dictionary=d)
+        assert np.all(above == 0.0)
+        assert np.abs(below).max() > 0.0

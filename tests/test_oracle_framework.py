@@ -90,3 +90,25 @@ def test_snr_improves_over_cycles(small_setup2):
         loop.exchange()
         snrs.append(framework.snr_db(truth, loop.combine()))
     assert snrs[-1] > snrs[0]
+
+
+def test_single_partition_sara_with_lambda_schedule_is_serial(obs_small):
+    """P = 1 with the concatenated db1..db8 dictionary and the paper's
+    lambda_n = a ||i^n||_2 b^n is serial FISTA (Eq. 4) with that dictionary."""
+    from oracle import wavelet
+    o = obs_small
+    a, b = 2e-4, 1.5
+    st = framework.setup(o.uvw, o.freq, o.weight, o.n, o.cell_rad, 0, 1)
+    loop = framework.run(st, o.vis, o.weight, 2, "fista", n_iter=8, levels=2, dictionary="sara", schedule=(a, b))
+    g = gridder.geometry(o.uvw, o.freq, o.n, o.cell_rad, W=8, nw=0)
+    g2 = gridder.geometry(o.uvw, o.freq, o.n, o.cell_rad, W=8, nw=0, image_scale=2)
+    w = o.weight.reshape(-1).astype(np.float64)
+    hs = filters.psf_spectrum(gridder.psf(w, g2))
+    d = wavelet.Concatenation(2)
+    model = np.zeros((o.n, o.n))
+    for n in (1, 2):
+        res = gridder.residual(o.vis.reshape(-1), w, model, g)
+        prob = fista.problem(filters.image_spectrum(res), hs, np.ones_like(hs.real), [], 0.0)
+        model = model + fista.solve(prob, a * np.linalg.norm(res) * b ** n, 8, 2, dictionary=d)[0]
+    assert np.max(np.abs(loop.combine() - model)) < 1e-12
+    assert np.abs(model).max() > 0.0
