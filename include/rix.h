@@ -104,11 +104,19 @@ typedef struct {
 } rix_msclean_params;
 
 /* FISTA parameters (Eq. 4-5; Sec. 5.2). */
+#define RIX_DICT_DB4 0        /* W = the orthonormal periodic Db4 basis */
+#define RIX_DICT_DB1_8 1      /* W = [Psi_db1 ... Psi_db8] / sqrt(8), the paper's concatenation of the
+                               * first 8 Daubechies wavelets (a tight frame: W W^T = I) */
 typedef struct {
   double lambda;              /* > 0: absolute regularisation weight */
   double lambda_rel;          /* used when lambda <= 0: lambda = lambda_rel * max|residual| of cycle 1 */
   int32_t iters;              /* FISTA iterations per major cycle (50 in the paper) */
-  int32_t levels;             /* Db4 decomposition levels, 1 .. log2(N) - 3 */
+  int32_t levels;             /* wavelet decomposition levels, 1 .. log2(N) - 3 */
+  int32_t dictionary;         /* RIX_DICT_DB4 or RIX_DICT_DB1_8 */
+  int32_t reserved;           /* 0 */
+  double sched_a, sched_b;    /* sched_a > 0: lambda_n = sched_a * ||residual of cycle n||_2 * sched_b^n
+                               * (Sec. 5.2; n = the cycle number from 1), overriding lambda and
+                               * lambda_rel; sched_b > 0 */
 } rix_fista_params;
 
 /* ---- context and job lifetime --------------------------------------------- */
@@ -215,8 +223,8 @@ int rix_minor_cycle_msclean(rix_job_t job, int part, const rix_msclean_params* p
  * n_part = 1): FISTA on
  *   ||Gamma_p (i_p - H_p W alpha)||^2 + gamma_n sum_q ||rho_{q->p} - Gamma_q W alpha||^2
  *   + lambda ||alpha||_1
- * with W the orthonormal periodic Db4 wavelet basis, gamma_n = 0 at n = 1
- * and 1 afterwards. */
+ * with W the orthonormal periodic Db4 wavelet basis or the concatenation of
+ * db1 .. db8 (params->dictionary), gamma_n = 0 at n = 1 and 1 afterwards. */
 int rix_minor_cycle_fista(rix_job_t job, int part, const rix_fista_params* params,
                           void* delta_out, rix_stream_t stream);
 
@@ -285,6 +293,12 @@ uint64_t rix_kernel_launches(void);
 #define RIX_TIME_PARTITION 2
 int rix_timing_enable(int on);
 int rix_timing_read(int kernel_class, double* total_ms, double* busy_ms, int64_t* launches);
+
+/* The Daubechies low-pass filter with p vanishing moments (p in 1 .. 8) that
+ * the concatenated dictionary uses: writes its 2p taps to h_out (host memory,
+ * room for 2p doubles), minimum phase, sum sqrt(2), and returns 2p (a
+ * negative RIX_E* code on bad arguments).  Host-only; no device needed. */
+int rix_daubechies_lowpass(int p, double* h_out);
 
 /* Self-test of the failure-detection path (a diagnostic; the paper has no
  * counterpart).  Launches, on the context's device, a cooperative kernel of

@@ -13,6 +13,11 @@
 //               momentum-accelerated step fused into the final coefficients.
 // Phases hand their units (wavelet tiles, row pairs, column batches) out over
 // the CTAs.  All image-sized buffers stay in L2 between phases.
+//
+// With the concatenated dictionary (db1 .. db8, scaled by 1/sqrt 8) every
+// wavelet phase runs the levels of all eight members at once (units =
+// member x tile), the row phase sums the members' syntheses, and a last
+// synthesis of alpha writes the minor cycle's image.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -26,7 +31,7 @@
 namespace rix {
 namespace {
 
-template <typename R, int LOGL>
+template <typename R, int LOGL, int DICT = RIX_DICT_DB4>
 struct FistaShape {
   static constexpr int L = 1 << LOGL;
   static constexpr int N = L / 2;          // image side
@@ -41,10 +46,10 @@ struct FistaShape {
   static constexpr int kRowUnits = N / (2 * B);
   static constexpr int kColUnits = (S + B - 1) / B;
   static constexpr size_t kFftSmem = 2 * (size_t)B * STRIDE * sizeof(cplx<R>);
-  static constexpr size_t kSmem = kFftSmem > sizeof(DwtSmem<R>)
-                                      ? (kFftSmem > sizeof(IdwtSmem<R>) ? kFftSmem : sizeof(IdwtSmem<R>))
-                                      : (sizeof(DwtSmem<R>) > sizeof(IdwtSmem<R>) ? sizeof(DwtSmem<R>)
-                                                                                 : sizeof(IdwtSmem<R>));
+  static constexpr int KMAX = DICT == RIX_DICT_DB4 ? 8 : kMaxTaps;
+  static constexpr size_t kWavSmem = sizeof(DwtSmem<R, KMAX>) > sizeof(IdwtSmem<R, KMAX>) ? sizeof(DwtSmem<R, KMAX>)
+                                                                                         : sizeof(IdwtSmem<R, KMAX>);
+  static constexpr size_t kSmem = kFftSmem > kWavSmem ? kFftSmem : kWavSmem;
 };
 
 template <typename C> __device__ __forceinline__ C cpx(typename std::conditional<sizeof(C) == 8, float, double>::type re,
@@ -55,10 +60,12 @@ template <typename C> __device__ __forceinline__ C cpx(typename std::conditional
   return r;
 }
 
-// rows b0 .. b0 + 2B of x -> window columns of their spectra, T[j][b]
-template <typename R, int LOGL>
-__device__ __forceinline__ void rows_fwd_unit(const R* __restrict__ x, cplx<R>* __restrict__ T,
-                                              const cplx<R>* __restrict__ tw, cplx<R>* s, cplx<R>* s2, int u) {
+// rows b0 .. b0 + 2B of x -> window columns of their spectra, T[j][b];
+// x = xscale * (sum of NSUM images xstride apart) when NSUM > 1
+template <typename R, int LOGL, int NSUM = 1>
+__device__ __forceinline__ void rows_fwd_unit(const R* __restrict__ x, int64_t xstride, R xscale,
+                                              cplx<R>* __restrict__ T, const cplx<R>* __restrict__ tw, cplx<R>* s,
+                                              cplx<R>* s2, int u) {
   using C = cplx<R>;
   using F = FistaShape<R, LOGL>;
   constexpr int L = F::L, N = F::N, H = F::H, B = F::B, STRIDE = F::STRIDE;
@@ -74,8 +81,19 @@ __device__ __forceinline__ void rows_fwd_unit(const R* __restrict__ x, cplx<R>* 
     if (NE % kFftThreads == 0 || e < NE) {
       const int q = e / N, a = e % N;
       const int64_t row = b0 + 2 * q;
-      va[k] = x[row * N + a];
-      vb[k] = x[(row + 1) * N + a];
+      if constexpr (NSUM == 1) {
+        va[k] = x[row * N + a];
+        vb[k] = x[(row + 1) * N + a];
+      } else {
+        R sa = R(0), sb = R(0);
+#pragma unroll
+        for (int m = 0; m < NSUM; ++m) {
+          sa += x[m * xstride + row * N + a];
+          sb += x[m * xstride + (row + 1) * N + a];
+        }
+        va[k] = xscale * sa;
+        vb[k] = xscale * sb;
+      }
     }
   }
 #pragma unroll
@@ -213,44 +231,128 @@ __device__ __forceinline__ void rows_inv_unit(const cplx<R>* __restrict__ T, R* 
   __syncthreads();
 }
 
+// member MM of the concatenated dictionary (db_{MM+1}, 2 (MM + 1) taps),
+// out of line: each member's tile gets its own register allocation
+template <typename R, int MM>
+__device__ __noinline__ void syn_member(const R* ll, const R* cm, int n, R* dst, int N, int bx, int by,
+                                        unsigned char* smem, const R* taps) {
+  auto& ism = *reinterpret_cast<IdwtSmem<R, 2 * (MM + 1)>*>(smem);
+  idwt_tile<R>(ll, cm, n, dst, N, bx, by, ism, RefTaps<R, 2 * (MM + 1)>{taps});
+}
+template <typename R, int MM>
+__device__ __noinline__ void ana_member(const R* src, int n, R* dst, int N, int last, const StepArgs<R>& sm,
+                                        int bx, int by, unsigned char* smem, const R* taps) {
+  auto& dsm = *reinterpret_cast<DwtSmem<R, 2 * (MM + 1)>*>(smem);
+  dwt_tile<R, true>(src, N, n, nullptr, dst, N, last, sm, bx, by, dsm, RefTaps<R, 2 * (MM + 1)>{taps});
+}
+
+// one synthesis level l of x = W c: level l of member m reads its level-l+1
+// output (or c's coarse block at the top level) and lands in (l odd ? B : A)
+template <typename R, int DICT, int N>
+__device__ __forceinline__ void synthesis_level(const FistaLoop<R>& f, const R* coef, int l, unsigned char* smem) {
+  const int n = N >> l, nt = (n + kTS - 1) / kTS, per = nt * nt;
+  const bool top = l == f.levels - 1;
+  if constexpr (DICT == RIX_DICT_DB4) {
+    const R* ll = top ? coef : (((l + 1) & 1) ? f.tmp : f.x);
+    R* dst = (l & 1) ? f.tmp : f.x;
+    auto& ism = *reinterpret_cast<IdwtSmem<R, 8>*>(smem);
+    for (int u = blockIdx.x; u < per; u += gridDim.x)
+      idwt_tile<R>(ll, coef, n, dst, N, u % nt, u / nt, ism, Db4Taps<R>{});
+  } else {
+    const int64_t NN = (int64_t)N * N;
+    for (int u = blockIdx.x; u < 8 * per; u += gridDim.x) {
+      const int m = u / per, t = u - m * per;
+      const R* cm = coef + m * NN;
+      R* am = f.xs + m * NN;
+      R* bm = f.bs + m * NN;
+      const R* ll = top ? cm : (((l + 1) & 1) ? bm : am);
+      R* dst = (l & 1) ? bm : am;
+      const int bx = t % nt, by = t / nt;
+#define RIX_SYN(MM)                                                                                     \
+  case MM: syn_member<R, MM>(ll, cm, n, dst, N, bx, by, smem, f.taps[MM]); break;
+      switch (m) { RIX_SYN(0) RIX_SYN(1) RIX_SYN(2) RIX_SYN(3) RIX_SYN(4) RIX_SYN(5) RIX_SYN(6) RIX_SYN(7) }
+#undef RIX_SYN
+    }
+  }
+}
+
+// one analysis level l of W^T g with the step fused into the final
+// coefficients: level l of member m reads g (l = 0) or its level l-1 LL and
+// writes its LL into (l odd ? B : A)
+template <typename R, int DICT, int N>
+__device__ __forceinline__ void analysis_level(const FistaLoop<R>& f, int l, const StepArgs<R>& sa,
+                                               unsigned char* smem) {
+  const int n = N >> l, nt = (n / 2 + kTB - 1) / kTB, per = nt * nt;
+  const int last = l == f.levels - 1;
+  if constexpr (DICT == RIX_DICT_DB4) {
+    const R* src = l == 0 ? f.g : (((l - 1) & 1) ? f.tmp : f.x);
+    R* dst = (l & 1) ? f.tmp : f.x;
+    auto& dsm = *reinterpret_cast<DwtSmem<R, 8>*>(smem);
+    for (int u = blockIdx.x; u < per; u += gridDim.x)
+      dwt_tile<R, true>(src, N, n, nullptr, dst, N, last, sa, u % nt, u / nt, dsm, Db4Taps<R>{});
+  } else {
+    const int64_t NN = (int64_t)N * N;
+    for (int u = blockIdx.x; u < 8 * per; u += gridDim.x) {
+      const int m = u / per, t = u - m * per;
+      R* am = f.xs + m * NN;
+      R* bm = f.bs + m * NN;
+      const R* src = l == 0 ? f.g : (((l - 1) & 1) ? bm : am);
+      R* dst = (l & 1) ? bm : am;
+      StepArgs<R> sm = sa;
+      sm.alpha += m * NN;
+      sm.y += m * NN;
+      const int bx = t % nt, by = t / nt;
+#define RIX_ANA(MM)                                                                                     \
+  case MM: ana_member<R, MM>(src, n, dst, N, last, sm, bx, by, smem, f.taps[MM]); break;
+      switch (m) { RIX_ANA(0) RIX_ANA(1) RIX_ANA(2) RIX_ANA(3) RIX_ANA(4) RIX_ANA(5) RIX_ANA(6) RIX_ANA(7) }
+#undef RIX_ANA
+    }
+  }
+}
+
 template <typename R>
 struct FistaArgs {
   FistaLoop<R> f;
   R gscale;
 };
 
-template <typename R, int LOGL>
+template <typename R, int LOGL, int DICT>
 __global__ void __launch_bounds__(kFftThreads, sizeof(R) == 4 && LOGL <= 12 ? 2 : 1)
-    k_fista_loop(FistaArgs<R> a) {
+    k_fista_loop(const __grid_constant__ FistaArgs<R> a) {
   using C = cplx<R>;
-  using F = FistaShape<R, LOGL>;
+  using F = FistaShape<R, LOGL, DICT>;
   constexpr int N = F::N;
+  constexpr bool kCat = DICT != RIX_DICT_DB4;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* s = reinterpret_cast<C*>(smem_raw);
   C* s2 = s + F::B * F::STRIDE;
-  DwtSmem<R>& dsm = *reinterpret_cast<DwtSmem<R>*>(smem_raw);
-  IdwtSmem<R>& ism = *reinterpret_cast<IdwtSmem<R>*>(smem_raw);
   const FistaLoop<R>& f = a.f;
   GridBarrier bar{f.barrier, f.status, 0u};
-  // L = 2 max Mx and lambda (absolute, or relative to max |residual| of the
-  // first cycle) are fixed during the minor cycle
+  // L = 2 max Mx and lambda are fixed during the minor cycle: lambda is
+  // absolute, or lambda_rel max |residual| of the first cycle, or the
+  // schedule a ||residual_n||_2 b^n
   const double lip = 2.0 * (double)f.state[0];
-  const double lam = f.lambda > 0.0 ? f.lambda : f.lambda_rel * (double)f.state[1];
+  const double lam = f.sched_a > 0.0   ? f.sched_a * sqrt((double)f.state[2]) * f.sched_bn
+                     : f.lambda > 0.0 ? f.lambda
+                                      : f.lambda_rel * (double)f.state[1];
   const bool active = lip > 0.0;
-  const R inv_l = active ? (R)(1.0 / lip) : R(0);
+  // the concatenation's 1/sqrt 8 enters the analysis through 1/L
+  const double ascale = kCat ? 1.0 / sqrt(8.0) : 1.0;
+  const R inv_l = active ? (R)(ascale / lip) : R(0);
   const R thr = active ? (R)(lam / lip) : R(0);
+  const R sscale = (R)(1.0 / sqrt(8.0));
+  const int64_t NN = (int64_t)N * N;
   double t = 1.0;
   for (int it = 0; it < f.iters; ++it) {
-    // x = W y; level l lands in x for even l and in tmp for odd l
-    const R* ll = f.y;
+    // x = W y, coarsest level first
     for (int l = f.levels - 1; l >= 0; --l) {
-      const int n = N >> l, nt = (n + kTS - 1) / kTS;
-      R* dst = (l & 1) ? f.tmp : f.x;
-      for (int u = blockIdx.x; u < nt * nt; u += gridDim.x) idwt_tile<R>(ll, f.y, n, dst, N, u % nt, u / nt, ism);
+      synthesis_level<R, DICT, N>(f, f.y, l, smem_raw);
       if (!grid_barrier(bar)) return;
-      ll = dst;
     }
-    for (int u = blockIdx.x; u < F::kRowUnits; u += gridDim.x) rows_fwd_unit<R, LOGL>(f.x, f.ta, f.tw, s, s2, u);
+    for (int u = blockIdx.x; u < F::kRowUnits; u += gridDim.x) {
+      if constexpr (kCat) rows_fwd_unit<R, LOGL, 8>(f.xs, NN, sscale, f.ta, f.tw, s, s2, u);
+      else rows_fwd_unit<R, LOGL>(f.x, 0, R(1), f.ta, f.tw, s, s2, u);
+    }
     if (!grid_barrier(bar)) return;
     for (int u = blockIdx.x; u < F::kColUnits; u += gridDim.x)
       cols_conv_unit<R, LOGL>(f.ta, f.mx, f.c, f.tb, f.tw, s, s2, u);
@@ -261,23 +363,31 @@ __global__ void __launch_bounds__(kFftThreads, sizeof(R) == 4 && LOGL <= 12 ? 2 
     // operation rounded on its own
     const double tn = __dmul_rn(0.5, __dadd_rn(1.0, __dsqrt_rn(__dadd_rn(1.0, __dmul_rn(__dmul_rn(4.0, t), t)))));
     const StepArgs<R> sa{f.alpha, f.y, inv_l, thr, active, (R)__ddiv_rn(__dadd_rn(t, -1.0), tn)};
-    const R* src = f.g;
     for (int l = 0; l < f.levels; ++l) {
-      const int n = N >> l, nt = (n / 2 + kTB - 1) / kTB;
-      R* dst = (l & 1) ? f.tmp : f.x;
-      for (int u = blockIdx.x; u < nt * nt; u += gridDim.x)
-        dwt_tile<R, true>(src, N, n, nullptr, dst, N, l == f.levels - 1, sa, u % nt, u / nt, dsm);
+      analysis_level<R, DICT, N>(f, l, sa, smem_raw);
       if (!grid_barrier(bar)) return;
-      src = dst;
     }
     t = tn;
   }
+  if constexpr (kCat) {
+    // the minor cycle's image W alpha: the members' syntheses, summed
+    for (int l = f.levels - 1; l >= 0; --l) {
+      synthesis_level<R, DICT, N>(f, f.alpha, l, smem_raw);
+      if (!grid_barrier(bar)) return;
+    }
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < NN; i += (int64_t)gridDim.x * blockDim.x) {
+      R acc = R(0);
+#pragma unroll
+      for (int m = 0; m < 8; ++m) acc += f.xs[m * NN + i];
+      f.delta[i] = sscale * acc;
+    }
+  }
 }
 
-template <typename R, int LOGL>
+template <typename R, int LOGL, int DICT>
 int launch_fista_loop(const Ctx* ctx, const FistaLoop<R>& f, cudaStream_t st) {
-  using F = FistaShape<R, LOGL>;
-  auto kern = k_fista_loop<R, LOGL>;
+  using F = FistaShape<R, LOGL, DICT>;
+  auto kern = k_fista_loop<R, LOGL, DICT>;
   const size_t smem = F::kSmem;
   RIX_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int per_sm = 0;
@@ -294,19 +404,20 @@ int launch_fista_loop(const Ctx* ctx, const FistaLoop<R>& f, cudaStream_t st) {
 }
 
 // dispatch on the transform length 2N (N a power of two in [32, KMAXN])
-template <typename R, int LOGL, int LOGL_MAX>
+template <typename R, int DICT, int LOGL, int LOGL_MAX>
 int fista_loop_dispatch(const Ctx* ctx, const FistaLoop<R>& f, int logl, cudaStream_t st) {
-  if (logl == LOGL) return launch_fista_loop<R, LOGL>(ctx, f, st);
-  if constexpr (LOGL < LOGL_MAX) return fista_loop_dispatch<R, LOGL + 1, LOGL_MAX>(ctx, f, logl, st);
+  if (logl == LOGL) return launch_fista_loop<R, LOGL, DICT>(ctx, f, st);
+  if constexpr (LOGL < LOGL_MAX) return fista_loop_dispatch<R, DICT, LOGL + 1, LOGL_MAX>(ctx, f, logl, st);
   return set_error(RIX_EINVAL, "FISTA loop: image side %d not supported", f.n);
 }
 
 }  // namespace
 
-template <typename R>
-int fista_loop(const Ctx* ctx, const FistaLoop<R>& f, cudaStream_t st) {
+// the instances of one dictionary (k_fista_*.cu, one translation unit each)
+template <typename R, int DICT>
+int fista_loop_dict(const Ctx* ctx, const FistaLoop<R>& f, cudaStream_t st) {
   constexpr int kMaxLogL = std::is_same<R, float>::value ? 13 : 12;   // N <= 4096 (FP32), 2048 (FP64)
-  return fista_loop_dispatch<R, 6, kMaxLogL>(ctx, f, ilog2(2 * (int64_t)f.n), st);
+  return fista_loop_dispatch<R, DICT, 6, kMaxLogL>(ctx, f, ilog2(2 * (int64_t)f.n), st);
 }
 
 }  // namespace rix

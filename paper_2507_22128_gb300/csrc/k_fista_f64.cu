@@ -1,6 +1,7 @@
-// FP64 instances of the persistent FISTA loop (one kernel per transform length).
+// FP64 instances of the persistent FISTA loop with the Db4 dictionary
+// (one kernel per transform length).
 #include "k_fista.cuh"
 
 namespace rix {
-template int fista_loop<double>(const Ctx*, const FistaLoop<double>&, cudaStream_t);
+template int fista_loop_dict<double, RIX_DICT_DB4>(const Ctx*, const FistaLoop<double>&, cudaStream_t);
 }  // namespace rix

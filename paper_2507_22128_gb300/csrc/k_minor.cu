@@ -131,6 +131,16 @@ __global__ void k_absmax(const R* __restrict__ x, int64_t n, R* __restrict__ out
   if ((threadIdx.x & 31) == 0) atomic_max_nonneg(out, m);
 }
 
+// out += sum of x^2 (per warp, then atomically)
+template <typename R>
+__global__ void k_sumsq(const R* __restrict__ x, int64_t n, R* __restrict__ out) {
+  R a = R(0);
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    a += x[i] * x[i];
+  for (int o = 16; o; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+  if ((threadIdx.x & 31) == 0) atomicAdd(out, a);
+}
+
 // ------------------------------------------------------------ fill kernels ----
 // ms-CLEAN composite dirty spectrum and PSF spectrum (Eq. 7):
 //   D = g Gam_p I_p + sum_q mu_q H_q Rho_q,   P = g Gam_p H_p + sum_q mu_q Gam_q H_q
@@ -201,8 +211,8 @@ namespace {
 template <typename R>
 __global__ void __launch_bounds__(256) k_idwt_level(const R* __restrict__ llin, const R* __restrict__ coef, int n,
                                                     R* __restrict__ out, int ld) {
-  __shared__ IdwtSmem<R> sm;
-  idwt_tile<R>(llin, coef, n, out, ld, blockIdx.x, blockIdx.y, sm);
+  __shared__ IdwtSmem<R, 8> sm;
+  idwt_tile<R>(llin, coef, n, out, ld, blockIdx.x, blockIdx.y, sm, Db4Taps<R>{});
 }
 
 // coefficients c (N x N) -> image out; tmp: N x N scratch.  Levels are
@@ -514,7 +524,7 @@ int fill_init(Job* job, cudaStream_t st) {
     RIX_TRY(alloc_zero<R>(job, pt.outbox[1], npix * sizeof(R), st));
     for (int q = 0; q < P; ++q)
       if (q != p) RIX_TRY(alloc_zero<R>(job, pt.rho[q], npix * sizeof(R), st));
-    RIX_TRY(alloc_zero<R>(job, pt.fi_state, 2 * sizeof(R), st));
+    RIX_TRY(alloc_zero<R>(job, pt.fi_state, 4 * sizeof(R), st));
   }
   return RIX_OK;
 }
@@ -666,15 +676,25 @@ int op_fista(Job* job, int p, const rix_fista_params* prm, R* delta_out, cudaStr
   ::rix::note_launch(); k_fill_fista<R><<<blocks_for(ctx, tot), 256, 0, st>>>(fa, gn, pt.fi_mx.as<R>(), pt.fi_c.as<cplx<R>>(),
                                                         pt.fi_state.as<R>());
   RIX_LAUNCH_CHECK();
-  RIX_TRY(alloc_zero<R>(job, pt.fi_alpha, npix * sizeof(R), st));
-  RIX_TRY(alloc_zero<R>(job, pt.fi_y, npix * sizeof(R), st));
-  RIX_TRY(ensure<R>(job, pt.fi_x, npix * sizeof(R)));
-  RIX_TRY(ensure<R>(job, pt.fi_alpha_prev, npix * sizeof(R)));
+  const bool cat = prm->dictionary == RIX_DICT_DB1_8;
+  const int64_t ncoef = (cat ? 8 : 1) * npix;
+  RIX_TRY(alloc_zero<R>(job, pt.fi_alpha, ncoef * sizeof(R), st));
+  RIX_TRY(alloc_zero<R>(job, pt.fi_y, ncoef * sizeof(R), st));
+  RIX_TRY(ensure<R>(job, pt.fi_x, (cat ? 8 : 1) * npix * sizeof(R)));
+  RIX_TRY(ensure<R>(job, pt.fi_alpha_prev, (cat ? 8 : 1) * npix * sizeof(R)));
   R* alpha = pt.fi_alpha.as<R>();
   R* y = pt.fi_y.as<R>();
   R* x = pt.fi_x.as<R>();
   R* g = pt.fimg.as<R>();
   R* tmp = pt.fi_alpha_prev.as<R>();
+  double sched_bn = 0.0;
+  if (prm->sched_a > 0.0) {
+    // lambda_n = a ||residual of cycle n||_2 b^n: the squared norm goes to state[2]
+    RIX_CUDA(cudaMemsetAsync(pt.fi_state.as<R>() + 2, 0, sizeof(R), st));
+    ::rix::note_launch(); k_sumsq<R><<<blocks_for(ctx, npix), 256, 0, st>>>(pt.resid.as<R>(), npix, pt.fi_state.as<R>() + 2);
+    RIX_LAUNCH_CHECK();
+    sched_bn = std::pow(prm->sched_b, (double)cycle);
+  }
   if (prm->iters > 0) {
     // gradient of ||M x - C||^2 on the 2N grid: 2 crop F^-1 [Mx F pad x - C]
     RIX_TRY(ensure<R>(job, pt.sync, 16));
@@ -693,9 +713,31 @@ int op_fista(Job* job, int p, const rix_fista_params* prm, R* delta_out, cudaStr
     f.n = n;
     f.levels = prm->levels;
     f.iters = prm->iters;
-    RIX_TRY(fista_loop<R>(ctx, f, st));
+    f.dict = prm->dictionary;
+    f.sched_a = prm->sched_a;
+    f.sched_bn = sched_bn;
+    if (cat) {
+      // member level buffers: A in fi_x, B in fi_alpha_prev, 8 N^2 each
+      f.xs = x;
+      f.bs = tmp;
+      f.delta = pt.delta.as<R>();
+      for (int m = 0; m < 8; ++m) {
+        double h[16];
+        const int k = daubechies_lowpass(m + 1, h);
+        if (k != 2 * (m + 1)) return set_error(RIX_EINVAL, "daubechies filter %d", m + 1);
+        for (int i = 0; i < 16; ++i) f.taps[m][i] = i < k ? (R)h[i] : R(0);
+      }
+      RIX_TRY((fista_loop_dict<R, RIX_DICT_DB1_8>(ctx, f, st)));
+    } else {
+      RIX_TRY((fista_loop_dict<R, RIX_DICT_DB4>(ctx, f, st)));
+    }
   }
-  RIX_TRY(idwt2<R>(ctx, alpha, pt.delta.as<R>(), tmp, n, prm->levels, st));
+  if (cat) {
+    // the loop wrote W alpha into delta; with no iteration alpha = 0
+    if (prm->iters == 0) RIX_CUDA(cudaMemsetAsync(pt.delta.p, 0, npix * sizeof(R), st));
+  } else {
+    RIX_TRY(idwt2<R>(ctx, alpha, pt.delta.as<R>(), tmp, n, prm->levels, st));
+  }
   RIX_TRY(publish<R>(job, p, cycle, st));
   if (delta_out) RIX_CUDA(cudaMemcpyAsync(delta_out, pt.delta.p, npix * sizeof(R), cudaMemcpyDeviceToDevice, st));
   return RIX_OK;

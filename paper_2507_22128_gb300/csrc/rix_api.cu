@@ -525,7 +525,12 @@ static int rix_minor_cycle_fista_impl(rix_job_t job, int part, const rix_fista_p
   const int maxlev = ilog2(J.desc.n) - 3;
   if (prm->iters < 0 || prm->levels < 1 || prm->levels > maxlev)
     return set_error(RIX_EINVAL, "iters >= 0 and levels in [1, %d]", maxlev);
-  if (!(prm->lambda > 0.0) && !(prm->lambda_rel > 0.0)) return set_error(RIX_EINVAL, "lambda or lambda_rel must be > 0");
+  if (!(prm->lambda > 0.0) && !(prm->lambda_rel > 0.0) && !(prm->sched_a > 0.0))
+    return set_error(RIX_EINVAL, "lambda, lambda_rel or sched_a must be > 0");
+  if (prm->dictionary != RIX_DICT_DB4 && prm->dictionary != RIX_DICT_DB1_8)
+    return set_error(RIX_EINVAL, "dictionary must be RIX_DICT_DB4 or RIX_DICT_DB1_8");
+  if (prm->sched_a < 0.0 || (prm->sched_a > 0.0 && !(prm->sched_b > 0.0)))
+    return set_error(RIX_EINVAL, "schedule: sched_a >= 0 and sched_b > 0");
   RIX_TRY(minor_precheck(J, part, st));
   if (J.fp64) RIX_TRY(op_fista<double>(&J, part, prm, (double*)delta_out, st));
   else RIX_TRY(op_fista<float>(&J, part, prm, (float*)delta_out, st));

@@ -195,7 +195,7 @@ struct Part {
   // fill scratch: two (2N)^2 spectra, two [2N][N] transpose buffers, an image
   DevBuf fs_a, fs_b, ft_a, ft_b, fimg;
   DevBuf fspec;                             // P spectra: slot p = own residual, slot q = rho_{q->p}
-  DevBuf fi_state;                          // FISTA: [max Mx, max |residual| of cycle 1]
+  DevBuf fi_state;                          // FISTA: [max Mx, max |residual| of cycle 1, ||residual||^2, -]
   // minor-cycle state
   DevBuf ms_R, ms_P, ms_B, ms_comp, ms_state;   // ms-CLEAN
   DevBuf fi_alpha, fi_alpha_prev, fi_y, fi_mx, fi_c, fi_x;   // FISTA
@@ -242,6 +242,9 @@ int note_stream(Job* job, cudaStream_t st);
 // reads the job's device status word (the caller has synchronised the job's
 // streams); RIX_ETIMEOUT if a bounded device-side wait gave up
 int check_status(Job* job);
+// wavelet_filters.cu: Daubechies low-pass filter with p vanishing moments
+// (2p taps written to h); returns 2p or a negative RIX_E* code
+int daubechies_lowpass(int p, double* h);
 // k_selftest.cu: bounded-barrier timeout self-test (rix_selftest_barrier_timeout)
 int selftest_barrier(Ctx* ctx, int* status_out, int* gave_up_out);
 
@@ -296,9 +299,19 @@ struct FistaLoop {
   int* status;             // the job's status word
   double lambda, lambda_rel;
   int n, levels, iters;
+  int dict;                // RIX_DICT_DB4 or RIX_DICT_DB1_8
+  double sched_a, sched_bn;   // sched_a > 0: lambda = sched_a * sqrt(state[2]) * sched_bn
+  // RIX_DICT_DB1_8 only: member m's coefficients at alpha / y + m N^2, its
+  // level buffers at xs / bs + m N^2 (N x N each), W alpha written to delta
+  // after the last iteration, and the low-pass filters of db1 .. db8
+  R* xs;
+  R* bs;
+  R* delta;
+  R taps[8][16];
 };
-template <typename R>
-int fista_loop(const Ctx* ctx, const FistaLoop<R>& f, cudaStream_t st);
+// one instance per precision and dictionary (k_fista_*.cu)
+template <typename R, int DICT>
+int fista_loop_dict(const Ctx* ctx, const FistaLoop<R>& f, cudaStream_t st);
 int get_components(Job* job, int part, int32_t* count, int32_t capacity, int32_t* scale_out,
                    int32_t* pixel_out, double* amp_out, cudaStream_t st);
 

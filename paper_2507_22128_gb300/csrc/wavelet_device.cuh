@@ -1,7 +1,14 @@
-// Device code of the Db4 wavelet transform (the dictionary of the FISTA
-// minor cycle, Eq. 4-5): one tile of one analysis level (with the FISTA step
-// fused into the final coefficients) and one tile of one synthesis level.
-// Shared by the per-level kernels and the persistent minor-cycle loop.
+// Device code of the periodic orthonormal 2D Daubechies wavelet transforms
+// (the dictionaries of the FISTA minor cycle, Eq. 4-5; Sec. 5.2): one tile of
+// one analysis level (with the FISTA step fused into the final coefficients)
+// and one tile of one synthesis level, for a filter of K taps.  Shared by the
+// per-level kernels and the persistent minor-cycle loop.
+//
+// Transform (periodic, analysis by correlation), per level of an n x n block:
+//   a[k] = sum_i h[i] x[(2k + i) mod n],  d[k] = sum_i g[i] x[(2k + i) mod n],
+//   g[i] = (-1)^i h[K - 1 - i], along rows and then columns; subband layout
+//   [Y][X] with Y < n/2 column-low, X < n/2 row-low (Mallat); synthesis is
+//   the transpose.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -11,53 +18,69 @@
 namespace rix {
 namespace {
 
-// --------------------------------------------------------------- Db4 DWT ----
+// --------------------------------------------------------------- filters ----
 // Daubechies 4-vanishing-moment low-pass filter (8 taps, minimum phase,
-// normalised to sum sqrt(2)); g[i] = (-1)^i h[7 - i].
-// Compile-time constants: every use below has a compile-time tap index, so the
-// taps fold into immediates (no constant-bank loads or FP64 conversions).
+// normalised to sum sqrt(2)).  Compile-time constants: every use has a
+// compile-time tap index, so the taps fold into immediates (no constant-bank
+// loads or FP64 conversions).
 __device__ constexpr double kDb4[8] = {0.23037781330885523,  0.7148465705525415,   0.6308807679295904,
                                        -0.02798376941698385, -0.18703481171888114, 0.030841381835986965,
                                        0.032883011666982945, -0.010597401784997278};
 
-template <typename R> __device__ __forceinline__ constexpr R db_h(int i) { return (R)kDb4[i]; }
-template <typename R> __device__ __forceinline__ constexpr R db_g(int i) {
-  return (i & 1) ? -(R)kDb4[7 - i] : (R)kDb4[7 - i];
-}
+template <typename R>
+struct Db4Taps {
+  static constexpr int K = 8;
+  __device__ __forceinline__ constexpr R lo(int i) const { return (R)kDb4[i]; }
+  __device__ __forceinline__ constexpr R hi(int i) const {
+    return (i & 1) ? -(R)kDb4[7 - i] : (R)kDb4[7 - i];
+  }
+};
 
-// ------------------------------------------------- fused Db4 DWT levels ----
-// Analysis of one level: a CTA owns a kTB x kTB block of each of the four
-// subbands of an n x n block (n a power of two), stages the periodic
-// (2 kTB + 6)^2 input tile, filters its rows (low and high) and then its
-// columns.  Subband layout of a level: [Y][X] with Y < n/2 column-low,
-// X < n/2 row-low.  Every global load of a tile is issued before the first
-// one is used.
+// a filter of K taps read where it lives (a kernel parameter: the taps stay
+// constant-bank operands instead of occupying registers across loops)
+template <typename R, int KT>
+struct RefTaps {
+  static constexpr int K = KT;
+  const R* h;
+  __device__ __forceinline__ R lo(int i) const { return h[i]; }
+  __device__ __forceinline__ R hi(int i) const { return (i & 1) ? -h[KT - 1 - i] : h[KT - 1 - i]; }
+};
+
+// ------------------------------------------------- fused analysis levels ----
+// A CTA owns a kTB x kTB block of each of the four subbands of an n x n block
+// (n a power of two), stages the periodic (2 kTB + K - 2)^2 input tile,
+// filters its rows (low and high) and then its columns.  Every global load of
+// a tile is issued before the first one is used.
 constexpr int kTB = 16;
-constexpr int kTin = 2 * kTB + 6;
+constexpr int kMaxTaps = 16;                 // db8
+template <int K> constexpr int tin_side() { return 2 * kTB + K - 2; }
 
 // FISTA step fused into the analysis of the gradient (Beck & Teboulle 2009):
-// at each final coefficient g:  a' = S_{lam/L}(y - g/L),  y = a' + mom (a' - a),  a = a'
+// at each final coefficient c = s g:  a' = S_{lam/L}(y - c/L),
+// y = a' + mom (a' - a),  a = a'   (s: the dictionary's scale; inv_l folds it)
 template <typename R>
 struct StepArgs {
   R* alpha;
   R* y;
-  R inv_l, thr;         // 1 / L and lambda / L (both 0 when L = 0: the step is a no-op)
+  R inv_l, thr;         // s / L and lambda / L (both 0 when L = 0: the step is a no-op)
   bool active;
   R mom;
 };
 
-template <typename R>
+template <typename R, int K>
 struct DwtSmem {
-  R tin[kTin][kTin + 1];
-  R trow[kTin][2 * kTB + 1];     // [input row][lo x | hi x]
+  static constexpr int TIN = tin_side<K>();
+  R tin[TIN][TIN + 1];
+  R trow[TIN][2 * kTB + 1];     // [input row][lo x | hi x]
 };
 
 // one kTB x kTB output block (bx, by) of each subband; 256 threads
-template <typename R, bool kStep>
+template <typename R, bool kStep, typename TAPS>
 __device__ __forceinline__ void dwt_tile(const R* __restrict__ src, int lds, int n, R* __restrict__ coef,
                                          R* __restrict__ ll, int ld, int last, const StepArgs<R>& st, int bx, int by,
-                                         DwtSmem<R>& sm) {
-  constexpr int TIN = kTin;
+                                         DwtSmem<R, TAPS::K>& sm, const TAPS& tp) {
+  constexpr int K = TAPS::K;
+  constexpr int TIN = tin_side<K>();
   constexpr int NLD = (TIN * TIN + 255) / 256;
   auto& tin = sm.tin;
   auto& trow = sm.trow;
@@ -99,10 +122,10 @@ __device__ __forceinline__ void dwt_tile(const R* __restrict__ src, int lds, int
     const int r = t / kTB, xx = t - r * kTB;
     R a = R(0), d = R(0);
 #pragma unroll
-    for (int i = 0; i < 8; ++i) {
+    for (int i = 0; i < K; ++i) {
       const R w = tin[r][2 * xx + i];
-      a += db_h<R>(i) * w;
-      d += db_g<R>(i) * w;
+      a += tp.lo(i) * w;
+      d += tp.hi(i) * w;
     }
     trow[r][xx] = a;
     trow[r][kTB + xx] = d;
@@ -114,7 +137,7 @@ __device__ __forceinline__ void dwt_tile(const R* __restrict__ src, int lds, int
       const int cy = q >> 1, cx = q & 1;
       R g = R(0);
 #pragma unroll
-      for (int i = 0; i < 8; ++i) g += (cy ? db_g<R>(i) : db_h<R>(i)) * trow[2 * ty + i][cx * kTB + tx];
+      for (int i = 0; i < K; ++i) g += (cy ? tp.hi(i) : tp.lo(i)) * trow[2 * ty + i][cx * kTB + tx];
       const int64_t idx = (int64_t)(cy * h + y) * ld + cx * h + x;
       if (q == 0 && !last) {
         ll[(int64_t)y * ld + x] = g;
@@ -132,25 +155,31 @@ __device__ __forceinline__ void dwt_tile(const R* __restrict__ src, int lds, int
   __syncthreads();
 }
 
-// Synthesis of one level: out (n x n, ld) from the LL block `llin` (ld) and
-// the detail subbands of `coef` (ld); a CTA owns a kTS x kTS output block.
+// ------------------------------------------------------- synthesis level ----
+// out (n x n, ld) from the LL block `llin` (ld) and the detail subbands of
+// `coef` (ld); a CTA owns a kTS x kTS output block.
 constexpr int kTS = 32;
-constexpr int kRK = kTS / 2 + 4;
-template <typename R>
+template <int K> constexpr int rk_side() { return kTS / 2 + K / 2; }
+
+template <typename R, int K>
 struct IdwtSmem {
-  R cq[4][kRK][kRK + 1];         // quadrant tiles: LL, row-high, col-high, HH
-  R tr[2][kRK][kTS + 1];         // after row synthesis: [column half][coef row][c]
+  static constexpr int RK = rk_side<K>();
+  R cq[4][RK][RK + 1];         // quadrant tiles: LL, row-high, col-high, HH
+  R tr[2][RK][kTS + 1];        // after row synthesis: [column half][coef row][c]
 };
 
-template <typename R>
+template <typename R, typename TAPS>
 __device__ __forceinline__ void idwt_tile(const R* __restrict__ llin, const R* __restrict__ coef, int n,
-                                          R* __restrict__ out, int ld, int bx, int by, IdwtSmem<R>& sm) {
-  constexpr int RK = kRK;
+                                          R* __restrict__ out, int ld, int bx, int by, IdwtSmem<R, TAPS::K>& sm,
+                                          const TAPS& tp) {
+  constexpr int K = TAPS::K;
+  constexpr int RK = rk_side<K>();
   auto& cq = sm.cq;
   auto& tr = sm.tr;
   const int h = n / 2;
   const int m0 = by * kTS, c0 = bx * kTS;
-  const int kb_m = (m0 >> 1) - 4, kb_c = (c0 >> 1) - 4;
+  // output m uses coefficients (m - i) / 2 for the taps i of its parity
+  const int kb_m = (m0 >> 1) - K / 2, kb_c = (c0 >> 1) - K / 2;
   constexpr int NLD = (4 * RK * RK + 255) / 256;
   R v[NLD];
 #pragma unroll
@@ -174,21 +203,21 @@ __device__ __forceinline__ void idwt_tile(const R* __restrict__ llin, const R* _
     }
   }
   __syncthreads();
-  // rows: tr[cy][rk][c] = sum over the 4 taps of the parity of c
+  // rows: tr[cy][rk][c] = sum over the K/2 taps of the parity of c
   for (int t = threadIdx.x; t < 2 * RK * kTS; t += blockDim.x) {
     const int cy = t / (RK * kTS), rem = t - cy * RK * kTS;
     const int rk = rem / kTS, cl = rem - rk * kTS;
     const int c = c0 + cl;
     const bool odd = c & 1;
     const int kc = (c >> 1) - kb_c;             // tap i = 2 j + (c & 1) reads coefficient (c - i) / 2
-    R v = R(0);
+    R v2 = R(0);
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const R hh = odd ? db_h<R>(2 * j + 1) : db_h<R>(2 * j);
-      const R gg = odd ? db_g<R>(2 * j + 1) : db_g<R>(2 * j);
-      v += hh * cq[2 * cy][rk][kc - j] + gg * cq[2 * cy + 1][rk][kc - j];
+    for (int j = 0; j < K / 2; ++j) {
+      const R hh = odd ? tp.lo(2 * j + 1) : tp.lo(2 * j);
+      const R gg = odd ? tp.hi(2 * j + 1) : tp.hi(2 * j);
+      v2 += hh * cq[2 * cy][rk][kc - j] + gg * cq[2 * cy + 1][rk][kc - j];
     }
-    tr[cy][rk][cl] = v;
+    tr[cy][rk][cl] = v2;
   }
   __syncthreads();
   for (int t = threadIdx.x; t < kTS * kTS; t += blockDim.x) {
@@ -197,14 +226,14 @@ __device__ __forceinline__ void idwt_tile(const R* __restrict__ llin, const R* _
     if (m >= n || c >= n) continue;
     const bool odd = m & 1;
     const int km = (m >> 1) - kb_m;
-    R v = R(0);
+    R v2 = R(0);
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const R hh = odd ? db_h<R>(2 * j + 1) : db_h<R>(2 * j);
-      const R gg = odd ? db_g<R>(2 * j + 1) : db_g<R>(2 * j);
-      v += hh * tr[0][km - j][cl] + gg * tr[1][km - j][cl];
+    for (int j = 0; j < K / 2; ++j) {
+      const R hh = odd ? tp.lo(2 * j + 1) : tp.lo(2 * j);
+      const R gg = odd ? tp.hi(2 * j + 1) : tp.hi(2 * j);
+      v2 += hh * tr[0][km - j][cl] + gg * tr[1][km - j][cl];
     }
-    out[(int64_t)m * ld + c] = v;
+    out[(int64_t)m * ld + c] = v2;
   }
   __syncthreads();
 }

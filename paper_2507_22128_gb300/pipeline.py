@@ -26,6 +26,8 @@ class Method:
     lam_rel: float = 1e-3
     iters: int = 50
     levels: int = 4
+    dictionary: str = "db4"               # "db4" or "db1-8" (the paper's concatenation, Sec. 5.2)
+    schedule: tuple | None = None         # (a, b): lambda_n = a ||residual_n||_2 b^n
 
 
 class Reconstruction:
@@ -74,7 +76,9 @@ class Reconstruction:
         if m.kind == "msclean":
             rix.minor_cycle_msclean(self.job, p, m.scales, m.gain, m.niter, m.threshold, delta_out, stream)
         else:
-            rix.minor_cycle_fista(self.job, p, m.lam, m.lam_rel, m.iters, m.levels, delta_out, stream)
+            d = rix.DICT_DB4 if m.dictionary == "db4" else rix.DICT_DB1_8
+            rix.minor_cycle_fista(self.job, p, m.lam, m.lam_rel, m.iters, m.levels, delta_out, stream, d,
+                                  m.schedule)
 
     def cycle(self, m: Method, stream=None, concurrent: bool = True):
         """One major cycle of every partition, then the minor cycles.  With

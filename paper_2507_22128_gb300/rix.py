@@ -47,7 +47,11 @@ class MscleanParams(C.Structure):
 
 class FistaParams(C.Structure):
     _fields_ = [("lambda_", C.c_double), ("lambda_rel", C.c_double), ("iters", C.c_int32),
-                ("levels", C.c_int32)]
+                ("levels", C.c_int32), ("dictionary", C.c_int32), ("reserved", C.c_int32),
+                ("sched_a", C.c_double), ("sched_b", C.c_double)]
+
+
+DICT_DB4, DICT_DB1_8 = 0, 1
 
 
 def _load() -> C.CDLL:
@@ -80,6 +84,7 @@ def _load() -> C.CDLL:
         "rix_timing_enable": (C.c_int, [C.c_int]),
         "rix_timing_read": (C.c_int, [C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
         "rix_selftest_barrier_timeout": (C.c_int, [vp, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
+        "rix_daubechies_lowpass": (C.c_int, [C.c_int, C.POINTER(C.c_double)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -95,7 +100,7 @@ EXPORTED = ("rix_create", "rix_destroy", "rix_job_workspace_bytes", "rix_job_cre
             "rix_degrid", "rix_grid", "rix_psf", "rix_major_cycle", "rix_minor_cycle_msclean",
             "rix_minor_cycle_fista", "rix_get_components", "rix_get_model", "rix_combine", "rix_last_error",
             "rix_kernel_launches", "rix_timing_enable", "rix_timing_read", "rix_grid_noalloc",
-            "rix_selftest_barrier_timeout")
+            "rix_selftest_barrier_timeout", "rix_daubechies_lowpass")
 
 
 def _check(rc: int):
@@ -232,8 +237,11 @@ def minor_cycle_msclean(job, part, scales, gain, niter, threshold, delta_out=Non
                                         _stream(stream)))
 
 
-def minor_cycle_fista(job, part, lam=0.0, lam_rel=1e-3, iters=50, levels=4, delta_out=None, stream=None):
-    p = FistaParams(float(lam), float(lam_rel), int(iters), int(levels))
+def minor_cycle_fista(job, part, lam=0.0, lam_rel=1e-3, iters=50, levels=4, delta_out=None, stream=None,
+                      dictionary=DICT_DB4, schedule=None):
+    """schedule: (a, b) for lambda_n = a ||residual_n||_2 b^n, or None."""
+    a, b = schedule if schedule is not None else (0.0, 0.0)
+    p = FistaParams(float(lam), float(lam_rel), int(iters), int(levels), int(dictionary), 0, float(a), float(b))
     _check(_lib.rix_minor_cycle_fista(job, part, C.byref(p), _ptr(delta_out, _RT, name="delta_out"),
                                       _stream(stream)))
 
@@ -284,3 +292,11 @@ def selftest_barrier_timeout(ctx):
     status, gave_up = C.c_int(), C.c_int()
     _check(_lib.rix_selftest_barrier_timeout(ctx, C.byref(status), C.byref(gave_up)))
     return status.value, gave_up.value
+
+
+def daubechies_lowpass(p: int):
+    """The library's db_p low-pass filter (2p taps) as a list of floats."""
+    h = (C.c_double * 16)()
+    k = _lib.rix_daubechies_lowpass(int(p), h)
+    _check(min(k, 0))
+    return [h[i] for i in range(k)]

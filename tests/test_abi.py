@@ -39,3 +39,20 @@ def test_workspace_query_and_invalid_desc_need_no_gpu():
     assert ok > 0
     assert rix.job_workspace_bytes(1000, 4.85e-6, 16, [1.3e9], rix.FP32, 2, 1000) == 0      # n not a power of 2
     assert rix.job_workspace_bytes(1024, 4.85e-6, 4, [1.3e9], rix.FP32, 2, 1000) == 0       # too few w-planes
+
+
+def test_library_daubechies_filters():
+    """The library forms db1..db8 with its own root finder; they agree with the
+    oracle's spectral factorisation and with the db2 closed form."""
+    import numpy as np
+    from oracle import wavelet
+    from paper_2507_22128_gb300 import rix
+    for p in range(1, 9):
+        h = np.array(rix.daubechies_lowpass(p))
+        assert h.shape == (2 * p,)
+        assert np.max(np.abs(h - wavelet.daubechies(p))) < 1e-11
+    s3 = np.sqrt(3.0)
+    want = np.array([1 + s3, 3 + s3, 3 - s3, 1 - s3]) / (4 * np.sqrt(2.0))
+    assert np.max(np.abs(np.array(rix.daubechies_lowpass(2)) - want)) < 1e-15
+    with pytest.raises(rix.RixError):
+        rix.daubechies_lowpass(9)
