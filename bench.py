@@ -46,6 +46,10 @@ def parse():
     ap.add_argument("--cycles", type=int, default=10)
     ap.add_argument("--iters", type=int, default=50)
     ap.add_argument("--fp64", action="store_true", help="FP64 operator (comparator)")
+    ap.add_argument("--dictionary", default="db4", choices=["db4", "db1-8"],
+                    help="FISTA dictionary: Db4 alone, or the concatenation of db1..db8")
+    ap.add_argument("--schedule", default=None,
+                    help="a,b: lambda_n = a ||residual_n||_2 b^n instead of 1e-3 max |residual_1|")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-phases", action="store_true")
@@ -176,9 +180,11 @@ def cpu_baseline(a, steps=1, warmup=0):
 
 def config_dict(a):
     return {"workload": f"medium: {a.n}x{a.n} 1as, 64 ant log-spiral x {a.n_times} times x 4 ch "
-                        f"(1.3-1.5 GHz), 16 w-planes, 2 uv partitions, FISTA Db4 {a.iters} it, "
+                        f"(1.3-1.5 GHz), 16 w-planes, 2 uv partitions, FISTA {'Db4' if a.dictionary == 'db4' else 'db1..db8'} "
+                        f"{a.iters} it{'' if a.schedule is None else ', lambda schedule ' + a.schedule}, "
                         f"{a.cycles} major cycles",
             "n": a.n, "n_wplanes": 16, "n_part": 2, "major_cycles": a.cycles, "fista_iters": a.iters,
+            "fista_dictionary": a.dictionary,
             "l2": "flushed between steps (512 MiB write)", "precision": "fp64" if a.fp64 else "fp32"}
 
 
@@ -208,7 +214,8 @@ def main():
     img_h = torch.empty((obs.n, obs.n), dtype=rdt).pin_memory()
     ctx = rix.create(local)
     rec = pipeline.Reconstruction(ctx, obs.n, obs.cell_rad, obs.n_wplanes, obs.freq, obs.nrow, 2, prec)
-    meth = pipeline.Method("fista", lam_rel=1e-3, iters=a.iters, levels=4)
+    sched = None if a.schedule is None else tuple(float(v) for v in a.schedule.split(","))
+    meth = pipeline.Method("fista", lam_rel=1e-3, iters=a.iters, levels=4, dictionary=a.dictionary, schedule=sched)
     stream = torch.cuda.current_stream(dev)
     flush = torch.empty(128 * 1024 * 1024, dtype=torch.float32, device=dev)
     out = torch.empty((obs.n, obs.n), dtype=rdt, device=dev)
