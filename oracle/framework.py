@@ -23,7 +23,7 @@ import dataclasses
 
 import numpy as np
 
-from . import filters, fista, gridder, msclean, partition, wavelet
+from . import filters, fista, gridder, msclean, partition, wavelet, weighting
 
 
 @dataclasses.dataclass
@@ -39,10 +39,15 @@ class Setup:
     psf: list            # 2N x 2N per partition
     hspec: list          # centred spectra of the PSFs
     gam: np.ndarray      # Gamma_p on the 2N grid
+    weight: np.ndarray   # the weights imaged with (natural, or uniform per oracle.weighting)
 
 
-def setup(uvw, freq, weight, n, cell, nw, nparts, delta=1.0, ells=None, W=8) -> Setup:
+def setup(uvw, freq, weight, n, cell, nw, nparts, delta=1.0, ells=None, W=8, scheme="natural") -> Setup:
+    """``scheme``: "natural" (the given weights) or "uniform" (Sec. 5.1;
+    oracle.weighting), applied before the partition's weight sums and PSFs."""
     g = gridder.geometry(uvw, freq, n, cell, W=W, nw=nw)
+    if scheme == "uniform":
+        weight = weighting.uniform_weights(g, weight).reshape(np.shape(weight))
     r = partition.radius_px(g)
     if ells is None:
         ells = partition.ring_radii(r, nparts)
@@ -60,14 +65,15 @@ def setup(uvw, freq, weight, n, cell, nw, nparts, delta=1.0, ells=None, W=8) -> 
     wsum = partition.weight_sums(weight, mask, nparts)
     gam = filters.gammas(n, np.asarray(ells, dtype=np.float64), delta, nparts)
     return Setup(n, nparts, np.asarray(ells, dtype=np.float64), delta, g, mask, gparts, wsum,
-                 psfs, hs, gam)
+                 psfs, hs, gam, np.asarray(weight))
 
 
 class Loop:
-    def __init__(self, st: Setup, vis: np.ndarray, weight: np.ndarray):
+    def __init__(self, st: Setup, vis: np.ndarray, weight: np.ndarray | None = None):
+        """``weight`` None: the weights the setup images with (st.weight)."""
         self.st = st
         self.vis = vis.reshape(-1).astype(np.complex128)
-        self.w = weight.reshape(-1).astype(np.float64)
+        self.w = (st.weight if weight is None else weight).reshape(-1).astype(np.float64)
         P, n = st.nparts, st.n
         self.model = [np.zeros((n, n)) for _ in range(P)]
         self.rho = [[np.zeros((n, n)) for _ in range(P)] for _ in range(P)]   # rho[p][q]
