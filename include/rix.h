@@ -73,7 +73,16 @@ typedef struct {
   int32_t precision;      /* RIX_FP32 or RIX_FP64 */
   int32_t n_part;         /* number of uv partitions: 1 .. 4 */
   int32_t tile;           /* uv tile side for the sort and the gridder: 16 or 32; 0 = 16 */
+  int32_t weighting;      /* RIX_WEIGHT_NATURAL (the given weights) or RIX_WEIGHT_UNIFORM */
 } rix_job_desc;
+
+/* Visibility weighting.  Uniform (Sec. 5.1): each sample's weight is divided
+ * by the sum of the weights in its cell of the N x N image's Fourier grid
+ * (nearest cell centre, floor(u_lambda N dl + 1/2), likewise v) and in that
+ * cell's Hermitian mirror, over the samples inside the grid; the result is
+ * held in float32. */
+#define RIX_WEIGHT_NATURAL 0
+#define RIX_WEIGHT_UNIFORM 1
 
 /* Host-side statistics of a partitioned job (valid after rix_set_uv_partition). */
 typedef struct {
@@ -166,6 +175,11 @@ int rix_job_get_stats(rix_job_t job, rix_job_stats* out);
 int rix_set_uv_partition(rix_job_t job, const double* uvw_m, int64_t nrow, const float* weight,
                          const double* ell_px, double delta_px, uint8_t* mask_out,
                          rix_stream_t stream);
+
+/* Copies the weights the job images with ([nrow][nchan] float32, after the
+ * job's weighting; 1 for natural weighting without given weights) to the
+ * device buffer weight_out.  Needs rix_set_uv_partition. */
+int rix_get_weights(rix_job_t job, float* weight_out, rix_stream_t stream);
 
 /* Copies the sorted entries (keys and sample indices, rix_job_stats.n_entries
  * of each) to device buffers; keys are packed as

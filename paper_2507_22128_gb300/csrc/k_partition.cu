@@ -261,6 +261,47 @@ __global__ void k_pick(const uint64_t* sorted, int64_t ns, int nparts, double* e
   if (i < nparts) ells[i - 1] = __longlong_as_double((long long)sorted[((int64_t)i * (ns - 1)) / nparts]);
 }
 
+// Uniform weighting: density of the natural weights on the N x N uv grid
+// (nearest cell of each sample inside the grid and its Hermitian mirror),
+// accumulated in FP64, then w / D(cell) in FP64 rounded to float32.
+__device__ __forceinline__ void uniform_cell(const SampleGeomParams& g, const Coords& c, int& a, int& b) {
+  a = (int)floor(__dadd_rn(__dmul_rn(c.ul, g.ndl), 0.5));
+  b = (int)floor(__dadd_rn(__dmul_rn(c.vl, g.ndl), 0.5));
+}
+
+__global__ void k_uniform_density(SampleGeomParams g, int64_t ns, const float* __restrict__ w, int n,
+                                  double* __restrict__ dens) {
+  for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < ns; s += (int64_t)gridDim.x * blockDim.x) {
+    const Coords c = sample_coords(g, s);
+    if (!c.inside) continue;
+    const double ws = w ? (double)w[s] : 1.0;
+    int a, b;
+    uniform_cell(g, c, a, b);
+    const int h = n / 2;
+    if (a + h >= 0 && a + h < n && b + h >= 0 && b + h < n) atomicAdd(&dens[(int64_t)(a + h) * n + (b + h)], ws);
+    if (h - a >= 0 && h - a < n && h - b >= 0 && h - b < n) atomicAdd(&dens[(int64_t)(h - a) * n + (h - b)], ws);
+  }
+}
+
+__global__ void k_uniform_apply(SampleGeomParams g, int64_t ns, const float* __restrict__ w_in, int n,
+                                const double* __restrict__ dens, float* __restrict__ w_out) {
+  for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < ns; s += (int64_t)gridDim.x * blockDim.x) {
+    const Coords c = sample_coords(g, s);
+    const double ws = w_in ? (double)w_in[s] : 1.0;
+    double out = ws;
+    if (c.inside) {
+      int a, b;
+      uniform_cell(g, c, a, b);
+      const int h = n / 2;
+      if (a + h >= 0 && a + h < n && b + h >= 0 && b + h < n) {
+        const double d = dens[(int64_t)(a + h) * n + (b + h)];
+        if (d > 0.0) out = __ddiv_rn(ws, d);
+      }
+    }
+    w_out[s] = (float)out;
+  }
+}
+
 struct ClassifyOut {
   uint8_t* mask_out;       // may be null
   uint32_t* counts;        // per sample: number of partitions
@@ -517,6 +558,28 @@ int partition_job(Job* job, const double* uvw, int64_t nrow, const float* weight
   }
   g.w_min = w_min;
   g.dw = dw;
+
+  // --- uniform weighting (before the weight sums and every gridding) ------
+  if (job->desc.weighting == RIX_WEIGHT_UNIFORM && ns > 0) {
+    const int n = job->desc.n;
+    double* dens = nullptr;
+    if (cudaMallocAsync(&dens, (size_t)n * n * sizeof(double), st) != cudaSuccess)
+      return fail(set_error(RIX_ENOMEM, "uniform weighting density"));
+    const bool had = job->weight.p != nullptr;
+    if (!had) {
+      const int rc = job->weight.alloc(ctx, ns * sizeof(float));
+      if (rc != RIX_OK) { cudaFreeAsync(dens, st); return fail(rc); }
+    }
+    const float* w_in = had ? job->weight.as<float>() : nullptr;
+    if (cudaMemsetAsync(dens, 0, (size_t)n * n * sizeof(double), st) != cudaSuccess) {
+      cudaFreeAsync(dens, st);
+      return fail(set_error(RIX_ECUDA, "uniform weighting memset"));
+    }
+    ::rix::note_launch(); k_uniform_density<<<blocks, 256, 0, st>>>(g, ns, w_in, n, dens);
+    ::rix::note_launch(); k_uniform_apply<<<blocks, 256, 0, st>>>(g, ns, w_in, n, dens, job->weight.as<float>());
+    cudaFreeAsync(dens, st);
+    if (cudaGetLastError() != cudaSuccess) return fail(set_error(RIX_ECUDA, "uniform weighting launch"));
+  }
 
   // --- ring radii ---------------------------------------------------------
   double ells[kMaxPart] = {0, 0, 0, 0};

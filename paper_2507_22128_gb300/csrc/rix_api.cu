@@ -149,6 +149,8 @@ static int check_desc(const rix_job_desc* d) {
   if (d->tile != 0 && d->tile != 16 && d->tile != 32) return set_error(RIX_EINVAL, "tile must be 16 or 32");
   if (d->tile == 32 && d->n_wplanes > 0) return set_error(RIX_EINVAL, "tile 32 needs a coplanar job (shared memory)");
   if (d->precision == RIX_FP64 && d->n > 2048) return set_error(RIX_EINVAL, "FP64 jobs support n <= 2048");
+  if (d->weighting != RIX_WEIGHT_NATURAL && d->weighting != RIX_WEIGHT_UNIFORM)
+    return set_error(RIX_EINVAL, "weighting must be RIX_WEIGHT_NATURAL or RIX_WEIGHT_UNIFORM");
   return RIX_OK;
 }
 
@@ -407,6 +409,29 @@ static int rix_get_sorted_entries_impl(rix_job_t job, uint32_t* keys_out, uint32
   return RIX_OK;
 }
 
+__global__ void k_fill_ones(float* __restrict__ out, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = 1.0f;
+}
+
+static int rix_get_weights_impl(rix_job_t job, float* weight_out, rix_stream_t stream) {
+  if (!job || !weight_out) return set_error(RIX_EINVAL, "NULL argument");
+  Job& J = job->j;
+  if (!J.partitioned) return set_error(RIX_ESTATE, "not partitioned");
+  RIX_CUDA(cudaSetDevice(J.ctx->device));
+  cudaStream_t st = (cudaStream_t)stream;
+  const int64_t ns = J.stats.n_samples;
+  if (ns == 0) return RIX_OK;
+  if (J.weight.p) {
+    RIX_CUDA(cudaMemcpyAsync(weight_out, J.weight.p, ns * sizeof(float), cudaMemcpyDeviceToDevice, st));
+  } else {
+    note_launch();
+    k_fill_ones<<<(unsigned)std::min<int64_t>(ceil_div(ns, 256), (int64_t)J.ctx->num_sms * 8), 256, 0, st>>>(weight_out, ns);
+    RIX_CUDA(cudaGetLastError());
+  }
+  return RIX_OK;
+}
+
 static int rix_degrid_impl(rix_job_t job, int part, const void* image, void* vis_out, rix_stream_t stream) {
   if (!job) return set_error(RIX_EINVAL, "job is NULL");
   Job& J = job->j;
@@ -585,6 +610,9 @@ int rix_set_uv_partition(rix_job_t job, const double* uvw_m, int64_t nrow, const
 }
 int rix_get_sorted_entries(rix_job_t job, uint32_t* keys_out, uint32_t* samples_out, rix_stream_t stream) {
   RIX_NOTE(job, stream, rix_get_sorted_entries_impl(job, keys_out, samples_out, stream));
+}
+int rix_get_weights(rix_job_t job, float* weight_out, rix_stream_t stream) {
+  RIX_NOTE(job, stream, rix_get_weights_impl(job, weight_out, stream));
 }
 int rix_degrid(rix_job_t job, int part, const void* image, void* vis_out, rix_stream_t stream) {
   RIX_NOTE(job, stream, rix_degrid_impl(job, part, image, vis_out, stream));

@@ -29,7 +29,10 @@ class RixError(RuntimeError):
 class JobDesc(C.Structure):
     _fields_ = [("n", C.c_int32), ("cell_rad", C.c_double), ("n_wplanes", C.c_int32),
                 ("nchan", C.c_int32), ("freq_hz", C.POINTER(C.c_double)), ("precision", C.c_int32),
-                ("n_part", C.c_int32), ("tile", C.c_int32)]
+                ("n_part", C.c_int32), ("tile", C.c_int32), ("weighting", C.c_int32)]
+
+
+WEIGHT_NATURAL, WEIGHT_UNIFORM = 0, 1
 
 
 class JobStats(C.Structure):
@@ -69,6 +72,7 @@ def _load() -> C.CDLL:
         "rix_job_get_stats": (C.c_int, [vp, C.POINTER(JobStats)]),
         "rix_set_uv_partition": (C.c_int, [vp, vp, i64, vp, C.POINTER(dbl), dbl, vp, vp]),
         "rix_get_sorted_entries": (C.c_int, [vp, vp, vp, vp]),
+        "rix_get_weights": (C.c_int, [vp, vp, vp]),
         "rix_degrid": (C.c_int, [vp, C.c_int, vp, vp, vp]),
         "rix_grid": (C.c_int, [vp, C.c_int, vp, vp, vp]),
         "rix_grid_noalloc": (C.c_int, [vp, C.c_int, vp, vp, vp]),
@@ -100,7 +104,7 @@ EXPORTED = ("rix_create", "rix_destroy", "rix_job_workspace_bytes", "rix_job_cre
             "rix_degrid", "rix_grid", "rix_psf", "rix_major_cycle", "rix_minor_cycle_msclean",
             "rix_minor_cycle_fista", "rix_get_components", "rix_get_model", "rix_combine", "rix_last_error",
             "rix_kernel_launches", "rix_timing_enable", "rix_timing_read", "rix_grid_noalloc",
-            "rix_selftest_barrier_timeout", "rix_daubechies_lowpass")
+            "rix_selftest_barrier_timeout", "rix_daubechies_lowpass", "rix_get_weights")
 
 
 def _check(rc: int):
@@ -141,20 +145,22 @@ def destroy(ctx: int):
     _check(_lib.rix_destroy(ctx))
 
 
-def _desc(n, cell_rad, n_wplanes, freq_hz, precision, n_part, tile):
+def _desc(n, cell_rad, n_wplanes, freq_hz, precision, n_part, tile, weighting=WEIGHT_NATURAL):
     f = (C.c_double * len(freq_hz))(*[float(x) for x in freq_hz])
     d = JobDesc(n, cell_rad, n_wplanes, len(freq_hz), C.cast(f, C.POINTER(C.c_double)), precision,
-                n_part, tile)
+                n_part, tile, weighting)
     return d, f
 
 
-def job_workspace_bytes(n, cell_rad, n_wplanes, freq_hz, precision, n_part, nrow, tile=0) -> int:
-    d, _keep = _desc(n, cell_rad, n_wplanes, freq_hz, precision, n_part, tile)
+def job_workspace_bytes(n, cell_rad, n_wplanes, freq_hz, precision, n_part, nrow, tile=0,
+                        weighting=WEIGHT_NATURAL) -> int:
+    d, _keep = _desc(n, cell_rad, n_wplanes, freq_hz, precision, n_part, tile, weighting)
     return int(_lib.rix_job_workspace_bytes(C.byref(d), nrow))
 
 
-def job_create(ctx, n, cell_rad, n_wplanes, freq_hz, precision, n_part, max_rows, tile=0) -> int:
-    d, _keep = _desc(n, cell_rad, n_wplanes, freq_hz, precision, n_part, tile)
+def job_create(ctx, n, cell_rad, n_wplanes, freq_hz, precision, n_part, max_rows, tile=0,
+               weighting=WEIGHT_NATURAL) -> int:
+    d, _keep = _desc(n, cell_rad, n_wplanes, freq_hz, precision, n_part, tile, weighting)
     h = C.c_void_p()
     _check(_lib.rix_job_create(ctx, C.byref(d), max_rows, C.byref(h)))
     return h.value
@@ -194,6 +200,11 @@ def set_uv_partition(job, uvw, weight=None, ell_px=None, delta_px=1.0, mask_out=
 def get_sorted_entries(job, keys_out, samples_out, stream=None):
     _check(_lib.rix_get_sorted_entries(job, _ptr(keys_out, torch.int32, name="keys_out"),
                                        _ptr(samples_out, torch.int32, name="samples_out"), _stream(stream)))
+
+
+def get_weights(job, weight_out, stream=None):
+    """The weights the job images with (after its weighting), float32 [nrow * nchan]."""
+    _check(_lib.rix_get_weights(job, _ptr(weight_out, torch.float32, name="weight_out"), _stream(stream)))
 
 
 # --------------------------------------------------------------- a4 - a7 --
