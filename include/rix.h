@@ -47,6 +47,8 @@
 extern "C" {
 #endif
 
+#define RIX_MAX_PART 8      /* most uv partitions per job (ring partitions, Sec. 3 generalised) */
+
 #define RIX_OK 0
 #define RIX_EINVAL (-1)   /* bad argument, size or pointer */
 #define RIX_ENOMEM (-2)   /* device allocation failed or memory budget exceeded */
@@ -71,7 +73,7 @@ typedef struct {
   int32_t nchan;          /* channels per row, 1 .. 65536 */
   const double* freq_hz;  /* host [nchan], copied at rix_job_create */
   int32_t precision;      /* RIX_FP32 or RIX_FP64 */
-  int32_t n_part;         /* number of uv partitions: 1 .. 4 */
+  int32_t n_part;         /* number of uv partitions: 1 .. RIX_MAX_PART */
   int32_t tile;           /* uv tile side for the sort and the gridder: 16 or 32; 0 = 16 */
   int32_t weighting;      /* RIX_WEIGHT_NATURAL (the given weights) or RIX_WEIGHT_UNIFORM */
 } rix_job_desc;
@@ -90,17 +92,17 @@ typedef struct {
   int64_t n_samples;          /* nrow * nchan */
   int64_t n_outside;          /* samples whose kernel footprint leaves the grid (excluded) */
   int64_t n_entries;          /* sum over partitions of samples in the partition */
-  int64_t part_count[4];      /* samples per partition (overlap counted in each) */
-  double part_weight[4];      /* weight sum per partition */
-  double ell_px[3];           /* ring radii used (pixels of the N-grid's Fourier plane) */
+  int64_t part_count[RIX_MAX_PART];   /* samples per partition (overlap counted in each) */
+  double part_weight[RIX_MAX_PART];   /* weight sum per partition */
+  double ell_px[RIX_MAX_PART - 1];    /* ring radii used (pixels of the N-grid's Fourier plane) */
   double delta_px;
   double w_min;               /* lowest w (wavelengths) */
   double dw;                  /* w-plane spacing (wavelengths) */
   double max_dw_nm1;          /* max |dw (n - 1)| over the image (w-stacking accuracy) */
-  int32_t window_lo[4];       /* per partition uv-grid window [lo, lo + size) on both axes */
-  int32_t window_size[4];
+  int32_t window_lo[RIX_MAX_PART];    /* per partition uv-grid window [lo, lo + size) on both axes */
+  int32_t window_size[RIX_MAX_PART];
   int64_t n_work_items;       /* gridder work items (tile chunks) over all partitions */
-  int32_t cycle[4];           /* major cycles completed per partition */
+  int32_t cycle[RIX_MAX_PART];        /* major cycles completed per partition */
 } rix_job_stats;
 
 /* ms-CLEAN parameters (Eq. 6-7; Sec. 5.2). */

@@ -582,7 +582,7 @@ int partition_job(Job* job, const double* uvw, int64_t nrow, const float* weight
   }
 
   // --- ring radii ---------------------------------------------------------
-  double ells[kMaxPart] = {0, 0, 0, 0};
+  double ells[kMaxPart] = {};
   if (P > 1) {
     if (ell_px) {
       for (int i = 0; i < P - 1; ++i) ells[i] = ell_px[i];

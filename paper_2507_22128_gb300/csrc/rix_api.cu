@@ -145,7 +145,7 @@ static int check_desc(const rix_job_desc* d) {
   for (int c = 0; c < d->nchan; ++c)
     if (!(d->freq_hz[c] > 0.0)) return set_error(RIX_EINVAL, "frequencies must be positive");
   if (d->precision != RIX_FP32 && d->precision != RIX_FP64) return set_error(RIX_EINVAL, "bad precision");
-  if (d->n_part < 1 || d->n_part > kMaxPart) return set_error(RIX_EINVAL, "n_part must be in [1, 4]");
+  if (d->n_part < 1 || d->n_part > kMaxPart) return set_error(RIX_EINVAL, "n_part must be in [1, %d]", kMaxPart);
   if (d->tile != 0 && d->tile != 16 && d->tile != 32) return set_error(RIX_EINVAL, "tile must be 16 or 32");
   if (d->tile == 32 && d->n_wplanes > 0) return set_error(RIX_EINVAL, "tile 32 needs a coplanar job (shared memory)");
   if (d->precision == RIX_FP64 && d->n > 2048) return set_error(RIX_EINVAL, "FP64 jobs support n <= 2048");

@@ -172,7 +172,7 @@ int radix_sort_u64_keys(uint64_t* keys, uint64_t* keys_tmp, int64_t n, int bits,
 // ---------------------------------------------------------------------------
 // job
 // ---------------------------------------------------------------------------
-constexpr int kMaxPart = 4;
+constexpr int kMaxPart = RIX_MAX_PART;
 constexpr int kMaxScales = 8;
 
 struct Part {

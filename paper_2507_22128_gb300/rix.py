@@ -35,12 +35,16 @@ class JobDesc(C.Structure):
 WEIGHT_NATURAL, WEIGHT_UNIFORM = 0, 1
 
 
+MAX_PART = 8
+
+
 class JobStats(C.Structure):
     _fields_ = [("nrow", C.c_int64), ("n_samples", C.c_int64), ("n_outside", C.c_int64),
-                ("n_entries", C.c_int64), ("part_count", C.c_int64 * 4), ("part_weight", C.c_double * 4),
-                ("ell_px", C.c_double * 3), ("delta_px", C.c_double), ("w_min", C.c_double),
-                ("dw", C.c_double), ("max_dw_nm1", C.c_double), ("window_lo", C.c_int32 * 4),
-                ("window_size", C.c_int32 * 4), ("n_work_items", C.c_int64), ("cycle", C.c_int32 * 4)]
+                ("n_entries", C.c_int64), ("part_count", C.c_int64 * MAX_PART),
+                ("part_weight", C.c_double * MAX_PART), ("ell_px", C.c_double * (MAX_PART - 1)),
+                ("delta_px", C.c_double), ("w_min", C.c_double), ("dw", C.c_double), ("max_dw_nm1", C.c_double),
+                ("window_lo", C.c_int32 * MAX_PART), ("window_size", C.c_int32 * MAX_PART),
+                ("n_work_items", C.c_int64), ("cycle", C.c_int32 * MAX_PART)]
 
 
 class MscleanParams(C.Structure):

@@ -113,9 +113,10 @@ def test_fista_loop_matches_oracle(ctx, obs_wstack, prec):
     assert rel_l2(img, loop.combine()) < tol
 
 
-def test_fista_four_partitions(ctx, obs_wstack):
+@pytest.mark.parametrize("nparts", [4, 8])
+def test_fista_ring_partitions(ctx, obs_wstack, nparts):
     prm = dict(lam_rel=1e-3, n_iter=10, levels=2)
-    loop, img, _ = _run_both(ctx, obs_wstack, 1, 4, "fista", 2, **prm)
+    loop, img, _ = _run_both(ctx, obs_wstack, 1, nparts, "fista", 2, **prm)
     assert rel_l2(img, loop.combine()) < 1e-9
 
 

@@ -39,7 +39,7 @@ def _oracle(obs, nparts):
     return framework.setup(obs.uvw, obs.freq, obs.weight, obs.n, obs.cell_rad, obs.n_wplanes, nparts)
 
 
-CASES = [("small", 0, 2), ("small", 1, 2), ("wstack", 0, 2), ("wstack", 1, 2), ("wstack", 0, 4)]
+CASES = [("small", 0, 2), ("small", 1, 2), ("wstack", 0, 2), ("wstack", 1, 2), ("wstack", 0, 4), ("wstack", 1, 8)]
 
 
 def _obs(name, obs_small, obs_wstack):
