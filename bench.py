@@ -372,8 +372,8 @@ def phase_split(rec, rix, a, meth, stream, uvw, vis, w, out, flush):
 # timed job (profiles/k_tiles_ws_medium_dram.md): residual launches of
 # partitions 0 and 1, PSF launches of partitions 0 and 1.  Reported only for
 # that workload and while k_grid.cu is the source the counters were taken on.
-TILES_TRAFFIC = {"k_grid_sha1": "f00709e1c5bbc07f0b29a43cec683a0dd2474bb2",
-                 "resid": (134.10e6, 271.75e6), "psf": (85.59e6, 221.12e6)}
+TILES_TRAFFIC = {"k_grid_sha1": "cb9c2262ddf59759316b789e95dfe9524cf84088",
+                 "resid": (161.74e6, 261.73e6), "psf": (85.82e6, 218.28e6)}
 
 
 def tiles_traffic(a):
@@ -420,6 +420,8 @@ def roofline_tiles(tiles_ms, tiles_n, st, a, entries_timed):
                     "algorithmic_bytes_per_launch": (ent_b + plane_b) / tiles_n, "peak_source": kind},
             "traffic": tiles_traffic(a), "traffic_unit": "B per launch",
             "launches_timed": tiles_n, "busy_ms_per_launch": tiles_ms / tiles_n,
+            "ncu_binding_unit": "shared memory: L1/shared throughput 86 % of peak, FMA pipe 20 % "
+                                "(profiles/k_tiles_ws_medium_300t.md)",
             "peak_source": f"152 SMs x {lanes} {'FP64' if a.fp64 else 'FP32'} lanes x 2 flop x {clk:.0f} MHz "
                            f"(max SM clock of {kind} peaks)"}
 
