@@ -59,6 +59,23 @@ def parse():
     return ap.parse_args()
 
 
+def max_over_ranks(x: float, device) -> float:
+    """The largest x over all ranks of the process group (x itself without
+    one): the timed region ends when the slowest rank does."""
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return x
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_value(units_per_rank: float, world: int, ms_per_step: float) -> float:
+    """Mvis/s of the whole job: every rank processes units_per_rank per step
+    (weak scaling), divided by the slowest rank's time."""
+    return units_per_rank * world / (ms_per_step * 1e-3) / 1e6
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -255,13 +272,9 @@ def main():
     if world > 1:
         torch.distributed.barrier()
     step_ms = [s.elapsed_time(e) for s, e in ev]
-    total_ms = sum(step_ms)
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(sum(step_ms), dev)
     ms = total_ms / a.steps
-    value = units * world / (ms * 1e-3) / 1e6
+    value = whole_job_value(units, world, ms)
 
     # ---- per-phase split of one job (diagnostic) ----
     phases = None if a.no_phases else phase_split(rec, rix, a, meth, stream, uvw_d, vis_d, w_d, out, flush)
