@@ -256,6 +256,7 @@ def main():
     torch.cuda.synchronize()
     rix.timing_read(rix.TIME_TILES)
     rix.timing_read(rix.TIME_FFT)
+    rix.timing_read(rix.TIME_MINOR_LOOP)
     rix.timing_enable(True)
     launches0 = rix.kernel_launches()
     with ClockSampler(local) as clk:
@@ -269,6 +270,7 @@ def main():
     rix.timing_enable(False)
     tiles_ms, tiles_busy, tiles_n = rix.timing_read(rix.TIME_TILES)
     fft_ms, fft_busy, fft_n = rix.timing_read(rix.TIME_FFT)
+    loop_ms, loop_busy, loop_n = rix.timing_read(rix.TIME_MINOR_LOOP)
     if world > 1:
         torch.distributed.barrier()
     step_ms = [s.elapsed_time(e) for s, e in ev]
@@ -309,7 +311,8 @@ def main():
             "config": config_dict(a), "clocks": clk.summary(), "e2e": e2e, "gpu_launches": int(launches),
             "roofline": roof, "phases_ms": phases,
             "kernel_ms_per_step": {"grid_tiles_busy": tiles_busy / a.steps, "grid_tiles_sum": tiles_ms / a.steps,
-                                   "fft_passes_outside_graphs_busy": fft_busy / a.steps},
+                                   "fft_passes_busy": fft_busy / a.steps,
+                                   "minor_loop_busy": loop_busy / a.steps, "minor_loop_sum": loop_ms / a.steps},
             "samples_per_cycle": int(sum(st["part_count"][:2])), "step_ms": step_ms}
     if a.serve_jobs > 0:
         line["serving"] = serving_experiment(ctx, a, rank)

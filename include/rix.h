@@ -303,10 +303,12 @@ uint64_t rix_kernel_launches(void);
  * the summed launch durations (ms), the busy time (ms: the union of the
  * launch intervals, which differs from the sum when launches on different
  * streams overlap) and the number of launches, then clears them.
- * Classes: 0 = tiled degrid/grid kernel, 1 = FFT passes, 2 = partition. */
+ * Classes: 0 = tiled degrid/grid kernel, 1 = FFT passes, 2 = partition,
+ * 3 = minor-cycle loop kernels. */
 #define RIX_TIME_TILES 0
 #define RIX_TIME_FFT 1
 #define RIX_TIME_PARTITION 2
+#define RIX_TIME_MINOR_LOOP 3   /* the persistent FISTA loop and the ms-CLEAN kernel */
 int rix_timing_enable(int on);
 int rix_timing_read(int kernel_class, double* total_ms, double* busy_ms, int64_t* launches);
 

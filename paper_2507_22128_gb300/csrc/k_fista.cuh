@@ -399,7 +399,9 @@ int launch_fista_loop(const Ctx* ctx, const FistaLoop<R>& f, cudaStream_t st) {
   RIX_CUDA(cudaMemsetAsync(f.barrier, 0, sizeof(unsigned int), st));
   void* params[] = {&args};
   ::rix::note_launch();
+  timing_mark(kTimeMinorLoop, st, true);
   RIX_CUDA(cudaLaunchCooperativeKernel((const void*)kern, dim3(nblk), dim3(kFftThreads), params, smem, st));
+  timing_mark(kTimeMinorLoop, st, false);
   return RIX_OK;
 }
 

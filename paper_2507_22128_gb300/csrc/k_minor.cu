@@ -646,7 +646,10 @@ int op_msclean(Job* job, int p, const rix_msclean_params* prm, R* delta_out, cud
   ca.comp_pix = ca.comp_s + cap;
   ca.count = ca.comp_pix + cap;
   void* args[] = {&ca};
-  ::rix::note_launch(); RIX_CUDA(cudaLaunchCooperativeKernel((const void*)k_msclean<R>, dim3(nblk), dim3(256), args, 0, st));
+  ::rix::note_launch();
+  timing_mark(kTimeMinorLoop, st, true);
+  RIX_CUDA(cudaLaunchCooperativeKernel((const void*)k_msclean<R>, dim3(nblk), dim3(256), args, 0, st));
+  timing_mark(kTimeMinorLoop, st, false);
   RIX_TRY(publish<R>(job, p, cycle, st));
   if (delta_out) RIX_CUDA(cudaMemcpyAsync(delta_out, pt.delta.p, npix * sizeof(R), cudaMemcpyDeviceToDevice, st));
   return RIX_OK;

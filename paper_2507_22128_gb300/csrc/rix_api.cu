@@ -42,7 +42,7 @@ unsigned long long launch_count() { return g_launches.load(); }
 static std::atomic<bool> g_timing{false};
 static std::mutex g_tmu;
 static std::vector<std::pair<cudaEvent_t, cudaEvent_t>> g_tev[kTimeClasses];
-static cudaEvent_t g_topen[kTimeClasses] = {nullptr, nullptr, nullptr};
+static cudaEvent_t g_topen[kTimeClasses] = {};
 bool timing_on() { return g_timing.load(std::memory_order_relaxed); }
 
 void timing_mark(int cls, cudaStream_t st, bool begin) {

@@ -24,7 +24,7 @@ unsigned long long launch_count();
 
 // Opt-in device timing of kernel classes (CUDA events recorded on the launch
 // stream around each launch; streams under capture are skipped).
-enum TimedClass : int { kTimeTiles = 0, kTimeFft = 1, kTimePartition = 2, kTimeClasses = 3 };
+enum TimedClass : int { kTimeTiles = 0, kTimeFft = 1, kTimePartition = 2, kTimeMinorLoop = 3, kTimeClasses = 4 };
 bool timing_on();
 void timing_mark(int cls, cudaStream_t st, bool begin);
 

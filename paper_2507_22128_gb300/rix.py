@@ -281,7 +281,7 @@ def kernel_launches() -> int:
     return int(_lib.rix_kernel_launches())
 
 
-TIME_TILES, TIME_FFT, TIME_PARTITION = 0, 1, 2
+TIME_TILES, TIME_FFT, TIME_PARTITION, TIME_MINOR_LOOP = 0, 1, 2, 3
 
 
 def timing_enable(on: bool = True):
