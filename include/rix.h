@@ -244,6 +244,21 @@ int rix_minor_cycle_msclean(rix_job_t job, int part, const rix_msclean_params* p
 int rix_minor_cycle_fista(rix_job_t job, int part, const rix_fista_params* params,
                           void* delta_out, rix_stream_t stream);
 
+/* The FISTA minor cycles of several partitions of the same cycle, with the
+ * same parameters, as one launch of the iteration loop: equivalent to
+ * rix_minor_cycle_fista for parts[0], ..., parts[n_parts - 1] in turn
+ * (without delta_out), with the same call-order rules for each.  parts: host
+ * array of n_parts distinct partition indices, 1 <= n_parts <= n_part.  Each
+ * partition's preparation (fill tables) and finish (image update, exchange
+ * terms) run on a stream the job owns, after the caller's work on `stream`
+ * and after that partition's own major cycle and the other partitions'
+ * previous minor cycles, whatever streams those ran on; the loop runs on
+ * `stream`, which on return waits for all of it.  The loops of the batch
+ * advance together, so every phase of an iteration serves all of them with
+ * one grid barrier. */
+int rix_minor_cycle_fista_batch(rix_job_t job, int n_parts, const int32_t* parts, const rix_fista_params* params,
+                                rix_stream_t stream);
+
 /* ms-CLEAN components found by the last minor cycle of `part`: count (host)
  * and, when non-NULL, up to `capacity` entries of scale index and row-major
  * pixel index (host int32) and amplitude (host double), in the order found.

@@ -1,5 +1,6 @@
-// a10: the FISTA minor cycle (Eq. 4-5, Db4 dictionary) as one persistent
-// cooperative kernel per call, compiled for each transform length 2N.
+// a10: the FISTA minor cycles (Eq. 4-5) of one or more partitions as one
+// persistent cooperative kernel per call, compiled for each transform length
+// 2N and dictionary.
 //
 // Every iteration is a chain of grid-wide phases separated by a bounded grid
 // barrier:
@@ -246,76 +247,100 @@ __device__ __noinline__ void ana_member(const R* src, int n, R* dst, int N, int 
   dwt_tile<R, true>(src, N, n, nullptr, dst, N, last, sm, bx, by, dsm, RefTaps<R, 2 * (MM + 1)>{taps});
 }
 
-// one synthesis level l of x = W c: level l of member m reads its level-l+1
-// output (or c's coarse block at the top level) and lands in (l odd ? B : A)
+template <typename R>
+struct FistaArgs {
+  FistaLoop<R> f[kMaxPart];   // the batch's loops, [0, nb)
+  int nb;
+  R gscale;
+  R taps[8][16];              // RIX_DICT_DB1_8: low-pass filters of db1 .. db8
+};
+
+// units of one wavelet level of one loop: tiles of side `tile` over an n x n
+// block, times the eight members with the concatenated dictionary
+template <int DICT>
+__device__ __forceinline__ int level_units(int n, int tile) {
+  const int nt = (n + tile - 1) / tile;
+  return (DICT == RIX_DICT_DB4 ? 1 : 8) * nt * nt;
+}
+
+// unit t of synthesis level l of x = W c for loop f: level l of member m
+// reads its level-l+1 output (or c's coarse block at the top level) and lands
+// in (l odd ? B : A) (Db4: tmp : x)
 template <typename R, int DICT, int N>
-__device__ __forceinline__ void synthesis_level(const FistaLoop<R>& f, const R* coef, int l, unsigned char* smem) {
+__device__ __forceinline__ void synthesis_unit(const FistaLoop<R>& f, const R* coef, int l, int t,
+                                               unsigned char* smem, const R (&taps)[8][16]) {
   const int n = N >> l, nt = (n + kTS - 1) / kTS, per = nt * nt;
   const bool top = l == f.levels - 1;
   if constexpr (DICT == RIX_DICT_DB4) {
     const R* ll = top ? coef : (((l + 1) & 1) ? f.tmp : f.x);
     R* dst = (l & 1) ? f.tmp : f.x;
     auto& ism = *reinterpret_cast<IdwtSmem<R, 8>*>(smem);
-    for (int u = blockIdx.x; u < per; u += gridDim.x)
-      idwt_tile<R>(ll, coef, n, dst, N, u % nt, u / nt, ism, Db4Taps<R>{});
+    idwt_tile<R>(ll, coef, n, dst, N, t % nt, t / nt, ism, Db4Taps<R>{});
   } else {
     const int64_t NN = (int64_t)N * N;
-    for (int u = blockIdx.x; u < 8 * per; u += gridDim.x) {
-      const int m = u / per, t = u - m * per;
-      const R* cm = coef + m * NN;
-      R* am = f.xs + m * NN;
-      R* bm = f.bs + m * NN;
-      const R* ll = top ? cm : (((l + 1) & 1) ? bm : am);
-      R* dst = (l & 1) ? bm : am;
-      const int bx = t % nt, by = t / nt;
+    const int m = t / per, tt = t - m * per;
+    const R* cm = coef + m * NN;
+    R* am = f.xs + m * NN;
+    R* bm = f.bs + m * NN;
+    const R* ll = top ? cm : (((l + 1) & 1) ? bm : am);
+    R* dst = (l & 1) ? bm : am;
+    const int bx = tt % nt, by = tt / nt;
 #define RIX_SYN(MM)                                                                                     \
-  case MM: syn_member<R, MM>(ll, cm, n, dst, N, bx, by, smem, f.taps[MM]); break;
-      switch (m) { RIX_SYN(0) RIX_SYN(1) RIX_SYN(2) RIX_SYN(3) RIX_SYN(4) RIX_SYN(5) RIX_SYN(6) RIX_SYN(7) }
+  case MM: syn_member<R, MM>(ll, cm, n, dst, N, bx, by, smem, taps[MM]); break;
+    switch (m) { RIX_SYN(0) RIX_SYN(1) RIX_SYN(2) RIX_SYN(3) RIX_SYN(4) RIX_SYN(5) RIX_SYN(6) RIX_SYN(7) }
 #undef RIX_SYN
-    }
   }
 }
 
-// one analysis level l of W^T g with the step fused into the final
-// coefficients: level l of member m reads g (l = 0) or its level l-1 LL and
-// writes its LL into (l odd ? B : A)
+// unit t of analysis level l of W^T g with the step fused into the final
+// coefficients, for loop f: level l of member m reads g (l = 0) or its level
+// l-1 LL and writes its LL into (l odd ? B : A) (Db4: tmp : x)
 template <typename R, int DICT, int N>
-__device__ __forceinline__ void analysis_level(const FistaLoop<R>& f, int l, const StepArgs<R>& sa,
-                                               unsigned char* smem) {
+__device__ __forceinline__ void analysis_unit(const FistaLoop<R>& f, int l, int t, const StepArgs<R>& sa,
+                                              unsigned char* smem, const R (&taps)[8][16]) {
   const int n = N >> l, nt = (n / 2 + kTB - 1) / kTB, per = nt * nt;
   const int last = l == f.levels - 1;
   if constexpr (DICT == RIX_DICT_DB4) {
     const R* src = l == 0 ? f.g : (((l - 1) & 1) ? f.tmp : f.x);
     R* dst = (l & 1) ? f.tmp : f.x;
     auto& dsm = *reinterpret_cast<DwtSmem<R, 8>*>(smem);
-    for (int u = blockIdx.x; u < per; u += gridDim.x)
-      dwt_tile<R, true>(src, N, n, nullptr, dst, N, last, sa, u % nt, u / nt, dsm, Db4Taps<R>{});
+    dwt_tile<R, true>(src, N, n, nullptr, dst, N, last, sa, t % nt, t / nt, dsm, Db4Taps<R>{});
   } else {
     const int64_t NN = (int64_t)N * N;
-    for (int u = blockIdx.x; u < 8 * per; u += gridDim.x) {
-      const int m = u / per, t = u - m * per;
-      R* am = f.xs + m * NN;
-      R* bm = f.bs + m * NN;
-      const R* src = l == 0 ? f.g : (((l - 1) & 1) ? bm : am);
-      R* dst = (l & 1) ? bm : am;
-      StepArgs<R> sm = sa;
-      sm.alpha += m * NN;
-      sm.y += m * NN;
-      const int bx = t % nt, by = t / nt;
+    const int m = t / per, tt = t - m * per;
+    R* am = f.xs + m * NN;
+    R* bm = f.bs + m * NN;
+    const R* src = l == 0 ? f.g : (((l - 1) & 1) ? bm : am);
+    R* dst = (l & 1) ? bm : am;
+    StepArgs<R> sm = sa;
+    sm.alpha += m * NN;
+    sm.y += m * NN;
+    const int bx = tt % nt, by = tt / nt;
 #define RIX_ANA(MM)                                                                                     \
-  case MM: ana_member<R, MM>(src, n, dst, N, last, sm, bx, by, smem, f.taps[MM]); break;
-      switch (m) { RIX_ANA(0) RIX_ANA(1) RIX_ANA(2) RIX_ANA(3) RIX_ANA(4) RIX_ANA(5) RIX_ANA(6) RIX_ANA(7) }
+  case MM: ana_member<R, MM>(src, n, dst, N, last, sm, bx, by, smem, taps[MM]); break;
+    switch (m) { RIX_ANA(0) RIX_ANA(1) RIX_ANA(2) RIX_ANA(3) RIX_ANA(4) RIX_ANA(5) RIX_ANA(6) RIX_ANA(7) }
 #undef RIX_ANA
-    }
   }
 }
 
-template <typename R>
-struct FistaArgs {
-  FistaLoop<R> f;
-  R gscale;
-};
+// step constants of one loop: L = 2 max Mx and lambda are fixed during the
+// minor cycle (lambda absolute, or lambda_rel max |residual| of the first
+// cycle, or the schedule a ||residual_n||_2 b^n); the concatenation's
+// 1/sqrt 8 enters the analysis through 1/L
+template <typename R, int DICT>
+__device__ __forceinline__ StepArgs<R> step_args(const FistaLoop<R>& f, R mom) {
+  const double lip = 2.0 * (double)f.state[0];
+  const double lam = f.sched_a > 0.0   ? f.sched_a * sqrt((double)f.state[2]) * f.sched_bn
+                     : f.lambda > 0.0 ? f.lambda
+                                      : f.lambda_rel * (double)f.state[1];
+  const bool active = lip > 0.0;
+  const double ascale = DICT == RIX_DICT_DB4 ? 1.0 : 1.0 / sqrt(8.0);
+  return StepArgs<R>{f.alpha, f.y, active ? (R)(ascale / lip) : R(0), active ? (R)(lam / lip) : R(0), active, mom};
+}
 
+// The loops of the batch advance together: every phase hands out the units
+// of all loops (unit u: loop u / per, its unit u % per), so one grid barrier
+// per phase serves the whole batch.
 template <typename R, int LOGL, int DICT>
 __global__ void __launch_bounds__(kFftThreads, sizeof(R) == 4 && LOGL <= 12 ? 2 : 1)
     k_fista_loop(const __grid_constant__ FistaArgs<R> a) {
@@ -326,77 +351,104 @@ __global__ void __launch_bounds__(kFftThreads, sizeof(R) == 4 && LOGL <= 12 ? 2 
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* s = reinterpret_cast<C*>(smem_raw);
   C* s2 = s + F::B * F::STRIDE;
-  const FistaLoop<R>& f = a.f;
-  GridBarrier bar{f.barrier, f.status, 0u};
-  // L = 2 max Mx and lambda are fixed during the minor cycle: lambda is
-  // absolute, or lambda_rel max |residual| of the first cycle, or the
-  // schedule a ||residual_n||_2 b^n
-  const double lip = 2.0 * (double)f.state[0];
-  const double lam = f.sched_a > 0.0   ? f.sched_a * sqrt((double)f.state[2]) * f.sched_bn
-                     : f.lambda > 0.0 ? f.lambda
-                                      : f.lambda_rel * (double)f.state[1];
-  const bool active = lip > 0.0;
-  // the concatenation's 1/sqrt 8 enters the analysis through 1/L
-  const double ascale = kCat ? 1.0 / sqrt(8.0) : 1.0;
-  const R inv_l = active ? (R)(ascale / lip) : R(0);
-  const R thr = active ? (R)(lam / lip) : R(0);
+  const int nb = a.nb;
+  const FistaLoop<R>& f0 = a.f[0];
+  GridBarrier bar{f0.barrier, f0.status, 0u};
   const R sscale = (R)(1.0 / sqrt(8.0));
   const int64_t NN = (int64_t)N * N;
+  const int levels = f0.levels;
   double t = 1.0;
-  for (int it = 0; it < f.iters; ++it) {
+  for (int it = 0; it < f0.iters; ++it) {
     // x = W y, coarsest level first
-    for (int l = f.levels - 1; l >= 0; --l) {
-      synthesis_level<R, DICT, N>(f, f.y, l, smem_raw);
+    for (int l = levels - 1; l >= 0; --l) {
+      const int per = level_units<DICT>(N >> l, kTS);
+      for (int u = blockIdx.x; u < nb * per; u += gridDim.x) {
+        const FistaLoop<R>& f = a.f[u / per];
+        synthesis_unit<R, DICT, N>(f, f.y, l, u % per, smem_raw, a.taps);
+      }
       if (!grid_barrier(bar)) return;
     }
-    for (int u = blockIdx.x; u < F::kRowUnits; u += gridDim.x) {
-      if constexpr (kCat) rows_fwd_unit<R, LOGL, 8>(f.xs, NN, sscale, f.ta, f.tw, s, s2, u);
-      else rows_fwd_unit<R, LOGL>(f.x, 0, R(1), f.ta, f.tw, s, s2, u);
+    for (int u = blockIdx.x; u < nb * F::kRowUnits; u += gridDim.x) {
+      const FistaLoop<R>& f = a.f[u / F::kRowUnits];
+      if constexpr (kCat) rows_fwd_unit<R, LOGL, 8>(f.xs, NN, sscale, f.ta, f.tw, s, s2, u % F::kRowUnits);
+      else rows_fwd_unit<R, LOGL>(f.x, 0, R(1), f.ta, f.tw, s, s2, u % F::kRowUnits);
     }
     if (!grid_barrier(bar)) return;
-    for (int u = blockIdx.x; u < F::kColUnits; u += gridDim.x)
-      cols_conv_unit<R, LOGL>(f.ta, f.mx, f.c, f.tb, f.tw, s, s2, u);
+    for (int u = blockIdx.x; u < nb * F::kColUnits; u += gridDim.x) {
+      const FistaLoop<R>& f = a.f[u / F::kColUnits];
+      cols_conv_unit<R, LOGL>(f.ta, f.mx, f.c, f.tb, f.tw, s, s2, u % F::kColUnits);
+    }
     if (!grid_barrier(bar)) return;
-    for (int u = blockIdx.x; u < F::kRowUnits; u += gridDim.x) rows_inv_unit<R, LOGL>(f.tb, f.g, a.gscale, f.tw, s, s2, u);
+    for (int u = blockIdx.x; u < nb * F::kRowUnits; u += gridDim.x) {
+      const FistaLoop<R>& f = a.f[u / F::kRowUnits];
+      rows_inv_unit<R, LOGL>(f.tb, f.g, a.gscale, f.tw, s, s2, u % F::kRowUnits);
+    }
     if (!grid_barrier(bar)) return;
     // t_{k+1} = (1 + sqrt(1 + 4 t_k^2)) / 2, momentum (t_k - 1) / t_{k+1}, each
     // operation rounded on its own
     const double tn = __dmul_rn(0.5, __dadd_rn(1.0, __dsqrt_rn(__dadd_rn(1.0, __dmul_rn(__dmul_rn(4.0, t), t)))));
-    const StepArgs<R> sa{f.alpha, f.y, inv_l, thr, active, (R)__ddiv_rn(__dadd_rn(t, -1.0), tn)};
-    for (int l = 0; l < f.levels; ++l) {
-      analysis_level<R, DICT, N>(f, l, sa, smem_raw);
+    const R mom = (R)__ddiv_rn(__dadd_rn(t, -1.0), tn);
+    for (int l = 0; l < levels; ++l) {
+      const int per = level_units<DICT>((N >> l) / 2, kTB);
+      for (int u = blockIdx.x; u < nb * per; u += gridDim.x) {
+        const FistaLoop<R>& f = a.f[u / per];
+        analysis_unit<R, DICT, N>(f, l, u % per, step_args<R, DICT>(f, mom), smem_raw, a.taps);
+      }
       if (!grid_barrier(bar)) return;
     }
     t = tn;
   }
   if constexpr (kCat) {
-    // the minor cycle's image W alpha: the members' syntheses, summed
-    for (int l = f.levels - 1; l >= 0; --l) {
-      synthesis_level<R, DICT, N>(f, f.alpha, l, smem_raw);
+    // each loop's image W alpha: the members' syntheses, summed
+    for (int l = levels - 1; l >= 0; --l) {
+      const int per = level_units<DICT>(N >> l, kTS);
+      for (int u = blockIdx.x; u < nb * per; u += gridDim.x) {
+        const FistaLoop<R>& f = a.f[u / per];
+        synthesis_unit<R, DICT, N>(f, f.alpha, l, u % per, smem_raw, a.taps);
+      }
       if (!grid_barrier(bar)) return;
     }
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < NN; i += (int64_t)gridDim.x * blockDim.x) {
-      R acc = R(0);
+    for (int b = 0; b < nb; ++b) {
+      const FistaLoop<R>& f = a.f[b];
+      for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < NN; i += (int64_t)gridDim.x * blockDim.x) {
+        R acc = R(0);
 #pragma unroll
-      for (int m = 0; m < 8; ++m) acc += f.xs[m * NN + i];
-      f.delta[i] = sscale * acc;
+        for (int m = 0; m < 8; ++m) acc += f.xs[m * NN + i];
+        f.delta[i] = sscale * acc;
+      }
     }
   }
 }
 
 template <typename R, int LOGL, int DICT>
-int launch_fista_loop(const Ctx* ctx, const FistaLoop<R>& f, cudaStream_t st) {
+int launch_fista_loop(const Ctx* ctx, const FistaLoop<R>* f, int nb, cudaStream_t st) {
   using F = FistaShape<R, LOGL, DICT>;
+  if (nb < 1 || nb > kMaxPart) return set_error(RIX_EINVAL, "FISTA batch of %d loops", nb);
+  for (int b = 1; b < nb; ++b)
+    if (f[b].n != f[0].n || f[b].levels != f[0].levels || f[b].iters != f[0].iters || f[b].dict != f[0].dict)
+      return set_error(RIX_EINVAL, "FISTA batch: the loops differ in size, levels, iterations or dictionary");
   auto kern = k_fista_loop<R, LOGL, DICT>;
   const size_t smem = F::kSmem;
   RIX_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int per_sm = 0;
   RIX_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kFftThreads, smem));
   if (per_sm < 1) return set_error(RIX_EINVAL, "FISTA loop does not fit on an SM (%zu B shared)", smem);
-  // one CTA per SM: the loop of another partition or job fits beside it
-  const int nblk = ctx->num_sms;
-  FistaArgs<R> args{f, (R)(2.0 / (4.0 * (double)F::N * (double)F::N))};
-  RIX_CUDA(cudaMemsetAsync(f.barrier, 0, sizeof(unsigned int), st));
+  // one CTA per SM for a single loop (another partition's loop or gridder fits
+  // beside it); a batch of loops takes up to two
+  const int nblk = ctx->num_sms * std::min(per_sm, nb > 1 ? 2 : 1);
+  FistaArgs<R> args{};
+  for (int b = 0; b < nb; ++b) args.f[b] = f[b];
+  args.nb = nb;
+  args.gscale = (R)(2.0 / (4.0 * (double)F::N * (double)F::N));
+  if constexpr (DICT == RIX_DICT_DB1_8) {
+    for (int m = 0; m < 8; ++m) {
+      double h[16];
+      const int k = daubechies_lowpass(m + 1, h);
+      if (k != 2 * (m + 1)) return set_error(RIX_EINVAL, "daubechies filter %d", m + 1);
+      for (int i = 0; i < 16; ++i) args.taps[m][i] = i < k ? (R)h[i] : R(0);
+    }
+  }
+  RIX_CUDA(cudaMemsetAsync(f[0].barrier, 0, sizeof(unsigned int), st));
   void* params[] = {&args};
   ::rix::note_launch();
   timing_mark(kTimeMinorLoop, st, true);
@@ -407,19 +459,19 @@ int launch_fista_loop(const Ctx* ctx, const FistaLoop<R>& f, cudaStream_t st) {
 
 // dispatch on the transform length 2N (N a power of two in [32, KMAXN])
 template <typename R, int DICT, int LOGL, int LOGL_MAX>
-int fista_loop_dispatch(const Ctx* ctx, const FistaLoop<R>& f, int logl, cudaStream_t st) {
-  if (logl == LOGL) return launch_fista_loop<R, LOGL, DICT>(ctx, f, st);
-  if constexpr (LOGL < LOGL_MAX) return fista_loop_dispatch<R, DICT, LOGL + 1, LOGL_MAX>(ctx, f, logl, st);
-  return set_error(RIX_EINVAL, "FISTA loop: image side %d not supported", f.n);
+int fista_loop_dispatch(const Ctx* ctx, const FistaLoop<R>* f, int nb, int logl, cudaStream_t st) {
+  if (logl == LOGL) return launch_fista_loop<R, LOGL, DICT>(ctx, f, nb, st);
+  if constexpr (LOGL < LOGL_MAX) return fista_loop_dispatch<R, DICT, LOGL + 1, LOGL_MAX>(ctx, f, nb, logl, st);
+  return set_error(RIX_EINVAL, "FISTA loop: image side %d not supported", f[0].n);
 }
 
 }  // namespace
 
 // the instances of one dictionary (k_fista_*.cu, one translation unit each)
 template <typename R, int DICT>
-int fista_loop_dict(const Ctx* ctx, const FistaLoop<R>& f, cudaStream_t st) {
+int fista_loop_dict(const Ctx* ctx, const FistaLoop<R>* f, int nb, cudaStream_t st) {
   constexpr int kMaxLogL = std::is_same<R, float>::value ? 13 : 12;   // N <= 4096 (FP32), 2048 (FP64)
-  return fista_loop_dispatch<R, DICT, 6, kMaxLogL>(ctx, f, ilog2(2 * (int64_t)f.n), st);
+  return fista_loop_dispatch<R, DICT, 6, kMaxLogL>(ctx, f, nb, ilog2(2 * (int64_t)f[0].n), st);
 }
 
 }  // namespace rix

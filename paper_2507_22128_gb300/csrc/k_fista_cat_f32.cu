@@ -3,5 +3,5 @@
 #include "k_fista.cuh"
 
 namespace rix {
-template int fista_loop_dict<float, RIX_DICT_DB1_8>(const Ctx*, const FistaLoop<float>&, cudaStream_t);
+template int fista_loop_dict<float, RIX_DICT_DB1_8>(const Ctx*, const FistaLoop<float>*, int, cudaStream_t);
 }  // namespace rix

@@ -3,5 +3,5 @@
 #include "k_fista.cuh"
 
 namespace rix {
-template int fista_loop_dict<double, RIX_DICT_DB1_8>(const Ctx*, const FistaLoop<double>&, cudaStream_t);
+template int fista_loop_dict<double, RIX_DICT_DB1_8>(const Ctx*, const FistaLoop<double>*, int, cudaStream_t);
 }  // namespace rix

@@ -655,8 +655,11 @@ int op_msclean(Job* job, int p, const rix_msclean_params* prm, R* delta_out, cud
   return RIX_OK;
 }
 
+// Everything of partition p's FISTA minor cycle before the iteration loop:
+// ingest the received images, the fill tables (Mx, C), lambda's reference,
+// the coefficient buffers; *f receives the loop's description.
 template <typename R>
-int op_fista(Job* job, int p, const rix_fista_params* prm, R* delta_out, cudaStream_t st) {
+int fista_prepare(Job* job, int p, const rix_fista_params* prm, FistaLoop<R>* f, cudaStream_t st) {
   Part& pt = job->part[p];
   const Ctx* ctx = job->ctx;
   const int n = job->desc.n;
@@ -685,11 +688,6 @@ int op_fista(Job* job, int p, const rix_fista_params* prm, R* delta_out, cudaStr
   RIX_TRY(alloc_zero<R>(job, pt.fi_y, ncoef * sizeof(R), st));
   RIX_TRY(ensure<R>(job, pt.fi_x, (cat ? 8 : 1) * npix * sizeof(R)));
   RIX_TRY(ensure<R>(job, pt.fi_alpha_prev, (cat ? 8 : 1) * npix * sizeof(R)));
-  R* alpha = pt.fi_alpha.as<R>();
-  R* y = pt.fi_y.as<R>();
-  R* x = pt.fi_x.as<R>();
-  R* g = pt.fimg.as<R>();
-  R* tmp = pt.fi_alpha_prev.as<R>();
   double sched_bn = 0.0;
   if (prm->sched_a > 0.0) {
     // lambda_n = a ||residual of cycle n||_2 b^n: the squared norm goes to state[2]
@@ -698,51 +696,93 @@ int op_fista(Job* job, int p, const rix_fista_params* prm, R* delta_out, cudaStr
     RIX_LAUNCH_CHECK();
     sched_bn = std::pow(prm->sched_b, (double)cycle);
   }
-  if (prm->iters > 0) {
-    // gradient of ||M x - C||^2 on the 2N grid: 2 crop F^-1 [Mx F pad x - C]
-    RIX_TRY(ensure<R>(job, pt.sync, 16));
-    FistaLoop<R> f{};
-    f.alpha = alpha; f.y = y; f.x = x; f.g = g; f.tmp = tmp;
-    f.ta = pt.ft_a.as<cplx<R>>();
-    f.tb = pt.ft_b.as<cplx<R>>();
-    f.mx = pt.fi_mx.as<R>();
-    f.c = pt.fi_c.as<cplx<R>>();
-    f.state = pt.fi_state.as<R>();
-    f.tw = twiddles<R>(ctx);
-    f.barrier = pt.sync.as<unsigned int>();
-    f.status = job->status.as<int>();
-    f.lambda = prm->lambda;
-    f.lambda_rel = prm->lambda_rel;
-    f.n = n;
-    f.levels = prm->levels;
-    f.iters = prm->iters;
-    f.dict = prm->dictionary;
-    f.sched_a = prm->sched_a;
-    f.sched_bn = sched_bn;
-    if (cat) {
-      // member level buffers: A in fi_x, B in fi_alpha_prev, 8 N^2 each
-      f.xs = x;
-      f.bs = tmp;
-      f.delta = pt.delta.as<R>();
-      for (int m = 0; m < 8; ++m) {
-        double h[16];
-        const int k = daubechies_lowpass(m + 1, h);
-        if (k != 2 * (m + 1)) return set_error(RIX_EINVAL, "daubechies filter %d", m + 1);
-        for (int i = 0; i < 16; ++i) f.taps[m][i] = i < k ? (R)h[i] : R(0);
-      }
-      RIX_TRY((fista_loop_dict<R, RIX_DICT_DB1_8>(ctx, f, st)));
-    } else {
-      RIX_TRY((fista_loop_dict<R, RIX_DICT_DB4>(ctx, f, st)));
-    }
-  }
+  RIX_TRY(ensure<R>(job, pt.sync, 16));
+  *f = FistaLoop<R>{};
+  f->alpha = pt.fi_alpha.as<R>();
+  f->y = pt.fi_y.as<R>();
+  f->x = pt.fi_x.as<R>();
+  f->g = pt.fimg.as<R>();
+  f->tmp = pt.fi_alpha_prev.as<R>();
+  f->ta = pt.ft_a.as<cplx<R>>();
+  f->tb = pt.ft_b.as<cplx<R>>();
+  f->mx = pt.fi_mx.as<R>();
+  f->c = pt.fi_c.as<cplx<R>>();
+  f->state = pt.fi_state.as<R>();
+  f->tw = twiddles<R>(ctx);
+  f->barrier = pt.sync.as<unsigned int>();
+  f->status = job->status.as<int>();
+  f->lambda = prm->lambda;
+  f->lambda_rel = prm->lambda_rel;
+  f->n = n;
+  f->levels = prm->levels;
+  f->iters = prm->iters;
+  f->dict = prm->dictionary;
+  f->sched_a = prm->sched_a;
+  f->sched_bn = sched_bn;
   if (cat) {
+    // member level buffers: A in fi_x, B in fi_alpha_prev, 8 N^2 each
+    f->xs = f->x;
+    f->bs = f->tmp;
+    f->delta = pt.delta.as<R>();
+  }
+  return RIX_OK;
+}
+
+// the loops of f[0 .. nb) in one launch
+template <typename R>
+int fista_run(const Ctx* ctx, const FistaLoop<R>* f, int nb, const rix_fista_params* prm, cudaStream_t st) {
+  if (prm->iters <= 0 || nb <= 0) return RIX_OK;
+  if (prm->dictionary == RIX_DICT_DB1_8) return fista_loop_dict<R, RIX_DICT_DB1_8>(ctx, f, nb, st);
+  return fista_loop_dict<R, RIX_DICT_DB4>(ctx, f, nb, st);
+}
+
+// Everything after the loop: i_bar_p = W alpha, the image update and the
+// Phi / rho exchange terms (publish).
+template <typename R>
+int fista_finish(Job* job, int p, const rix_fista_params* prm, R* delta_out, cudaStream_t st) {
+  Part& pt = job->part[p];
+  const int n = job->desc.n;
+  const int64_t npix = (int64_t)n * n;
+  if (prm->dictionary == RIX_DICT_DB1_8) {
     // the loop wrote W alpha into delta; with no iteration alpha = 0
     if (prm->iters == 0) RIX_CUDA(cudaMemsetAsync(pt.delta.p, 0, npix * sizeof(R), st));
   } else {
-    RIX_TRY(idwt2<R>(ctx, alpha, pt.delta.as<R>(), tmp, n, prm->levels, st));
+    RIX_TRY(idwt2<R>(job->ctx, pt.fi_alpha.as<R>(), pt.delta.as<R>(), pt.fi_alpha_prev.as<R>(), n, prm->levels, st));
   }
-  RIX_TRY(publish<R>(job, p, cycle, st));
+  RIX_TRY(publish<R>(job, p, pt.cycle, st));
   if (delta_out) RIX_CUDA(cudaMemcpyAsync(delta_out, pt.delta.p, npix * sizeof(R), cudaMemcpyDeviceToDevice, st));
+  return RIX_OK;
+}
+
+template <typename R>
+int op_fista(Job* job, int p, const rix_fista_params* prm, R* delta_out, cudaStream_t st) {
+  FistaLoop<R> f;
+  RIX_TRY(fista_prepare<R>(job, p, prm, &f, st));
+  RIX_TRY(fista_run<R>(job->ctx, &f, 1, prm, st));
+  return fista_finish<R>(job, p, prm, delta_out, st);
+}
+
+template <typename R>
+int op_fista_batch(Job* job, int nb, const int* parts, const rix_fista_params* prm, cudaStream_t st,
+                   const cudaStream_t* ps) {
+  FistaLoop<R> f[kMaxPart];
+  // each partition's preparation on its own stream, the loop after all of them
+  for (int i = 0; i < nb; ++i) {
+    Part& pt = job->part[parts[i]];
+    RIX_TRY(fista_prepare<R>(job, parts[i], prm, &f[i], ps[i]));
+    RIX_CUDA(cudaEventRecord(pt.ev_prep, ps[i]));
+    RIX_CUDA(cudaStreamWaitEvent(st, pt.ev_prep, 0));
+  }
+  RIX_TRY(fista_run<R>(job->ctx, f, nb, prm, st));
+  RIX_CUDA(cudaEventRecord(job->ev_batch, st));
+  // each partition's finish on its own stream, `st` after all of them
+  for (int i = 0; i < nb; ++i) {
+    Part& pt = job->part[parts[i]];
+    RIX_CUDA(cudaStreamWaitEvent(ps[i], job->ev_batch, 0));
+    RIX_TRY(fista_finish<R>(job, parts[i], prm, nullptr, ps[i]));
+    RIX_CUDA(cudaEventRecord(pt.ev_done, ps[i]));
+    RIX_CUDA(cudaStreamWaitEvent(st, pt.ev_done, 0));
+  }
   return RIX_OK;
 }
 
@@ -765,6 +805,8 @@ int op_combine(Job* job, R* out, cudaStream_t st) {
   template int fill_init<R>(Job*, cudaStream_t);                                            \
   template int op_msclean<R>(Job*, int, const rix_msclean_params*, R*, cudaStream_t);       \
   template int op_fista<R>(Job*, int, const rix_fista_params*, R*, cudaStream_t);           \
+  template int op_fista_batch<R>(Job*, int, const int*, const rix_fista_params*, cudaStream_t,          \
+                                 const cudaStream_t*);                                                     \
   template int op_combine<R>(Job*, R*, cudaStream_t);
 RIX_MINOR_INST(float)
 RIX_MINOR_INST(double)

@@ -321,8 +321,13 @@ int rix_job_create(rix_ctx_t ctx, const rix_job_desc* desc, int64_t max_rows, ri
   for (int p = 0; rc == RIX_OK && p < kMaxPart; ++p)
     if (cudaEventCreateWithFlags(&J.part[p].ev_minor[0], cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&J.part[p].ev_minor[1], cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&J.part[p].ev_psf, cudaEventDisableTiming) != cudaSuccess)
+        cudaEventCreateWithFlags(&J.part[p].ev_psf, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&J.part[p].ev_major, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&J.part[p].ev_prep, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&J.part[p].ev_done, cudaEventDisableTiming) != cudaSuccess)
       rc = set_error(RIX_ECUDA, "event creation");
+  if (rc == RIX_OK && cudaEventCreateWithFlags(&J.ev_batch, cudaEventDisableTiming) != cudaSuccess)
+    rc = set_error(RIX_ECUDA, "event creation");
   if (rc != RIX_OK) {
     delete js;
     return rc;
@@ -348,7 +353,15 @@ int rix_job_destroy(rix_job_t job) {
     for (int k = 0; k < 2; ++k)
       if (J.part[p].ev_minor[k]) cudaEventDestroy(J.part[p].ev_minor[k]);
     if (J.part[p].ev_psf) cudaEventDestroy(J.part[p].ev_psf);
+    if (J.part[p].ev_major) cudaEventDestroy(J.part[p].ev_major);
+    if (J.part[p].ev_prep) cudaEventDestroy(J.part[p].ev_prep);
+    if (J.part[p].ev_done) cudaEventDestroy(J.part[p].ev_done);
+    if (J.part[p].own_stream) {
+      cudaStreamSynchronize(J.part[p].own_stream);
+      cudaStreamDestroy(J.part[p].own_stream);
+    }
   }
+  if (J.ev_batch) cudaEventDestroy(J.ev_batch);
   J.ctx->reserved -= J.reserved;
   J.ctx->jobs -= 1;
   delete job;
@@ -498,6 +511,7 @@ static int rix_major_cycle_impl(rix_job_t job, int part, const void* vis_obs, co
   if (model) RIX_CUDA(cudaMemcpyAsync(pt.model.p, model, img, cudaMemcpyDeviceToDevice, st));
   if (J.fp64) RIX_TRY(op_major<double>(&J, part, (const double2*)vis_obs, pt.resid.as<double>(), st));
   else RIX_TRY(op_major<float>(&J, part, (const float2*)vis_obs, pt.resid.as<float>(), st));
+  RIX_CUDA(cudaEventRecord(pt.ev_major, st));
   if (residual_out) RIX_CUDA(cudaMemcpyAsync(residual_out, pt.resid.p, img, cudaMemcpyDeviceToDevice, st));
   pt.cycle += 1;
   return RIX_OK;
@@ -509,6 +523,8 @@ static int minor_precheck(Job& J, int part, cudaStream_t st) {
   if (pt.cycle == 0 || pt.minor_done >= pt.cycle)
     return set_error(RIX_ESTATE, "partition %d: run the major cycle before the minor cycle", part);
   const int n = pt.cycle;
+  // this partition's major cycle of this cycle, whatever stream it ran on
+  RIX_CUDA(cudaStreamWaitEvent(st, pt.ev_major, 0));
   for (int q = 0; q < J.n_part; ++q) {
     if (q == part) continue;
     if (J.part[q].minor_done < n - 1)
@@ -541,12 +557,7 @@ static int rix_minor_cycle_msclean_impl(rix_job_t job, int part, const rix_mscle
   return RIX_OK;
 }
 
-static int rix_minor_cycle_fista_impl(rix_job_t job, int part, const rix_fista_params* prm, void* delta_out,
-                          rix_stream_t stream) {
-  if (!job || !prm) return set_error(RIX_EINVAL, "NULL argument");
-  Job& J = job->j;
-  RIX_CUDA(cudaSetDevice(J.ctx->device));
-  cudaStream_t st = (cudaStream_t)stream;
+static int check_fista_params(const Job& J, const rix_fista_params* prm) {
   const int maxlev = ilog2(J.desc.n) - 3;
   if (prm->iters < 0 || prm->levels < 1 || prm->levels > maxlev)
     return set_error(RIX_EINVAL, "iters >= 0 and levels in [1, %d]", maxlev);
@@ -556,6 +567,58 @@ static int rix_minor_cycle_fista_impl(rix_job_t job, int part, const rix_fista_p
     return set_error(RIX_EINVAL, "dictionary must be RIX_DICT_DB4 or RIX_DICT_DB1_8");
   if (prm->sched_a < 0.0 || (prm->sched_a > 0.0 && !(prm->sched_b > 0.0)))
     return set_error(RIX_EINVAL, "schedule: sched_a >= 0 and sched_b > 0");
+  return RIX_OK;
+}
+
+static int rix_minor_cycle_fista_batch_impl(rix_job_t job, int n_parts, const int32_t* parts,
+                                            const rix_fista_params* prm, rix_stream_t stream) {
+  if (!job || !prm || !parts) return set_error(RIX_EINVAL, "NULL argument");
+  Job& J = job->j;
+  if (n_parts < 1 || n_parts > J.n_part) return set_error(RIX_EINVAL, "n_parts must be in [1, %d]", J.n_part);
+  for (int i = 0; i < n_parts; ++i) {
+    RIX_TRY(check_part(&J, parts[i]));
+    for (int k = 0; k < i; ++k)
+      if (parts[k] == parts[i]) return set_error(RIX_EINVAL, "partition %d listed twice", parts[i]);
+  }
+  RIX_CUDA(cudaSetDevice(J.ctx->device));
+  cudaStream_t st = (cudaStream_t)stream;
+  RIX_TRY(check_fista_params(J, prm));
+  for (int i = 0; i < n_parts; ++i)
+    if (J.part[parts[i]].cycle != J.part[parts[0]].cycle)
+      return set_error(RIX_ESTATE, "the batch's partitions are at different cycles");
+  // Each partition prepares and finishes on a stream of its own (the job's),
+  // which starts after the caller's work on `stream` and waits, as one call
+  // per partition would, for this partition's major cycle and the other
+  // partitions' previous minor cycles only; `stream` runs the loop and, at
+  // return, waits for everything.
+  RIX_CUDA(cudaEventRecord(J.ev_batch, st));
+  int pl[kMaxPart];
+  cudaStream_t ps[kMaxPart];
+  for (int i = 0; i < n_parts; ++i) {
+    Part& pt = J.part[parts[i]];
+    if (!pt.own_stream) RIX_CUDA(cudaStreamCreateWithFlags(&pt.own_stream, cudaStreamNonBlocking));
+    RIX_CUDA(cudaStreamWaitEvent(pt.own_stream, J.ev_batch, 0));
+    RIX_TRY(minor_precheck(J, parts[i], pt.own_stream));
+    pl[i] = parts[i];
+    ps[i] = pt.own_stream;
+  }
+  if (J.fp64) RIX_TRY(op_fista_batch<double>(&J, n_parts, pl, prm, st, ps));
+  else RIX_TRY(op_fista_batch<float>(&J, n_parts, pl, prm, st, ps));
+  for (int i = 0; i < n_parts; ++i) {
+    Part& pt = J.part[parts[i]];
+    pt.minor_done += 1;
+    RIX_CUDA(cudaEventRecord(pt.ev_minor[pt.minor_done & 1], st));
+  }
+  return RIX_OK;
+}
+
+static int rix_minor_cycle_fista_impl(rix_job_t job, int part, const rix_fista_params* prm, void* delta_out,
+                          rix_stream_t stream) {
+  if (!job || !prm) return set_error(RIX_EINVAL, "NULL argument");
+  Job& J = job->j;
+  RIX_CUDA(cudaSetDevice(J.ctx->device));
+  cudaStream_t st = (cudaStream_t)stream;
+  RIX_TRY(check_fista_params(J, prm));
   RIX_TRY(minor_precheck(J, part, st));
   if (J.fp64) RIX_TRY(op_fista<double>(&J, part, prm, (double*)delta_out, st));
   else RIX_TRY(op_fista<float>(&J, part, prm, (float*)delta_out, st));
@@ -630,6 +693,10 @@ int rix_major_cycle(rix_job_t job, int part, const void* vis_obs, const void* mo
 int rix_minor_cycle_msclean(rix_job_t job, int part, const rix_msclean_params* prm, void* delta_out,
                             rix_stream_t stream) {
   RIX_NOTE(job, stream, rix_minor_cycle_msclean_impl(job, part, prm, delta_out, stream));
+}
+int rix_minor_cycle_fista_batch(rix_job_t job, int n_parts, const int32_t* parts, const rix_fista_params* prm,
+                                rix_stream_t stream) {
+  RIX_NOTE(job, stream, rix_minor_cycle_fista_batch_impl(job, n_parts, parts, prm, stream));
 }
 int rix_minor_cycle_fista(rix_job_t job, int part, const rix_fista_params* prm, void* delta_out,
                           rix_stream_t stream) {

@@ -203,6 +203,10 @@ struct Part {
   // recorded after the minor cycle of each cycle parity (cycle n -> [n % 2])
   cudaEvent_t ev_minor[2] = {nullptr, nullptr};
   cudaEvent_t ev_psf = nullptr;             // recorded after the PSF is computed
+  cudaEvent_t ev_major = nullptr;           // recorded after each major cycle
+  // batched minor cycles: the partition's own stream and two join events
+  cudaStream_t own_stream = nullptr;
+  cudaEvent_t ev_prep = nullptr, ev_done = nullptr;
   DevBuf sync;                              // grid-barrier arrival counters of the cooperative kernels
 };
 
@@ -231,7 +235,7 @@ struct Job {
   Part part[kMaxPart];
   double ells[kMaxPart];
   int n_part = 1;
-  cudaEvent_t ev_tmp = nullptr;
+  cudaEvent_t ev_batch = nullptr;           // batched minor cycles: call entry, then loop end
   DevBuf status;                            // int: 0, or the RIX_E* code a device-side wait raised
   // streams the job's calls ran on, each with an event recorded after the call
   std::vector<std::pair<cudaStream_t, cudaEvent_t>> touched;
@@ -276,12 +280,19 @@ template <typename R>
 int op_msclean(Job* job, int p, const rix_msclean_params* prm, R* delta_out, cudaStream_t st);
 template <typename R>
 int op_fista(Job* job, int p, const rix_fista_params* prm, R* delta_out, cudaStream_t st);
+// The FISTA minor cycles of partitions parts[0 .. nb) with one loop launch on
+// `st`; the preparation and finish of parts[i] run on ps[i], ordered after
+// the caller's work by the caller.
+template <typename R>
+int op_fista_batch(Job* job, int nb, const int* parts, const rix_fista_params* prm, cudaStream_t st,
+                   const cudaStream_t* ps);
 template <typename R>
 int op_combine(Job* job, R* out, cudaStream_t st);
 
 // persistent FISTA iteration loop (k_fista*.cu): all `iters` iterations of
-// one minor cycle in one cooperative launch.  Images are N x N, the
-// transposes (N+1) x N complex, mx / c the u-major (2N)^2 fill tables.
+// the minor cycles of one or more partitions in one cooperative launch.
+// Images are N x N, the transposes (N+1) x N complex, mx / c the u-major
+// (2N)^2 fill tables.
 template <typename R>
 struct FistaLoop {
   R* alpha;
@@ -303,15 +314,16 @@ struct FistaLoop {
   double sched_a, sched_bn;   // sched_a > 0: lambda = sched_a * sqrt(state[2]) * sched_bn
   // RIX_DICT_DB1_8 only: member m's coefficients at alpha / y + m N^2, its
   // level buffers at xs / bs + m N^2 (N x N each), W alpha written to delta
-  // after the last iteration, and the low-pass filters of db1 .. db8
+  // after the last iteration
   R* xs;
   R* bs;
   R* delta;
-  R taps[8][16];
 };
-// one instance per precision and dictionary (k_fista_*.cu)
+// The loops f[0 .. nb) (nb <= kMaxPart) share n, levels, iters and the
+// dictionary; they run as one launch with f[0].barrier as its barrier.  One
+// instance per precision and dictionary (k_fista_*.cu).
 template <typename R, int DICT>
-int fista_loop_dict(const Ctx* ctx, const FistaLoop<R>& f, cudaStream_t st);
+int fista_loop_dict(const Ctx* ctx, const FistaLoop<R>* f, int nb, cudaStream_t st);
 int get_components(Job* job, int part, int32_t* count, int32_t capacity, int32_t* scale_out,
                    int32_t* pixel_out, double* amp_out, cudaStream_t st);
 

@@ -82,9 +82,11 @@ class Reconstruction:
 
     def cycle(self, m: Method, stream=None, concurrent: bool = True):
         """One major cycle of every partition, then the minor cycles.  With
-        `concurrent`, each partition runs on its own stream (the partitions
-        are concurrent instances on the device; the library orders the
-        exchange between them with events) and `stream` waits for them."""
+        `concurrent`, each partition's major cycle runs on its own stream (the
+        partitions are concurrent instances on the device; the library orders
+        the exchange between them with events); FISTA minor cycles then run as
+        one batched loop launch on `stream`, ms-CLEAN ones on the partitions'
+        streams, and `stream` waits for them."""
         if not concurrent or self.n_part == 1:
             for p in range(self.n_part):
                 self.major(p, stream=stream)
@@ -99,6 +101,11 @@ class Reconstruction:
         for p, s in enumerate(self._pstreams):
             s.wait_event(start)
             self.major(p, stream=s)
+        if m.kind == "fista":
+            # FISTA minor cycles of all partitions: one batched loop launch
+            # (the library orders it after each partition's major cycle)
+            self.minor_all(m, main)
+            return
         for p, s in enumerate(self._pstreams):
             self.minor(p, m, stream=s)
         for s in self._pstreams:
@@ -106,11 +113,26 @@ class Reconstruction:
             ev.record(s)
             main.wait_event(ev)
 
-    def cycles(self, m: Method, n_major: int, stream=None):
-        """`n_major` major+minor cycles with each partition on its own stream
-        and no join between cycles: a partition starts its next major cycle as
-        soon as its own minor cycle is done, while the library's events order
-        the exchange with the other partitions.  `stream` waits for all."""
+    def minor_all(self, m: Method, stream):
+        """The minor cycles of every partition on `stream`: FISTA as one batched
+        loop launch (rix_minor_cycle_fista_batch), ms-CLEAN one call each."""
+        if m.kind == "fista" and self.n_part > 1:
+            d = rix.DICT_DB4 if m.dictionary == "db4" else rix.DICT_DB1_8
+            rix.minor_cycle_fista_batch(self.job, list(range(self.n_part)), m.lam, m.lam_rel, m.iters, m.levels,
+                                        stream, d, m.schedule)
+        else:
+            for p in range(self.n_part):
+                self.minor(p, m, stream=stream)
+
+    def cycles(self, m: Method, n_major: int, stream=None, batch: bool = True):
+        """`n_major` major+minor cycles with each partition's major cycle on its
+        own stream and no join between cycles: a partition starts its next major
+        cycle as soon as its own minor cycle is done, while the library's events
+        order the exchange with the other partitions.  With `batch`, FISTA minor
+        cycles of a cycle run together (one loop launch for all partitions) on
+        the first partition's stream; the library starts each partition's
+        preparation as soon as that partition's major cycle is done.  ms-CLEAN
+        minor cycles run on their partitions' streams.  `stream` waits for all."""
         if self.n_part == 1:
             for _ in range(n_major):
                 self.cycle(m, stream)
@@ -125,8 +147,11 @@ class Reconstruction:
         for _ in range(n_major):
             for p, s in enumerate(self._pstreams):
                 self.major(p, stream=s)
-            for p, s in enumerate(self._pstreams):
-                self.minor(p, m, stream=s)
+            if batch and m.kind == "fista":
+                self.minor_all(m, self._pstreams[0])
+            else:
+                for p, s in enumerate(self._pstreams):
+                    self.minor(p, m, stream=s)
         for s in self._pstreams:
             ev = torch.cuda.Event()
             ev.record(s)

@@ -84,6 +84,7 @@ def _load() -> C.CDLL:
         "rix_major_cycle": (C.c_int, [vp, C.c_int, vp, vp, vp, vp]),
         "rix_minor_cycle_msclean": (C.c_int, [vp, C.c_int, C.POINTER(MscleanParams), vp, vp]),
         "rix_minor_cycle_fista": (C.c_int, [vp, C.c_int, C.POINTER(FistaParams), vp, vp]),
+        "rix_minor_cycle_fista_batch": (C.c_int, [vp, C.c_int, C.POINTER(C.c_int32), C.POINTER(FistaParams), vp]),
         "rix_get_components": (C.c_int, [vp, C.c_int, C.POINTER(i32), i32, vp, vp, vp, vp]),
         "rix_get_model": (C.c_int, [vp, C.c_int, vp, vp]),
         "rix_combine": (C.c_int, [vp, vp, vp]),
@@ -108,7 +109,8 @@ EXPORTED = ("rix_create", "rix_destroy", "rix_job_workspace_bytes", "rix_job_cre
             "rix_degrid", "rix_grid", "rix_psf", "rix_major_cycle", "rix_minor_cycle_msclean",
             "rix_minor_cycle_fista", "rix_get_components", "rix_get_model", "rix_combine", "rix_last_error",
             "rix_kernel_launches", "rix_timing_enable", "rix_timing_read", "rix_grid_noalloc",
-            "rix_selftest_barrier_timeout", "rix_daubechies_lowpass", "rix_get_weights")
+            "rix_selftest_barrier_timeout", "rix_daubechies_lowpass", "rix_get_weights",
+            "rix_minor_cycle_fista_batch")
 
 
 def _check(rc: int):
@@ -259,6 +261,15 @@ def minor_cycle_fista(job, part, lam=0.0, lam_rel=1e-3, iters=50, levels=4, delt
     p = FistaParams(float(lam), float(lam_rel), int(iters), int(levels), int(dictionary), 0, float(a), float(b))
     _check(_lib.rix_minor_cycle_fista(job, part, C.byref(p), _ptr(delta_out, _RT, name="delta_out"),
                                       _stream(stream)))
+
+
+def minor_cycle_fista_batch(job, parts, lam=0.0, lam_rel=1e-3, iters=50, levels=4, stream=None,
+                            dictionary=DICT_DB4, schedule=None):
+    """The FISTA minor cycles of `parts` (same cycle, same parameters) as one loop launch."""
+    a, b = schedule if schedule is not None else (0.0, 0.0)
+    p = FistaParams(float(lam), float(lam_rel), int(iters), int(levels), int(dictionary), 0, float(a), float(b))
+    arr = (C.c_int32 * max(len(parts), 1))(*[int(q) for q in parts])
+    _check(_lib.rix_minor_cycle_fista_batch(job, len(parts), arr, C.byref(p), _stream(stream)))
 
 
 def get_components(job, part, capacity=1 << 16, stream=None):

@@ -144,7 +144,8 @@ def test_call_order_is_enforced(ctx, obs_small):
 @pytest.mark.parametrize("method,prec", [("msclean", 1), ("fista", 0)])
 def test_concurrent_partitions_match_sequential(ctx, obs_small, obs_wstack, method, prec):
     """Partitions on their own streams (ordered by the library's events), with
-    or without a join after every cycle, give the same result as issuing
+    or without a join after every cycle, and with the FISTA minor cycles of a
+    cycle batched into one loop launch, give the same result as issuing
     everything on one stream."""
     from paper_2507_22128_gb300 import pipeline
     obs = obs_small if method == "msclean" else obs_wstack
@@ -153,11 +154,11 @@ def test_concurrent_partitions_match_sequential(ctx, obs_small, obs_wstack, meth
     else:
         m = pipeline.Method("fista", lam_rel=1e-3, iters=15, levels=3)
     out = []
-    for mode in ("sequential", "per-cycle join", "no join"):
+    for mode in ("sequential", "per-cycle join", "no join", "no join, batched"):
         rec = pipeline.observation_job(ctx, obs, 2, prec)
         try:
-            if mode == "no join":
-                rec.cycles(m, 3)
+            if mode.startswith("no join"):
+                rec.cycles(m, 3, batch=mode.endswith("batched"))
             else:
                 for _ in range(3):
                     rec.cycle(m, concurrent=(mode != "sequential"))
@@ -217,5 +218,45 @@ def test_fista_concatenated_dictionary_with_schedule(ctx, obs_wstack, prec):
                 assert rel_l2(out.cpu().numpy(), loop.model[p]) < tol
         assert rel_l2(rec.combine().cpu().numpy(), loop.combine()) < tol
         assert np.abs(loop.combine()).max() > 0.0
+    finally:
+        rec.close()
+
+
+@pytest.mark.parametrize("nparts,dictionary", [(2, "db4"), (4, "db4"), (2, "db1-8")])
+def test_fista_batched_minor_cycles_match_oracle(ctx, obs_wstack, nparts, dictionary):
+    """rix_minor_cycle_fista_batch: the minor cycles of all partitions of a
+    cycle in one loop launch, against the oracle's loop (FP64)."""
+    from oracle import framework
+    from paper_2507_22128_gb300 import pipeline
+    obs = obs_wstack
+    st = framework.setup(obs.uvw, obs.freq, obs.weight, obs.n, obs.cell_rad, obs.n_wplanes, nparts)
+    loop = framework.Loop(st, obs.vis, obs.weight)
+    rec = pipeline.observation_job(ctx, obs, nparts, 1)
+    m = pipeline.Method("fista", lam_rel=1e-3, iters=12, levels=3, dictionary=dictionary)
+    try:
+        for c in range(1, 4):
+            for p in range(nparts):
+                loop.major(p)
+                rec.major(p)
+            for p in range(nparts):
+                loop.minor_fista(p, c, lam_rel=1e-3, n_iter=12, levels=3,
+                                 dictionary="db4" if dictionary == "db4" else "sara")
+            rec.minor_all(m, torch.cuda.current_stream())
+            loop.exchange()
+        assert rel_l2(rec.combine().cpu().numpy(), loop.combine()) < 1e-9
+    finally:
+        rec.close()
+
+
+def test_fista_batch_rejects_bad_lists(ctx, obs_wstack):
+    from paper_2507_22128_gb300 import pipeline, rix
+    rec = pipeline.observation_job(ctx, obs_wstack, 2, rix.FP32)
+    try:
+        rec.major(0)
+        rec.major(1)
+        for parts in ([0, 0], [0, 5], []):
+            with pytest.raises(rix.RixError) as e:
+                rix.minor_cycle_fista_batch(rec.job, parts, iters=2, levels=2)
+            assert e.value.code == rix.EINVAL
     finally:
         rec.close()
