@@ -46,6 +46,8 @@ def parse():
     ap.add_argument("--cycles", type=int, default=10)
     ap.add_argument("--iters", type=int, default=50)
     ap.add_argument("--fp64", action="store_true", help="FP64 operator (comparator)")
+    ap.add_argument("--no-batch-minor", action="store_true",
+                    help="run each partition's FISTA minor cycle as its own loop launch instead of one batched launch")
     ap.add_argument("--dictionary", default="db4", choices=["db4", "db1-8"],
                     help="FISTA dictionary: Db4 alone, or the concatenation of db1..db8")
     ap.add_argument("--schedule", default=None,
@@ -201,7 +203,7 @@ def config_dict(a):
                         f"{a.iters} it{'' if a.schedule is None else ', lambda schedule ' + a.schedule}, "
                         f"{a.cycles} major cycles",
             "n": a.n, "n_wplanes": 16, "n_part": 2, "major_cycles": a.cycles, "fista_iters": a.iters,
-            "fista_dictionary": a.dictionary,
+            "fista_dictionary": a.dictionary, "fista_batched": not a.no_batch_minor,
             "l2": "flushed between steps (512 MiB write)", "precision": "fp64" if a.fp64 else "fp32"}
 
 
@@ -240,7 +242,7 @@ def main():
     def one_job(uvw, vis, w):
         rec.uvw, rec.vis, rec.weight = uvw, vis, w
         rix.set_uv_partition(rec.job, uvw, w, None, 1.0, None, stream)
-        rec.cycles(meth, a.cycles, stream)
+        rec.cycles(meth, a.cycles, stream, batch=not a.no_batch_minor)
         rix.combine(rec.job, out, stream)
 
     for _ in range(max(a.warmup, 1)):

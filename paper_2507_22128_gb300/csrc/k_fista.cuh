@@ -326,16 +326,17 @@ __device__ __forceinline__ void analysis_unit(const FistaLoop<R>& f, int l, int 
 // step constants of one loop: L = 2 max Mx and lambda are fixed during the
 // minor cycle (lambda absolute, or lambda_rel max |residual| of the first
 // cycle, or the schedule a ||residual_n||_2 b^n); the concatenation's
-// 1/sqrt 8 enters the analysis through 1/L
+// 1/sqrt 8 enters the analysis through 1/L.  Formed once per launch (FP64
+// divisions): inv_l and thr per loop, 0 when L = 0 (the step is a no-op).
 template <typename R, int DICT>
-__device__ __forceinline__ StepArgs<R> step_args(const FistaLoop<R>& f, R mom) {
+__device__ __forceinline__ void step_constants(const FistaLoop<R>& f, R* inv_l, R* thr) {
   const double lip = 2.0 * (double)f.state[0];
   const double lam = f.sched_a > 0.0   ? f.sched_a * sqrt((double)f.state[2]) * f.sched_bn
                      : f.lambda > 0.0 ? f.lambda
                                       : f.lambda_rel * (double)f.state[1];
-  const bool active = lip > 0.0;
   const double ascale = DICT == RIX_DICT_DB4 ? 1.0 : 1.0 / sqrt(8.0);
-  return StepArgs<R>{f.alpha, f.y, active ? (R)(ascale / lip) : R(0), active ? (R)(lam / lip) : R(0), active, mom};
+  *inv_l = lip > 0.0 ? (R)(ascale / lip) : R(0);
+  *thr = lip > 0.0 ? (R)(lam / lip) : R(0);
 }
 
 // The loops of the batch advance together: every phase hands out the units
@@ -357,6 +358,9 @@ __global__ void __launch_bounds__(kFftThreads, sizeof(R) == 4 && LOGL <= 12 ? 2 
   const R sscale = (R)(1.0 / sqrt(8.0));
   const int64_t NN = (int64_t)N * N;
   const int levels = f0.levels;
+  __shared__ R s_inv_l[kMaxPart], s_thr[kMaxPart];
+  if (threadIdx.x < nb) step_constants<R, DICT>(a.f[threadIdx.x], &s_inv_l[threadIdx.x], &s_thr[threadIdx.x]);
+  __syncthreads();
   double t = 1.0;
   for (int it = 0; it < f0.iters; ++it) {
     // x = W y, coarsest level first
@@ -392,7 +396,9 @@ __global__ void __launch_bounds__(kFftThreads, sizeof(R) == 4 && LOGL <= 12 ? 2 
       const int per = level_units<DICT>((N >> l) / 2, kTB);
       for (int u = blockIdx.x; u < nb * per; u += gridDim.x) {
         const FistaLoop<R>& f = a.f[u / per];
-        analysis_unit<R, DICT, N>(f, l, u % per, step_args<R, DICT>(f, mom), smem_raw, a.taps);
+        const int b = u / per;
+        const StepArgs<R> sa{f.alpha, f.y, s_inv_l[b], s_thr[b], s_inv_l[b] != R(0), mom};
+        analysis_unit<R, DICT, N>(f, l, u % per, sa, smem_raw, a.taps);
       }
       if (!grid_barrier(bar)) return;
     }

@@ -80,13 +80,13 @@ class Reconstruction:
             rix.minor_cycle_fista(self.job, p, m.lam, m.lam_rel, m.iters, m.levels, delta_out, stream, d,
                                   m.schedule)
 
-    def cycle(self, m: Method, stream=None, concurrent: bool = True):
+    def cycle(self, m: Method, stream=None, concurrent: bool = True, batch: bool = True):
         """One major cycle of every partition, then the minor cycles.  With
         `concurrent`, each partition's major cycle runs on its own stream (the
         partitions are concurrent instances on the device; the library orders
-        the exchange between them with events); FISTA minor cycles then run as
-        one batched loop launch on `stream`, ms-CLEAN ones on the partitions'
-        streams, and `stream` waits for them."""
+        the exchange between them with events); the minor cycles follow on the
+        partitions' streams, or with `batch` the FISTA ones as one batched loop
+        launch on `stream`; `stream` waits for them."""
         if not concurrent or self.n_part == 1:
             for p in range(self.n_part):
                 self.major(p, stream=stream)
@@ -101,7 +101,7 @@ class Reconstruction:
         for p, s in enumerate(self._pstreams):
             s.wait_event(start)
             self.major(p, stream=s)
-        if m.kind == "fista":
+        if batch and m.kind == "fista":
             # FISTA minor cycles of all partitions: one batched loop launch
             # (the library orders it after each partition's major cycle)
             self.minor_all(m, main)
@@ -131,8 +131,10 @@ class Reconstruction:
         order the exchange with the other partitions.  With `batch`, FISTA minor
         cycles of a cycle run together (one loop launch for all partitions) on
         the first partition's stream; the library starts each partition's
-        preparation as soon as that partition's major cycle is done.  ms-CLEAN
-        minor cycles run on their partitions' streams.  `stream` waits for all."""
+        preparation as soon as that partition's major cycle is done (the
+        default: one grid barrier per phase for all loops, two CTAs per SM).
+        Without it every minor cycle runs on its partition's stream.  `stream`
+        waits for all."""
         if self.n_part == 1:
             for _ in range(n_major):
                 self.cycle(m, stream)
