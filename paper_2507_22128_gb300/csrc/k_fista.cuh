@@ -7,9 +7,15 @@
 //   synthesis   x = W y, one phase per level, coarsest first;
 //   rows        F of the rows of pad(x), two real rows per complex transform,
 //               window columns k_u in [-N, 0] written transposed (ta);
-//   columns     per window column: F, Mx X - C, F^-1, crop  (ta -> tb);
+//   columns     per window column: F, Mx X, F^-1, crop  (ta -> tb);
 //   rows        F^-1 of the rows (Hermitian completion, two real rows per
-//               complex transform), crop: g = 2 crop F^-1 [Mx F pad x - C];
+//               complex transform), crop, minus the constant image d:
+//               g = 2 crop F^-1 [Mx F pad x] - d,  d = 2 crop F^-1 C,
+//               which equals 2 crop F^-1 [Mx F pad x - C] (the transforms
+//               and the crop are linear); d is formed once per launch, by
+//               the column and row phases run on C before the first
+//               iteration, so the iterations read N^2 values of d instead of
+//               (N + 1) 2N values of C.
 //   analysis    W^T g, one phase per level, with the thresholded,
 //               momentum-accelerated step fused into the final coefficients.
 // Phases hand their units (wavelet tiles, row pairs, column batches) out over
@@ -47,10 +53,13 @@ struct FistaShape {
   static constexpr int kRowUnits = N / (2 * B);
   static constexpr int kColUnits = (S + B - 1) / B;
   static constexpr size_t kFftSmem = 2 * (size_t)B * STRIDE * sizeof(cplx<R>);
+  // a unit's slice of Mx (B window columns of length L) or of d (2B rows of
+  // N), copied asynchronously while the unit's transform runs
+  static constexpr size_t kStage = (size_t)B * L * sizeof(R);
   static constexpr int KMAX = DICT == RIX_DICT_DB4 ? 8 : kMaxTaps;
   static constexpr size_t kWavSmem = sizeof(DwtSmem<R, KMAX>) > sizeof(IdwtSmem<R, KMAX>) ? sizeof(DwtSmem<R, KMAX>)
                                                                                          : sizeof(IdwtSmem<R, KMAX>);
-  static constexpr size_t kSmem = kFftSmem > kWavSmem ? kFftSmem : kWavSmem;
+  static constexpr size_t kSmem = kFftSmem + kStage > kWavSmem ? kFftSmem + kStage : kWavSmem;
 };
 
 template <typename C> __device__ __forceinline__ C cpx(typename std::conditional<sizeof(C) == 8, float, double>::type re,
@@ -59,6 +68,21 @@ template <typename C> __device__ __forceinline__ C cpx(typename std::conditional
   r.x = re;
   r.y = im;
   return r;
+}
+
+// 16-byte copies global -> shared that bypass the registers (cp.async, cached
+// in L2 only); a thread's copies are complete after cp_async_wait_all, and
+// everyone's after that and a CTA barrier
+__device__ __forceinline__ void cp_async16(void* sdst, const void* gsrc) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(sdst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+// `bytes` (a multiple of 16; both addresses 16-byte aligned) from src to dst
+__device__ __forceinline__ void stage_async(void* dst, const void* src, int bytes) {
+  for (int o = threadIdx.x * 16; o < bytes; o += kFftThreads * 16)
+    cp_async16(static_cast<char*>(dst) + o, static_cast<const char*>(src) + o);
 }
 
 // rows b0 .. b0 + 2B of x -> window columns of their spectra, T[j][b];
@@ -123,15 +147,19 @@ __device__ __forceinline__ void rows_fwd_unit(const R* __restrict__ x, int64_t x
   __syncthreads();
 }
 
-// window columns j0 .. j0 + B: F, Mx X - C, F^-1, crop to the image rows
+// window columns j0 .. j0 + B: F, Mx X, F^-1, crop to the image rows.  The
+// unit's Mx (rows j0 .. j0 + B of the table, contiguous) is staged in shared
+// memory while the forward transform runs.
 template <typename R, int LOGL>
 __device__ __forceinline__ void cols_conv_unit(const cplx<R>* __restrict__ Tin, const R* __restrict__ mx,
-                                               const cplx<R>* __restrict__ ctab, cplx<R>* __restrict__ Tout,
-                                               const cplx<R>* __restrict__ tw, cplx<R>* s, cplx<R>* s2, int u) {
+                                               cplx<R>* __restrict__ Tout, const cplx<R>* __restrict__ tw,
+                                               cplx<R>* s, cplx<R>* s2, R* stage, int u) {
   using C = cplx<R>;
   using F = FistaShape<R, LOGL>;
   constexpr int L = F::L, N = F::N, H = F::H, B = F::B, S = F::S, STRIDE = F::STRIDE;
   const int j0 = u * B;
+  // rows j0 .. j0 + B - 1 < L of the L x L table: in bounds even past S
+  stage_async(stage, mx + (int64_t)j0 * L, (int)F::kStage);
   constexpr int NE = B * N;
   constexpr int NLD = (NE + kFftThreads - 1) / kFftThreads;
   C v[NLD];
@@ -154,21 +182,17 @@ __device__ __forceinline__ void cols_conv_unit(const cplx<R>* __restrict__ Tin, 
   }
   __syncthreads();
   C* res = fft_ct<R, -1, LOGL, B>(s, s2, tw);
-  // Mx X - C on the window columns (the tables are read here rather than
-  // prefetched into registers: that would cost the co-residency of two loops)
+  cp_async_wait_all();
+  __syncthreads();
   constexpr int NT = (B * L) / kFftThreads;
-#pragma unroll 4
+#pragma unroll
   for (int k = 0; k < NT; ++k) {
     const int e = threadIdx.x + k * kFftThreads;
     const int q = e >> LOGL, c = e & (L - 1);
-    const int j = j0 + q;
-    if (j < S) {
-      C* p = &res[q * STRIDE + padi(c)];
-      const C z = *p;
-      const R m = mx[(int64_t)j * L + c];
-      const C cc = ctab[(int64_t)j * L + c];
-      *p = cpx<C>(z.x * m - cc.x, z.y * m - cc.y);
-    }
+    C* p = &res[q * STRIDE + padi(c)];
+    const C z = *p;
+    const R m = stage[e];
+    *p = cpx<C>(z.x * m, z.y * m);
   }
   __syncthreads();
   C* other = (res == s) ? s2 : s;
@@ -181,15 +205,44 @@ __device__ __forceinline__ void cols_conv_unit(const cplx<R>* __restrict__ Tin, 
   __syncthreads();
 }
 
-// rows b0 .. b0 + 2B of g = scale * crop F^-1 [spectrum], the spectrum given
-// by its window columns k_u in [-N, 0] (T[j][b]) and Hermitian symmetry
+// window columns j0 .. j0 + B of a full-length spectrum (C[j][c], c < L):
+// F^-1, crop to the image rows (the first half of d = 2 crop F^-1 C)
 template <typename R, int LOGL>
-__device__ __forceinline__ void rows_inv_unit(const cplx<R>* __restrict__ T, R* __restrict__ g, R scale,
+__device__ __forceinline__ void cols_inv_unit(const cplx<R>* __restrict__ Cs, cplx<R>* __restrict__ Tout,
                                               const cplx<R>* __restrict__ tw, cplx<R>* s, cplx<R>* s2, int u) {
   using C = cplx<R>;
   using F = FistaShape<R, LOGL>;
   constexpr int L = F::L, N = F::N, H = F::H, B = F::B, S = F::S, STRIDE = F::STRIDE;
+  const int j0 = u * B;
+  for (int e = threadIdx.x; e < B * L; e += kFftThreads) {
+    const int q = e >> LOGL, c = e & (L - 1);
+    const int j = j0 + q;
+    s[q * STRIDE + padi(c)] = j < S ? Cs[(int64_t)j * L + c] : cpx<C>(R(0), R(0));
+  }
+  __syncthreads();
+  const C* out = fft_ct<R, +1, LOGL, B>(s, s2, tw);
+  for (int e = threadIdx.x; e < B * N; e += kFftThreads) {
+    const int q = e / N, b = e % N;
+    const int j = j0 + q;
+    if (j < S) Tout[(int64_t)j * N + b] = out[q * STRIDE + padi((b - H) & (L - 1))];
+  }
+  __syncthreads();
+}
+
+// rows b0 .. b0 + 2B of g = scale * crop F^-1 [spectrum] (minus the same rows
+// of d when kSubD: they are staged in shared memory during the transform),
+// the spectrum given by its window columns k_u in [-N, 0] (T[j][b]) and
+// Hermitian symmetry
+template <typename R, int LOGL, bool kSubD>
+__device__ __forceinline__ void rows_inv_unit(const cplx<R>* __restrict__ T, R* __restrict__ g, R scale,
+                                              const R* __restrict__ d, const cplx<R>* __restrict__ tw, cplx<R>* s,
+                                              cplx<R>* s2, R* stage, int u) {
+  using C = cplx<R>;
+  using F = FistaShape<R, LOGL>;
+  constexpr int L = F::L, N = F::N, H = F::H, B = F::B, S = F::S, STRIDE = F::STRIDE;
   const int b0 = u * 2 * B;
+  static_assert(2 * B * N * sizeof(R) <= F::kStage, "d rows exceed the stage");
+  if constexpr (kSubD) stage_async(stage, d + (int64_t)b0 * N, 2 * B * N * (int)sizeof(R));
   // Z = Y_a + i Y_b over all columns: Z[c] from window column c and
   // Z[L - c] = conj Y_a[c] + i conj Y_b[c]; the self-conjugate columns 0 and
   // N keep their real parts (the imaginary parts only feed Im F^-1 Y)
@@ -219,6 +272,10 @@ __device__ __forceinline__ void rows_inv_unit(const cplx<R>* __restrict__ T, R* 
   }
   __syncthreads();
   const C* res = fft_ct<R, +1, LOGL, B>(s, s2, tw);
+  if constexpr (kSubD) {
+    cp_async_wait_all();
+    __syncthreads();
+  }
   constexpr int NO = B * N;
   for (int e = threadIdx.x; e < NO; e += kFftThreads) {
     const int q = e / N, a = e % N;
@@ -226,8 +283,13 @@ __device__ __forceinline__ void rows_inv_unit(const cplx<R>* __restrict__ T, R* 
     const int64_t row = b0 + 2 * q;
     const bool odd = (a + b0) & 1;
     const R va = z.x * scale, vb = z.y * scale;
-    g[row * N + a] = odd ? -va : va;
-    g[(row + 1) * N + a] = odd ? vb : -vb;
+    R ga = odd ? -va : va, gb = odd ? vb : -vb;
+    if constexpr (kSubD) {
+      ga -= stage[2 * q * N + a];
+      gb -= stage[(2 * q + 1) * N + a];
+    }
+    g[row * N + a] = ga;
+    g[(row + 1) * N + a] = gb;
   }
   __syncthreads();
 }
@@ -352,6 +414,7 @@ __global__ void __launch_bounds__(kFftThreads, sizeof(R) == 4 && LOGL <= 12 ? 2 
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* s = reinterpret_cast<C*>(smem_raw);
   C* s2 = s + F::B * F::STRIDE;
+  R* stage = reinterpret_cast<R*>(smem_raw + F::kFftSmem);
   const int nb = a.nb;
   const FistaLoop<R>& f0 = a.f[0];
   GridBarrier bar{f0.barrier, f0.status, 0u};
@@ -361,6 +424,17 @@ __global__ void __launch_bounds__(kFftThreads, sizeof(R) == 4 && LOGL <= 12 ? 2 
   __shared__ R s_inv_l[kMaxPart], s_thr[kMaxPart];
   if (threadIdx.x < nb) step_constants<R, DICT>(a.f[threadIdx.x], &s_inv_l[threadIdx.x], &s_thr[threadIdx.x]);
   __syncthreads();
+  // the constant image d = 2 crop F^-1 C of every loop
+  for (int u = blockIdx.x; u < nb * F::kColUnits; u += gridDim.x) {
+    const FistaLoop<R>& f = a.f[u / F::kColUnits];
+    cols_inv_unit<R, LOGL>(f.c, f.tb, f.tw, s, s2, u % F::kColUnits);
+  }
+  if (!grid_barrier(bar)) return;
+  for (int u = blockIdx.x; u < nb * F::kRowUnits; u += gridDim.x) {
+    const FistaLoop<R>& f = a.f[u / F::kRowUnits];
+    rows_inv_unit<R, LOGL, false>(f.tb, f.d, a.gscale, nullptr, f.tw, s, s2, stage, u % F::kRowUnits);
+  }
+  if (!grid_barrier(bar)) return;
   double t = 1.0;
   for (int it = 0; it < f0.iters; ++it) {
     // x = W y, coarsest level first
@@ -380,12 +454,12 @@ __global__ void __launch_bounds__(kFftThreads, sizeof(R) == 4 && LOGL <= 12 ? 2 
     if (!grid_barrier(bar)) return;
     for (int u = blockIdx.x; u < nb * F::kColUnits; u += gridDim.x) {
       const FistaLoop<R>& f = a.f[u / F::kColUnits];
-      cols_conv_unit<R, LOGL>(f.ta, f.mx, f.c, f.tb, f.tw, s, s2, u % F::kColUnits);
+      cols_conv_unit<R, LOGL>(f.ta, f.mx, f.tb, f.tw, s, s2, stage, u % F::kColUnits);
     }
     if (!grid_barrier(bar)) return;
     for (int u = blockIdx.x; u < nb * F::kRowUnits; u += gridDim.x) {
       const FistaLoop<R>& f = a.f[u / F::kRowUnits];
-      rows_inv_unit<R, LOGL>(f.tb, f.g, a.gscale, f.tw, s, s2, u % F::kRowUnits);
+      rows_inv_unit<R, LOGL, true>(f.tb, f.g, a.gscale, f.d, f.tw, s, s2, stage, u % F::kRowUnits);
     }
     if (!grid_barrier(bar)) return;
     // t_{k+1} = (1 + sqrt(1 + 4 t_k^2)) / 2, momentum (t_k - 1) / t_{k+1}, each

@@ -688,6 +688,7 @@ int fista_prepare(Job* job, int p, const rix_fista_params* prm, FistaLoop<R>* f,
   RIX_TRY(alloc_zero<R>(job, pt.fi_y, ncoef * sizeof(R), st));
   RIX_TRY(ensure<R>(job, pt.fi_x, (cat ? 8 : 1) * npix * sizeof(R)));
   RIX_TRY(ensure<R>(job, pt.fi_alpha_prev, (cat ? 8 : 1) * npix * sizeof(R)));
+  RIX_TRY(ensure<R>(job, pt.fi_d, npix * sizeof(R)));
   double sched_bn = 0.0;
   if (prm->sched_a > 0.0) {
     // lambda_n = a ||residual of cycle n||_2 b^n: the squared norm goes to state[2]
@@ -707,6 +708,7 @@ int fista_prepare(Job* job, int p, const rix_fista_params* prm, FistaLoop<R>* f,
   f->tb = pt.ft_b.as<cplx<R>>();
   f->mx = pt.fi_mx.as<R>();
   f->c = pt.fi_c.as<cplx<R>>();
+  f->d = pt.fi_d.as<R>();
   f->state = pt.fi_state.as<R>();
   f->tw = twiddles<R>(ctx);
   f->barrier = pt.sync.as<unsigned int>();

@@ -198,7 +198,7 @@ struct Part {
   DevBuf fi_state;                          // FISTA: [max Mx, max |residual| of cycle 1, ||residual||^2, -]
   // minor-cycle state
   DevBuf ms_R, ms_P, ms_B, ms_comp, ms_state;   // ms-CLEAN
-  DevBuf fi_alpha, fi_alpha_prev, fi_y, fi_mx, fi_c, fi_x;   // FISTA
+  DevBuf fi_alpha, fi_alpha_prev, fi_y, fi_mx, fi_c, fi_x, fi_d;   // FISTA
   int ms_ncomp_cap = 0;
   // recorded after the minor cycle of each cycle parity (cycle n -> [n % 2])
   cudaEvent_t ev_minor[2] = {nullptr, nullptr};
@@ -304,6 +304,7 @@ struct FistaLoop {
   cplx<R>* tb;
   const R* mx;
   const cplx<R>* c;
+  R* d;                    // N x N: 2 crop F^-1 c, formed by the loop
   const R* state;          // [max Mx, max |residual| of cycle 1]
   const cplx<R>* tw;       // twiddle table, length kTwMax
   unsigned int* barrier;   // arrival counter (zeroed by the call, stream-ordered)
