@@ -106,6 +106,12 @@ class ClockSampler:
             self.thread.start()
         except OSError:
             self.proc = None
+            return self
+        # nvidia-smi's start-up (NVML initialisation) runs before the timed
+        # steps, not inside them: wait for its first sample
+        t0 = time.time()
+        while not self.lines and self.proc.poll() is None and time.time() - t0 < 10.0:
+            time.sleep(0.02)
         return self
 
     def _read(self):
