@@ -204,7 +204,8 @@ struct TileArgs {
   const void* vis_in;       // cplx per sample
   void* vis_out;            // cplx per sample
   const float* weight;      // per sample or null
-  const void* geom;         // EntryGeom<R> per sorted entry (image-grid modes), null for the PSF
+  const void* geom;         // EntryGeom<R> per sorted entry, from entry geom_off on
+  int64_t geom_off;
 };
 
 // Per sorted entry, fixed for the job: the kernel offsets du = ceil(xs) - xs,
@@ -218,21 +219,34 @@ struct alignas(4 * sizeof(R)) EntryGeom {
   uint32_t ouv;
 };
 
+// On the PSF's 2N grid (x_psf = 2 x exactly), an image-grid tile of side T
+// at tx T maps to first taps in [2 tx T + 3, 2 tx T + 2 T + 2]: the staged
+// region starts kPsfOrg cells after 2 tx T and has side 2 T + 9.
+constexpr int kPsfOrg = 2;
+template <int T> constexpr int psf_staged_side() { return 2 * T + 9; }
+
 template <int T, int MODE> struct TileGeom {
   // staged side and origin offset (in grid cells) relative to the tile origin
-  static constexpr int SP = (MODE == kPsf) ? 2 * T + 9 : T + kW - 1;
-  static constexpr int ORG = (MODE == kPsf) ? 2 : 0;
+  static constexpr int SP = (MODE == kPsf) ? psf_staged_side<T>() : T + kW - 1;
+  static constexpr int ORG = (MODE == kPsf) ? kPsfOrg : 0;
   // plane stride in elements, == 8 (mod 16) so that the two plane halves of a
   // half-warp land on disjoint banks
   static constexpr int PL = ((SP * SP + 7) / 16) * 16 + 8;
 };
 
-template <typename R>
-__global__ void k_entry_geom(TileArgs a, int64_t n, int T, EntryGeom<R>* __restrict__ out) {
+// geometry of the sorted entries [e_off, e_off + n) into out[0, n): on the
+// image grid (first tap relative to the tile origin tx T) or, kPsfGrid, on the
+// PSF's 2N grid (a.scale, a.half of that grid; relative to 2 tx T + kPsfOrg)
+template <typename R, bool kPsfGrid, int T>
+__global__ void k_entry_geom(TileArgs a, int64_t e_off, int64_t n, EntryGeom<R>* __restrict__ out) {
   const uint32_t tmask = (1u << a.bt) - 1u;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+  constexpr int kLim = kPsfGrid ? psf_staged_side<T>() - kW : T - 1;   // largest first-tap offset
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t e = e_off + i;
     const uint32_t key = a.keys[e];
-    const int gu0 = (int)(key & tmask) * T, gv0 = (int)((key >> a.bt) & tmask) * T;
+    const int tx = (int)(key & tmask), ty = (int)((key >> a.bt) & tmask);
+    const int gu0 = kPsfGrid ? 2 * tx * T + kPsfOrg : tx * T;
+    const int gv0 = kPsfGrid ? 2 * ty * T + kPsfOrg : ty * T;
     const uint32_t s = a.samples[e];
     const int64_t row = s / (uint32_t)a.nchan;
     const int ch = (int)(s - row * a.nchan);
@@ -254,10 +268,11 @@ __global__ void k_entry_geom(TileArgs a, int64_t n, int T, EntryGeom<R>* __restr
       const double pc = fmin(fmax(ceil(tw), 0.0), (double)(a.nw - a.ww));
       g.dw = (R)__dadd_rn(pc, -tw);
     }
-    // the first tap lies in the entry's tile by construction of the key
-    if (ou < 0 || ov < 0 || ou >= T || ov >= T) { ou = 0; ov = 0; }
+    // the first tap lies in the entry's tile (staged region) by construction
+    // of the key
+    if (ou < 0 || ov < 0 || ou > kLim || ov > kLim) { ou = 0; ov = 0; }
     g.ouv = (uint32_t)ou | ((uint32_t)ov << 8);
-    out[e] = g;
+    out[i] = g;
   }
 }
 
@@ -314,33 +329,13 @@ __global__ void __launch_bounds__(256) k_tiles(TileArgs a) {
       const uint32_t s = valid ? a.samples[base + lane] : 0u;
       int ou = 0, ov = 0;
       R du = R(0), dv = R(0), dwo = R(0);
-      if constexpr (MODE != kPsf) {
-        // precomputed per entry at partition time
-        if (valid) {
-          const EntryGeom<R> g = static_cast<const EntryGeom<R>*>(a.geom)[base + lane];
-          ou = (int)(g.ouv & 0xffu);
-          ov = (int)(g.ouv >> 8);
-          du = g.du; dv = g.dv; dwo = g.dw;
-        }
-      } else {
-        // PSF: the 2N grid's geometry, in FP64 (once per partition and job)
-        const int64_t row = s / (uint32_t)a.nchan;
-        const int ch = (int)(s - row * a.nchan);
-        const double sc = a.inv_lambda[ch];
-        const double ul = __dmul_rn(a.uvw[row * 3 + 0], sc);
-        const double vl = __dmul_rn(a.uvw[row * 3 + 1], sc);
-        const double x = __dadd_rn(__dmul_rn(ul, a.scale), a.half);
-        const double y = __dadd_rn(__dmul_rn(vl, a.scale), a.half);
-        const double xs = __dadd_rn(x, -0.5 * kW), ys = __dadd_rn(y, -0.5 * kW);
-        const double cx = ceil(xs), cy = ceil(ys);
-        ou = (int)cx - gu0; ov = (int)cy - gv0;
-        du = (R)__dadd_rn(cx, -xs); dv = (R)__dadd_rn(cy, -ys);
-        if (WW > 1) {
-          const double wl = __dmul_rn(a.uvw[row * 3 + 2], sc);
-          const double tw = __ddiv_rn(__dadd_rn(wl, -a.w_min), a.dw);
-          double pc = fmin(fmax(ceil(tw), 0.0), (double)(a.nw - a.ww));
-          dwo = (R)__dadd_rn(pc, -tw);
-        }
+      // precomputed per entry (image grid: at partition time; PSF: before
+      // the PSF's launch)
+      if (valid) {
+        const EntryGeom<R> g = static_cast<const EntryGeom<R>*>(a.geom)[base + lane - a.geom_off];
+        ou = (int)(g.ouv & 0xffu);
+        ov = (int)(g.ouv >> 8);
+        du = g.du; dv = g.dv; dwo = g.dw;
       }
       if (!valid) { ou = 0; ov = 0; }
       // guard against any sample outside the staged region (never expected)
@@ -484,8 +479,8 @@ int launch_tiles_impl(const Ctx* ctx, const TileArgs& a, cudaStream_t st) {
 // read-modify-writes: lane (v row = lane & 7, u taps lane >> 3 and +4) touches
 // distinct cells, warps touch distinct planes, so nothing races.
 template <int T, int MODE> struct WsGeom {
-  static constexpr int SP = (MODE == kPsf) ? 2 * T + 9 : T + kW - 1;       // staged side
-  static constexpr int ORG = (MODE == kPsf) ? 2 : 0;
+  static constexpr int SP = (MODE == kPsf) ? psf_staged_side<T>() : T + kW - 1;       // staged side
+  static constexpr int ORG = (MODE == kPsf) ? kPsfOrg : 0;
   static constexpr int SPP = (MODE == kPsf) ? SP : ((SP + 7) / 16) * 16 + 8;   // row stride, 8 mod 16
   static constexpr int PL = ((SP * SPP + 7) / 16) * 16 + 8;                // plane stride, 8 mod 16
 };
@@ -526,7 +521,6 @@ __global__ void __launch_bounds__(256) k_tiles_ws(TileArgs a) {
   C* sm_model = reinterpret_cast<C*>(smem_raw);
   C* sm_grid = sm_model + (kUseModel ? kW * PL : 0);
   WsRecord<R>* rec = reinterpret_cast<WsRecord<R>*>(sm_grid + kW * PL);
-  EntryGeom<R>* psf_geo = reinterpret_cast<EntryGeom<R>*>(rec + kWsBatch);   // PSF only
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
   const int64_t SS = (int64_t)a.S * a.S;
@@ -561,34 +555,6 @@ __global__ void __launch_bounds__(256) k_tiles_ws(TileArgs a) {
 
     for (uint32_t base = e0; base < e1; base += kWsBatch) {
       const int nb = (int)min((uint32_t)kWsBatch, e1 - base);
-      if constexpr (MODE == kPsf) {
-        // the 2N grid's geometry of the batch, in FP64, one sample per lane of
-        // warp 0 (once per partition and job)
-        if (warp == 0 && lane < nb) {
-          const uint32_t s = a.samples[base + lane];
-          const int64_t row = s / (uint32_t)a.nchan;
-          const int ch = (int)(s - row * a.nchan);
-          const double sc = a.inv_lambda[ch];
-          const double ul = __dmul_rn(a.uvw[row * 3 + 0], sc);
-          const double vl = __dmul_rn(a.uvw[row * 3 + 1], sc);
-          const double wl = __dmul_rn(a.uvw[row * 3 + 2], sc);
-          const double x = __dadd_rn(__dmul_rn(ul, a.scale), a.half);
-          const double y = __dadd_rn(__dmul_rn(vl, a.scale), a.half);
-          const double xs = __dadd_rn(x, -0.5 * kW), ys = __dadd_rn(y, -0.5 * kW);
-          const double cx = ceil(xs), cy = ceil(ys);
-          int ou = (int)cx - gu0, ov = (int)cy - gv0;
-          if (ou < 0 || ov < 0 || ou > SP - kW || ov > SP - kW) { ou = 0; ov = 0; }
-          const double tw = __ddiv_rn(__dadd_rn(wl, -a.w_min), a.dw);
-          const double pc = fmin(fmax(ceil(tw), 0.0), (double)(a.nw - a.ww));
-          EntryGeom<R> g;
-          g.du = (R)__dadd_rn(cx, -xs);
-          g.dv = (R)__dadd_rn(cy, -ys);
-          g.dw = (R)__dadd_rn(pc, -tw);
-          g.ouv = (uint32_t)ou | ((uint32_t)ov << 8);
-          psf_geo[lane] = g;
-        }
-        __syncthreads();
-      }
       // ---------------- phase A: weights, degrid, records ----------------------
       {
         const int j0 = warp * per_warp;
@@ -597,10 +563,9 @@ __global__ void __launch_bounds__(256) k_tiles_ws(TileArgs a) {
         int ou = 0, ov = 0;
         R du = R(0), dv = R(0), dwo = R(0);
         if (valid) {
-          // image grid: precomputed per entry at partition time; PSF: formed
-          // for the batch by warp 0 above
-          const EntryGeom<R> g = (MODE == kPsf) ? psf_geo[j0 + lane]
-                                                : static_cast<const EntryGeom<R>*>(a.geom)[base + j0 + lane];
+          // precomputed per entry (image grid: at partition time; PSF: before
+          // the PSF's launch)
+          const EntryGeom<R> g = static_cast<const EntryGeom<R>*>(a.geom)[base + j0 + lane - a.geom_off];
           ou = (int)(g.ouv & 0xffu);
           ov = (int)(g.ouv >> 8);
           du = g.du; dv = g.dv; dwo = g.dw;
@@ -708,8 +673,7 @@ template <typename R, int T, int MODE>
 int launch_tiles_ws(const Ctx* ctx, const TileArgs& a, cudaStream_t st) {
   using TG = WsGeom<T, MODE>;
   constexpr bool kUseModel = (MODE == kResid);
-  const size_t sm = (size_t)(int(kUseModel) + 1) * kW * TG::PL * sizeof(cplx<R>) + kWsBatch * sizeof(WsRecord<R>) +
-                    (MODE == kPsf ? kWsBatch * sizeof(EntryGeom<R>) : 0);
+  const size_t sm = (size_t)(int(kUseModel) + 1) * kW * TG::PL * sizeof(cplx<R>) + kWsBatch * sizeof(WsRecord<R>);
   auto kern = k_tiles_ws<R, T, MODE>;
   RIX_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
   int per_sm = 0;
@@ -760,6 +724,7 @@ TileArgs base_args(const Job* job, const Part& pt) {
   a.S = pt.win_n;
   a.weight = job->weight.as<float>();
   a.geom = job->egeom.p;
+  a.geom_off = 0;
   return a;
 }
 
@@ -891,6 +856,7 @@ int op_psf(Job* job, int p, cudaStream_t st) {
   const size_t tb = std::max((size_t)np * pt.pwin_n * 2 * n, (size_t)4 * n * n);
   cplx<R>* pp = nullptr;
   cplx<R>* tt = nullptr;
+  EntryGeom<R>* pg = nullptr;
   RIX_CUDA(cudaMallocAsync(&pp, planes * sizeof(cplx<R>), st));
   if (cudaMallocAsync(&tt, tb * sizeof(cplx<R>), st) != cudaSuccess) {
     cudaFreeAsync(pp, st);
@@ -902,10 +868,24 @@ int op_psf(Job* job, int p, cudaStream_t st) {
     TileArgs a = base_args(job, pt);
     a.scale = job->desc.cell_rad * (double)(2 * job->ng);
     a.half = (double)job->ng;
-    a.geom = nullptr;
     a.win_lo = pt.pwin_lo;
     a.S = pt.pwin_n;
     a.out = pp;
+    // the partition's entries' geometry on the 2N grid, in FP64 (one thread
+    // per entry), for the one PSF launch
+    if (cudaMallocAsync(&pg, (size_t)pt.ent_count * sizeof(EntryGeom<R>), st) != cudaSuccess) {
+      rc = set_error(RIX_ENOMEM, "PSF entry geometry");
+      break;
+    }
+    {
+      const int blocks = (int)std::min<int64_t>(ceil_div(pt.ent_count, 256), (int64_t)job->ctx->num_sms * 16);
+      ::rix::note_launch();
+      if (job->tile == 16) k_entry_geom<R, true, 16><<<blocks, 256, 0, st>>>(a, pt.ent_begin, pt.ent_count, pg);
+      else k_entry_geom<R, true, 32><<<blocks, 256, 0, st>>>(a, pt.ent_begin, pt.ent_count, pg);
+      RIX_LAUNCH_CHECK();
+    }
+    a.geom = pg;
+    a.geom_off = pt.ent_begin;
     if ((rc = launch_tiles<R, kPsf>(job, a, st)) != RIX_OK) break;
     const XformGeom g = plane_geom(job, pt, true);
     if ((rc = inv_cols<R>(job->ctx, g, pp, kOpNone, nullptr, nullptr, tt, st)) != RIX_OK) break;
@@ -919,6 +899,7 @@ int op_psf(Job* job, int p, cudaStream_t st) {
   } while (0);
   cudaFreeAsync(pp, st);
   cudaFreeAsync(tt, st);
+  if (pg) cudaFreeAsync(pg, st);
   if (rc == RIX_OK) pt.psf_ready = true;
   return rc;
 }
@@ -961,7 +942,8 @@ int grid_entry_geometry(Job* job, cudaStream_t st) {
   const TileArgs a = base_args(job, job->part[0]);   // job-level fields only
   const int blocks = (int)std::min<int64_t>(ceil_div(n, 256), (int64_t)job->ctx->num_sms * 16);
   ::rix::note_launch();
-  k_entry_geom<R><<<blocks, 256, 0, st>>>(a, n, job->tile, job->egeom.as<EntryGeom<R>>());
+  if (job->tile == 16) k_entry_geom<R, false, 16><<<blocks, 256, 0, st>>>(a, 0, n, job->egeom.as<EntryGeom<R>>());
+  else k_entry_geom<R, false, 32><<<blocks, 256, 0, st>>>(a, 0, n, job->egeom.as<EntryGeom<R>>());
   RIX_LAUNCH_CHECK();
   return RIX_OK;
 }
