@@ -4,7 +4,8 @@
 //
 // Every iteration is a chain of grid-wide phases separated by a bounded grid
 // barrier:
-//   synthesis   x = W y, one phase per level, coarsest first;
+//   synthesis   x = W y, one phase per level, coarsest first (with Db4 the
+//               finest level runs inside the row phase, rows_fwd_syn_unit);
 //   rows        F of the rows of pad(x), two real rows per complex transform,
 //               window columns k_u in [-N, 0] written transposed (ta);
 //   columns     per window column: F, Mx X, F^-1, crop  (ta -> tb);
@@ -134,6 +135,96 @@ __device__ __forceinline__ void rows_fwd_unit(const R* __restrict__ x, int64_t x
   __syncthreads();
   const C* res = fft_ct<R, -1, LOGL, B>(s, s2, tw);
   // X_a[j] = (Z[j] + conj Z[-j]) / 2,  X_b[j] = (Z[j] - conj Z[-j]) / 2i
+  constexpr int NO = B * F::S;
+  for (int e = threadIdx.x; e < NO; e += kFftThreads) {
+    const int q = e % B, j = e / B;
+    const C z = res[q * STRIDE + padi(j)];
+    const C w = res[q * STRIDE + padi((L - j) & (L - 1))];
+    const R h = R(0.5);
+    C* dst = T + (int64_t)j * N + b0 + 2 * q;
+    dst[0] = cpx<C>(h * (z.x + w.x), h * (z.y - w.y));
+    dst[1] = cpx<C>(h * (z.y + w.y), h * (w.x - z.x));
+  }
+  __syncthreads();
+}
+
+// rows_fwd_unit with the finest synthesis level fused in (Db4): rows b0 ..
+// b0 + 2B of x = W y are synthesised from the level-1 LL block `ll` and the
+// level-0 detail subbands of `coef` (N x N buffers, Mallat layout) straight
+// into the transform's input, so x is never written.  The level is separable
+// and its two passes commute; the columns go first, into tv (shared memory):
+//   tv[cx][r][k] = sum_j lo(2j + m&1) Q(0,cx)[(m>>1) - j][k]
+//                      + hi(2j + m&1) Q(1,cx)[(m>>1) - j][k],   m = b0 + r,
+// then the rows: x[m][c] = sum_j lo(2j + c&1) tv[0][r][(c>>1) - j]
+//                               + hi(2j + c&1) tv[1][r][(c>>1) - j],
+// indices periodic modulo N/2; Q(cy,cx) is subband (cy, cx) of the level.
+template <typename R, int LOGL>
+__device__ __forceinline__ void rows_fwd_syn_unit(const R* __restrict__ ll, const R* __restrict__ coef,
+                                                  cplx<R>* __restrict__ T, const cplx<R>* __restrict__ tw, cplx<R>* s,
+                                                  cplx<R>* s2, R* tv, int u) {
+  using C = cplx<R>;
+  using F = FistaShape<R, LOGL>;
+  constexpr int L = F::L, N = F::N, H = F::H, B = F::B, STRIDE = F::STRIDE;
+  static_assert(2 * B * N * sizeof(R) <= F::kStage, "tv exceeds the stage");
+  const Db4Taps<R> tp;
+  const int b0 = u * 2 * B;
+  const int k0 = b0 >> 1;
+  // columns: thread per (cx, k), a window of four coefficient rows per
+  // subband sliding down the unit's row pairs
+  for (int col = threadIdx.x; col < N; col += kFftThreads) {
+    const int cx = col / H, k = col - cx * H;
+    const R* q0 = cx == 0 ? ll + k : coef + H + k;              // Q(0, cx), row km at km N
+    const R* q1 = coef + (int64_t)H * N + cx * H + k;           // Q(1, cx)
+    R w0[4], w1[4];                                             // rows k0 + pr - 3 .. k0 + pr
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      const int km = (k0 - 3 + i) & (H - 1);
+      w0[i] = q0[(int64_t)km * N];
+      w1[i] = q1[(int64_t)km * N];
+    }
+#pragma unroll
+    for (int pr = 0; pr < B; ++pr) {
+      const int km = (k0 + pr) & (H - 1);
+      w0[3] = q0[(int64_t)km * N];
+      w1[3] = q1[(int64_t)km * N];
+      R ev = R(0), od = R(0);
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        ev += tp.lo(2 * j) * w0[3 - j] + tp.hi(2 * j) * w1[3 - j];
+        od += tp.lo(2 * j + 1) * w0[3 - j] + tp.hi(2 * j + 1) * w1[3 - j];
+      }
+      tv[(cx * 2 * B + 2 * pr) * H + k] = ev;
+      tv[(cx * 2 * B + 2 * pr + 1) * H + k] = od;
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        w0[i] = w0[i + 1];
+        w1[i] = w1[i + 1];
+      }
+    }
+  }
+  __syncthreads();
+  // rows, packed two real rows per complex row and centred as rows_fwd_unit
+  for (int e = threadIdx.x; e < B * N; e += kFftThreads) {
+    const int q = e / N, c = e - q * N;
+    const int kc = c >> 1;
+    const bool oc = c & 1;
+    const R* t0a = tv + (2 * q) * H;                  // cx = 0, row 2q
+    const R* t1a = tv + (2 * B + 2 * q) * H;          // cx = 1, row 2q
+    R va = R(0), vb = R(0);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int kk = (kc - j) & (H - 1);
+      const R lo = oc ? tp.lo(2 * j + 1) : tp.lo(2 * j);
+      const R hi = oc ? tp.hi(2 * j + 1) : tp.hi(2 * j);
+      va += lo * t0a[kk] + hi * t1a[kk];
+      vb += lo * t0a[H + kk] + hi * t1a[H + kk];
+    }
+    const bool odd = (c + b0) & 1;
+    s[q * STRIDE + padi((c - H) & (L - 1))] = cpx<C>(odd ? -va : va, odd ? vb : -vb);
+    s[q * STRIDE + padi(H + c)] = cpx<C>(R(0), R(0));
+  }
+  __syncthreads();
+  const C* res = fft_ct<R, -1, LOGL, B>(s, s2, tw);
   constexpr int NO = B * F::S;
   for (int e = threadIdx.x; e < NO; e += kFftThreads) {
     const int q = e % B, j = e / B;
@@ -437,8 +528,9 @@ __global__ void __launch_bounds__(kFftThreads, sizeof(R) == 4 && LOGL <= 12 ? 2 
   if (!grid_barrier(bar)) return;
   double t = 1.0;
   for (int it = 0; it < f0.iters; ++it) {
-    // x = W y, coarsest level first
-    for (int l = levels - 1; l >= 0; --l) {
+    // x = W y, coarsest level first; with Db4 the finest level is fused into
+    // the row transforms
+    for (int l = levels - 1; l >= (kCat ? 0 : 1); --l) {
       const int per = level_units<DICT>(N >> l, kTS);
       for (int u = blockIdx.x; u < nb * per; u += gridDim.x) {
         const FistaLoop<R>& f = a.f[u / per];
@@ -449,7 +541,7 @@ __global__ void __launch_bounds__(kFftThreads, sizeof(R) == 4 && LOGL <= 12 ? 2 
     for (int u = blockIdx.x; u < nb * F::kRowUnits; u += gridDim.x) {
       const FistaLoop<R>& f = a.f[u / F::kRowUnits];
       if constexpr (kCat) rows_fwd_unit<R, LOGL, 8>(f.xs, NN, sscale, f.ta, f.tw, s, s2, u % F::kRowUnits);
-      else rows_fwd_unit<R, LOGL>(f.x, 0, R(1), f.ta, f.tw, s, s2, u % F::kRowUnits);
+      else rows_fwd_syn_unit<R, LOGL>(levels > 1 ? f.tmp : f.y, f.y, f.ta, f.tw, s, s2, stage, u % F::kRowUnits);
     }
     if (!grid_barrier(bar)) return;
     for (int u = blockIdx.x; u < nb * F::kColUnits; u += gridDim.x) {
