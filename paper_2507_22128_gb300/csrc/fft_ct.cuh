@@ -29,10 +29,69 @@ __host__ __device__ constexpr int ct_logp(int logl, int ps) {
   return logp;
 }
 
+// Pruning for the centred, zero-padded transforms of the minor cycle: the
+// data of an N-long row sits at positions [0, L/4) and [3L/4, L) of the
+// L = 2N transform (centred) and the rest is zero (kPruneIn), or only those
+// positions of the result are read (kPruneOut).  In the first pass (p = 1)
+// item i < L/RAD reads i + r L/RAD, which is in the zero half exactly when
+// RAD/4 <= r < 3 RAD/4; in the last pass (p = L/RAD) item i writes i + r p,
+// needed exactly when r < RAD/4 or r >= 3 RAD/4.  So the loads and stores
+// skipped are known at compile time for RAD >= 4.
+template <int RAD>
+__host__ __device__ constexpr bool ct_outer(int r) { return r < RAD / 4 || r >= 3 * RAD / 4; }
+
+// dft4 with a1 = a2 = 0 (their values are not read)
+template <int DIR, typename C>
+__device__ __forceinline__ void dft4_z12(C& a0, C& a1, C& a2, C& a3) {
+  const C x = a0, r = rot90<DIR>(a3);
+  a0 = x + a3; a2 = x - a3; a1 = x - r; a3 = x + r;
+}
+
+// dft<RAD, DIR> of v with v[r] = 0 for RAD/4 <= r < 3 RAD/4 (not read): the
+// first stage of each decomposition meets those zeros as a1 = a2 of its
+// length-4 transforms
+template <int RAD, int DIR, typename C>
+__device__ __forceinline__ void dft_zin(C* v) {
+  if constexpr (RAD == 4) {
+    dft4_z12<DIR>(v[0], v[1], v[2], v[3]);
+  } else if constexpr (RAD == 8) {
+    dft4_z12<DIR>(v[0], v[2], v[4], v[6]);
+    dft4_z12<DIR>(v[1], v[3], v[5], v[7]);
+    C o[8];
+#pragma unroll
+    for (int k1 = 0; k1 < 4; ++k1) {
+      const C a = v[2 * k1];
+      const C b = k1 ? cmul(v[2 * k1 + 1], wconst<8, DIR, C>(k1)) : v[2 * k1 + 1];
+      o[k1] = a + b;
+      o[k1 + 4] = a - b;
+    }
+#pragma unroll
+    for (int i = 0; i < 8; ++i) v[i] = o[i];
+  } else {
+    static_assert(RAD == 16, "radix");
+#pragma unroll
+    for (int n2 = 0; n2 < 4; ++n2) dft4_z12<DIR>(v[n2], v[4 + n2], v[8 + n2], v[12 + n2]);
+    C y[16];
+#pragma unroll
+    for (int k1 = 0; k1 < 4; ++k1)
+#pragma unroll
+      for (int n2 = 0; n2 < 4; ++n2) {
+        const C t = v[4 * k1 + n2];
+        y[4 * k1 + n2] = (n2 * k1) ? cmul(t, wconst<16, DIR, C>(n2 * k1)) : t;
+      }
+#pragma unroll
+    for (int k1 = 0; k1 < 4; ++k1) {
+      dft4<DIR>(y[4 * k1], y[4 * k1 + 1], y[4 * k1 + 2], y[4 * k1 + 3]);
+#pragma unroll
+      for (int k2 = 0; k2 < 4; ++k2) v[k1 + 4 * k2] = y[4 * k1 + k2];
+    }
+  }
+}
+
 // One Stockham pass of radix 2^LR over B rows of length 2^LOGL (row stride
 // padded_len(L)): item i of a row, k = i mod p, reads i + r L/RAD, applies
 // exp(DIR 2 pi i r k / (p RAD)), writes ((i - k) RAD + k) + r p.
-template <typename R, int DIR, int LR, int LOGL, int LOGP, int B>
+template <typename R, int DIR, int LR, int LOGL, int LOGP, int B, bool kPruneIn = false, bool kPruneOut = false>
 __device__ __forceinline__ void pass_ct(const cplx<R>* __restrict__ src, cplx<R>* __restrict__ dst,
                                         const cplx<R>* __restrict__ tw) {
   using C = cplx<R>;
@@ -50,6 +109,8 @@ __device__ __forceinline__ void pass_ct(const cplx<R>* __restrict__ src, cplx<R>
   // them stay inside one 16-entry group (P RAD <= 16 and P RAD | 16)
   constexpr bool kLinOut16 = (P % 16) == 0;
   constexpr bool kLinOutSmall = (P * RAD <= 16) && (16 % (P * RAD) == 0);
+  constexpr bool kZin = kPruneIn && LOGP == 0 && RAD >= 4;
+  constexpr bool kZout = kPruneOut && LOGP + LR == LOGL && RAD >= 4;
 #pragma unroll
   for (int it = 0; it < NIT; ++it) {
     const int g = threadIdx.x + it * kFftThreads;
@@ -62,47 +123,58 @@ __device__ __forceinline__ void pass_ct(const cplx<R>* __restrict__ src, cplx<R>
     if constexpr (kLinIn) {
       const C* b = rs + padi(i);
 #pragma unroll
-      for (int r = 0; r < RAD; ++r) v[r] = b[r * (IPR + IPR / 16)];
+      for (int r = 0; r < RAD; ++r)
+        if (!kZin || ct_outer<RAD>(r)) v[r] = b[r * (IPR + IPR / 16)];
     } else {
 #pragma unroll
-      for (int r = 0; r < RAD; ++r) v[r] = rs[padi(i + r * IPR)];
+      for (int r = 0; r < RAD; ++r)
+        if (!kZin || ct_outer<RAD>(r)) v[r] = rs[padi(i + r * IPR)];
     }
     if constexpr (LOGP > 0) {
       if (k) apply_twiddles<R, DIR, RAD>(v, tw, k, TWSHIFT);
     }
-    dft<RAD, DIR>(v);
+    if constexpr (kZin) dft_zin<RAD, DIR>(v);
+    else dft<RAD, DIR>(v);
     C* rd = dst + row * STRIDE;
     const int o = ((i - k) << LR) + k;
     if constexpr (kLinOut16) {
       C* b = rd + padi(o);
 #pragma unroll
-      for (int r = 0; r < RAD; ++r) b[r * (P + P / 16)] = v[r];
+      for (int r = 0; r < RAD; ++r)
+        if (!kZout || ct_outer<RAD>(r)) b[r * (P + P / 16)] = v[r];
     } else if constexpr (kLinOutSmall) {
       C* b = rd + padi(o);
 #pragma unroll
-      for (int r = 0; r < RAD; ++r) b[r * P] = v[r];
+      for (int r = 0; r < RAD; ++r)
+        if (!kZout || ct_outer<RAD>(r)) b[r * P] = v[r];
     } else {
 #pragma unroll
-      for (int r = 0; r < RAD; ++r) rd[padi(o + r * P)] = v[r];
+      for (int r = 0; r < RAD; ++r)
+        if (!kZout || ct_outer<RAD>(r)) rd[padi(o + r * P)] = v[r];
     }
   }
   __syncthreads();
 }
 
-template <typename R, int DIR, int LOGL, int B, int PS>
+template <typename R, int DIR, int LOGL, int B, int PS, bool kPruneIn, bool kPruneOut>
 __device__ __forceinline__ void passes_ct(cplx<R>* a, cplx<R>* b, const cplx<R>* __restrict__ tw) {
   if constexpr (PS < ct_npass(LOGL)) {
-    pass_ct<R, DIR, ct_lr(LOGL, PS), LOGL, ct_logp(LOGL, PS), B>(a, b, tw);
-    passes_ct<R, DIR, LOGL, B, PS + 1>(b, a, tw);
+    pass_ct<R, DIR, ct_lr(LOGL, PS), LOGL, ct_logp(LOGL, PS), B, kPruneIn, kPruneOut>(a, b, tw);
+    passes_ct<R, DIR, LOGL, B, PS + 1, kPruneIn, kPruneOut>(b, a, tw);
   }
 }
 
 // FFT (unnormalised, DIR = -1 forward) of B rows held in `a`; the result ends
 // in the buffer returned (a after an even number of passes, else b).  The
-// caller has written `a` and synchronised.
-template <typename R, int DIR, int LOGL, int B>
+// caller has written `a` and synchronised.  kPruneIn: only the centred
+// positions [0, L/4) and [3L/4, L) of `a` hold data (the rest is zero and
+// need not be written); kPruneOut: only those positions of the result are
+// valid.
+template <typename R, int DIR, int LOGL, int B, bool kPruneIn = false, bool kPruneOut = false>
 __device__ __forceinline__ cplx<R>* fft_ct(cplx<R>* a, cplx<R>* b, const cplx<R>* __restrict__ tw) {
-  passes_ct<R, DIR, LOGL, B, 0>(a, b, tw);
+  static_assert(!(kPruneIn || kPruneOut) || (ct_lr(LOGL, 0) >= 2 && ct_lr(LOGL, ct_npass(LOGL) - 1) >= 2),
+                "pruning needs radix >= 4 at both ends");
+  passes_ct<R, DIR, LOGL, B, 0, kPruneIn, kPruneOut>(a, b, tw);
   return (ct_npass(LOGL) & 1) ? b : a;
 }
 

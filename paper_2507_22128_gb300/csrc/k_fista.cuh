@@ -129,11 +129,11 @@ __device__ __forceinline__ void rows_fwd_unit(const R* __restrict__ x, int64_t x
       const int q = e / N, a = e % N;
       const bool odd = (a + b0) & 1;               // b0 + 2q has the parity of b0
       s[q * STRIDE + padi((a - H) & (L - 1))] = cpx<C>(odd ? -va[k] : va[k], odd ? vb[k] : -vb[k]);
-      s[q * STRIDE + padi(H + a)] = cpx<C>(R(0), R(0));   // zero padding: columns N/2 .. 3N/2 - 1
     }
   }
   __syncthreads();
-  const C* res = fft_ct<R, -1, LOGL, B>(s, s2, tw);
+  // the zero padding (columns N/2 .. 3N/2 - 1) is never read: pruned input
+  const C* res = fft_ct<R, -1, LOGL, B, true, false>(s, s2, tw);
   // X_a[j] = (Z[j] + conj Z[-j]) / 2,  X_b[j] = (Z[j] - conj Z[-j]) / 2i
   constexpr int NO = B * F::S;
   for (int e = threadIdx.x; e < NO; e += kFftThreads) {
@@ -221,10 +221,9 @@ __device__ __forceinline__ void rows_fwd_syn_unit(const R* __restrict__ ll, cons
     }
     const bool odd = (c + b0) & 1;
     s[q * STRIDE + padi((c - H) & (L - 1))] = cpx<C>(odd ? -va : va, odd ? vb : -vb);
-    s[q * STRIDE + padi(H + c)] = cpx<C>(R(0), R(0));
   }
   __syncthreads();
-  const C* res = fft_ct<R, -1, LOGL, B>(s, s2, tw);
+  const C* res = fft_ct<R, -1, LOGL, B, true, false>(s, s2, tw);
   constexpr int NO = B * F::S;
   for (int e = threadIdx.x; e < NO; e += kFftThreads) {
     const int q = e % B, j = e / B;
@@ -268,11 +267,10 @@ __device__ __forceinline__ void cols_conv_unit(const cplx<R>* __restrict__ Tin, 
     if (NE % kFftThreads == 0 || e < NE) {
       const int q = e / N, b = e % N;
       s[q * STRIDE + padi((b - H) & (L - 1))] = v[k];
-      s[q * STRIDE + padi(H + b)] = cpx<C>(R(0), R(0));
     }
   }
   __syncthreads();
-  C* res = fft_ct<R, -1, LOGL, B>(s, s2, tw);
+  C* res = fft_ct<R, -1, LOGL, B, true, false>(s, s2, tw);
   cp_async_wait_all();
   __syncthreads();
   constexpr int NT = (B * L) / kFftThreads;
@@ -287,7 +285,7 @@ __device__ __forceinline__ void cols_conv_unit(const cplx<R>* __restrict__ Tin, 
   }
   __syncthreads();
   C* other = (res == s) ? s2 : s;
-  const C* out = fft_ct<R, +1, LOGL, B>(res, other, tw);
+  const C* out = fft_ct<R, +1, LOGL, B, false, true>(res, other, tw);
   for (int e = threadIdx.x; e < NE; e += kFftThreads) {
     const int q = e / N, b = e % N;
     const int j = j0 + q;
@@ -311,7 +309,7 @@ __device__ __forceinline__ void cols_inv_unit(const cplx<R>* __restrict__ Cs, cp
     s[q * STRIDE + padi(c)] = j < S ? Cs[(int64_t)j * L + c] : cpx<C>(R(0), R(0));
   }
   __syncthreads();
-  const C* out = fft_ct<R, +1, LOGL, B>(s, s2, tw);
+  const C* out = fft_ct<R, +1, LOGL, B, false, true>(s, s2, tw);
   for (int e = threadIdx.x; e < B * N; e += kFftThreads) {
     const int q = e / N, b = e % N;
     const int j = j0 + q;
@@ -362,7 +360,7 @@ __device__ __forceinline__ void rows_inv_unit(const cplx<R>* __restrict__ T, R* 
     }
   }
   __syncthreads();
-  const C* res = fft_ct<R, +1, LOGL, B>(s, s2, tw);
+  const C* res = fft_ct<R, +1, LOGL, B, false, true>(s, s2, tw);
   if constexpr (kSubD) {
     cp_async_wait_all();
     __syncthreads();
