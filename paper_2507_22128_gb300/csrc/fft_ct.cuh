@@ -88,12 +88,26 @@ __device__ __forceinline__ void dft_zin(C* v) {
   }
 }
 
+// Input and output hooks of a transform.  The first pass takes its values
+// from ld(row, pos) and the last pass hands its results to st(row, pos, v)
+// (pos in natural order), instead of reading / writing the ping-pong
+// buffers, so loads, scatters and epilogues fuse into the passes; pre() runs
+// in every thread before the barrier that ends the second-to-last pass (to
+// complete asynchronous copies that the last pass reads).  SmemIO / NoHook
+// keep the buffers.
+struct SmemIO {};
+struct NoHook {
+  __device__ __forceinline__ void operator()() const {}
+};
+
 // One Stockham pass of radix 2^LR over B rows of length 2^LOGL (row stride
 // padded_len(L)): item i of a row, k = i mod p, reads i + r L/RAD, applies
 // exp(DIR 2 pi i r k / (p RAD)), writes ((i - k) RAD + k) + r p.
-template <typename R, int DIR, int LR, int LOGL, int LOGP, int B, bool kPruneIn = false, bool kPruneOut = false>
+template <typename R, int DIR, int LR, int LOGL, int LOGP, int B, bool kPruneIn = false, bool kPruneOut = false,
+          class LD = SmemIO, class ST = SmemIO, class PRE = NoHook, bool kPre = false>
 __device__ __forceinline__ void pass_ct(const cplx<R>* __restrict__ src, cplx<R>* __restrict__ dst,
-                                        const cplx<R>* __restrict__ tw) {
+                                        const cplx<R>* __restrict__ tw, const LD& ld = LD{}, const ST& st = ST{},
+                                        const PRE& pre = PRE{}) {
   using C = cplx<R>;
   constexpr int RAD = 1 << LR;
   constexpr int L = 1 << LOGL;
@@ -111,6 +125,8 @@ __device__ __forceinline__ void pass_ct(const cplx<R>* __restrict__ src, cplx<R>
   constexpr bool kLinOutSmall = (P * RAD <= 16) && (16 % (P * RAD) == 0);
   constexpr bool kZin = kPruneIn && LOGP == 0 && RAD >= 4;
   constexpr bool kZout = kPruneOut && LOGP + LR == LOGL && RAD >= 4;
+  constexpr bool kLd = LOGP == 0 && !std::is_same<LD, SmemIO>::value;
+  constexpr bool kSt = LOGP + LR == LOGL && !std::is_same<ST, SmemIO>::value;
 #pragma unroll
   for (int it = 0; it < NIT; ++it) {
     const int g = threadIdx.x + it * kFftThreads;
@@ -120,7 +136,11 @@ __device__ __forceinline__ void pass_ct(const cplx<R>* __restrict__ src, cplx<R>
     const int k = i % P;
     const C* rs = src + row * STRIDE;
     C v[RAD];
-    if constexpr (kLinIn) {
+    if constexpr (kLd) {
+#pragma unroll
+      for (int r = 0; r < RAD; ++r)
+        if (!kZin || ct_outer<RAD>(r)) v[r] = ld(row, i + r * IPR);
+    } else if constexpr (kLinIn) {
       const C* b = rs + padi(i);
 #pragma unroll
       for (int r = 0; r < RAD; ++r)
@@ -137,7 +157,11 @@ __device__ __forceinline__ void pass_ct(const cplx<R>* __restrict__ src, cplx<R>
     else dft<RAD, DIR>(v);
     C* rd = dst + row * STRIDE;
     const int o = ((i - k) << LR) + k;
-    if constexpr (kLinOut16) {
+    if constexpr (kSt) {
+#pragma unroll
+      for (int r = 0; r < RAD; ++r)
+        if (!kZout || ct_outer<RAD>(r)) st(row, o + r * P, v[r]);
+    } else if constexpr (kLinOut16) {
       C* b = rd + padi(o);
 #pragma unroll
       for (int r = 0; r < RAD; ++r)
@@ -153,14 +177,17 @@ __device__ __forceinline__ void pass_ct(const cplx<R>* __restrict__ src, cplx<R>
         if (!kZout || ct_outer<RAD>(r)) rd[padi(o + r * P)] = v[r];
     }
   }
+  if constexpr (kPre) pre();
   __syncthreads();
 }
 
-template <typename R, int DIR, int LOGL, int B, int PS, bool kPruneIn, bool kPruneOut>
-__device__ __forceinline__ void passes_ct(cplx<R>* a, cplx<R>* b, const cplx<R>* __restrict__ tw) {
+template <typename R, int DIR, int LOGL, int B, int PS, bool kPruneIn, bool kPruneOut, class LD, class ST, class PRE>
+__device__ __forceinline__ void passes_ct(cplx<R>* a, cplx<R>* b, const cplx<R>* __restrict__ tw, const LD& ld,
+                                          const ST& st, const PRE& pre) {
   if constexpr (PS < ct_npass(LOGL)) {
-    pass_ct<R, DIR, ct_lr(LOGL, PS), LOGL, ct_logp(LOGL, PS), B, kPruneIn, kPruneOut>(a, b, tw);
-    passes_ct<R, DIR, LOGL, B, PS + 1, kPruneIn, kPruneOut>(b, a, tw);
+    pass_ct<R, DIR, ct_lr(LOGL, PS), LOGL, ct_logp(LOGL, PS), B, kPruneIn, kPruneOut, LD, ST, PRE,
+            PS == ct_npass(LOGL) - 2>(a, b, tw, ld, st, pre);
+    passes_ct<R, DIR, LOGL, B, PS + 1, kPruneIn, kPruneOut>(b, a, tw, ld, st, pre);
   }
 }
 
@@ -170,11 +197,17 @@ __device__ __forceinline__ void passes_ct(cplx<R>* a, cplx<R>* b, const cplx<R>*
 // positions [0, L/4) and [3L/4, L) of `a` hold data (the rest is zero and
 // need not be written); kPruneOut: only those positions of the result are
 // valid.
-template <typename R, int DIR, int LOGL, int B, bool kPruneIn = false, bool kPruneOut = false>
-__device__ __forceinline__ cplx<R>* fft_ct(cplx<R>* a, cplx<R>* b, const cplx<R>* __restrict__ tw) {
+// With hooks (ld, st, pre as described above pass_ct), `a` need not be
+// written before the call when ld is given, and the result buffer is not
+// written when st is given.
+template <typename R, int DIR, int LOGL, int B, bool kPruneIn = false, bool kPruneOut = false, class LD = SmemIO,
+          class ST = SmemIO, class PRE = NoHook>
+__device__ __forceinline__ cplx<R>* fft_ct(cplx<R>* a, cplx<R>* b, const cplx<R>* __restrict__ tw, const LD& ld = LD{},
+                                           const ST& st = ST{}, const PRE& pre = PRE{}) {
   static_assert(!(kPruneIn || kPruneOut) || (ct_lr(LOGL, 0) >= 2 && ct_lr(LOGL, ct_npass(LOGL) - 1) >= 2),
                 "pruning needs radix >= 4 at both ends");
-  passes_ct<R, DIR, LOGL, B, 0, kPruneIn, kPruneOut>(a, b, tw);
+  static_assert(ct_npass(LOGL) >= 2, "hooks assume at least two passes");
+  passes_ct<R, DIR, LOGL, B, 0, kPruneIn, kPruneOut>(a, b, tw, ld, st, pre);
   return (ct_npass(LOGL) & 1) ? b : a;
 }
 

@@ -8,7 +8,8 @@
 //               finest level runs inside the row phase, rows_fwd_syn_unit);
 //   rows        F of the rows of pad(x), two real rows per complex transform,
 //               window columns k_u in [-N, 0] written transposed (ta);
-//   columns     per window column: F, Mx X, F^-1, crop  (ta -> tb);
+//   columns     per window column: F, Mx X, F^-1, crop  (ta -> tb; tb in
+//               blocks of the 2B image rows of one row unit, tb_index);
 //   rows        F^-1 of the rows (Hermitian completion, two real rows per
 //               complex transform), crop, minus the constant image d:
 //               g = 2 crop F^-1 [Mx F pad x] - d,  d = 2 crop F^-1 C,
@@ -69,6 +70,38 @@ template <typename C> __device__ __forceinline__ C cpx(typename std::conditional
   r.x = re;
   r.y = im;
   return r;
+}
+
+// Layout of tb (the column phase's output, the inverse row phase's input):
+// blocks of the 2B image rows that one row unit transforms, each block
+// [window column j][row b mod 2B], so that a row unit reads one contiguous
+// block; the column phase writes 2B-element runs instead.
+template <typename F>
+__device__ __forceinline__ int64_t tb_index(int j, int b) {
+  constexpr int RB = 2 * F::B;
+  return (int64_t)(b / RB) * (F::S * RB) + j * RB + (b % RB);
+}
+
+// a pair of complex values at 16-byte-aligned memory (one 16-byte access in
+// FP32)
+template <typename C>
+__device__ __forceinline__ void ld_pair(const C* p, C& a, C& b) {
+  if constexpr (sizeof(C) == 8) {
+    const float4 w = *reinterpret_cast<const float4*>(p);
+    a.x = w.x; a.y = w.y; b.x = w.z; b.y = w.w;
+  } else {
+    a = p[0];
+    b = p[1];
+  }
+}
+template <typename C>
+__device__ __forceinline__ void st_pair(C* p, const C& a, const C& b) {
+  if constexpr (sizeof(C) == 8) {
+    *reinterpret_cast<float4*>(p) = make_float4(a.x, a.y, b.x, b.y);
+  } else {
+    p[0] = a;
+    p[1] = b;
+  }
 }
 
 // 16-byte copies global -> shared that bypass the registers (cp.async, cached
@@ -141,9 +174,8 @@ __device__ __forceinline__ void rows_fwd_unit(const R* __restrict__ x, int64_t x
     const C z = res[q * STRIDE + padi(j)];
     const C w = res[q * STRIDE + padi((L - j) & (L - 1))];
     const R h = R(0.5);
-    C* dst = T + (int64_t)j * N + b0 + 2 * q;
-    dst[0] = cpx<C>(h * (z.x + w.x), h * (z.y - w.y));
-    dst[1] = cpx<C>(h * (z.y + w.y), h * (w.x - z.x));
+    st_pair(T + (int64_t)j * N + b0 + 2 * q, cpx<C>(h * (z.x + w.x), h * (z.y - w.y)),
+            cpx<C>(h * (z.y + w.y), h * (w.x - z.x)));
   }
   __syncthreads();
 }
@@ -203,9 +235,11 @@ __device__ __forceinline__ void rows_fwd_syn_unit(const R* __restrict__ ll, cons
     }
   }
   __syncthreads();
-  // rows, packed two real rows per complex row and centred as rows_fwd_unit
-  for (int e = threadIdx.x; e < B * N; e += kFftThreads) {
-    const int q = e / N, c = e - q * N;
+  // rows, computed by the transform's first pass as it loads them: complex
+  // row q = x[b0 + 2q] + i x[b0 + 2q + 1], centred as in rows_fwd_unit
+  // (position p holds column (p + N/2) mod L; the pruned half is zero)
+  auto ld_x = [&](int q, int p) -> C {
+    const int c = (p + H) & (L - 1);
     const int kc = c >> 1;
     const bool oc = c & 1;
     const R* t0a = tv + (2 * q) * H;                  // cx = 0, row 2q
@@ -220,26 +254,26 @@ __device__ __forceinline__ void rows_fwd_syn_unit(const R* __restrict__ ll, cons
       vb += lo * t0a[H + kk] + hi * t1a[H + kk];
     }
     const bool odd = (c + b0) & 1;
-    s[q * STRIDE + padi((c - H) & (L - 1))] = cpx<C>(odd ? -va : va, odd ? vb : -vb);
-  }
-  __syncthreads();
-  const C* res = fft_ct<R, -1, LOGL, B, true, false>(s, s2, tw);
+    return cpx<C>(odd ? -va : va, odd ? vb : -vb);
+  };
+  const C* res = fft_ct<R, -1, LOGL, B, true, false>(s, s2, tw, ld_x);
   constexpr int NO = B * F::S;
   for (int e = threadIdx.x; e < NO; e += kFftThreads) {
     const int q = e % B, j = e / B;
     const C z = res[q * STRIDE + padi(j)];
     const C w = res[q * STRIDE + padi((L - j) & (L - 1))];
     const R h = R(0.5);
-    C* dst = T + (int64_t)j * N + b0 + 2 * q;
-    dst[0] = cpx<C>(h * (z.x + w.x), h * (z.y - w.y));
-    dst[1] = cpx<C>(h * (z.y + w.y), h * (w.x - z.x));
+    st_pair(T + (int64_t)j * N + b0 + 2 * q, cpx<C>(h * (z.x + w.x), h * (z.y - w.y)),
+            cpx<C>(h * (z.y + w.y), h * (w.x - z.x)));
   }
   __syncthreads();
 }
 
 // window columns j0 .. j0 + B: F, Mx X, F^-1, crop to the image rows.  The
-// unit's Mx (rows j0 .. j0 + B of the table, contiguous) is staged in shared
-// memory while the forward transform runs.
+// forward transform's first pass reads the columns from Tin, the inverse's
+// first pass multiplies by Mx as it loads and its last pass writes the
+// cropped rows to Tout (tb_index layout); the unit's Mx (rows j0 .. j0 + B of the table,
+// contiguous) is copied to shared memory during the forward transform.
 template <typename R, int LOGL>
 __device__ __forceinline__ void cols_conv_unit(const cplx<R>* __restrict__ Tin, const R* __restrict__ mx,
                                                cplx<R>* __restrict__ Tout, const cplx<R>* __restrict__ tw,
@@ -250,48 +284,25 @@ __device__ __forceinline__ void cols_conv_unit(const cplx<R>* __restrict__ Tin, 
   const int j0 = u * B;
   // rows j0 .. j0 + B - 1 < L of the L x L table: in bounds even past S
   stage_async(stage, mx + (int64_t)j0 * L, (int)F::kStage);
-  constexpr int NE = B * N;
-  constexpr int NLD = (NE + kFftThreads - 1) / kFftThreads;
-  C v[NLD];
-#pragma unroll
-  for (int k = 0; k < NLD; ++k) {
-    const int e = threadIdx.x + k * kFftThreads;
-    const int q = e / N, b = e % N;
+  // centred: position p holds image row (p + N/2) mod L; the pruned half is zero
+  auto ld_in = [&](int q, int p) -> C {
     const int j = j0 + q;
-    v[k] = cpx<C>(R(0), R(0));
-    if ((NE % kFftThreads == 0 || e < NE) && j < S) v[k] = Tin[(int64_t)j * N + b];
-  }
-#pragma unroll
-  for (int k = 0; k < NLD; ++k) {
-    const int e = threadIdx.x + k * kFftThreads;
-    if (NE % kFftThreads == 0 || e < NE) {
-      const int q = e / N, b = e % N;
-      s[q * STRIDE + padi((b - H) & (L - 1))] = v[k];
-    }
-  }
-  __syncthreads();
-  C* res = fft_ct<R, -1, LOGL, B, true, false>(s, s2, tw);
-  cp_async_wait_all();
-  __syncthreads();
-  constexpr int NT = (B * L) / kFftThreads;
-#pragma unroll
-  for (int k = 0; k < NT; ++k) {
-    const int e = threadIdx.x + k * kFftThreads;
-    const int q = e >> LOGL, c = e & (L - 1);
-    C* p = &res[q * STRIDE + padi(c)];
-    const C z = *p;
-    const R m = stage[e];
-    *p = cpx<C>(z.x * m, z.y * m);
-  }
-  __syncthreads();
+    return j < S ? Tin[(int64_t)j * N + ((p + H) & (L - 1))] : cpx<C>(R(0), R(0));
+  };
+  auto wait = [] { cp_async_wait_all(); };
+  C* res = fft_ct<R, -1, LOGL, B, true, false>(s, s2, tw, ld_in, SmemIO{}, wait);
+  const C* rin = res;
+  auto ld_mul = [&](int q, int p) -> C {
+    const C z = rin[q * STRIDE + padi(p)];
+    const R m = stage[q * L + p];
+    return cpx<C>(z.x * m, z.y * m);
+  };
+  auto st_out = [&](int q, int p, const C& v) {
+    const int j = j0 + q;
+    if (j < S) Tout[tb_index<F>(j, (p + H) & (L - 1))] = v;
+  };
   C* other = (res == s) ? s2 : s;
-  const C* out = fft_ct<R, +1, LOGL, B, false, true>(res, other, tw);
-  for (int e = threadIdx.x; e < NE; e += kFftThreads) {
-    const int q = e / N, b = e % N;
-    const int j = j0 + q;
-    if (j < S) Tout[(int64_t)j * N + b] = out[q * STRIDE + padi((b - H) & (L - 1))];
-  }
-  __syncthreads();
+  fft_ct<R, +1, LOGL, B, false, true>(res, other, tw, ld_mul, st_out);
 }
 
 // window columns j0 .. j0 + B of a full-length spectrum (C[j][c], c < L):
@@ -301,27 +312,24 @@ __device__ __forceinline__ void cols_inv_unit(const cplx<R>* __restrict__ Cs, cp
                                               const cplx<R>* __restrict__ tw, cplx<R>* s, cplx<R>* s2, int u) {
   using C = cplx<R>;
   using F = FistaShape<R, LOGL>;
-  constexpr int L = F::L, N = F::N, H = F::H, B = F::B, S = F::S, STRIDE = F::STRIDE;
+  constexpr int L = F::L, N = F::N, H = F::H, B = F::B, S = F::S;
   const int j0 = u * B;
-  for (int e = threadIdx.x; e < B * L; e += kFftThreads) {
-    const int q = e >> LOGL, c = e & (L - 1);
+  auto ld_c = [&](int q, int p) -> C {
     const int j = j0 + q;
-    s[q * STRIDE + padi(c)] = j < S ? Cs[(int64_t)j * L + c] : cpx<C>(R(0), R(0));
-  }
-  __syncthreads();
-  const C* out = fft_ct<R, +1, LOGL, B, false, true>(s, s2, tw);
-  for (int e = threadIdx.x; e < B * N; e += kFftThreads) {
-    const int q = e / N, b = e % N;
+    return j < S ? Cs[(int64_t)j * L + p] : cpx<C>(R(0), R(0));
+  };
+  auto st_out = [&](int q, int p, const C& v) {
     const int j = j0 + q;
-    if (j < S) Tout[(int64_t)j * N + b] = out[q * STRIDE + padi((b - H) & (L - 1))];
-  }
-  __syncthreads();
+    if (j < S) Tout[tb_index<F>(j, (p + H) & (L - 1))] = v;
+  };
+  fft_ct<R, +1, LOGL, B, false, true>(s, s2, tw, ld_c, st_out);
 }
 
 // rows b0 .. b0 + 2B of g = scale * crop F^-1 [spectrum] (minus the same rows
 // of d when kSubD: they are staged in shared memory during the transform),
-// the spectrum given by its window columns k_u in [-N, 0] (T[j][b]) and
-// Hermitian symmetry
+// the spectrum given by its window columns k_u in [-N, 0] (T, tb_index
+// layout: the unit's block is contiguous) and Hermitian symmetry; the last
+// pass writes g.
 template <typename R, int LOGL, bool kSubD>
 __device__ __forceinline__ void rows_inv_unit(const cplx<R>* __restrict__ T, R* __restrict__ g, R scale,
                                               const R* __restrict__ d, const cplx<R>* __restrict__ tw, cplx<R>* s,
@@ -335,18 +343,14 @@ __device__ __forceinline__ void rows_inv_unit(const cplx<R>* __restrict__ T, R* 
   // Z = Y_a + i Y_b over all columns: Z[c] from window column c and
   // Z[L - c] = conj Y_a[c] + i conj Y_b[c]; the self-conjugate columns 0 and
   // N keep their real parts (the imaginary parts only feed Im F^-1 Y)
+  const C* blk = T + tb_index<F>(0, b0);
   constexpr int NE = B * S;
   constexpr int NLD = (NE + kFftThreads - 1) / kFftThreads;
   C ya[NLD], yb[NLD];
 #pragma unroll
   for (int k = 0; k < NLD; ++k) {
     const int e = threadIdx.x + k * kFftThreads;
-    if (e < NE) {
-      const int q = e % B, c = e / B;
-      const C* src = T + (int64_t)c * N + b0 + 2 * q;
-      ya[k] = src[0];
-      yb[k] = src[1];
-    }
+    if (e < NE) ld_pair(blk + 2 * e, ya[k], yb[k]);   // column e / B, rows 2 (e % B) and 2 (e % B) + 1
   }
 #pragma unroll
   for (int k = 0; k < NLD; ++k) {
@@ -354,21 +358,18 @@ __device__ __forceinline__ void rows_inv_unit(const cplx<R>* __restrict__ T, R* 
     if (e < NE) {
       const int q = e % B, c = e / B;
       C a = ya[k], b = yb[k];
-      if (c == 0 || c == N) { a.y = R(0); b.y = R(0); }
+      if (c == 0 || c == N) {
+        a.y = R(0);
+        b.y = R(0);
+      }
       s[q * STRIDE + padi(c)] = cpx<C>(a.x - b.y, a.y + b.x);
       if (c != 0 && c != N) s[q * STRIDE + padi(L - c)] = cpx<C>(a.x + b.y, b.x - a.y);
     }
   }
   __syncthreads();
-  const C* res = fft_ct<R, +1, LOGL, B, false, true>(s, s2, tw);
-  if constexpr (kSubD) {
-    cp_async_wait_all();
-    __syncthreads();
-  }
-  constexpr int NO = B * N;
-  for (int e = threadIdx.x; e < NO; e += kFftThreads) {
-    const int q = e / N, a = e % N;
-    const C z = res[q * STRIDE + padi((a - H) & (L - 1))];
+  // crop (position p holds column (p + N/2) mod L), centring sign, scale
+  auto st_g = [&](int q, int p, const C& z) {
+    const int a = (p + H) & (L - 1);
     const int64_t row = b0 + 2 * q;
     const bool odd = (a + b0) & 1;
     const R va = z.x * scale, vb = z.y * scale;
@@ -379,8 +380,11 @@ __device__ __forceinline__ void rows_inv_unit(const cplx<R>* __restrict__ T, R* 
     }
     g[row * N + a] = ga;
     g[(row + 1) * N + a] = gb;
-  }
-  __syncthreads();
+  };
+  auto wait = [] {
+    if constexpr (kSubD) cp_async_wait_all();
+  };
+  fft_ct<R, +1, LOGL, B, false, true>(s, s2, tw, SmemIO{}, st_g, wait);
 }
 
 // member MM of the concatenated dictionary (db_{MM+1}, 2 (MM + 1) taps),
