@@ -40,6 +40,19 @@
 namespace rix {
 namespace {
 
+// analysis block side: 32 at the fine levels with FP32 and Db4 (at least 256
+// blocks per loop; with fewer, the smaller blocks keep more CTAs busy), kTB
+// otherwise
+template <typename R, int DICT>
+__host__ __device__ constexpr int ana_fine_block() {
+  return sizeof(R) == 4 && DICT == RIX_DICT_DB4 ? 32 : kTB;
+}
+template <typename R, int DICT>
+__device__ __forceinline__ int ana_block(int h) {
+  constexpr int TBF = ana_fine_block<R, DICT>();
+  return (TBF != kTB && (h / TBF) * (h / TBF) >= 256) ? TBF : kTB;
+}
+
 template <typename R, int LOGL, int DICT = RIX_DICT_DB4>
 struct FistaShape {
   static constexpr int L = 1 << LOGL;
@@ -59,8 +72,13 @@ struct FistaShape {
   // N), copied asynchronously while the unit's transform runs
   static constexpr size_t kStage = (size_t)B * L * sizeof(R);
   static constexpr int KMAX = DICT == RIX_DICT_DB4 ? 8 : kMaxTaps;
-  static constexpr size_t kWavSmem = sizeof(DwtSmem<R, KMAX>) > sizeof(IdwtSmem<R, KMAX>) ? sizeof(DwtSmem<R, KMAX>)
-                                                                                         : sizeof(IdwtSmem<R, KMAX>);
+  // analysis block side of the fine levels (kTB at the coarse ones; and with
+  // FP64, for shared memory)
+  static constexpr int TBF = ana_fine_block<R, DICT>();
+  static constexpr size_t kDwtSmem = sizeof(DwtSmem<R, TBF, KMAX>) > sizeof(DwtSmem<R, kTB, KMAX>)
+                                         ? sizeof(DwtSmem<R, TBF, KMAX>)
+                                         : sizeof(DwtSmem<R, kTB, KMAX>);
+  static constexpr size_t kWavSmem = kDwtSmem > sizeof(IdwtSmem<R, KMAX>) ? kDwtSmem : sizeof(IdwtSmem<R, KMAX>);
   static constexpr size_t kSmem = kFftSmem + kStage > kWavSmem ? kFftSmem + kStage : kWavSmem;
 };
 
@@ -103,15 +121,6 @@ __device__ __forceinline__ void st_pair(C* p, const C& a, const C& b) {
     p[1] = b;
   }
 }
-
-// 16-byte copies global -> shared that bypass the registers (cp.async, cached
-// in L2 only); a thread's copies are complete after cp_async_wait_all, and
-// everyone's after that and a CTA barrier
-__device__ __forceinline__ void cp_async16(void* sdst, const void* gsrc) {
-  const unsigned sa = (unsigned)__cvta_generic_to_shared(sdst);
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gsrc) : "memory");
-}
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
 // `bytes` (a multiple of 16; both addresses 16-byte aligned) from src to dst
 __device__ __forceinline__ void stage_async(void* dst, const void* src, int bytes) {
@@ -398,8 +407,8 @@ __device__ __noinline__ void syn_member(const R* ll, const R* cm, int n, R* dst,
 template <typename R, int MM>
 __device__ __noinline__ void ana_member(const R* src, int n, R* dst, int N, int last, const StepArgs<R>& sm,
                                         int bx, int by, unsigned char* smem, const R* taps) {
-  auto& dsm = *reinterpret_cast<DwtSmem<R, 2 * (MM + 1)>*>(smem);
-  dwt_tile<R, true>(src, N, n, nullptr, dst, N, last, sm, bx, by, dsm, RefTaps<R, 2 * (MM + 1)>{taps});
+  auto& dsm = *reinterpret_cast<DwtSmem<R, kTB, 2 * (MM + 1)>*>(smem);
+  dwt_tile<R, kTB, true>(src, N, n, nullptr, dst, N, last, sm, bx, by, dsm, RefTaps<R, 2 * (MM + 1)>{taps});
 }
 
 template <typename R>
@@ -453,13 +462,19 @@ __device__ __forceinline__ void synthesis_unit(const FistaLoop<R>& f, const R* c
 template <typename R, int DICT, int N>
 __device__ __forceinline__ void analysis_unit(const FistaLoop<R>& f, int l, int t, const StepArgs<R>& sa,
                                               unsigned char* smem, const R (&taps)[8][16]) {
-  const int n = N >> l, nt = (n / 2 + kTB - 1) / kTB, per = nt * nt;
+  const int n = N >> l, tb = ana_block<R, DICT>(n / 2), nt = (n / 2 + tb - 1) / tb, per = nt * nt;
   const int last = l == f.levels - 1;
   if constexpr (DICT == RIX_DICT_DB4) {
     const R* src = l == 0 ? f.g : (((l - 1) & 1) ? f.tmp : f.x);
     R* dst = (l & 1) ? f.tmp : f.x;
-    auto& dsm = *reinterpret_cast<DwtSmem<R, 8>*>(smem);
-    dwt_tile<R, true>(src, N, n, nullptr, dst, N, last, sa, t % nt, t / nt, dsm, Db4Taps<R>{});
+    constexpr int TBF = ana_fine_block<R, DICT>();
+    if (TBF != kTB && tb == TBF) {
+      auto& dsm = *reinterpret_cast<DwtSmem<R, TBF, 8>*>(smem);
+      dwt_tile<R, TBF, true>(src, N, n, nullptr, dst, N, last, sa, t % nt, t / nt, dsm, Db4Taps<R>{});
+    } else {
+      auto& dsm = *reinterpret_cast<DwtSmem<R, kTB, 8>*>(smem);
+      dwt_tile<R, kTB, true>(src, N, n, nullptr, dst, N, last, sa, t % nt, t / nt, dsm, Db4Taps<R>{});
+    }
   } else {
     const int64_t NN = (int64_t)N * N;
     const int m = t / per, tt = t - m * per;
@@ -561,7 +576,7 @@ __global__ void __launch_bounds__(kFftThreads, sizeof(R) == 4 && LOGL <= 12 ? 2 
     const double tn = __dmul_rn(0.5, __dadd_rn(1.0, __dsqrt_rn(__dadd_rn(1.0, __dmul_rn(__dmul_rn(4.0, t), t)))));
     const R mom = (R)__ddiv_rn(__dadd_rn(t, -1.0), tn);
     for (int l = 0; l < levels; ++l) {
-      const int per = level_units<DICT>((N >> l) / 2, kTB);
+      const int per = level_units<DICT>((N >> l) / 2, ana_block<R, DICT>((N >> l) / 2));
       for (int u = blockIdx.x; u < nb * per; u += gridDim.x) {
         const FistaLoop<R>& f = a.f[u / per];
         const int b = u / per;

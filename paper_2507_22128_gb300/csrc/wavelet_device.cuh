@@ -46,14 +46,32 @@ struct RefTaps {
   __device__ __forceinline__ R hi(int i) const { return (i & 1) ? -h[KT - 1 - i] : h[KT - 1 - i]; }
 };
 
+// ----------------------------------------------------- asynchronous copies --
+// global -> shared copies that bypass the registers (cp.async); a thread's
+// copies are complete after cp_async_wait_all, and everyone's after that and
+// a CTA barrier.  BYTES = 4, 8 (cached in L1 and L2) or 16 (L2 only); both
+// addresses aligned to BYTES.
+template <int BYTES>
+__device__ __forceinline__ void cp_async(void* sdst, const void* gsrc) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(sdst);
+  if constexpr (BYTES == 16) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gsrc) : "memory");
+  } else {
+    static_assert(BYTES == 4 || BYTES == 8, "cp.async size");
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(sa), "l"(gsrc), "n"(BYTES) : "memory");
+  }
+}
+__device__ __forceinline__ void cp_async16(void* sdst, const void* gsrc) { cp_async<16>(sdst, gsrc); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
 // ------------------------------------------------- fused analysis levels ----
-// A CTA owns a kTB x kTB block of each of the four subbands of an n x n block
-// (n a power of two), stages the periodic (2 kTB + K - 2)^2 input tile,
-// filters its rows (low and high) and then its columns.  Every global load of
-// a tile is issued before the first one is used.
-constexpr int kTB = 16;
+// A CTA owns a TB x TB block of each of the four subbands of an n x n block
+// (n a power of two), stages the periodic (2 TB + K - 2)^2 input tile and the
+// step's inputs (y and alpha of the block) with asynchronous copies, filters
+// the tile's rows (low and high) and then its columns.
+constexpr int kTB = 16;                      // the smaller block side
 constexpr int kMaxTaps = 16;                 // db8
-template <int K> constexpr int tin_side() { return 2 * kTB + K - 2; }
+template <int TB, int K> constexpr int tin_side() { return 2 * TB + K - 2; }
 
 // FISTA step fused into the analysis of the gradient (Beck & Teboulle 2009):
 // at each final coefficient c = s g:  a' = S_{lam/L}(y - c/L),
@@ -67,59 +85,51 @@ struct StepArgs {
   R mom;
 };
 
-template <typename R, int K>
+template <typename R, int TB, int K>
 struct DwtSmem {
-  static constexpr int TIN = tin_side<K>();
+  static constexpr int TIN = tin_side<TB, K>();
   R tin[TIN][TIN + 1];
-  R trow[TIN][2 * kTB + 1];     // [input row][lo x | hi x]
+  R trow[TIN][2 * TB + 1];             // [input row][lo x | hi x]
+  alignas(16) R ys[4][TB * TB];        // step inputs per quadrant, [row][column] of the block
+  alignas(16) R as[4][TB * TB];
 };
 
-// one kTB x kTB output block (bx, by) of each subband; 256 threads
-template <typename R, bool kStep, typename TAPS>
+// one TB x TB output block (bx, by) of each subband; 256 threads
+template <typename R, int TB, bool kStep, typename TAPS>
 __device__ __forceinline__ void dwt_tile(const R* __restrict__ src, int lds, int n, R* __restrict__ coef,
                                          R* __restrict__ ll, int ld, int last, const StepArgs<R>& st, int bx, int by,
-                                         DwtSmem<R, TAPS::K>& sm, const TAPS& tp) {
+                                         DwtSmem<R, TB, TAPS::K>& sm, const TAPS& tp) {
   constexpr int K = TAPS::K;
-  constexpr int TIN = tin_side<K>();
-  constexpr int NLD = (TIN * TIN + 255) / 256;
+  constexpr int TIN = tin_side<TB, K>();
+  static_assert((TB * TB) % 256 == 0, "block side");
   auto& tin = sm.tin;
   auto& trow = sm.trow;
   const int h = n / 2;
-  const int y0 = by * kTB, x0 = bx * kTB;
-  const int ty = threadIdx.x / kTB, tx = threadIdx.x - ty * kTB;   // 256 threads = kTB x kTB
-  const int y = y0 + ty, x = x0 + tx;
-  const bool own = y < h && x < h;
-  // the coefficients this thread updates: quadrants 1-3, and 0 at the last level
-  R yq[4], aq[4];
-  if (kStep && own) {
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      if (q == 0 && !last) continue;
-      const int64_t i = (int64_t)((q >> 1) * h + y) * ld + (q & 1) * h + x;
-      yq[q] = st.y[i];
-      aq[q] = st.alpha[i];
+  const int y0 = by * TB, x0 = bx * TB;
+  // the coefficients this block updates: quadrants 1-3, and 0 at the last
+  // level; 16-byte copies of whole block rows (h is a multiple of the chunk)
+  if constexpr (kStep) {
+    constexpr int CH = 16 / (int)sizeof(R);
+    constexpr int CPR = TB / CH;
+    for (int c = threadIdx.x; c < 4 * TB * CPR; c += blockDim.x) {
+      const int q = c / (TB * CPR), rem = c - q * (TB * CPR);
+      const int r = rem / CPR, k = rem - r * CPR;
+      const int y = y0 + r, x = x0 + k * CH;
+      if ((q != 0 || last) && y < h && x < h) {
+        const int64_t i = (int64_t)((q >> 1) * h + y) * ld + (q & 1) * h + x;
+        cp_async16(&sm.ys[q][r * TB + k * CH], st.y + i);
+        cp_async16(&sm.as[q][r * TB + k * CH], st.alpha + i);
+      }
     }
   }
-  R v[NLD];
-#pragma unroll
-  for (int k = 0; k < NLD; ++k) {
-    const int t = threadIdx.x + 256 * k;
-    if (t < TIN * TIN) {
-      const int r = t / TIN, c = t - r * TIN;
-      v[k] = src[(int64_t)((2 * y0 + r) & (n - 1)) * lds + ((2 * x0 + c) & (n - 1))];
-    }
+  for (int t = threadIdx.x; t < TIN * TIN; t += blockDim.x) {
+    const int r = t / TIN, c = t - r * TIN;
+    cp_async<(int)sizeof(R)>(&tin[r][c], src + (int64_t)((2 * y0 + r) & (n - 1)) * lds + ((2 * x0 + c) & (n - 1)));
   }
-#pragma unroll
-  for (int k = 0; k < NLD; ++k) {
-    const int t = threadIdx.x + 256 * k;
-    if (t < TIN * TIN) {
-      const int r = t / TIN, c = t - r * TIN;
-      tin[r][c] = v[k];
-    }
-  }
+  cp_async_wait_all();
   __syncthreads();
-  for (int t = threadIdx.x; t < TIN * kTB; t += blockDim.x) {
-    const int r = t / kTB, xx = t - r * kTB;
+  for (int t = threadIdx.x; t < TIN * TB; t += blockDim.x) {
+    const int r = t / TB, xx = t - r * TB;
     R a = R(0), d = R(0);
 #pragma unroll
     for (int i = 0; i < K; ++i) {
@@ -128,27 +138,33 @@ __device__ __forceinline__ void dwt_tile(const R* __restrict__ src, int lds, int
       d += tp.hi(i) * w;
     }
     trow[r][xx] = a;
-    trow[r][kTB + xx] = d;
+    trow[r][TB + xx] = d;
   }
   __syncthreads();
-  if (own) {
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int cy = q >> 1, cx = q & 1;
-      R g = R(0);
+  for (int k = 0; k < TB * TB / 256; ++k) {
+    const int pidx = threadIdx.x + 256 * k;
+    const int ty = pidx / TB, tx = pidx - ty * TB;
+    const int y = y0 + ty, x = x0 + tx;
+    if (y < h && x < h) {
 #pragma unroll
-      for (int i = 0; i < K; ++i) g += (cy ? tp.hi(i) : tp.lo(i)) * trow[2 * ty + i][cx * kTB + tx];
-      const int64_t idx = (int64_t)(cy * h + y) * ld + cx * h + x;
-      if (q == 0 && !last) {
-        ll[(int64_t)y * ld + x] = g;
-      } else if (kStep) {
-        const R z = yq[q] - g * st.inv_l;
-        const R az = fabs(z) - st.thr;
-        const R an = (st.active && az > R(0)) ? copysign(az, z) : R(0);
-        st.y[idx] = an + st.mom * (an - aq[q]);
-        st.alpha[idx] = an;
-      } else {
-        coef[idx] = g;
+      for (int q = 0; q < 4; ++q) {
+        const int cy = q >> 1, cx = q & 1;
+        R g = R(0);
+#pragma unroll
+        for (int i = 0; i < K; ++i) g += (cy ? tp.hi(i) : tp.lo(i)) * trow[2 * ty + i][cx * TB + tx];
+        const int64_t idx = (int64_t)(cy * h + y) * ld + cx * h + x;
+        if (q == 0 && !last) {
+          ll[(int64_t)y * ld + x] = g;
+        } else if (kStep) {
+          const R z = sm.ys[q][pidx] - g * st.inv_l;
+          const R az = fabs(z) - st.thr;
+          const R an = (st.active && az > R(0)) ? copysign(az, z) : R(0);
+          st.y[idx] = an + st.mom * (an - sm.as[q][pidx]);
+          st.alpha[idx] = an;
+        } else {
+          coef[idx] = g;
+        }
       }
     }
   }
