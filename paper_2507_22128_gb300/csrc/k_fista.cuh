@@ -47,6 +47,12 @@ template <typename R, int DICT>
 __host__ __device__ constexpr int ana_fine_block() {
   return sizeof(R) == 4 && DICT == RIX_DICT_DB4 ? 32 : kTB;
 }
+// block side of the chained coarse synthesis (the level-1 output per unit)
+template <typename R>
+__host__ __device__ constexpr int chain_block() {
+  return sizeof(R) == 4 ? 64 : 32;
+}
+
 template <typename R, int DICT>
 __device__ __forceinline__ int ana_block(int h) {
   constexpr int TBF = ana_fine_block<R, DICT>();
@@ -78,7 +84,10 @@ struct FistaShape {
   static constexpr size_t kDwtSmem = sizeof(DwtSmem<R, TBF, KMAX>) > sizeof(DwtSmem<R, kTB, KMAX>)
                                          ? sizeof(DwtSmem<R, TBF, KMAX>)
                                          : sizeof(DwtSmem<R, kTB, KMAX>);
-  static constexpr size_t kWavSmem = kDwtSmem > sizeof(IdwtSmem<R, KMAX>) ? kDwtSmem : sizeof(IdwtSmem<R, KMAX>);
+  static constexpr size_t kIdwtSmem = sizeof(IdwtSmem<R, KMAX>) > chain_smem_bytes<R, chain_block<R>(), 8>()
+                                          ? sizeof(IdwtSmem<R, KMAX>)
+                                          : chain_smem_bytes<R, chain_block<R>(), 8>();
+  static constexpr size_t kWavSmem = kDwtSmem > kIdwtSmem ? kDwtSmem : kIdwtSmem;
   static constexpr size_t kSmem = kFftSmem + kStage > kWavSmem ? kFftSmem + kStage : kWavSmem;
 };
 
@@ -545,13 +554,24 @@ __global__ void __launch_bounds__(kFftThreads, sizeof(R) == 4 && LOGL <= 12 ? 2 
   if (!grid_barrier(bar)) return;
   double t = 1.0;
   for (int it = 0; it < f0.iters; ++it) {
-    // x = W y, coarsest level first; with Db4 the finest level is fused into
-    // the row transforms
-    for (int l = levels - 1; l >= (kCat ? 0 : 1); --l) {
-      const int per = level_units<DICT>(N >> l, kTS);
+    // x = W y, coarsest level first.  Db4: levels levels-1 .. 1 in one
+    // phase (chained synthesis, into tmp), the finest level fused into the
+    // row transforms
+    if constexpr (kCat) {
+      for (int l = levels - 1; l >= 0; --l) {
+        const int per = level_units<DICT>(N >> l, kTS);
+        for (int u = blockIdx.x; u < nb * per; u += gridDim.x) {
+          const FistaLoop<R>& f = a.f[u / per];
+          synthesis_unit<R, DICT, N>(f, f.y, l, u % per, smem_raw, a.taps);
+        }
+        if (!grid_barrier(bar)) return;
+      }
+    } else if (levels > 1) {
+      constexpr int T1 = chain_block<R>();
+      constexpr int nt = (N / 2 + T1 - 1) / T1, per = nt * nt;
       for (int u = blockIdx.x; u < nb * per; u += gridDim.x) {
         const FistaLoop<R>& f = a.f[u / per];
-        synthesis_unit<R, DICT, N>(f, f.y, l, u % per, smem_raw, a.taps);
+        syn_chain_tile<R, T1>(f.y, levels, N, f.tmp, (u % per) % nt, (u % per) / nt, smem_raw, Db4Taps<R>{});
       }
       if (!grid_barrier(bar)) return;
     }

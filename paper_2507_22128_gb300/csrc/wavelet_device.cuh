@@ -254,5 +254,166 @@ __device__ __forceinline__ void idwt_tile(const R* __restrict__ llin, const R* _
   __syncthreads();
 }
 
+// ------------------------------------------- chained coarse synthesis ----
+// The level-1 output block [m0, m0 + T1) x [c0, c0 + T1) of x = W c depends,
+// at each coarser level, only on the region of that level's output that the
+// taps reach: output rows m of level l read coefficient rows (m >> 1) - j,
+// j < K/2, of level l (periodic modulo the level's side), i.e. rows
+// [(lo >> 1) - K/2 + 1, ((lo + len - 1) >> 1)] for a region [lo, lo + len).
+// A unit loads the coefficients of all those regions at once (the top LL
+// block and the three detail subbands of every level, with asynchronous
+// copies) and synthesises the regions coarsest first in shared memory; so
+// the levels levels-1 .. 1 take one grid phase instead of one each, at the
+// price of recomputing the (small) coarse regions per unit.
+constexpr int kChainMaxLev = 12;
+
+// an upper bound of the region side at chain step s (s = 0: the block)
+template <int T1, int K>
+__host__ __device__ constexpr int chain_max_len(int step) {
+  int n = T1;
+  for (int i = 0; i < step; ++i) n = n / 2 + K / 2;
+  return n;
+}
+
+// shared-memory elements of a chain of up to kChainMaxLev levels
+template <int T1, int K>
+__host__ __device__ constexpr int chain_smem_elems() {
+  int e = 0;
+  for (int s = 1; s <= kChainMaxLev; ++s) e += 3 * chain_max_len<T1, K>(s) * chain_max_len<T1, K>(s);   // details
+  const int m2 = chain_max_len<T1, K>(1);
+  e += m2 * m2;                  // top LL region
+  e += 2 * m2 * m2;              // region ping-pong
+  e += 2 * m2 * T1;              // row pass
+  return e;
+}
+template <typename R, int T1, int K>
+__host__ __device__ constexpr size_t chain_smem_bytes() {
+  return 16 * sizeof(int) * (kChainMaxLev + 1) + (size_t)chain_smem_elems<T1, K>() * sizeof(R);
+}
+
+// block (bx, by) of the level-1 output (side n1 = N / 2, ld N) into dst,
+// from the coefficients `coef` (N x N, Mallat layout, `levels` levels)
+template <typename R, int T1, typename TAPS>
+__device__ __forceinline__ void syn_chain_tile(const R* __restrict__ coef, int levels, int N, R* __restrict__ dst,
+                                               int bx, int by, unsigned char* smem, const TAPS& tp) {
+  constexpr int K = TAPS::K, HK = K / 2;
+  // table per level l = 1 .. levels: region rows [lr, lr + nr), cols
+  // [lc, lc + nc) of level l's output (l = levels: the top LL block), and the
+  // offset of level l's details (the region of level l + 1)
+  int* tab = reinterpret_cast<int*>(smem);
+  int* lr = tab;
+  int* nr = tab + (kChainMaxLev + 1);
+  int* lc = tab + 2 * (kChainMaxLev + 1);
+  int* nc = tab + 3 * (kChainMaxLev + 1);
+  int* doff = tab + 4 * (kChainMaxLev + 1);
+  R* pool = reinterpret_cast<R*>(smem + 16 * sizeof(int) * (kChainMaxLev + 1));
+  constexpr int M2 = chain_max_len<T1, K>(1);
+  if (threadIdx.x == 0) {
+    lr[1] = by * T1; nr[1] = T1; lc[1] = bx * T1; nc[1] = T1;
+    int off = 0;
+    for (int l = 1; l < levels; ++l) {
+      lr[l + 1] = (lr[l] >> 1) - (HK - 1);
+      nr[l + 1] = ((lr[l] + nr[l] - 1) >> 1) - lr[l + 1] + 1;
+      lc[l + 1] = (lc[l] >> 1) - (HK - 1);
+      nc[l + 1] = ((lc[l] + nc[l] - 1) >> 1) - lc[l + 1] + 1;
+      doff[l] = off;
+      off += 3 * nr[l + 1] * nc[l + 1];
+    }
+    doff[levels] = off;          // the top LL region
+  }
+  __syncthreads();
+  // threads as TC columns x (256 / TC) row groups: no divisions in the
+  // loops, and a thread's column fixes its taps' parity
+  constexpr int TC = T1;
+  constexpr int RG = 256 / TC;
+  static_assert(256 % TC == 0, "block side");
+  const int tc = threadIdx.x % TC, tg = threadIdx.x / TC;
+  // every coefficient the block needs, in one batch of asynchronous copies
+  for (int l = 1; l < levels; ++l) {
+    const int h = N >> (l + 1);                // side of level l's subbands
+    const int r0 = lr[l + 1], c0 = lc[l + 1], rn = nr[l + 1], cn = nc[l + 1];
+    R* dl = pool + doff[l];
+    if (tc < cn) {
+      const int col = (c0 + tc) & (h - 1);
+      for (int rr = tg; rr < 3 * rn; rr += RG) {
+        const int q = rr >= 2 * rn ? 3 : rr >= rn ? 2 : 1;
+        const int row = (r0 + rr - (q - 1) * rn) & (h - 1);
+        cp_async<(int)sizeof(R)>(dl + rr * cn + tc, coef + (int64_t)((q >> 1) * h + row) * N + (q & 1) * h + col);
+      }
+    }
+  }
+  {
+    const int h = N >> levels;
+    const int r0 = lr[levels], c0 = lc[levels], rn = nr[levels], cn = nc[levels];
+    R* tl = pool + doff[levels];
+    if (tc < cn) {
+      const int col = (c0 + tc) & (h - 1);
+      for (int rk = tg; rk < rn; rk += RG)
+        cp_async<(int)sizeof(R)>(tl + rk * cn + tc, coef + (int64_t)((r0 + rk) & (h - 1)) * N + col);
+    }
+  }
+  cp_async_wait_all();
+  __syncthreads();
+  R* buf[2] = {pool + doff[levels] + M2 * M2, pool + doff[levels] + 2 * M2 * M2};
+  R* tr = pool + doff[levels] + 3 * M2 * M2;
+  const R* ll = pool + doff[levels];
+  int llw = nc[levels];                         // row stride of ll
+  const int n1 = N >> 1;
+  for (int l = levels - 1; l >= 1; --l) {
+    const int ir0 = lr[l + 1], irn = nr[l + 1], ic0 = lc[l + 1], icn = nc[l + 1];
+    const int or0 = lr[l], orn = nr[l], oc0 = lc[l], ocn = nc[l];
+    const R* d1 = pool + doff[l];               // (0, 1): row-high
+    const R* d2 = d1 + irn * icn;               // (1, 0): column-high
+    const R* d3 = d2 + irn * icn;               // (1, 1)
+    // rows: tr[cy][rk][c] for the output columns c
+    if (tc < ocn) {
+      const int ca = oc0 + tc;
+      const int kc = (ca >> 1) - ic0;
+      const int par = ca & 1;
+      R tl[HK], th[HK];
+#pragma unroll
+      for (int j = 0; j < HK; ++j) {
+        tl[j] = par ? tp.lo(2 * j + 1) : tp.lo(2 * j);
+        th[j] = par ? tp.hi(2 * j + 1) : tp.hi(2 * j);
+      }
+      for (int rr = tg; rr < 2 * irn; rr += RG) {
+        const bool cy = rr >= irn;
+        const int rk = cy ? rr - irn : rr;
+        const R* q0 = cy ? d2 + rk * icn : ll + rk * llw;
+        const R* q1 = (cy ? d3 : d1) + rk * icn;
+        R v = R(0);
+#pragma unroll
+        for (int j = 0; j < HK; ++j) v += tl[j] * q0[kc - j] + th[j] * q1[kc - j];
+        tr[rr * ocn + tc] = v;
+      }
+    }
+    __syncthreads();
+    // columns, into the next region (or the level-1 output)
+    R* out = buf[l & 1];
+    if (tc < ocn) {
+      for (int r = tg; r < orn; r += RG) {
+        const int ma = or0 + r;
+        const int km = (ma >> 1) - ir0;
+        const int par = ma & 1;
+        R v = R(0);
+#pragma unroll
+        for (int j = 0; j < HK; ++j) {
+          const R lo = par ? tp.lo(2 * j + 1) : tp.lo(2 * j);
+          const R hi = par ? tp.hi(2 * j + 1) : tp.hi(2 * j);
+          v += lo * tr[(km - j) * ocn + tc] + hi * tr[(irn + km - j) * ocn + tc];
+        }
+        if (l > 1) {
+          out[r * ocn + tc] = v;
+        } else if (ma < n1 && oc0 + tc < n1) {
+          dst[(int64_t)ma * N + oc0 + tc] = v;
+        }
+      }
+    }
+    __syncthreads();
+    ll = out;
+    llw = ocn;
+  }
+}
+
 }  // namespace
 }  // namespace rix
