@@ -288,6 +288,7 @@ struct KArgs {
   const void* corr;
   const double* nm1;
   double w0, dw;
+  const void* screen;   // tabulated corr x phase screen per plane, or null
 };
 
 // Shared-memory layout of every transform kernel: s = B rows of padded_len(L)
@@ -309,6 +310,7 @@ __device__ __forceinline__ void fwd_rows_block(KArgs a, const R* __restrict__ im
   const int L = a.L, M = a.M, half = M / 2;
   const R* corr = static_cast<const R*>(a.corr);
   const double wp = a.w0 + p * a.dw;
+  const C* scr = a.mode == kFacPhase && a.screen ? static_cast<const C*>(a.screen) + (int64_t)p * M * M : nullptr;
 #pragma unroll 4
   for (int idx = threadIdx.x; idx < a.B * L; idx += kFftThreads) {
     const int r = idx >> a.logL, c = idx & (L - 1);
@@ -320,9 +322,13 @@ __device__ __forceinline__ void fwd_rows_block(KArgs a, const R* __restrict__ im
       const int64_t pix = (int64_t)b * M + aa;
       R x = img[pix];
       if ((aa + b) & 1) x = -x;
-      if (a.mode != kFacNone) x *= corr[pix];
-      if (a.mode == kFacPhase) val = wscreen<R, -1>(wp, a.nm1[pix]) * x;
-      else val = cmake<C>(x, 0.0);
+      if (scr) {
+        val = scr[pix] * x;
+      } else {
+        if (a.mode != kFacNone) x *= corr[pix];
+        if (a.mode == kFacPhase) val = wscreen<R, -1>(wp, a.nm1[pix]) * x;
+        else val = cmake<C>(x, 0.0);
+      }
     }
     s[r * a.stride + padi(c)] = val;
   }
@@ -381,6 +387,7 @@ __device__ __forceinline__ void inv_rows_block(KArgs a, const cplx<R>* __restric
     __syncthreads();
     const C* res = fft_any<R, VPT, +1>(s, s2, a.B, a.logL, a.stride, tw);
     const double wp = a.w0 + p * a.dw;
+    const C* scr = a.mode == kFacPhase && a.screen ? static_cast<const C*>(a.screen) + (int64_t)p * M * M : nullptr;
     // the output image accumulates the planes; the first plane initialises it
     for (int idx = threadIdx.x; idx < nout; idx += kFftThreads) {
       const int r = idx / M, aa = idx - r * M;
@@ -389,7 +396,11 @@ __device__ __forceinline__ void inv_rows_block(KArgs a, const cplx<R>* __restric
       const int64_t pix = (int64_t)b * M + aa;
       const C z = res[r * a.stride + padi((aa - half) & (L - 1))];
       R v;
-      if (a.mode == kFacPhase) {
+      if (scr) {
+        // Re(z conj(t)) with t = corr exp(-2 pi i w_p (n-1)): corr folded in
+        const C t = scr[pix];
+        v = z.x * t.x + z.y * t.y;
+      } else if (a.mode == kFacPhase) {
         const C e = wscreen<R, +1>(wp, a.nm1[pix]);
         v = z.x * e.x - z.y * e.y;
       } else {
@@ -397,7 +408,7 @@ __device__ __forceinline__ void inv_rows_block(KArgs a, const cplx<R>* __restric
       }
       v *= rscale;
       if ((aa + b) & 1) v = -v;
-      if (a.mode != kFacNone) v *= corr[pix];
+      if (a.mode != kFacNone && !scr) v *= corr[pix];
       img[pix] = (p == 0 && !accumulate) ? v : img[pix] + v;
     }
     __syncthreads();
@@ -540,6 +551,7 @@ KArgs make_args(const XformGeom& g, int B) {
   a.M = g.M; a.L = g.L; a.logL = g.logL; a.lo = g.lo; a.S = g.S; a.nplanes = g.nplanes;
   a.mode = g.mode; a.B = B; a.stride = padded_len(g.L); a.herm = g.herm;
   a.corr = g.corr; a.nm1 = g.nm1; a.w0 = g.w0; a.dw = g.dw;
+  a.screen = g.screen;
   return a;
 }
 

@@ -73,6 +73,21 @@ __global__ void __launch_bounds__(kFftThreads, (VPT == 0 && sizeof(R) == 4) ? 4 
   conv_cols_block<R, VPT>(a, Tin, op, tab, tab2, Tout, tw, s, s2, blockIdx.x, blockIdx.y);
 }
 
+// screen[p][pix] = corr[pix] * exp(-2 pi i (w0 + p dw) nm1[pix]), formed as
+// the row passes form it (wscreen)
+template <typename R>
+__global__ void k_screen_table(int64_t npix, int nplanes, double w0, double dw, const R* __restrict__ corr,
+                               const double* __restrict__ nm1, cplx<R>* __restrict__ screen) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < npix * nplanes;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int p = (int)(i / npix);
+    const int64_t pix = i - (int64_t)p * npix;
+    const cplx<R> e = wscreen<R, -1>(w0 + p * dw, nm1[pix]);
+    const R c = corr[pix];
+    screen[i] = cmake<cplx<R>>(e.x * c, e.y * c);
+  }
+}
+
 // ------------------------------------------------------------------- host ----
 // rows per CTA for a given values-per-thread setting
 template <typename R>
@@ -142,6 +157,18 @@ int fft_init_twiddles(Ctx* ctx) {
 }
 
 template <typename R>
+int build_screen_table(const Ctx* ctx, const XformGeom& g, cplx<R>* screen, cudaStream_t st) {
+  if (g.mode != kFacPhase || !g.corr || !g.nm1 || g.M <= 0 || g.nplanes <= 0)
+    return set_error(RIX_EINVAL, "screen table needs a w-stacked geometry");
+  const int64_t npix = (int64_t)g.M * g.M;
+  const int blocks = (int)std::min<int64_t>(ceil_div(npix * g.nplanes, 256), (int64_t)ctx->num_sms * 16);
+  ::rix::note_launch();
+  k_screen_table<R><<<blocks, 256, 0, st>>>(npix, g.nplanes, g.w0, g.dw, static_cast<const R*>(g.corr), g.nm1,
+                                            screen);
+  RIX_LAUNCH_CHECK();
+  return RIX_OK;
+}
+template <typename R>
 int fwd_rows(const Ctx* ctx, const XformGeom& g, const R* img, cplx<R>* T, cudaStream_t st) {
   RIX_TRY(check_geom<R>(g));
   RIX_FFT_LAUNCH(k_fwd_rows, g.M, g.nplanes, img, T, twiddles<R>(ctx));
@@ -187,7 +214,8 @@ int inv_rows(const Ctx* ctx, const XformGeom& g, const cplx<R>* T, R* img, doubl
                            cplx<R>*, cudaStream_t);                                                      \
   template int conv_cols<R>(const Ctx*, const XformGeom&, const cplx<R>*, int, const void*, const void*,  \
                             cplx<R>*, cudaStream_t);                                                     \
-  template int inv_rows<R>(const Ctx*, const XformGeom&, const cplx<R>*, R*, double, int, cudaStream_t);
+  template int inv_rows<R>(const Ctx*, const XformGeom&, const cplx<R>*, R*, double, int, cudaStream_t);    \
+  template int build_screen_table<R>(const Ctx*, const XformGeom&, cplx<R>*, cudaStream_t);
 RIX_FFT_INST(float)
 RIX_FFT_INST(double)
 

@@ -50,7 +50,7 @@ __host__ __device__ constexpr int ana_fine_block() {
 // block side of the chained coarse synthesis (the level-1 output per unit)
 template <typename R>
 __host__ __device__ constexpr int chain_block() {
-  return sizeof(R) == 4 ? 64 : 32;
+  return 32;
 }
 
 template <typename R, int DICT>

@@ -742,6 +742,9 @@ XformGeom plane_geom(const Job* job, const Part& pt, bool psf) {
   g.nm1 = psf ? job->nm1_psf.as<double>() : job->nm1_img.as<double>();
   g.w0 = job->stats.w_min - 0.5 * job->ww * job->stats.dw;
   g.dw = job->stats.dw;
+  // the image grid's factors are tabulated once per job (the PSF's grid is
+  // transformed once per job: it forms them on the fly)
+  if (!psf && g.mode == kFacPhase && job->screen_img.p) g.screen = job->screen_img.p;
   return g;
 }
 
@@ -785,6 +788,15 @@ int grid_build_corrections(Job* job, cudaStream_t st) {
   job->stats.max_dw_nm1 = 0.0;
   RIX_TRY(build_correction<R>(job, n, job->ng, job->corr_img, job->nm1_img, st));
   RIX_TRY(build_correction<R>(job, 2 * n, 2 * job->ng, job->corr_psf, job->nm1_psf, st));
+  if (job->nw > 0) {
+    // corr x phase screen of every w-plane on the image grid: read by the
+    // row passes of every major cycle instead of forming them in FP64
+    XformGeom g = plane_geom(job, job->part[0], false);
+    g.screen = nullptr;
+    const size_t bytes = (size_t)g.nplanes * g.M * g.M * sizeof(cplx<R>);
+    RIX_TRY(job->screen_img.alloc(job->ctx, bytes));
+    RIX_TRY(build_screen_table<R>(job->ctx, g, job->screen_img.as<cplx<R>>(), st));
+  }
   return RIX_OK;
 }
 

@@ -125,6 +125,7 @@ static size_t workspace_bytes(const rix_job_desc& d, int64_t nrow) {
   b += ns * std::min<size_t>(P, 2) * 4 * real;     // per-entry kernel geometry
   b += ns / 512 * 4 + 64;                          // work items
   b += n * n * (real + 8) + 4 * n * n * (real + 8); // corrections + n-1 tables (image and PSF)
+  if (d.n_wplanes > 0) b += np * n * n * cplx;     // corr x phase screens of the image grid's planes
   b += P * 4 * n * n * real;                       // Gamma filters
   b += 3 * 4 * n * n * cplx + 2 * n * n * real;    // fill scratch
   // per partition: planes (windows are at most the full grid), transpose buffer,

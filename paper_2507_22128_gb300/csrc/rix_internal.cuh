@@ -126,7 +126,15 @@ struct XformGeom {
   const double* nm1;           // double [M][M]: n - 1 per pixel (kFacPhase)
   double w0, dw;               // plane p sits at w0 + p * dw (kFacPhase)
   int herm = 0;                // inverse rows: complete columns [S, L) by conjugate symmetry
+  // kFacPhase, optional: cplx [nplanes][M][M] of corr * exp(-2 pi i w_p (n-1)),
+  // the factors tabulated once per job (build_screen_table); corr and nm1
+  // are then not read by the row passes
+  const void* screen = nullptr;
 };
+// screen[p][b][a] = corr[b][a] * exp(-2 pi i (w0 + p dw) nm1[b][a]) for the
+// geometry g (kFacPhase), the same values the row passes would form
+template <typename R>
+int build_screen_table(const Ctx* ctx, const XformGeom& g, cplx<R>* screen, cudaStream_t st);
 
 template <typename R>
 int fwd_rows(const Ctx* ctx, const XformGeom& g, const R* img, cplx<R>* T, cudaStream_t st);
@@ -231,6 +239,7 @@ struct Job {
   // corrections
   DevBuf corr_img, corr_psf;                // Real [N][N], [2N][2N]
   DevBuf nm1_img, nm1_psf;                  // double n - 1 per pixel (w-stacked)
+  DevBuf screen_img;                        // w-stacked: corr x phase screen per plane, image grid
   DevBuf gam;                               // Real [P][2N][2N] filters (u-major spectra)
   Part part[kMaxPart];
   double ells[kMaxPart];
