@@ -289,6 +289,7 @@ struct KArgs {
   const double* nm1;
   double w0, dw;
   const void* screen;   // tabulated corr x phase screen per plane, or null
+  int pg;               // inverse rows: planes per grid row y (0: all planes, one image)
 };
 
 // Shared-memory layout of every transform kernel: s = B rows of padded_len(L)
@@ -357,7 +358,12 @@ __device__ __forceinline__ void inv_rows_block(KArgs a, const cplx<R>* __restric
   const int nout = a.B * M;
   const R* corr = static_cast<const R*>(a.corr);
   const R rscale = (R)scale;
-  for (int p = 0; p < a.nplanes; ++p) {
+  // planes [pb, pe) into image `by` of the output (a.pg > 0: one partial sum
+  // per group of planes, summed by the caller)
+  const int pb = a.pg > 0 ? by * a.pg : 0;
+  const int pe = a.pg > 0 ? pb + a.pg : a.nplanes;
+  if (a.pg > 0) img += (int64_t)by * M * M;
+  for (int p = pb; p < pe; ++p) {
     const C* Tp = T + (int64_t)p * a.S * M;
   #pragma unroll 4
   for (int idx = threadIdx.x; idx < a.B * L; idx += kFftThreads) {
@@ -409,7 +415,7 @@ __device__ __forceinline__ void inv_rows_block(KArgs a, const cplx<R>* __restric
       v *= rscale;
       if ((aa + b) & 1) v = -v;
       if (a.mode != kFacNone && !scr) v *= corr[pix];
-      img[pix] = (p == 0 && !accumulate) ? v : img[pix] + v;
+      img[pix] = (p == pb && !accumulate) ? v : img[pix] + v;
     }
     __syncthreads();
   }
@@ -552,6 +558,7 @@ KArgs make_args(const XformGeom& g, int B) {
   a.mode = g.mode; a.B = B; a.stride = padded_len(g.L); a.herm = g.herm;
   a.corr = g.corr; a.nm1 = g.nm1; a.w0 = g.w0; a.dw = g.dw;
   a.screen = g.screen;
+  a.pg = g.pg;
   return a;
 }
 

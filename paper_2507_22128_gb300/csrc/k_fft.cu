@@ -88,6 +88,16 @@ __global__ void k_screen_table(int64_t npix, int nplanes, double w0, double dw, 
   }
 }
 
+// img = (accumulate ? img : 0) + sum over g < G of part[g]
+template <typename R>
+__global__ void k_sum_groups(R* __restrict__ img, const R* __restrict__ part, int G, int64_t n, int accumulate) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    R v = accumulate ? img[i] : R(0);
+    for (int g = 0; g < G; ++g) v += part[(int64_t)g * n + i];
+    img[i] = v;
+  }
+}
+
 // ------------------------------------------------------------------- host ----
 // rows per CTA for a given values-per-thread setting
 template <typename R>
@@ -200,11 +210,56 @@ int conv_cols(const Ctx* ctx, const XformGeom& g, const cplx<R>* Tin, int op, co
 }
 
 template <typename R>
-int inv_rows(const Ctx* ctx, const XformGeom& g, const cplx<R>* T, R* img, double scale, int accumulate,
+int inv_rows(const Ctx* ctx, const XformGeom& g0, const cplx<R>* T, R* img, double scale, int accumulate,
              cudaStream_t st) {
-  RIX_TRY(check_geom<R>(g));
-  RIX_FFT_LAUNCH(k_inv_rows, g.M, 1, T, img, scale, accumulate, twiddles<R>(ctx));
-  return RIX_OK;
+  RIX_TRY(check_geom<R>(g0));
+  XformGeom g = g0;
+  // The planes of one row batch are summed by one CTA.  With many planes and
+  // few row batches the grid ends in a nearly empty wave; split the planes
+  // into G groups (grid rows) when that takes fewer plane-transforms per SM
+  // slot, each group summing into its own image, and add the G images after.
+  const int P = g.nplanes;
+  int G = 1;
+  if (P > 1) {
+    const int V = use_inplace<R>(g.L) ? Vpt<R>::kLarge : kPingPongVals<R>;
+    const int B = batch_for<R>(ctx, V, g.L, g.M, 1);
+    const size_t sm = (use_inplace<R>(g.L) ? 1 : 2) * (size_t)B * padded_len(g.L) * sizeof(cplx<R>);
+    int per_sm = 0;
+    if (use_inplace<R>(g.L)) {
+      RIX_TRY(set_smem(k_inv_rows<R, Vpt<R>::kLarge>, sm));
+      RIX_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_inv_rows<R, Vpt<R>::kLarge>, kFftThreads, sm));
+    } else {
+      RIX_TRY(set_smem(k_inv_rows<R, 0>, sm));
+      RIX_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_inv_rows<R, 0>, kFftThreads, sm));
+    }
+    const int64_t slots = (int64_t)ctx->num_sms * std::max(per_sm, 1);
+    const int64_t rowb = ceil_div(g.M, B);
+    double best = 1e300;
+    for (int c = 1; c <= P && c <= 16; c *= 2) {
+      if (P % c) continue;
+      const double cost = (double)ceil_div(rowb * c, slots) * (P / c) + 0.1 * c;   // + the group sum
+      if (cost < best) { best = cost; G = c; }
+    }
+  }
+  if (G == 1) {
+    RIX_FFT_LAUNCH(k_inv_rows, g.M, 1, T, img, scale, accumulate, twiddles<R>(ctx));
+    return RIX_OK;
+  }
+  const int64_t n = (int64_t)g.M * g.M;
+  R* part = nullptr;
+  if (cudaMallocAsync((void**)&part, (size_t)G * n * sizeof(R), st) != cudaSuccess)
+    return set_error(RIX_ENOMEM, "plane-group images (%zu bytes)", (size_t)G * n * sizeof(R));
+  g.pg = P / G;
+  int rc = RIX_OK;
+  do {
+    RIX_FFT_LAUNCH(k_inv_rows, g.M, G, T, part, scale, 0, twiddles<R>(ctx));
+    ::rix::note_launch();
+    k_sum_groups<R><<<(int)std::min<int64_t>(ceil_div(n, 256), (int64_t)ctx->num_sms * 8), 256, 0, st>>>(
+        img, part, G, n, accumulate);
+    if (cudaGetLastError() != cudaSuccess) rc = set_error(RIX_ECUDA, "group sum launch");
+  } while (0);
+  cudaFreeAsync(part, st);
+  return rc;
 }
 
 #define RIX_FFT_INST(R)                                                                                  \

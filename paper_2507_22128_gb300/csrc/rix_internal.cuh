@@ -130,6 +130,8 @@ struct XformGeom {
   // the factors tabulated once per job (build_screen_table); corr and nm1
   // are then not read by the row passes
   const void* screen = nullptr;
+  // inverse rows: planes per CTA row of the grid (0: all), set by inv_rows
+  int pg = 0;
 };
 // screen[p][b][a] = corr[b][a] * exp(-2 pi i (w0 + p dw) nm1[b][a]) for the
 // geometry g (kFacPhase), the same values the row passes would form
