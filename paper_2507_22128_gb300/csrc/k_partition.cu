@@ -256,9 +256,82 @@ __global__ void k_radius_bits(SampleGeomParams g, int64_t ns, uint64_t* out) {
   }
 }
 
-__global__ void k_pick(const uint64_t* sorted, int64_t ns, int nparts, double* ells) {
-  int i = threadIdx.x + 1;
-  if (i < nparts) ells[i - 1] = __longlong_as_double((long long)sorted[((int64_t)i * (ns - 1)) / nparts]);
+// Radix select of the ring radii: the order statistics k_i = i (ns - 1) / P,
+// i = 1 .. P-1, of the 64-bit radius keys, one 8-bit digit per pass from the
+// most significant: each pass histograms the digit of the keys that match
+// target i's prefix so far, then k_select_step finds the digit value holding
+// rank k_i and extends the prefix.  After eight passes the prefix is the
+// key of rank k_i itself, the same value a full sort would put there.
+struct SelectState {
+  uint64_t prefix[kMaxPart];
+  int64_t rank[kMaxPart];
+  unsigned int hist[kMaxPart][256];
+};
+
+__global__ void k_select_init(SelectState* st, int64_t ns, int nparts) {
+  const int i = threadIdx.x;
+  if (i < kMaxPart) {
+    st->prefix[i] = 0ull;
+    st->rank[i] = (i + 1 < nparts) ? ((int64_t)(i + 1) * (ns - 1)) / nparts : 0;
+  }
+  for (int j = threadIdx.x; j < kMaxPart * 256; j += blockDim.x) (&st->hist[0][0])[j] = 0u;
+}
+
+// keys matching each target's prefix of the bits above `shift`: histogram of
+// bits [shift, shift + 8)
+__global__ void k_select_hist(const uint64_t* __restrict__ keys, int64_t n, int ntg, int shift, SelectState* st) {
+  __shared__ unsigned int h[kMaxPart][256];
+  for (int j = threadIdx.x; j < kMaxPart * 256; j += blockDim.x) (&h[0][0])[j] = 0u;
+  __shared__ uint64_t pre[kMaxPart];
+  if (threadIdx.x < kMaxPart) pre[threadIdx.x] = st->prefix[threadIdx.x];
+  __syncthreads();
+  // the early digits take few values: lanes with equal digits add once
+  // (warp-aggregated), so the shared atomics do not serialise
+  const int lane = threadIdx.x & 31;
+  for (int64_t b = (int64_t)blockIdx.x * blockDim.x; b < n; b += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t e = b + threadIdx.x;
+    const bool valid = e < n;
+    const uint64_t k = valid ? keys[e] : 0ull;
+    const uint64_t hi = shift + 8 < 64 ? (k >> (shift + 8)) : 0ull;
+    const unsigned d = (unsigned)(k >> shift) & 255u;
+    for (int t = 0; t < ntg; ++t) {
+      const bool m = valid && hi == pre[t];
+      const unsigned act = __ballot_sync(0xffffffffu, m);
+      if (m) {
+        const unsigned grp = __match_any_sync(act, d);
+        if (lane == __ffs(grp) - 1) atomicAdd(&h[t][d], (unsigned)__popc(grp));
+      }
+    }
+  }
+  __syncthreads();
+  for (int j = threadIdx.x; j < ntg * 256; j += blockDim.x) {
+    const unsigned v = (&h[0][0])[j];
+    if (v) atomicAdd(&(&st->hist[0][0])[j], v);
+  }
+}
+
+// one thread per target: the digit holding rank k, the rank within it; the
+// histograms are cleared for the next pass
+__global__ void k_select_step(SelectState* st, int ntg) {
+  const int t = threadIdx.x;
+  if (t < ntg) {
+    int64_t k = st->rank[t];
+    unsigned d = 0;
+    for (; d < 255u; ++d) {
+      const int64_t c = st->hist[t][d];
+      if (k < c) break;
+      k -= c;
+    }
+    st->rank[t] = k;
+    st->prefix[t] = (st->prefix[t] << 8) | d;
+  }
+  __syncthreads();
+  for (int j = threadIdx.x; j < kMaxPart * 256; j += blockDim.x) (&st->hist[0][0])[j] = 0u;
+}
+
+__global__ void k_select_out(const SelectState* st, int ntg, double* ells) {
+  const int t = threadIdx.x;
+  if (t < ntg) ells[t] = __longlong_as_double((long long)st->prefix[t]);
 }
 
 // Uniform weighting: density of the natural weights on the N x N uv grid
@@ -313,6 +386,20 @@ struct ClassifyOut {
 };
 
 __global__ void k_classify(SampleGeomParams g, int64_t ns, Thresholds th, ClassifyOut o) {
+  // per-block partial results (shared-memory atomics), merged into the
+  // global ones once per block: a global atomic per warp on the same dozen
+  // addresses serialised the kernel
+  __shared__ int s_win[kMaxPart * 4];
+  __shared__ unsigned long long s_cnt[kMaxPart];
+  __shared__ double s_w[kMaxPart];
+  __shared__ unsigned long long s_out;
+  for (int i = threadIdx.x; i < kMaxPart * 4; i += blockDim.x) s_win[i] = (i & 1) ? INT_MIN : INT_MAX;
+  for (int i = threadIdx.x; i < kMaxPart; i += blockDim.x) {
+    s_cnt[i] = 0ull;
+    s_w[i] = 0.0;
+  }
+  if (threadIdx.x == 0) s_out = 0ull;
+  __syncthreads();
   const int lane = threadIdx.x & 31;
   for (int64_t s0 = (int64_t)blockIdx.x * blockDim.x; s0 < ns; s0 += (int64_t)gridDim.x * blockDim.x) {
     const int64_t s = s0 + threadIdx.x;
@@ -341,7 +428,7 @@ __global__ void k_classify(SampleGeomParams g, int64_t ns, Thresholds th, Classi
       o.counts[s] = __popc(mask);
     }
     const unsigned outside = __ballot_sync(0xffffffffu, live && !c.inside);
-    if (lane == 0 && outside) atomicAdd(o.n_outside, (unsigned long long)__popc(outside));
+    if (lane == 0 && outside) atomicAdd(&s_out, (unsigned long long)__popc(outside));
     for (int p = 0; p < th.nparts; ++p) {
       const bool in = (mask >> p) & 1u;
       const unsigned bal = __ballot_sync(0xffffffffu, in);
@@ -357,15 +444,26 @@ __global__ void k_classify(SampleGeomParams g, int64_t ns, Thresholds th, Classi
       pmx = __reduce_max_sync(0xffffffffu, pmx);
       for (int off = 16; off; off >>= 1) w += __shfl_xor_sync(0xffffffffu, w, off);
       if (lane == 0) {
-        atomicMin(&o.win[p * 4 + 0], mn);
-        atomicMax(&o.win[p * 4 + 1], mx);
-        atomicMin(&o.win[p * 4 + 2], pmn);
-        atomicMax(&o.win[p * 4 + 3], pmx);
-        atomicAdd(&o.part_count[p], (unsigned long long)__popc(bal));
-        atomicAdd(&o.wsum[p], w);
+        atomicMin(&s_win[p * 4 + 0], mn);
+        atomicMax(&s_win[p * 4 + 1], mx);
+        atomicMin(&s_win[p * 4 + 2], pmn);
+        atomicMax(&s_win[p * 4 + 3], pmx);
+        atomicAdd(&s_cnt[p], (unsigned long long)__popc(bal));
+        atomicAdd(&s_w[p], w);
       }
     }
   }
+  __syncthreads();
+  if (threadIdx.x < th.nparts && s_cnt[threadIdx.x] > 0ull) {
+    const int p = threadIdx.x;
+    atomicMin(&o.win[p * 4 + 0], s_win[p * 4 + 0]);
+    atomicMax(&o.win[p * 4 + 1], s_win[p * 4 + 1]);
+    atomicMin(&o.win[p * 4 + 2], s_win[p * 4 + 2]);
+    atomicMax(&o.win[p * 4 + 3], s_win[p * 4 + 3]);
+    atomicAdd(&o.part_count[p], s_cnt[p]);
+    atomicAdd(&o.wsum[p], s_w[p]);
+  }
+  if (threadIdx.x == 0 && s_out) atomicAdd(o.n_outside, s_out);
 }
 
 struct KeyLayout {
@@ -589,17 +687,24 @@ int partition_job(Job* job, const double* uvw, int64_t nrow, const float* weight
       for (int i = 1; i < P - 1; ++i)
         if (!(ells[i] > ells[i - 1])) return fail(set_error(RIX_EINVAL, "ell_px must be ascending"));
     } else if (ns > 0) {
-      uint64_t *rb = nullptr, *rt = nullptr;
+      uint64_t* rb = nullptr;
+      SelectState* sel = nullptr;
       if (cudaMallocAsync(&rb, ns * sizeof(uint64_t), st) != cudaSuccess ||
-          cudaMallocAsync(&rt, ns * sizeof(uint64_t), st) != cudaSuccess)
-        return fail(set_error(RIX_ENOMEM, "radius sort scratch"));
+          cudaMallocAsync(&sel, sizeof(SelectState), st) != cudaSuccess) {
+        if (rb) cudaFreeAsync(rb, st);
+        return fail(set_error(RIX_ENOMEM, "radius select scratch"));
+      }
       ::rix::note_launch(); k_radius_bits<<<blocks, 256, 0, st>>>(g, ns, rb);
-      bool in_tmp = false;
-      int rc = radix_sort_u64_keys(rb, rt, ns, 64, st, &in_tmp);
-      if (rc == RIX_OK) { ::rix::note_launch(); k_pick<<<1, 32, 0, st>>>(in_tmp ? rt : rb, ns, P, sm_d->ells); }
+      ::rix::note_launch(); k_select_init<<<1, 256, 0, st>>>(sel, ns, P);
+      const int hb = std::min(blocks, 4 * ctx->num_sms);
+      for (int shift = 56; shift >= 0; shift -= 8) {
+        ::rix::note_launch(); k_select_hist<<<hb, 256, 0, st>>>(rb, ns, P - 1, shift, sel);
+        ::rix::note_launch(); k_select_step<<<1, 256, 0, st>>>(sel, P - 1);
+      }
+      ::rix::note_launch(); k_select_out<<<1, 32, 0, st>>>(sel, P - 1, sm_d->ells);
       cudaFreeAsync(rb, st);
-      cudaFreeAsync(rt, st);
-      if (rc != RIX_OK) return fail(rc);
+      cudaFreeAsync(sel, st);
+      if (cudaGetLastError() != cudaSuccess) return fail(set_error(RIX_ECUDA, "radius select launch"));
       if (cudaMemcpyAsync(ells, sm_d->ells, sizeof(ells), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
           cudaStreamSynchronize(st) != cudaSuccess)
         return fail(set_error(RIX_ECUDA, "quantile readback"));
