@@ -396,8 +396,8 @@ def phase_split(rec, rix, a, meth, stream, uvw, vis, w, out, flush):
 # timed job (profiles/k_tiles_ws_medium_dram.md): residual launches of
 # partitions 0 and 1, PSF launches of partitions 0 and 1.  Reported only for
 # that workload and while k_grid.cu is the source the counters were taken on.
-TILES_TRAFFIC = {"k_grid_sha1": "cb9c2262ddf59759316b789e95dfe9524cf84088",
-                 "resid": (161.74e6, 261.73e6), "psf": (85.82e6, 218.28e6)}
+TILES_TRAFFIC = {"k_grid_sha1": "dab75048113381c5baa1a22cc19111f811558f46",
+                 "resid": (162.13e6, 261.79e6), "psf": (115.38e6, 237.54e6)}
 
 
 def tiles_traffic(a):

@@ -552,8 +552,19 @@ __global__ void __launch_bounds__(kFftThreads, sizeof(R) == 4 && LOGL <= 12 ? 2 
     rows_inv_unit<R, LOGL, false>(f.tb, f.d, a.gscale, nullptr, f.tw, s, s2, stage, u % F::kRowUnits);
   }
   if (!grid_barrier(bar)) return;
+  // FISTA's momentum: t_{k+1} = (1 + sqrt(1 + 4 t_k^2)) / 2, momentum
+  // (t_k - 1) / t_{k+1}, each operation rounded on its own; one thread per
+  // CTA forms it (FP64 square root and division at 1/64 of the FP32 rate),
+  // at the start of the iteration: the grid barriers before the analysis
+  // phases publish it to the CTA
+  __shared__ R s_mom;
   double t = 1.0;
   for (int it = 0; it < f0.iters; ++it) {
+    if (threadIdx.x == 0) {
+      const double tn = __dmul_rn(0.5, __dadd_rn(1.0, __dsqrt_rn(__dadd_rn(1.0, __dmul_rn(__dmul_rn(4.0, t), t)))));
+      s_mom = (R)__ddiv_rn(__dadd_rn(t, -1.0), tn);
+      t = tn;
+    }
     // x = W y, coarsest level first.  Db4: levels levels-1 .. 1 in one
     // phase (chained synthesis, into tmp), the finest level fused into the
     // row transforms
@@ -591,10 +602,7 @@ __global__ void __launch_bounds__(kFftThreads, sizeof(R) == 4 && LOGL <= 12 ? 2 
       rows_inv_unit<R, LOGL, true>(f.tb, f.g, a.gscale, f.d, f.tw, s, s2, stage, u % F::kRowUnits);
     }
     if (!grid_barrier(bar)) return;
-    // t_{k+1} = (1 + sqrt(1 + 4 t_k^2)) / 2, momentum (t_k - 1) / t_{k+1}, each
-    // operation rounded on its own
-    const double tn = __dmul_rn(0.5, __dadd_rn(1.0, __dsqrt_rn(__dadd_rn(1.0, __dmul_rn(__dmul_rn(4.0, t), t)))));
-    const R mom = (R)__ddiv_rn(__dadd_rn(t, -1.0), tn);
+    const R mom = s_mom;
     for (int l = 0; l < levels; ++l) {
       const int per = level_units<DICT>((N >> l) / 2, ana_block<R, DICT>((N >> l) / 2));
       for (int u = blockIdx.x; u < nb * per; u += gridDim.x) {
@@ -605,7 +613,6 @@ __global__ void __launch_bounds__(kFftThreads, sizeof(R) == 4 && LOGL <= 12 ? 2 
       }
       if (!grid_barrier(bar)) return;
     }
-    t = tn;
   }
   if constexpr (kCat) {
     // each loop's image W alpha: the members' syntheses, summed
