@@ -365,7 +365,10 @@ def serving_experiment(ctx, a, rank):
 
 
 def phase_split(rec, rix, a, meth, stream, uvw, vis, w, out, flush):
-    """Event-timed phases of one job: partition, major cycles, minor cycles."""
+    """Event-timed phases of one job on one stream (the timed steps overlap
+    the partitions' work on their own streams): partition, major cycles,
+    minor cycles (batched as in the steps unless --no-batch-minor; the first
+    cycle's minor phase includes the PSFs)."""
     def ev():
         e = torch.cuda.Event(enable_timing=True)
         e.record(stream)
@@ -380,8 +383,11 @@ def phase_split(rec, rix, a, meth, stream, uvw, vis, w, out, flush):
         for p in range(2):
             rix.major_cycle(rec.job, p, vis, None, None, stream)
         s1 = ev()
-        for p in range(2):
-            rec.minor(p, meth, stream=stream)
+        if a.no_batch_minor:
+            for p in range(2):
+                rec.minor(p, meth, stream=stream)
+        else:
+            rec.minor_all(meth, stream)
         s2 = ev()
         torch.cuda.synchronize()
         maj += s0.elapsed_time(s1)
