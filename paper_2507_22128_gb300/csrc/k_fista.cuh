@@ -426,6 +426,12 @@ struct FistaArgs {
   int nb;
   R gscale;
   R taps[8][16];              // RIX_DICT_DB1_8: low-pass filters of db1 .. db8
+  // dataflow schedule (k_fista_flow): ticket counter, completed units per
+  // loop and stage ([loop][stage], zeroed before the launch), momentum per
+  // iteration
+  unsigned int* ticket;
+  unsigned int* done;
+  const R* mom;
 };
 
 // units of one wavelet level of one loop: tiles of side `tile` over an n x n
@@ -636,6 +642,166 @@ __global__ void __launch_bounds__(kFftThreads, sizeof(R) == 4 && LOGL <= 12 ? 2 
   }
 }
 
+// ------------------------------------------------------ dataflow schedule --
+// The loops of a batch are independent; only the phases of one loop are
+// ordered.  Instead of one grid barrier per phase, the units of every phase
+// of every loop form one ordered list: stage by stage (the two phases that
+// form d, then the phases of each iteration), each stage's loops in turn.  A
+// CTA takes the next unit with an atomic ticket and, before running it,
+// waits until the previous stage of the unit's loop has completed (a counter
+// per loop and stage); so a CTA that would idle at a barrier runs another
+// loop's units instead.  Every dependency is on a smaller ticket, taken by a
+// resident CTA (cooperative launch) that is running or waiting on a still
+// smaller one, so the schedule always progresses; every wait is bounded as
+// the grid barrier's is (2 s or 2^26 polls, then RIX_ETIMEOUT in the job's
+// status word).
+
+// completed units of a stage: release after the CTA's writes
+__device__ __forceinline__ void flow_done(unsigned int* ctr) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    red_release_gpu_add(ctr, 1u);
+  }
+}
+
+// wait until *ctr reaches `target`, then acquire (every thread of the CTA
+// sees the stage's writes); false when the wait gave up
+__device__ __forceinline__ bool flow_wait(const unsigned int* ctr, unsigned int target, int* status) {
+  __shared__ int ok;
+  if (threadIdx.x == 0) {
+    int good = 1;
+    const unsigned long long t0 = global_ns();
+    unsigned int spins = 0;
+    while (ld_acquire_gpu(ctr) < target) {
+      if ((++spins & 63u) == 0) {
+        if (*reinterpret_cast<volatile int*>(status) != 0) { good = 0; break; }
+        if (spins >= kBarrierMaxSpins || global_ns() - t0 > kBarrierTimeoutNs) {
+          atomicCAS(status, 0, RIX_ETIMEOUT);
+          good = 0;
+          break;
+        }
+      }
+      __nanosleep(32);
+    }
+    __threadfence();
+    ok = good;
+  }
+  __syncthreads();
+  return ok != 0;
+}
+
+// phase kinds of one iteration (Db4)
+enum FlowKind : int { kFlowChain = 0, kFlowRowsFwd, kFlowCols, kFlowRowsInv, kFlowAna };
+
+template <typename R, int LOGL>
+__global__ void __launch_bounds__(kFftThreads, sizeof(R) == 4 && LOGL <= 12 ? 2 : 1)
+    k_fista_flow(const __grid_constant__ FistaArgs<R> a) {
+  using C = cplx<R>;
+  using F = FistaShape<R, LOGL, RIX_DICT_DB4>;
+  constexpr int N = F::N;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* s = reinterpret_cast<C*>(smem_raw);
+  C* s2 = s + F::B * F::STRIDE;
+  R* stage = reinterpret_cast<R*>(smem_raw + F::kFftSmem);
+  const int nb = a.nb;
+  const FistaLoop<R>& f0 = a.f[0];
+  const int levels = f0.levels;
+  constexpr int T1 = chain_block<R>();
+  constexpr int kChainNt = (N / 2 + T1 - 1) / T1;
+  // the phases of one iteration: kind, analysis level, units per loop
+  __shared__ int ph_kind[kChainMaxLev + 4], ph_lev[kChainMaxLev + 4], ph_units[kChainMaxLev + 4];
+  __shared__ int s_nph, s_iter_units;
+  __shared__ R s_inv_l[kMaxPart], s_thr[kMaxPart];
+  __shared__ unsigned int s_ticket;
+  if (threadIdx.x == 0) {
+    int k = 0;
+    if (levels > 1) { ph_kind[k] = kFlowChain; ph_lev[k] = 0; ph_units[k++] = kChainNt * kChainNt; }
+    ph_kind[k] = kFlowRowsFwd; ph_lev[k] = 0; ph_units[k++] = F::kRowUnits;
+    ph_kind[k] = kFlowCols; ph_lev[k] = 0; ph_units[k++] = F::kColUnits;
+    ph_kind[k] = kFlowRowsInv; ph_lev[k] = 0; ph_units[k++] = F::kRowUnits;
+    for (int l = 0; l < levels; ++l) {
+      const int h = (N >> l) / 2, tb = ana_block<R, RIX_DICT_DB4>(h), nt = (h + tb - 1) / tb;
+      ph_kind[k] = kFlowAna; ph_lev[k] = l; ph_units[k++] = nt * nt;
+    }
+    int tot = 0;
+    for (int i = 0; i < k; ++i) tot += ph_units[i];
+    s_nph = k;
+    s_iter_units = tot;
+    s_ticket = atomicAdd(a.ticket, 1u);
+  }
+  if (threadIdx.x < nb)
+    step_constants<R, RIX_DICT_DB4>(a.f[threadIdx.x], &s_inv_l[threadIdx.x], &s_thr[threadIdx.x]);
+  __syncthreads();
+  const int nph = s_nph;
+  const int64_t nstage = 2 + (int64_t)f0.iters * nph;
+  const int64_t pro0 = (int64_t)nb * F::kColUnits, pro1 = pro0 + (int64_t)nb * F::kRowUnits;
+  const int64_t per_iter = (int64_t)nb * s_iter_units;
+  const int64_t total = pro1 + per_iter * f0.iters;
+  unsigned int t = s_ticket;
+  while ((int64_t)t < total) {
+    // the unit: stage, loop, unit index; the stage before it and its size
+    int64_t stg;
+    int b, u, kind = -1, lev = 0, it = 0, prev_units = 0;
+    if ((int64_t)t < pro0) {
+      stg = 0; b = (int)(t / F::kColUnits); u = (int)(t % F::kColUnits);
+    } else if ((int64_t)t < pro1) {
+      const int64_t r = t - pro0;
+      stg = 1; b = (int)(r / F::kRowUnits); u = (int)(r % F::kRowUnits); prev_units = F::kColUnits;
+    } else {
+      const int64_t r0 = t - pro1;
+      it = (int)(r0 / per_iter);
+      int64_t r = r0 - (int64_t)it * per_iter;
+      int k = 0;
+      while (r >= (int64_t)nb * ph_units[k]) { r -= (int64_t)nb * ph_units[k]; ++k; }
+      b = (int)(r / ph_units[k]);
+      u = (int)(r % ph_units[k]);
+      kind = ph_kind[k];
+      lev = ph_lev[k];
+      stg = 2 + (int64_t)it * nph + k;
+      prev_units = k > 0 ? ph_units[k - 1] : (it > 0 ? ph_units[nph - 1] : F::kRowUnits);
+    }
+    unsigned int* done_b = a.done + (int64_t)b * nstage;
+    if (stg > 0 && !flow_wait(done_b + stg - 1, (unsigned int)prev_units, f0.status)) return;
+    // the next ticket, taken while this unit runs
+    unsigned int next = 0;
+    if (threadIdx.x == 0) next = atomicAdd(a.ticket, 1u);
+    const FistaLoop<R>& f = a.f[b];
+    if (stg == 0) {
+      cols_inv_unit<R, LOGL>(f.c, f.tb, f.tw, s, s2, u);
+    } else if (stg == 1) {
+      rows_inv_unit<R, LOGL, false>(f.tb, f.d, a.gscale, nullptr, f.tw, s, s2, stage, u);
+    } else if (kind == kFlowChain) {
+      syn_chain_tile<R, T1>(f.y, levels, N, f.tmp, u % kChainNt, u / kChainNt, smem_raw, Db4Taps<R>{});
+    } else if (kind == kFlowRowsFwd) {
+      rows_fwd_syn_unit<R, LOGL>(levels > 1 ? f.tmp : f.y, f.y, f.ta, f.tw, s, s2, stage, u);
+    } else if (kind == kFlowCols) {
+      cols_conv_unit<R, LOGL>(f.ta, f.mx, f.tb, f.tw, s, s2, stage, u);
+    } else if (kind == kFlowRowsInv) {
+      rows_inv_unit<R, LOGL, true>(f.tb, f.g, a.gscale, f.d, f.tw, s, s2, stage, u);
+    } else {
+      const StepArgs<R> sa{f.alpha, f.y, s_inv_l[b], s_thr[b], s_inv_l[b] != R(0), a.mom[it]};
+      analysis_unit<R, RIX_DICT_DB4, N>(f, lev, u, sa, smem_raw, a.taps);
+    }
+    flow_done(done_b + stg);
+    if (threadIdx.x == 0) s_ticket = next;
+    __syncthreads();
+    t = s_ticket;
+  }
+}
+
+// FISTA's momentum per iteration: t_{k+1} = (1 + sqrt(1 + 4 t_k^2)) / 2,
+// momentum (t_k - 1) / t_{k+1}, each operation rounded on its own
+template <typename R>
+__global__ void k_mom_table(int iters, R* mom) {
+  double t = 1.0;
+  for (int it = 0; it < iters; ++it) {
+    const double tn = __dmul_rn(0.5, __dadd_rn(1.0, __dsqrt_rn(__dadd_rn(1.0, __dmul_rn(__dmul_rn(4.0, t), t)))));
+    mom[it] = (R)__ddiv_rn(__dadd_rn(t, -1.0), tn);
+    t = tn;
+  }
+}
+
 template <typename R, int LOGL, int DICT>
 int launch_fista_loop(const Ctx* ctx, const FistaLoop<R>* f, int nb, cudaStream_t st) {
   using F = FistaShape<R, LOGL, DICT>;
@@ -662,6 +828,47 @@ int launch_fista_loop(const Ctx* ctx, const FistaLoop<R>* f, int nb, cudaStream_
       const int k = daubechies_lowpass(m + 1, h);
       if (k != 2 * (m + 1)) return set_error(RIX_EINVAL, "daubechies filter %d", m + 1);
       for (int i = 0; i < 16; ++i) args.taps[m][i] = i < k ? (R)h[i] : R(0);
+    }
+  }
+  if constexpr (DICT == RIX_DICT_DB4) {
+    if (nb > 1) {
+      // several loops (Db4): the dataflow schedule instead of grid barriers
+      auto fk = k_fista_flow<R, LOGL>;
+      RIX_CUDA(cudaFuncSetAttribute(fk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      int fper = 0;
+      RIX_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fper, fk, kFftThreads, smem));
+      if (fper < 1) return set_error(RIX_EINVAL, "FISTA loop does not fit on an SM (%zu B shared)", smem);
+      const int fblk = ctx->num_sms * std::min(fper, 2);
+      const int levels = f[0].levels;
+      const int64_t nph = (levels > 1 ? 1 : 0) + 3 + levels;
+      const int64_t nctl = 1 + (int64_t)nb * (2 + (int64_t)f[0].iters * nph);
+      unsigned int* ctl = nullptr;
+      R* mom = nullptr;
+      RIX_CUDA(cudaMallocAsync((void**)&ctl, (size_t)nctl * sizeof(unsigned int), st));
+      if (cudaMallocAsync((void**)&mom, (size_t)std::max(f[0].iters, 1) * sizeof(R), st) != cudaSuccess) {
+        cudaFreeAsync(ctl, st);
+        return set_error(RIX_ENOMEM, "FISTA schedule tables");
+      }
+      int rc = RIX_OK;
+      if (cudaMemsetAsync(ctl, 0, (size_t)nctl * sizeof(unsigned int), st) != cudaSuccess) {
+        rc = set_error(RIX_ECUDA, "FISTA schedule reset");
+      } else {
+        ::rix::note_launch();
+        k_mom_table<R><<<1, 1, 0, st>>>(f[0].iters, mom);
+        args.ticket = ctl;
+        args.done = ctl + 1;
+        args.mom = mom;
+        void* params[] = {&args};
+        ::rix::note_launch();
+        timing_mark(kTimeMinorLoop, st, true);
+        const cudaError_t e =
+            cudaLaunchCooperativeKernel((const void*)fk, dim3(fblk), dim3(kFftThreads), params, smem, st);
+        timing_mark(kTimeMinorLoop, st, false);
+        if (e != cudaSuccess) rc = set_error(RIX_ECUDA, "FISTA loop launch: %s", cudaGetErrorString(e));
+      }
+      cudaFreeAsync(ctl, st);
+      cudaFreeAsync(mom, st);
+      return rc;
     }
   }
   RIX_CUDA(cudaMemsetAsync(f[0].barrier, 0, sizeof(unsigned int), st));
