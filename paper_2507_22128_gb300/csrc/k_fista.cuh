@@ -2,10 +2,12 @@
 // persistent cooperative kernel per call, compiled for each transform length
 // 2N and dictionary.
 //
-// Every iteration is a chain of grid-wide phases separated by a bounded grid
-// barrier:
-//   synthesis   x = W y, one phase per level, coarsest first (with Db4 the
-//               finest level runs inside the row phase, rows_fwd_syn_unit);
+// Every iteration is a chain of phases; k_fista_loop separates them by a
+// bounded grid barrier, k_fista_flow (a batch of Db4 loops) by per-loop
+// stage counters in a dataflow schedule:
+//   synthesis   x = W y, coarsest level first: with Db4, levels levels-1 .. 1
+//               in one phase (syn_chain_tile) and the finest inside the row
+//               phase (rows_fwd_syn_unit); otherwise one phase per level;
 //   rows        F of the rows of pad(x), two real rows per complex transform,
 //               window columns k_u in [-N, 0] written transposed (ta);
 //   columns     per window column: F, Mx X, F^-1, crop  (ta -> tb; tb in

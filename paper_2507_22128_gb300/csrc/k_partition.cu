@@ -567,10 +567,7 @@ int radix_sort_u32(uint32_t* keys, uint32_t* vals, uint32_t* keys_tmp, uint32_t*
   return radix_sort_impl<uint32_t, true>(keys, vals, keys_tmp, vals_tmp, n, bits, st, in_tmp);
 }
 
-int radix_sort_u64_keys(uint64_t* keys, uint64_t* keys_tmp, int64_t n, int bits, cudaStream_t st,
-                        bool* in_tmp) {
-  return radix_sort_impl<uint64_t, false>(keys, nullptr, keys_tmp, nullptr, n, bits, st, in_tmp);
-}
+
 
 static int grid_blocks(const Ctx* ctx, int64_t n, int threads) {
   int64_t b = ceil_div(std::max<int64_t>(n, 1), threads);

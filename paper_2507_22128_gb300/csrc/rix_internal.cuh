@@ -176,8 +176,6 @@ int scan_exclusive_u32(const uint32_t* in, uint32_t* out, int64_t n, uint32_t* t
                        cudaStream_t st);
 int radix_sort_u32(uint32_t* keys, uint32_t* vals, uint32_t* keys_tmp, uint32_t* vals_tmp,
                    int64_t n, int bits, cudaStream_t st, bool* result_in_tmp);
-int radix_sort_u64_keys(uint64_t* keys, uint64_t* keys_tmp, int64_t n, int bits, cudaStream_t st,
-                        bool* result_in_tmp);
 
 // ---------------------------------------------------------------------------
 // job
