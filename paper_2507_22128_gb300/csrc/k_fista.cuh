@@ -740,9 +740,13 @@ __global__ void __launch_bounds__(kFftThreads, sizeof(R) == 4 && LOGL <= 12 ? 2 
   const int64_t pro0 = (int64_t)nb * F::kColUnits, pro1 = pro0 + (int64_t)nb * F::kRowUnits;
   const int64_t per_iter = (int64_t)nb * s_iter_units;
   const int64_t total = pro1 + per_iter * f0.iters;
-  unsigned int t = s_ticket;
-  while ((int64_t)t < total) {
-    // the unit: stage, loop, unit index; the stage before it and its size
+  // thread 0 decodes each ticket for the CTA: stage, loop, unit, phase kind
+  // and level, iteration, and the size of the stage before it
+  __shared__ long long u_stg;
+  __shared__ int u_b, u_u, u_kind, u_lev, u_it, u_prev, u_live;
+  auto decode = [&](unsigned int t) {
+    u_live = (int64_t)t < total;
+    if (!u_live) return;
     int64_t stg;
     int b, u, kind = -1, lev = 0, it = 0, prev_units = 0;
     if ((int64_t)t < pro0) {
@@ -763,6 +767,13 @@ __global__ void __launch_bounds__(kFftThreads, sizeof(R) == 4 && LOGL <= 12 ? 2 
       stg = 2 + (int64_t)it * nph + k;
       prev_units = k > 0 ? ph_units[k - 1] : (it > 0 ? ph_units[nph - 1] : F::kRowUnits);
     }
+    u_stg = stg; u_b = b; u_u = u; u_kind = kind; u_lev = lev; u_it = it; u_prev = prev_units;
+  };
+  if (threadIdx.x == 0) decode(s_ticket);
+  __syncthreads();
+  while (u_live) {
+    const int64_t stg = u_stg;
+    const int b = u_b, u = u_u, kind = u_kind, lev = u_lev, it = u_it, prev_units = u_prev;
     unsigned int* done_b = a.done + (int64_t)b * nstage;
     if (stg > 0 && !flow_wait(done_b + stg - 1, (unsigned int)prev_units, f0.status)) return;
     // the next ticket, taken while this unit runs
@@ -786,9 +797,8 @@ __global__ void __launch_bounds__(kFftThreads, sizeof(R) == 4 && LOGL <= 12 ? 2 
       analysis_unit<R, RIX_DICT_DB4, N>(f, lev, u, sa, smem_raw, a.taps);
     }
     flow_done(done_b + stg);
-    if (threadIdx.x == 0) s_ticket = next;
+    if (threadIdx.x == 0) decode(next);
     __syncthreads();
-    t = s_ticket;
   }
 }
 
