@@ -246,20 +246,26 @@ int inv_rows(const Ctx* ctx, const XformGeom& g0, const cplx<R>* T, R* img, doub
     return RIX_OK;
   }
   const int64_t n = (int64_t)g.M * g.M;
-  R* part = nullptr;
-  if (cudaMallocAsync((void**)&part, (size_t)G * n * sizeof(R), st) != cudaSuccess)
+  // the group images, released (stream-ordered) on every way out
+  struct StreamFree {
+    void* p = nullptr;
+    cudaStream_t s;
+    ~StreamFree() {
+      if (p) cudaFreeAsync(p, s);
+    }
+  } part{nullptr, st};
+  if (cudaMallocAsync(&part.p, (size_t)G * n * sizeof(R), st) != cudaSuccess) {
+    part.p = nullptr;
     return set_error(RIX_ENOMEM, "plane-group images (%zu bytes)", (size_t)G * n * sizeof(R));
+  }
+  R* parts = static_cast<R*>(part.p);
   g.pg = P / G;
-  int rc = RIX_OK;
-  do {
-    RIX_FFT_LAUNCH(k_inv_rows, g.M, G, T, part, scale, 0, twiddles<R>(ctx));
-    ::rix::note_launch();
-    k_sum_groups<R><<<(int)std::min<int64_t>(ceil_div(n, 256), (int64_t)ctx->num_sms * 8), 256, 0, st>>>(
-        img, part, G, n, accumulate);
-    if (cudaGetLastError() != cudaSuccess) rc = set_error(RIX_ECUDA, "group sum launch");
-  } while (0);
-  cudaFreeAsync(part, st);
-  return rc;
+  RIX_FFT_LAUNCH(k_inv_rows, g.M, G, T, parts, scale, 0, twiddles<R>(ctx));
+  ::rix::note_launch();
+  k_sum_groups<R><<<(int)std::min<int64_t>(ceil_div(n, 256), (int64_t)ctx->num_sms * 8), 256, 0, st>>>(
+      img, parts, G, n, accumulate);
+  if (cudaGetLastError() != cudaSuccess) return set_error(RIX_ECUDA, "group sum launch");
+  return RIX_OK;
 }
 
 #define RIX_FFT_INST(R)                                                                                  \
