@@ -253,9 +253,12 @@ int rix_minor_cycle_fista(rix_job_t job, int part, const rix_fista_params* param
  * terms) run on a stream the job owns, after the caller's work on `stream`
  * and after that partition's own major cycle and the other partitions'
  * previous minor cycles, whatever streams those ran on; the loop runs on
- * `stream`, which on return waits for all of it.  The loops of the batch
- * advance together, so every phase of an iteration serves all of them with
- * one grid barrier. */
+ * `stream`, which on return waits for all of it.  With the Db4 dictionary
+ * the loops of the batch run as a dataflow (each phase of a loop waits only
+ * for the previous phase of the same loop, so one loop's phase ends are
+ * filled with the others' work); with the concatenated dictionary they
+ * advance together, one grid barrier per phase serving all of them.  Every
+ * device-side wait is bounded (RIX_ETIMEOUT at rix_job_sync). */
 int rix_minor_cycle_fista_batch(rix_job_t job, int n_parts, const int32_t* parts, const rix_fista_params* params,
                                 rix_stream_t stream);
 
