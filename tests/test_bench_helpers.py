@@ -1,0 +1,90 @@
+"""Host-side helpers of bench.py that decide what a run reports: the clock
+summary (a run whose samples show a thermal or hardware slowdown must say
+so), the gridder's traffic figure (only for the workload and source it was
+measured on) and the roofline arithmetic.  CPU only."""
+import hashlib
+import os
+import sys
+import types
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+
+@pytest.fixture(scope="module")
+def bench():
+    pytest.importorskip("torch")
+    import bench as b
+    return b
+
+
+def _line(sm, mx, reasons=()):
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    flags = ["Active" if n in reasons else "Not Active" for n in names]
+    return ", ".join(["0", str(sm), str(mx), "900.5", "0x0"] + flags)
+
+
+def test_clock_summary_median_max_and_reasons(bench):
+    cs = bench.ClockSampler(0)
+    cs.lines = [_line(2070, 2070), _line(1900, 2070, ("sw_power_cap",)), _line(2070, 2070),
+                "garbage line", _line(2000, 2070, ("hw_thermal_slowdown",))]
+    s = cs.summary()
+    assert s["samples"] == 4
+    assert s["sm_mhz"] == 2035.0            # median of 2070, 1900, 2070, 2000
+    assert s["sm_max_mhz"] == 2070.0
+    assert s["reasons"] == ["hw_thermal_slowdown", "sw_power_cap"]
+
+
+def test_clock_summary_unsampled(bench):
+    cs = bench.ClockSampler(0)
+    cs.lines = []
+    assert cs.summary()["reasons"] == ["unsampled"]
+
+
+def _args(**kw):
+    a = dict(fp64=False, n=1024, n_times=1000, cycles=10, steps=5)
+    a.update(kw)
+    return types.SimpleNamespace(**a)
+
+
+def test_tiles_traffic_only_for_the_measured_source_and_workload(bench):
+    src = os.path.join(ROOT, "paper_2507_22128_gb300", "csrc", "k_grid.cu")
+    with open(src, "rb") as f:
+        sha = hashlib.sha1(f.read()).hexdigest()
+    t = bench.TILES_TRAFFIC
+    got = bench.tiles_traffic(_args())
+    if sha != t["k_grid_sha1"]:
+        assert got is None
+    else:
+        # ten residual launches per partition and one PSF launch each
+        want = (10 * sum(t["resid"]) + sum(t["psf"])) / 22
+        assert got == pytest.approx(want)
+    assert bench.tiles_traffic(_args(fp64=True)) is None
+    assert bench.tiles_traffic(_args(n=512)) is None
+    assert bench.tiles_traffic(_args(n_times=300)) is None
+
+
+def test_roofline_arithmetic(bench, monkeypatch):
+    monkeypatch.setattr(bench, "measured_peaks", lambda: ({"sm_max_mhz": 2000.0, "hbm_gbs": 5000.0}, "measured"))
+    st = {"window_size": [100, 200]}
+    a = _args(steps=1, cycles=2)
+    r = bench.roofline_tiles(tiles_ms=4.0, tiles_n=4, st=st, a=a, entries_timed=1_000_000)
+    peak = 152 * 128 * 2 * 2000e6 / 1e12
+    assert r["peak"] == pytest.approx(peak)
+    assert r["achieved"] == pytest.approx(4096.0 * 1e6 / 4e-3 / 1e12)
+    assert r["frac"] == pytest.approx(r["achieved"] / peak)
+    ent_b = (24.0 / 4 + 8 + 4 + 4) * 1e6
+    plane_b = 1 * 2 * (2 * 8.0 * 16 * (100 ** 2 + 200 ** 2))
+    assert r["hbm"]["algorithmic_bytes_per_launch"] == pytest.approx((ent_b + plane_b) / 4)
+    assert r["hbm"]["frac"] == pytest.approx((ent_b + plane_b) / 4e-3 / 1e9 / 5000.0)
+    assert bench.roofline_tiles(0.0, 4, st, a, 1) is None
+    assert bench.roofline_tiles(4.0, 0, st, a, 1) is None
+
+
+def test_whole_job_value_is_the_aggregate_over_ranks(bench):
+    # every rank processes the same units per step: the whole job's rate
+    # scales with the ranks over the slowest rank's time
+    assert bench.whole_job_value(82_466_880, 1, 140.0) == pytest.approx(82_466_880 / 0.140 / 1e6)
+    assert bench.whole_job_value(1e6, 4, 10.0) == pytest.approx(4 * 1e6 / 0.010 / 1e6)
