@@ -131,9 +131,9 @@ class Reconstruction:
         order the exchange with the other partitions.  With `batch`, FISTA minor
         cycles of a cycle run together (one loop launch for all partitions) on
         the first partition's stream; the library starts each partition's
-        preparation as soon as that partition's major cycle is done (the
-        default: one grid barrier per phase for all loops, two CTAs per SM).
-        Without it every minor cycle runs on its partition's stream.  `stream`
+        preparation as soon as that partition's major cycle is done and runs
+        the loops as one dataflow-scheduled launch (the default).  Without it
+        every minor cycle runs on its partition's stream.  `stream`
         waits for all."""
         if self.n_part == 1:
             for _ in range(n_major):
