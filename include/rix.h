@@ -292,18 +292,30 @@ int rix_combine(rix_job_t job, void* image_out, rix_stream_t stream);
  * partition's w-planes and transpose buffer live in one scratch area of
  * RIX_GRID_NOALLOC_MAX_BYTES compiled into the library as a device array:
  * every GPU that loads the library holds it until the process exits.  A
- * partition needing more (n_wplanes * S * (S + N) * 8 bytes, S = its uv
- * window side from rix_job_get_stats) is rejected with RIX_EINVAL.  The call
- * allocates no device memory; it zeroes the part of the scratch it
- * accumulates into, so each call starts clean, but all calls share the one
- * scratch: calls whose GPU work overlaps in time (other streams, other
- * threads, other jobs) race and corrupt each other's results.  The first
- * call on a device looks up the scratch's device address (once per device,
- * with that device current); make that first call before any stream
- * capture.  The job itself (rix_job_create, rix_set_uv_partition) is set up
- * beforehand as usual. */
+ * partition needing more (max(n_wplanes, 1) * S * (S + N) * 8 bytes, S = its
+ * uv window side from rix_job_get_stats) is rejected with RIX_EINVAL; the
+ * scratch left over holds the plane-group images of the inverse transform
+ * (fewer groups, down to one, when little is left: the result is the same).
+ * The call allocates no device memory (rix_device_allocations does not move
+ * across it); it zeroes the part of the scratch it accumulates into, so each
+ * call starts clean, but all calls share the one scratch: calls whose GPU
+ * work overlaps in time (other streams, other threads, other jobs) race and
+ * corrupt each other's results.  The first call on a device looks up the
+ * scratch's device address (once per device, with that device current) and
+ * keeps it for the life of the process, which assumes the device's primary
+ * context is never reset (no cudaDeviceReset before a later call); make that
+ * first call before any stream capture.  The call runs on the job's device
+ * and leaves the caller's current device as it found it.  It records
+ * `stream` with the job, so rix_job_destroy waits for its work.  The job
+ * itself (rix_job_create, rix_set_uv_partition) is set up beforehand as
+ * usual. */
 #define RIX_GRID_NOALLOC_MAX_BYTES (32u << 20)
 int rix_grid_noalloc(rix_job_t job, int part, const void* vis, void* image_out, rix_stream_t stream);
+
+/* Number of device allocations the library has made in this process (every
+ * one is a stream-ordered pool allocation; a diagnostic: the difference
+ * across a call sequence is that sequence's allocation count). */
+uint64_t rix_device_allocations(void);
 
 /* Thread-local message of the last failed call on this thread. */
 const char* rix_last_error(void);

@@ -209,18 +209,16 @@ int conv_cols(const Ctx* ctx, const XformGeom& g, const cplx<R>* Tin, int op, co
   return RIX_OK;
 }
 
+// The planes of one row batch are summed by one CTA.  With many planes and
+// few row batches the grid ends in a nearly empty wave; split the planes into
+// G groups (grid rows) when that takes fewer plane-transforms per SM slot,
+// each group summing into its own image, and add the G images after.  At most
+// max_groups groups (a divisor of the plane count).
 template <typename R>
-int inv_rows(const Ctx* ctx, const XformGeom& g0, const cplx<R>* T, R* img, double scale, int accumulate,
-             cudaStream_t st) {
-  RIX_TRY(check_geom<R>(g0));
-  XformGeom g = g0;
-  // The planes of one row batch are summed by one CTA.  With many planes and
-  // few row batches the grid ends in a nearly empty wave; split the planes
-  // into G groups (grid rows) when that takes fewer plane-transforms per SM
-  // slot, each group summing into its own image, and add the G images after.
+int inv_rows_groups(const Ctx* ctx, const XformGeom& g, int max_groups) {
   const int P = g.nplanes;
   int G = 1;
-  if (P > 1) {
+  if (P > 1 && max_groups > 1) {
     const int V = use_inplace<R>(g.L) ? Vpt<R>::kLarge : kPingPongVals<R>;
     const int B = batch_for<R>(ctx, V, g.L, g.M, 1);
     const size_t sm = (use_inplace<R>(g.L) ? 1 : 2) * (size_t)B * padded_len(g.L) * sizeof(cplx<R>);
@@ -235,18 +233,30 @@ int inv_rows(const Ctx* ctx, const XformGeom& g0, const cplx<R>* T, R* img, doub
     const int64_t slots = (int64_t)ctx->num_sms * std::max(per_sm, 1);
     const int64_t rowb = ceil_div(g.M, B);
     double best = 1e300;
-    for (int c = 1; c <= P && c <= 16; c *= 2) {
+    for (int c = 1; c <= P && c <= 16 && c <= max_groups; c *= 2) {
       if (P % c) continue;
       const double cost = (double)ceil_div(rowb * c, slots) * (P / c) + 0.1 * c;   // + the group sum
       if (cost < best) { best = cost; G = c; }
     }
   }
+  return G;
+}
+
+template <typename R>
+int inv_rows(const Ctx* ctx, const XformGeom& g0, const cplx<R>* T, R* img, double scale, int accumulate,
+             cudaStream_t st, R* group_buf, int max_groups) {
+  RIX_TRY(check_geom<R>(g0));
+  XformGeom g = g0;
+  const int P = g.nplanes;
+  const int G = inv_rows_groups<R>(ctx, g, max_groups < 0 ? 16 : max_groups);
+  if (G < 0) return G;
   if (G == 1) {
     RIX_FFT_LAUNCH(k_inv_rows, g.M, 1, T, img, scale, accumulate, twiddles<R>(ctx));
     return RIX_OK;
   }
   const int64_t n = (int64_t)g.M * g.M;
-  // the group images, released (stream-ordered) on every way out
+  // the group images: the caller's buffer, else a stream-ordered temporary
+  // released on every way out
   struct StreamFree {
     void* p = nullptr;
     cudaStream_t s;
@@ -254,11 +264,15 @@ int inv_rows(const Ctx* ctx, const XformGeom& g0, const cplx<R>* T, R* img, doub
       if (p) cudaFreeAsync(p, s);
     }
   } part{nullptr, st};
-  if (cudaMallocAsync(&part.p, (size_t)G * n * sizeof(R), st) != cudaSuccess) {
-    part.p = nullptr;
-    return set_error(RIX_ENOMEM, "plane-group images (%zu bytes)", (size_t)G * n * sizeof(R));
+  R* parts = group_buf;
+  if (!parts) {
+    if (malloc_async(&part.p, (size_t)G * n * sizeof(R), st) != cudaSuccess) {
+      part.p = nullptr;
+      cudaGetLastError();
+      return set_error(RIX_ENOMEM, "plane-group images (%zu bytes)", (size_t)G * n * sizeof(R));
+    }
+    parts = static_cast<R*>(part.p);
   }
-  R* parts = static_cast<R*>(part.p);
   g.pg = P / G;
   RIX_FFT_LAUNCH(k_inv_rows, g.M, G, T, parts, scale, 0, twiddles<R>(ctx));
   ::rix::note_launch();
@@ -275,7 +289,8 @@ int inv_rows(const Ctx* ctx, const XformGeom& g0, const cplx<R>* T, R* img, doub
                            cplx<R>*, cudaStream_t);                                                      \
   template int conv_cols<R>(const Ctx*, const XformGeom&, const cplx<R>*, int, const void*, const void*,  \
                             cplx<R>*, cudaStream_t);                                                     \
-  template int inv_rows<R>(const Ctx*, const XformGeom&, const cplx<R>*, R*, double, int, cudaStream_t);    \
+  template int inv_rows<R>(const Ctx*, const XformGeom&, const cplx<R>*, R*, double, int, cudaStream_t, R*, int); \
+  template int inv_rows_groups<R>(const Ctx*, const XformGeom&, int);                                     \
   template int build_screen_table<R>(const Ctx*, const XformGeom&, cplx<R>*, cudaStream_t);
 RIX_FFT_INST(float)
 RIX_FFT_INST(double)

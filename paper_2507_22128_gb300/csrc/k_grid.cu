@@ -161,7 +161,7 @@ int build_correction(Job* job, int M, int ng, DevBuf& corr, DevBuf& nm1, cudaStr
   RIX_TRY(corr.alloc(job->ctx, (size_t)M * M * sizeof(R)));
   if (ws) RIX_TRY(nm1.alloc(job->ctx, (size_t)M * M * sizeof(double)));
   double* p1d = nullptr;
-  RIX_CUDA(cudaMallocAsync((void**)&p1d, M * sizeof(double), st));
+  RIX_CUDA(::rix::malloc_async((void**)&p1d, M * sizeof(double), st));
   RIX_CUDA(cudaMemcpyAsync(p1d, p1.data(), M * sizeof(double), cudaMemcpyHostToDevice, st));
   ca.p1 = p1d;
   const int64_t tot = (int64_t)M * M;
@@ -769,14 +769,19 @@ int image_to_planes(Job* job, Part& pt, const R* image, cudaStream_t st) {
   return RIX_OK;
 }
 
-// residual planes -> image (scaled by 1 / W_p)
+// residual planes -> image (scaled by 1 / W_p); the plane-group images of the
+// inverse row pass are the partition's own, allocated at the first call
 template <typename R>
 int planes_to_image(Job* job, Part& pt, R* image, cudaStream_t st) {
   const XformGeom g = plane_geom(job, pt, false);
   RIX_TRY(inv_cols<R>(job->ctx, g, pt.resid_planes.as<cplx<R>>(), kOpNone, nullptr, nullptr,
                       pt.tbuf.as<cplx<R>>(), st));
   const double sc = pt.wsum > 0.0 ? 1.0 / pt.wsum : 0.0;
-  RIX_TRY(inv_rows<R>(job->ctx, g, pt.tbuf.as<cplx<R>>(), image, sc, 0, st));
+  const int G = inv_rows_groups<R>(job->ctx, g, 16);
+  if (G < 0) return G;
+  const size_t gb = (size_t)G * g.M * g.M * sizeof(R);
+  if (G > 1 && pt.groups.bytes < gb) RIX_TRY(pt.groups.alloc(job->ctx, gb));
+  RIX_TRY(inv_rows<R>(job->ctx, g, pt.tbuf.as<cplx<R>>(), image, sc, 0, st, pt.groups.as<R>(), G));
   return RIX_OK;
 }
 
@@ -869,8 +874,8 @@ int op_psf(Job* job, int p, cudaStream_t st) {
   cplx<R>* pp = nullptr;
   cplx<R>* tt = nullptr;
   EntryGeom<R>* pg = nullptr;
-  RIX_CUDA(cudaMallocAsync(&pp, planes * sizeof(cplx<R>), st));
-  if (cudaMallocAsync(&tt, tb * sizeof(cplx<R>), st) != cudaSuccess) {
+  RIX_CUDA(::rix::malloc_async(&pp, planes * sizeof(cplx<R>), st));
+  if (::rix::malloc_async(&tt, tb * sizeof(cplx<R>), st) != cudaSuccess) {
     cudaFreeAsync(pp, st);
     return set_error(RIX_ENOMEM, "PSF transpose buffer");
   }
@@ -885,7 +890,7 @@ int op_psf(Job* job, int p, cudaStream_t st) {
     a.out = pp;
     // the partition's entries' geometry on the 2N grid, in FP64 (one thread
     // per entry), for the one PSF launch
-    if (cudaMallocAsync(&pg, (size_t)pt.ent_count * sizeof(EntryGeom<R>), st) != cudaSuccess) {
+    if (::rix::malloc_async(&pg, (size_t)pt.ent_count * sizeof(EntryGeom<R>), st) != cudaSuccess) {
       rc = set_error(RIX_ENOMEM, "PSF entry geometry");
       break;
     }
@@ -916,9 +921,12 @@ int op_psf(Job* job, int p, cudaStream_t st) {
   return rc;
 }
 
-// Gridding of partition p (as op_grid) with its w-planes and transpose buffer
-// in caller-provided device scratch instead of the job's own buffers; FP32
-// jobs.  Returns RIX_EINVAL when the scratch is too small.
+// Gridding of partition p (as op_grid) with its w-planes, transpose buffer
+// and the inverse row pass's plane-group images in caller-provided device
+// scratch instead of the job's own buffers; FP32 jobs.  Allocates nothing.
+// The plane groups take what the scratch has left after the planes and the
+// transpose buffer (one group, no group images, when nothing is left).
+// Returns RIX_EINVAL when the planes and transpose buffer do not fit.
 int op_grid_into_scratch(Job* job, int p, const float2* vis, float* image_out, float2* scratch,
                          size_t scratch_elems, cudaStream_t st) {
   Part& pt = job->part[p];
@@ -935,6 +943,9 @@ int op_grid_into_scratch(Job* job, int p, const float2* vis, float* image_out, f
                      (plane_elems + t_elems) * sizeof(float2), scratch_elems * sizeof(float2));
   float2* planes = scratch;
   float2* tbuf = scratch + plane_elems;
+  float* group_imgs = reinterpret_cast<float*>(scratch + plane_elems + t_elems);
+  const size_t left_floats = 2 * (scratch_elems - plane_elems - t_elems);
+  const int max_groups = (int)std::min<size_t>(16, left_floats / ((size_t)n * n));
   RIX_CUDA(cudaMemsetAsync(planes, 0, plane_elems * sizeof(float2), st));   // the sub-grids accumulate
   TileArgs a = base_args(job, pt);
   a.out = planes;
@@ -943,7 +954,7 @@ int op_grid_into_scratch(Job* job, int p, const float2* vis, float* image_out, f
   const XformGeom g = plane_geom(job, pt, false);
   RIX_TRY(inv_cols<float>(job->ctx, g, planes, kOpNone, nullptr, nullptr, tbuf, st));
   const double sc = pt.wsum > 0.0 ? 1.0 / pt.wsum : 0.0;
-  return inv_rows<float>(job->ctx, g, tbuf, image_out, sc, 0, st);
+  return inv_rows<float>(job->ctx, g, tbuf, image_out, sc, 0, st, group_imgs, std::max(max_groups, 1));
 }
 
 template <typename R>

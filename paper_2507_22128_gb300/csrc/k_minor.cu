@@ -576,8 +576,8 @@ int op_msclean(Job* job, int p, const rix_msclean_params* prm, R* delta_out, cud
   // scratch 2N x 2N image and [2N][2N] transpose buffer
   R* img2 = nullptr;
   cplx<R>* t2 = nullptr;
-  RIX_CUDA(cudaMallocAsync(&img2, tot * sizeof(R), st));
-  if (cudaMallocAsync(&t2, tot * sizeof(cplx<R>), st) != cudaSuccess) {
+  RIX_CUDA(::rix::malloc_async(&img2, tot * sizeof(R), st));
+  if (::rix::malloc_async(&t2, tot * sizeof(cplx<R>), st) != cudaSuccess) {
     cudaFreeAsync(img2, st);
     return set_error(RIX_ENOMEM, "ms-CLEAN scratch");
   }
@@ -794,7 +794,7 @@ int op_combine(Job* job, R* out, cudaStream_t st) {
   const R* ptrs[kMaxPart];
   for (int q = 0; q < job->n_part; ++q) ptrs[q] = job->part[q].model.as<R>();
   const R** dptrs = nullptr;
-  RIX_CUDA(cudaMallocAsync((void**)&dptrs, sizeof(ptrs), st));
+  RIX_CUDA(::rix::malloc_async((void**)&dptrs, sizeof(ptrs), st));
   RIX_CUDA(cudaMemcpyAsync(dptrs, ptrs, sizeof(ptrs), cudaMemcpyHostToDevice, st));
   ::rix::note_launch(); k_mean<R><<<blocks_for(job->ctx, npix), 256, 0, st>>>(out, dptrs, job->n_part, npix);
   cudaFreeAsync(dptrs, st);

@@ -30,7 +30,10 @@ std::mutex g_mu;
 float2* g_addr[kMaxDevices] = {};
 
 // Device address of the scratch on `device` (which must be current), looked
-// up once per device.
+// up once per device and kept for the life of the process.  The cache
+// assumes the device's primary context lives as long as the process: after a
+// cudaDeviceReset the cached address is stale, so a process that resets a
+// device must not call rix_grid_noalloc on it again.
 int scratch_address(int device, float2** out) {
   if (device < 0 || device >= kMaxDevices) return set_error(RIX_EINVAL, "device %d out of range", device);
   std::lock_guard<std::mutex> lk(g_mu);
@@ -56,17 +59,34 @@ namespace rix {
 Job* job_of(rix_job_t job);
 }
 
-extern "C" int rix_grid_noalloc(rix_job_t job, int part, const void* vis, void* image_out, rix_stream_t stream) {
+namespace {
+int grid_noalloc_impl(rix::Job* J, int part, const void* vis, void* image_out, cudaStream_t st) {
   using namespace rix;
-  if (!job) return set_error(RIX_EINVAL, "job is NULL");
-  Job* J = job_of(job);
   if (!J->partitioned) return set_error(RIX_ESTATE, "rix_set_uv_partition has not been called");
   if (part < 0 || part >= J->n_part) return set_error(RIX_EINVAL, "partition %d out of range", part);
   if (J->fp64) return set_error(RIX_EINVAL, "rix_grid_noalloc supports FP32 jobs only");
   if (!vis || !image_out) return set_error(RIX_EINVAL, "NULL vis or image_out");
-  RIX_CUDA(cudaSetDevice(J->ctx->device));
   float2* scratch = nullptr;
   RIX_TRY(scratch_address(J->ctx->device, &scratch));
-  return op_grid_into_scratch(J, part, static_cast<const float2*>(vis), static_cast<float*>(image_out), scratch,
-                              kNoAllocElems, (cudaStream_t)stream);
+  RIX_TRY(op_grid_into_scratch(J, part, static_cast<const float2*>(vis), static_cast<float*>(image_out), scratch,
+                               kNoAllocElems, st));
+  // rix_job_destroy waits for the streams the job's calls ran on
+  return note_stream(J, st);
+}
+}  // namespace
+
+extern "C" int rix_grid_noalloc(rix_job_t job, int part, const void* vis, void* image_out, rix_stream_t stream) {
+  using namespace rix;
+  if (!job) return set_error(RIX_EINVAL, "job is NULL");
+  Job* J = job_of(job);
+  // run on the job's device and give the caller back the device it had current
+  int prev = -1;
+  RIX_CUDA(cudaGetDevice(&prev));
+  if (prev != J->ctx->device) RIX_CUDA(cudaSetDevice(J->ctx->device));
+  const int rc = grid_noalloc_impl(J, part, vis, image_out, (cudaStream_t)stream);
+  if (prev != J->ctx->device) {
+    const cudaError_t e = cudaSetDevice(prev);
+    if (rc == RIX_OK && e != cudaSuccess) return set_error(RIX_ECUDA, "restoring device %d: %s", prev, cudaGetErrorString(e));
+  }
+  return rc;
 }

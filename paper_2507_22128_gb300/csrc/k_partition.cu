@@ -158,7 +158,7 @@ int radix_sort_impl(K* keys, uint32_t* vals, K* keys_tmp, uint32_t* vals_tmp, in
   const int nblocks = (int)ceil_div(n, kSortTile);
   const int64_t hn = (int64_t)256 * nblocks;
   uint32_t* hist = nullptr;
-  RIX_CUDA(cudaMallocAsync(&hist, 2 * hn * sizeof(uint32_t), st));
+  RIX_CUDA(::rix::malloc_async(&hist, 2 * hn * sizeof(uint32_t), st));
   K* a = keys; K* b = keys_tmp;
   uint32_t* va = vals; uint32_t* vb = vals_tmp;
   int rc = RIX_OK;
@@ -550,7 +550,7 @@ int scan_exclusive_u32(const uint32_t* in, uint32_t* out, int64_t n, uint32_t* t
     ::rix::note_launch(); k_scan_block<<<1, kScanThreads, 0, st>>>(in, out, n, nullptr);
   } else {
     uint32_t* sums = nullptr;
-    RIX_CUDA(cudaMallocAsync(&sums, 2 * nb * sizeof(uint32_t), st));
+    RIX_CUDA(::rix::malloc_async(&sums, 2 * nb * sizeof(uint32_t), st));
     ::rix::note_launch(); k_scan_block<<<(unsigned)nb, kScanThreads, 0, st>>>(in, out, n, sums);
     int rc = scan_exclusive_u32(sums, sums + nb, nb, nullptr, st);
     if (rc == RIX_OK) { ::rix::note_launch(); k_scan_add<<<(unsigned)nb, kScanThreads, 0, st>>>(out, n, sums + nb); }
@@ -622,7 +622,7 @@ int partition_job(Job* job, const double* uvw, int64_t nrow, const float* weight
     int64_t item_range[kMaxPart + 1];
   };
   Small* sm_d = nullptr;
-  RIX_CUDA(cudaMallocAsync(&sm_d, sizeof(Small), st));
+  RIX_CUDA(::rix::malloc_async(&sm_d, sizeof(Small), st));
   Small sm_h;
   std::memset(&sm_h, 0, sizeof(sm_h));
   sm_h.wmm[0] = ~0ull;
@@ -658,7 +658,7 @@ int partition_job(Job* job, const double* uvw, int64_t nrow, const float* weight
   if (job->desc.weighting == RIX_WEIGHT_UNIFORM && ns > 0) {
     const int n = job->desc.n;
     double* dens = nullptr;
-    if (cudaMallocAsync(&dens, (size_t)n * n * sizeof(double), st) != cudaSuccess)
+    if (::rix::malloc_async(&dens, (size_t)n * n * sizeof(double), st) != cudaSuccess)
       return fail(set_error(RIX_ENOMEM, "uniform weighting density"));
     const bool had = job->weight.p != nullptr;
     if (!had) {
@@ -686,8 +686,8 @@ int partition_job(Job* job, const double* uvw, int64_t nrow, const float* weight
     } else if (ns > 0) {
       uint64_t* rb = nullptr;
       SelectState* sel = nullptr;
-      if (cudaMallocAsync(&rb, ns * sizeof(uint64_t), st) != cudaSuccess ||
-          cudaMallocAsync(&sel, sizeof(SelectState), st) != cudaSuccess) {
+      if (::rix::malloc_async(&rb, ns * sizeof(uint64_t), st) != cudaSuccess ||
+          ::rix::malloc_async(&sel, sizeof(SelectState), st) != cudaSuccess) {
         if (rb) cudaFreeAsync(rb, st);
         return fail(set_error(RIX_ENOMEM, "radius select scratch"));
       }
@@ -717,8 +717,8 @@ int partition_job(Job* job, const double* uvw, int64_t nrow, const float* weight
   // --- classify -----------------------------------------------------------
   uint32_t* counts = nullptr;
   uint32_t* offs = nullptr;
-  if (cudaMallocAsync(&counts, std::max<int64_t>(ns, 1) * sizeof(uint32_t), st) != cudaSuccess ||
-      cudaMallocAsync(&offs, std::max<int64_t>(ns, 1) * sizeof(uint32_t), st) != cudaSuccess)
+  if (::rix::malloc_async(&counts, std::max<int64_t>(ns, 1) * sizeof(uint32_t), st) != cudaSuccess ||
+      ::rix::malloc_async(&offs, std::max<int64_t>(ns, 1) * sizeof(uint32_t), st) != cudaSuccess)
     return fail(set_error(RIX_ENOMEM, "classify scratch"));
   ClassifyOut co{mask_out, counts, sm_d->win, sm_d->part_count, sm_d->wsum, &sm_d->n_outside,
                  job->weight.as<float>()};
@@ -745,8 +745,8 @@ int partition_job(Job* job, const double* uvw, int64_t nrow, const float* weight
   RIX_TRY(job->keys.alloc(ctx, std::max<int64_t>(n_ent, 1) * sizeof(uint32_t)));
   RIX_TRY(job->samples.alloc(ctx, std::max<int64_t>(n_ent, 1) * sizeof(uint32_t)));
   uint32_t *kt = nullptr, *vt = nullptr;
-  if (cudaMallocAsync(&kt, std::max<int64_t>(n_ent, 1) * sizeof(uint32_t), st) != cudaSuccess ||
-      cudaMallocAsync(&vt, std::max<int64_t>(n_ent, 1) * sizeof(uint32_t), st) != cudaSuccess)
+  if (::rix::malloc_async(&kt, std::max<int64_t>(n_ent, 1) * sizeof(uint32_t), st) != cudaSuccess ||
+      ::rix::malloc_async(&vt, std::max<int64_t>(n_ent, 1) * sizeof(uint32_t), st) != cudaSuccess)
     return fail(set_error(RIX_ENOMEM, "sort scratch"));
   if (ns > 0) {
     ::rix::note_launch(); 
@@ -769,8 +769,8 @@ int partition_job(Job* job, const double* uvw, int64_t nrow, const float* weight
   int64_t n_items = 0;
   uint32_t *wa = nullptr, *wb = nullptr;
   if (n_ent > 0) {
-    if (cudaMallocAsync(&wa, n_ent * sizeof(uint32_t), st) != cudaSuccess ||
-        cudaMallocAsync(&wb, n_ent * sizeof(uint32_t), st) != cudaSuccess)
+    if (::rix::malloc_async(&wa, n_ent * sizeof(uint32_t), st) != cudaSuccess ||
+        ::rix::malloc_async(&wb, n_ent * sizeof(uint32_t), st) != cudaSuccess)
       return fail(set_error(RIX_ENOMEM, "work-item scratch"));
     const int eb = grid_blocks(ctx, n_ent, 256);
     ::rix::note_launch(); k_seg_flags<<<eb, 256, 0, st>>>(job->keys.as<uint32_t>(), n_ent, kt);

@@ -20,7 +20,7 @@ __global__ void k_missing_arrival(unsigned int* count, int* status, int* gave_up
 int selftest_barrier(Ctx* ctx, int* status_out, int* gave_up_out) {
   cudaStream_t st = ctx->mem_stream;
   int* words = nullptr;            // [0] arrival counter, [1] status, [2] CTAs that gave up
-  RIX_CUDA(cudaMallocAsync((void**)&words, 4 * sizeof(int), st));
+  RIX_CUDA(::rix::malloc_async((void**)&words, 4 * sizeof(int), st));
   int rc = RIX_OK;
   if (cudaMemsetAsync(words, 0, 4 * sizeof(int), st) != cudaSuccess) rc = set_error(RIX_ECUDA, "memset");
   if (rc == RIX_OK) {

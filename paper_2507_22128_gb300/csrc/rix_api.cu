@@ -38,6 +38,12 @@ static std::atomic<unsigned long long> g_launches{0};
 void note_launch(long long n) { g_launches.fetch_add((unsigned long long)n, std::memory_order_relaxed); }
 unsigned long long launch_count() { return g_launches.load(); }
 
+static std::atomic<unsigned long long> g_allocs{0};
+cudaError_t malloc_async(void** p, size_t bytes, cudaStream_t st) {
+  g_allocs.fetch_add(1, std::memory_order_relaxed);
+  return cudaMallocAsync(p, bytes, st);
+}
+
 // ---- opt-in kernel timing ----
 static std::atomic<bool> g_timing{false};
 static std::mutex g_tmu;
@@ -71,7 +77,7 @@ int DevBuf::alloc(Ctx* ctx, size_t nbytes) {
   if (p && bytes >= nbytes) return RIX_OK;   // reuse: re-partitioning a job keeps its buffers
   release();
   void* q = nullptr;
-  cudaError_t e = cudaMallocAsync(&q, nbytes, ctx->mem_stream);
+  cudaError_t e = ::rix::malloc_async(&q, nbytes, ctx->mem_stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->mem_stream);
   if (e != cudaSuccess) {
     cudaGetLastError();
@@ -194,6 +200,8 @@ extern "C" {
 const char* rix_last_error(void) { return rix::last_error(); }
 
 uint64_t rix_kernel_launches(void) { return rix::g_launches.load(); }
+
+uint64_t rix_device_allocations(void) { return rix::g_allocs.load(); }
 
 int rix_timing_enable(int on) {
   rix::g_timing.store(on != 0);

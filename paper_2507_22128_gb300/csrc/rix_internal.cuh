@@ -21,6 +21,13 @@ const char* last_error();
 // kernel nodes of replayed CUDA graphs
 void note_launch(long long n = 1);
 unsigned long long launch_count();
+// Every device allocation of the library (pooled, stream-ordered) goes
+// through malloc_async, which counts it (rix_device_allocations).
+cudaError_t malloc_async(void** p, size_t bytes, cudaStream_t st);
+template <typename T>
+cudaError_t malloc_async(T** p, size_t bytes, cudaStream_t st) {
+  return malloc_async(reinterpret_cast<void**>(p), bytes, st);
+}
 
 // Opt-in device timing of kernel classes (CUDA events recorded on the launch
 // stream around each launch; streams under capture are skipped).
@@ -150,9 +157,17 @@ int inv_cols(const Ctx* ctx, const XformGeom& g, const cplx<R>* spec, int op, co
 template <typename R>
 int conv_cols(const Ctx* ctx, const XformGeom& g, const cplx<R>* Tin, int op, const void* tab,
               const void* tab2, cplx<R>* Tout, cudaStream_t st);
+// Inverse row pass: img = (accumulate ? img : 0) + scale * the planes' sum.
+// With several planes it may split them into G groups (inv_rows_groups, at
+// most max_groups; -1 = the pass's own limit), each summed into an image of
+// group_buf (G * M * M reals) or, when group_buf is null, of a temporary
+// stream-ordered allocation.
 template <typename R>
 int inv_rows(const Ctx* ctx, const XformGeom& g, const cplx<R>* T, R* img, double scale,
-             int accumulate, cudaStream_t st);
+             int accumulate, cudaStream_t st, R* group_buf = nullptr, int max_groups = -1);
+// the number of plane groups inv_rows uses for g with at most max_groups
+template <typename R>
+int inv_rows_groups(const Ctx* ctx, const XformGeom& g, int max_groups);
 
 int fft_init_twiddles(Ctx* ctx);
 
@@ -194,6 +209,7 @@ struct Part {
   bool psf_ready = false;
   bool lambda_set = false;
   DevBuf model_planes, resid_planes, tbuf;  // [nw][S][S], [nw][S][S], [nw][S][N]
+  DevBuf groups;                            // plane-group images of the inverse row pass, [G][N][N]
   DevBuf model, resid, delta;               // N x N Real
   DevBuf outbox[2];                         // Phi_p^n by cycle parity
   DevBuf rho[kMaxPart];                     // rho_{q->p}, N x N

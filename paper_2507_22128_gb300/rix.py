@@ -90,6 +90,7 @@ def _load() -> C.CDLL:
         "rix_combine": (C.c_int, [vp, vp, vp]),
         "rix_last_error": (C.c_char_p, []),
         "rix_kernel_launches": (C.c_uint64, []),
+        "rix_device_allocations": (C.c_uint64, []),
         "rix_timing_enable": (C.c_int, [C.c_int]),
         "rix_timing_read": (C.c_int, [C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
         "rix_selftest_barrier_timeout": (C.c_int, [vp, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
@@ -110,7 +111,7 @@ EXPORTED = ("rix_create", "rix_destroy", "rix_job_workspace_bytes", "rix_job_cre
             "rix_minor_cycle_fista", "rix_get_components", "rix_get_model", "rix_combine", "rix_last_error",
             "rix_kernel_launches", "rix_timing_enable", "rix_timing_read", "rix_grid_noalloc",
             "rix_selftest_barrier_timeout", "rix_daubechies_lowpass", "rix_get_weights",
-            "rix_minor_cycle_fista_batch")
+            "rix_minor_cycle_fista_batch", "rix_device_allocations")
 
 
 def _check(rc: int):
@@ -290,6 +291,11 @@ def get_model(job, part, image_out, stream=None):
 
 def kernel_launches() -> int:
     return int(_lib.rix_kernel_launches())
+
+
+def device_allocations() -> int:
+    """Device allocations the library has made in this process."""
+    return int(_lib.rix_device_allocations())
 
 
 TIME_TILES, TIME_FFT, TIME_PARTITION, TIME_MINOR_LOOP = 0, 1, 2, 3
