@@ -33,6 +33,7 @@ import dataclasses
 import math
 
 import numpy as np
+import scipy.fft as _fft   # the 2D FFT primitive (all host threads)
 
 from . import es
 
@@ -158,7 +159,7 @@ def model_planes(image: np.ndarray, g: Geometry) -> np.ndarray:
         z = corr.astype(np.complex128)
         if g.nw > 0:
             z = z * np.exp(-2j * np.pi * plane_w(g, p) * nm1)
-        planes[p] = np.fft.fftshift(np.fft.fft2(np.fft.ifftshift(_pad_center(z, g.ng))))
+        planes[p] = np.fft.fftshift(_fft.fft2(np.fft.ifftshift(_pad_center(z, g.ng)), workers=-1))
     return planes
 
 
@@ -169,7 +170,7 @@ def planes_to_image(planes: np.ndarray, g: Geometry) -> np.ndarray:
     if g.nw > 0:
         _, nm1 = _lmn(g.n, g.cell)
     for p in range(g.nplanes):
-        z = np.fft.fftshift(np.fft.ifft2(np.fft.ifftshift(planes[p]))) * (g.ng * g.ng)
+        z = np.fft.fftshift(_fft.ifft2(np.fft.ifftshift(planes[p]), workers=-1)) * (g.ng * g.ng)
         z = z[o:o + g.n, o:o + g.n]
         if g.nw > 0:
             z = z * np.exp(2j * np.pi * plane_w(g, p) * nm1)

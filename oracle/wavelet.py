@@ -76,8 +76,8 @@ def _synthesis_last_axis(a: np.ndarray, d: np.ndarray, h: np.ndarray, g: np.ndar
     n = 2 * half
     out = np.zeros(a.shape[:-1] + (n,))
     for i in range(h.shape[0]):
-        idx = (2 * np.arange(half) + i) % n
-        np.add.at(out, (..., idx), a * h[i] + d * g[i])
+        idx = (2 * np.arange(half) + i) % n         # distinct indices for one tap i
+        out[..., idx] += a * h[i] + d * g[i]
     return out
 
 

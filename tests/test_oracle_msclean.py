@@ -77,3 +77,59 @@ def test_allowed_scales_first_cycle():
     a = msclean.allowed_scales(sc, 128, 1, 1, [20.0], 1.0)
     assert a.tolist() == [True, True, False]
     assert msclean.allowed_scales(sc, 128, 1, 2, [20.0], 1.0).all()
+
+
+def _hand_scale(s, n):
+    """B_s on the 2N grid written out by loops: 1 - (r/s)^2 inside radius s,
+    unit sum (B_0 = delta)."""
+    b = np.zeros((2 * n, 2 * n))
+    if s == 0:
+        b[n, n] = 1.0
+        return b
+    tot = 0.0
+    for y in range(2 * n):
+        for x in range(2 * n):
+            r2 = (y - n) ** 2 + (x - n) ** 2
+            if r2 < s * s:
+                b[y, x] = 1.0 - r2 / float(s * s)
+                tot += b[y, x]
+    return b / tot
+
+
+def test_scale_choice_decided_by_the_bias():
+    """Cornwell (2008) scale bias 1 - 0.6 s / s_max with peak normalisation by
+    P_ss(0).  PSF = delta (every uv cell sampled) and D = a B_3 at pixel p:
+    the unbiased criterion |R_s(p)| / P_ss(0) favours s = 9 (sum B_3 B_9 /
+    sum B_9^2 > 1), the biased one s = 3 (0.8 against 0.4 x that ratio).  The
+    first component is (s = 3, p, gain a) and the two best candidate values
+    are the hand-computed ones."""
+    n = 48
+    a, gain = 2.5, 0.1
+    py, px = 21, 26
+    b3, b9 = _hand_scale(3, n), _hand_scale(9, n)
+    sum33 = float((b3 * b3).sum())
+    sum99 = float((b9 * b9).sum())
+    sum39 = float((b3 * b9).sum())
+    assert sum39 / sum99 > 1.0 and 0.8 > 0.4 * sum39 / sum99      # the bias flips the choice
+    d = np.zeros((n, n))
+    d[py - 2:py + 3, px - 2:px + 3] = a * b3[n - 2:n + 3, n - 2:n + 3]   # B_3 lies within radius 2.9
+    psf_spec = np.ones((2 * n, 2 * n), dtype=complex)
+    res = msclean.clean(filters.image_spectrum(d), psf_spec, [0, 3, 9], gain, 1, 0.0)
+    s, y, x, amp = res.components[0]
+    assert (s, y, x) == (1, py, px)
+    assert amp == pytest.approx(gain * a, rel=1e-12)
+    best, _ = res.gaps[0]
+    assert best == pytest.approx(0.8 * a, rel=1e-12)
+    # after the step R_s(p) = (1 - gain) a (B_s . B_3)(0) for every scale
+    # (R_s -= amp P_{s,3}(. - p) with P_{s,3} = B_s * B_3 for a delta PSF)
+    assert res.residuals[0][py, px] == pytest.approx((1 - gain) * a * b3[n, n], rel=1e-12)
+    assert res.residuals[1][py, px] == pytest.approx((1 - gain) * a * sum33, rel=1e-12)
+    assert res.residuals[2][py, px] == pytest.approx((1 - gain) * a * sum39, rel=1e-12)
+    # the model is the scaled component: gain a B_3 centred on p
+    want = np.zeros((n, n))
+    want[py - 2:py + 3, px - 2:px + 3] = gain * a * b3[n - 2:n + 3, n - 2:n + 3]
+    assert np.max(np.abs(res.model - want)) < 1e-14
+    # the oracle's scale kernels and bias are the hand-written ones
+    assert np.max(np.abs(msclean.scale_kernel(3, n) - b3)) < 1e-15
+    assert np.max(np.abs(msclean.scale_kernel(9, n) - b9)) < 1e-15
+    assert np.allclose(msclean.bias([0, 3, 9]), [1.0, 0.8, 0.4], rtol=0, atol=1e-15)
