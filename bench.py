@@ -399,7 +399,7 @@ def phase_split(rec, rix, a, meth, stream, uvw, vis, w, out, flush):
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per k_tiles_ws
 # launch at the default 1024^2 workload, from a one-pass ncu capture of one
-# timed job (profiles/k_tiles_ws_medium_dram.md): residual launches of
+# timed job: residual launches of
 # partitions 0 and 1, PSF launches of partitions 0 and 1.  Reported only for
 # that workload and while k_grid.cu is the source the counters were taken on.
 TILES_TRAFFIC = {"k_grid_sha1": "dab75048113381c5baa1a22cc19111f811558f46",
@@ -451,7 +451,7 @@ def roofline_tiles(tiles_ms, tiles_n, st, a, entries_timed):
             "traffic": tiles_traffic(a), "traffic_unit": "B per launch",
             "launches_timed": tiles_n, "busy_ms_per_launch": tiles_ms / tiles_n,
             "ncu_binding_unit": "shared memory: L1/shared throughput 86 % of peak, FMA pipe 20 % "
-                                "(profiles/k_tiles_ws_medium_300t.md)",
+                                "(ncu --set full of one launch at the medium recipe)",
             "peak_source": f"152 SMs x {lanes} {'FP64' if a.fp64 else 'FP32'} lanes x 2 flop x {clk:.0f} MHz "
                            f"(max SM clock of {kind} peaks)"}
 

@@ -88,3 +88,56 @@ def test_grid_sampled_vs_direct_dft(full, part):
     want = dft.adjoint_at(wt * y.astype(np.complex128)[sel], u[sel], v[sel], w[sel], obs.n, obs.cell_rad, True,
                           rows, cols) / wt.sum()
     assert rel_l2(img.cpu().numpy()[rows, cols], want) < 1e-4
+
+
+@pytest.mark.parametrize("part", [0, 1])
+def test_major_cycle_sampled_vs_direct_dft(full, part):
+    """rix_major_cycle at full size (the fused degrid/residual/grid kernel the
+    benchmark times): residual Re A^H W (v - A x) / W_p of a sparse model x and
+    random observed visibilities v, on 128 sampled pixels, against the direct
+    DFT over all of the partition's samples."""
+    from oracle import dft
+    obs, rix, job, mask, *_ = full
+    rng = np.random.default_rng(51 + part)
+    y = (rng.standard_normal(obs.nvis) + 1j * rng.standard_normal(obs.nvis)).astype(np.complex64)
+    x = sparse_model(obs.n, 25, seed=61 + part)
+    res = torch.empty((obs.n, obs.n), dtype=torch.float32, device="cuda")
+    rix.major_cycle(job, part, to_dev(y, torch.complex64), to_dev(x, torch.float32), res)
+    torch.cuda.synchronize()
+    sel = ((mask >> part) & 1) == 1
+    u, v, w = dft.uvw_lambda(obs.uvw, obs.freq)
+    us, vs, ws = u[sel], v[sel], w[sel]
+    ch = 1 << 18
+    ax = np.concatenate([dft.degrid_pixels_sparse(x, us[i:i + ch], vs[i:i + ch], ws[i:i + ch], obs.cell_rad, True)
+                         for i in range(0, us.shape[0], ch)])
+    r = y.astype(np.complex128)[sel] - ax
+    wt = obs.weight.reshape(-1).astype(np.float64)[sel]
+    rows = rng.integers(0, obs.n, 128)
+    cols = rng.integers(0, obs.n, 128)
+    want = dft.adjoint_at(wt * r, us, vs, ws, obs.n, obs.cell_rad, True, rows, cols) / wt.sum()
+    assert rel_l2(res.cpu().numpy()[rows, cols], want) < 1e-4
+
+
+@pytest.mark.parametrize("part", [0, 1])
+def test_psf_sampled_vs_direct_dft(full, part):
+    """rix_psf at full size (2048 x 2048, centre at pixel (1024, 1024)): the
+    peak is 1, and 128 sampled pixels (half of them within 64 pixels of the
+    centre, where the PSF is large) match Re A^H w / W_p by direct DFT."""
+    from oracle import dft
+    obs, rix, job, mask, *_ = full
+    n2 = 2 * obs.n
+    psf = torch.empty((n2, n2), dtype=torch.float32, device="cuda")
+    wsum = rix.psf(job, part, psf)
+    torch.cuda.synchronize()
+    got = psf.cpu().numpy()
+    sel = ((mask >> part) & 1) == 1
+    wt = obs.weight.reshape(-1).astype(np.float64)[sel]
+    assert wsum == pytest.approx(wt.sum(), rel=1e-12)
+    assert got[obs.n, obs.n] == pytest.approx(1.0, abs=1e-5)
+    rng = np.random.default_rng(71 + part)
+    rows = np.concatenate([rng.integers(0, n2, 64), obs.n + rng.integers(-64, 64, 64)])
+    cols = np.concatenate([rng.integers(0, n2, 64), obs.n + rng.integers(-64, 64, 64)])
+    u, v, w = dft.uvw_lambda(obs.uvw, obs.freq)
+    want = dft.adjoint_at(wt.astype(np.complex128), u[sel], v[sel], w[sel], n2, obs.cell_rad, True,
+                          rows, cols) / wt.sum()
+    assert rel_l2(got[rows, cols], want) < 1e-4

@@ -75,31 +75,38 @@ def _compare_components(res, gpu, rel_tie):
     return k, True
 
 
+# FP32 ms-CLEAN images after three cycles: relative L2 bound on the models and
+# the combined image, whatever the component lists do after a near-tie.
+TOL_MSCLEAN_FP32 = 2e-2
+
+
 @pytest.mark.parametrize("prec", [1, 0])
 def test_msclean_loop_matches_oracle(ctx, obs_small, prec):
+    """FP64: the component lists are identical to the oracle's (no near-tie
+    closer than 1e-6 relative is allowed to change a choice), then models and
+    combined image within 1e-9.  FP32: the lists agree up to the first choice
+    whose best and runner-up candidates are within 5e-3 relative (the FP32
+    error of the high partition's weak scale residuals), and the models and
+    combined image are always compared, within TOL_MSCLEAN_FP32."""
     prm = dict(scales=[0.0, 3.0, 9.0], gain=0.1, niter=300, threshold=1e-4)
     loop, img, log = _run_both(ctx, obs_small, prec, 2, "msclean", 3, **prm)
-    # FP32: the operator is within 1e-5 of the oracle over the whole image, but
-    # the high partition's composite dirty image is high-pass filtered and much
-    # weaker, and its scale residuals B_s * D (s > 0) weaker still, so CLEAN's
-    # candidate values there carry up to ~1e-3 relative error; choices closer
-    # than 5e-3 are near-ties at FP32 precision for this workload
-    rel_tie = 1e-9 if prec == 1 else 5e-3
-    all_identical = True
+    rel_tie = 1e-6 if prec == 1 else 5e-3
     for entry in log:
         if entry[0] == "models":
             continue
         c, p, res, gpu = entry
-        assert len(gpu[0]) == res.iterations or not all_identical
         k, same = _compare_components(res, gpu, rel_tie)
-        all_identical &= same and len(gpu[0]) == res.iterations
-    if all_identical:
-        tol = 1e-9 if prec == 1 else 1e-4
-        for entry in log:
-            if entry[0] == "models":
-                for g, o in zip(entry[2], entry[3]):
-                    assert rel_l2(g, o) < tol
-        assert rel_l2(img, loop.combine()) < tol
+        if prec == 1:
+            assert same and len(gpu[0]) == res.iterations, f"cycle {c} partition {p}: lists differ at {k}"
+    tol = 1e-9 if prec == 1 else TOL_MSCLEAN_FP32
+    errs = []
+    for entry in log:
+        if entry[0] == "models":
+            for g, o in zip(entry[2], entry[3]):
+                errs.append(rel_l2(g, o))
+    errs.append(rel_l2(img, loop.combine()))
+    print(f"ms-CLEAN prec={prec} model/combined rel L2 errors: {['%.2e' % e for e in errs]}")
+    assert max(errs) < tol
 
 
 @pytest.mark.parametrize("prec", [1, 0])
@@ -171,22 +178,43 @@ def test_concurrent_partitions_match_sequential(ctx, obs_small, obs_wstack, meth
 
 def test_msclean_four_partitions_large_recipe(ctx, obs_large):
     """P = 4 rings and the scale set {0, 4, 16, 32} of the 4096^2 recipe, at
-    reduced size, FP64: component lists up to the first near-tie, then images."""
+    reduced size, FP64: component lists identical to the oracle's (1e-6
+    near-tie rule), models and combined image within 1e-9."""
     prm = dict(scales=[0.0, 4.0, 16.0, 32.0], gain=0.1, niter=200, threshold=1e-4)
     loop, img, log = _run_both(ctx, obs_large, 1, 4, "msclean", 3, **prm)
-    all_identical = True
     for entry in log:
         if entry[0] == "models":
+            for g, o in zip(entry[2], entry[3]):
+                assert rel_l2(g, o) < 1e-9
             continue
         c, p, res, gpu = entry
-        k, same = _compare_components(res, gpu, 1e-9)
-        all_identical &= same and len(gpu[0]) == res.iterations
-    if all_identical:
-        for entry in log:
-            if entry[0] == "models":
-                for g, o in zip(entry[2], entry[3]):
-                    assert rel_l2(g, o) < 1e-9
-        assert rel_l2(img, loop.combine()) < 1e-9
+        k, same = _compare_components(res, gpu, 1e-6)
+        assert same and len(gpu[0]) == res.iterations, f"cycle {c} partition {p}: lists differ at {k}"
+    assert rel_l2(img, loop.combine()) < 1e-9
+
+
+@pytest.mark.parametrize("method,prec", [("msclean", 1), ("fista", 1), ("fista", 0)])
+def test_single_partition_is_the_serial_method(ctx, obs_small, obs_wstack, method, prec):
+    """P = 1: the framework reduces to the serial method (Eq. 4 with FISTA,
+    Eq. 6 with ms-CLEAN; Gamma = 1, no exchange), against the oracle's loop
+    with one partition."""
+    obs = obs_small if method == "msclean" else obs_wstack
+    if method == "msclean":
+        prm = dict(scales=[0.0, 3.0, 9.0], gain=0.1, niter=200, threshold=1e-4)
+    else:
+        prm = dict(lam_rel=1e-3, n_iter=20, levels=3)
+    loop, img, log = _run_both(ctx, obs, prec, 1, method, 3, **prm)
+    tol = 1e-9 if prec == 1 else 1e-4
+    for entry in log:
+        if entry[0] == "models":
+            for g, o in zip(entry[2], entry[3]):
+                assert rel_l2(g, o) < tol
+        elif prec == 1:
+            c, p, res, gpu = entry
+            k, same = _compare_components(res, gpu, 1e-6)
+            assert same and len(gpu[0]) == res.iterations
+    assert rel_l2(img, loop.combine()) < tol
+    assert np.abs(loop.combine()).max() > 0.0
 
 
 @pytest.mark.parametrize("prec", [1, 0])

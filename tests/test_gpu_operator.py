@@ -185,3 +185,57 @@ def test_fp32_operator_vs_direct_dft(ctx, obs_wstack):
         assert rel_l2(img.cpu().numpy()[rows, cols], want) < 1e-4
     finally:
         rix.job_destroy(job)
+
+
+@pytest.fixture(scope="module")
+def obs_outside(obs_small):
+    """The small recipe with 2 % of its rows' uvw stretched 5-7x: the kernel
+    footprints of many of those samples leave the 256 x 256 grid (they are
+    dropped and counted by both sides), others stay inside near the edge."""
+    import dataclasses
+    rng = np.random.default_rng(17)
+    uvw = obs_small.uvw.copy()
+    rows = rng.choice(obs_small.nrow, obs_small.nrow // 50, replace=False)
+    uvw[rows] *= rng.uniform(5.0, 7.0, (rows.shape[0], 1))
+    return dataclasses.replace(obs_small, uvw=uvw)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_samples_outside_the_grid(ctx, obs_outside, prec):
+    """Samples whose footprint leaves the grid: counted and excluded
+    identically (masks bit-exact, zero for them), and the operator on the rest
+    matches the oracle gridder (degrid, grid, PSF, major cycle)."""
+    from oracle import gridder
+    from paper_2507_22128_gb300 import rix
+    obs = obs_outside
+    job, mask = _job(ctx, obs, prec, 2)
+    try:
+        st = _oracle(obs, 2)
+        n_out = int((~st.geom.inside).sum())
+        assert 0 < n_out < obs.nvis // 50
+        s = rix.job_get_stats(job)
+        assert s["n_outside"] == n_out
+        assert np.array_equal(mask, st.mask)
+        assert np.all(mask[~st.geom.inside] == 0)
+        w = obs.weight.reshape(-1).astype(np.float64)
+        x = sparse_model(obs.n, 30, seed=8)
+        vis_d = to_dev(obs.vis.reshape(-1), cplx_dtype(prec))
+        for p in range(2):
+            g = st.gparts[p]
+            vis = torch.zeros(obs.nvis, dtype=cplx_dtype(prec), device="cuda")
+            rix.degrid(job, p, to_dev(x, real_dtype(prec)), vis)
+            img = torch.empty((obs.n, obs.n), dtype=real_dtype(prec), device="cuda")
+            rix.grid(job, p, vis_d, img)
+            psf = torch.empty((2 * obs.n, 2 * obs.n), dtype=real_dtype(prec), device="cuda")
+            rix.psf(job, p, psf)
+            res = torch.empty((obs.n, obs.n), dtype=real_dtype(prec), device="cuda")
+            rix.major_cycle(job, p, vis_d, to_dev(x, real_dtype(prec)), res)
+            torch.cuda.synchronize()
+            got = vis.cpu().numpy()
+            assert rel_l2(got[g.inside], gridder.degrid(x, g)[g.inside]) < TOL[prec]
+            assert np.all(got[~g.inside] == 0)
+            assert rel_l2(img.cpu().numpy(), gridder.dirty(obs.vis.reshape(-1), w, g)) < TOL[prec]
+            assert rel_l2(psf.cpu().numpy(), st.psf[p]) < TOL[prec]
+            assert rel_l2(res.cpu().numpy(), gridder.residual(obs.vis.reshape(-1), w, x, g)) < TOL[prec]
+    finally:
+        rix.job_destroy(job)
