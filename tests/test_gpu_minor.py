@@ -76,8 +76,9 @@ def _compare_components(res, gpu, rel_tie):
 
 
 # FP32 ms-CLEAN images after three cycles: relative L2 bound on the models and
-# the combined image, whatever the component lists do after a near-tie.
-TOL_MSCLEAN_FP32 = 2e-2
+# the combined image (the survey's 1e-4 image bar), checked whatever the
+# component lists do after a near-tie.
+TOL_MSCLEAN_FP32 = 1e-4
 
 
 @pytest.mark.parametrize("prec", [1, 0])
