@@ -17,6 +17,7 @@
 #include <algorithm>
 #include <cstddef>
 #include <cmath>
+#include <type_traits>
 #include <vector>
 
 #include "rix_internal.cuh"
@@ -24,7 +25,6 @@
 namespace rix {
 namespace {
 
-enum GridMode : int { kDegrid = 0, kGrid = 1, kResid = 2, kPsf = 3 };
 
 // ----------------------------------------------------------- host tables ----
 // Gauss-Legendre nodes and weights on [-1, 1] by Newton iteration on P_n.
@@ -174,17 +174,6 @@ int build_correction(Job* job, int M, int ng, DevBuf& corr, DevBuf& nm1, cudaStr
 }
 
 // --------------------------------------------------------------- kernels ----
-template <typename R> __device__ __forceinline__ R es_weight(R d, int i);
-template <> __device__ __forceinline__ float es_weight<float>(float d, int i) {
-  const float z = (d + (float)i) * (2.0f / kW) - 1.0f;
-  const float t = fmaxf(1.0f - z * z, 0.0f);
-  return expf((float)kBeta * (sqrtf(t) - 1.0f));
-}
-template <> __device__ __forceinline__ double es_weight<double>(double d, int i) {
-  const double z = (d + (double)i) * (2.0 / kW) - 1.0;
-  const double t = fmax(1.0 - z * z, 0.0);
-  return exp(kBeta * (sqrt(t) - 1.0));
-}
 
 struct TileArgs {
   const uint32_t* keys;
@@ -206,17 +195,6 @@ struct TileArgs {
   const float* weight;      // per sample or null
   const void* geom;         // EntryGeom<R> per sorted entry, from entry geom_off on
   int64_t geom_off;
-};
-
-// Per sorted entry, fixed for the job: the kernel offsets du = ceil(xs) - xs,
-// dv, dw (rounded once from FP64 to the job's precision) and the first tap
-// relative to the entry's tile origin (ou | ov << 8).  Computed once at
-// partition time with the FP64 arithmetic the kernels used to repeat every
-// major cycle (GB300 runs FP64 at 1/64 of the FP32 rate).
-template <typename R>
-struct alignas(4 * sizeof(R)) EntryGeom {
-  R du, dv, dw;
-  uint32_t ouv;
 };
 
 // On the PSF's 2N grid (x_psf = 2 x exactly), an image-grid tile of side T
@@ -691,6 +669,12 @@ int launch_tiles_ws(const Ctx* ctx, const TileArgs& a, cudaStream_t st) {
 template <typename R, int MODE>
 int launch_tiles(const Job* job, const TileArgs& a, cudaStream_t st) {
   const bool ws = job->nw > 0;
+  if constexpr (std::is_same<R, float>::value && (MODE == kGrid || MODE == kResid)) {
+    // FP32 w-stacked gridding on the image grid: register-resident
+    // footprints (k_tiles_fp.cu)
+    if (ws && job->tile == 16)
+      return launch_tiles_fp(job, MODE, a.item_begin, a.item_count, a.win_lo, a.S, a.model, a.out, a.vis_in, st);
+  }
   if constexpr (MODE != kDegrid) {
     // w-stacked gridding: plane-owned shared-memory sub-grid (tile 16 only)
     if (ws) return launch_tiles_ws<R, 16, MODE>(job->ctx, a, st);
@@ -704,7 +688,7 @@ int launch_tiles(const Job* job, const TileArgs& a, cudaStream_t st) {
 TileArgs base_args(const Job* job, const Part& pt) {
   TileArgs a{};
   a.keys = job->keys.as<uint32_t>();
-  a.samples = job->samples.as<uint32_t>();
+  a.samples = job->gsamples.as<uint32_t>();   // gridder order, matching egeom
   a.items = job->items.as<uint32_t>();
   a.item_begin = pt.item_begin;
   a.item_count = pt.item_count;
@@ -962,7 +946,8 @@ int grid_entry_geometry(Job* job, cudaStream_t st) {
   const int64_t n = job->n_entries;
   RIX_TRY(job->egeom.alloc(job->ctx, (size_t)std::max<int64_t>(n, 1) * sizeof(EntryGeom<R>)));
   if (n == 0) return RIX_OK;
-  const TileArgs a = base_args(job, job->part[0]);   // job-level fields only
+  TileArgs a = base_args(job, job->part[0]);   // job-level fields only
+  a.samples = job->samples.as<uint32_t>();      // the sorted order (grid_work_order reorders both after)
   const int blocks = (int)std::min<int64_t>(ceil_div(n, 256), (int64_t)job->ctx->num_sms * 16);
   ::rix::note_launch();
   if (job->tile == 16) k_entry_geom<R, false, 16><<<blocks, 256, 0, st>>>(a, 0, n, job->egeom.as<EntryGeom<R>>());

@@ -412,6 +412,8 @@ static int rix_set_uv_partition_impl(rix_job_t job, const double* uvw_m, int64_t
   else RIX_TRY(grid_build_corrections<float>(&J, st));
   if (J.fp64) RIX_TRY(grid_entry_geometry<double>(&J, st));
   else RIX_TRY(grid_entry_geometry<float>(&J, st));
+  if (J.fp64) RIX_TRY(grid_work_order<double>(&J, st));
+  else RIX_TRY(grid_work_order<float>(&J, st));
   if (J.fp64) RIX_TRY(fill_init<double>(&J, st));
   else RIX_TRY(fill_init<float>(&J, st));
   for (int p = 0; p < J.n_part; ++p) RIX_TRY(ensure_images(&J, J.part[p], st));

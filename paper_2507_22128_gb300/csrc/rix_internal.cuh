@@ -84,6 +84,37 @@ constexpr int kW = 8;            // ES kernel support (cells)
 constexpr double kBeta = 18.4;   // 2.30 * kW
 
 // ---------------------------------------------------------------------------
+// gridder building blocks shared by k_grid.cu and k_tiles_fp.cu
+// ---------------------------------------------------------------------------
+enum GridMode : int { kDegrid = 0, kGrid = 1, kResid = 2, kPsf = 3 };
+
+// Exponential-of-semicircle kernel weight of tap i for a sample whose first
+// tap sits d in [0, 1) cells after its kernel's left edge:
+// phi(z) = exp(beta (sqrt(1 - z^2) - 1)), z = (d + i) 2/W - 1.
+template <typename R> __device__ __forceinline__ R es_weight(R d, int i);
+template <> __device__ __forceinline__ float es_weight<float>(float d, int i) {
+  const float z = (d + (float)i) * (2.0f / kW) - 1.0f;
+  const float t = fmaxf(1.0f - z * z, 0.0f);
+  return expf((float)kBeta * (sqrtf(t) - 1.0f));
+}
+template <> __device__ __forceinline__ double es_weight<double>(double d, int i) {
+  const double z = (d + (double)i) * (2.0 / kW) - 1.0;
+  const double t = fmax(1.0 - z * z, 0.0);
+  return exp(kBeta * (sqrt(t) - 1.0));
+}
+
+// Per sorted entry, fixed for the job: the kernel offsets du = ceil(xs) - xs,
+// dv, dw (rounded once from FP64 to the job's precision) and the first tap
+// relative to the entry's tile origin (ou | ov << 8).  Computed once at
+// partition time with the FP64 arithmetic the kernels used to repeat every
+// major cycle (GB300 runs FP64 at 1/64 of the FP32 rate).
+template <typename R>
+struct alignas(4 * sizeof(R)) EntryGeom {
+  R du, dv, dw;
+  uint32_t ouv;
+};
+
+// ---------------------------------------------------------------------------
 // device buffers
 // ---------------------------------------------------------------------------
 struct Ctx;
@@ -249,7 +280,15 @@ struct Job {
   DevBuf uvw, weight, inv_lambda;
   // sort
   DevBuf keys, samples, items;              // entries and work-item begin offsets (+1 sentinel)
-  DevBuf egeom;                             // per sorted entry: kernel offsets and tap origin (see k_grid.cu)
+  // Gridder order: within every work item the entries are reordered by their
+  // first tap (the cell their kernel footprint starts at), so runs of
+  // entries with one footprint are contiguous; a chunk is a run of at most 32
+  // such entries.  egeom and gsamples are in this order; `samples` keeps the
+  // sorted order rix_get_sorted_entries reports.
+  DevBuf egeom;                             // per entry: kernel offsets and tap origin (EntryGeom<R>)
+  DevBuf gsamples;                          // per entry: sample index
+  DevBuf chunks;                            // entry offset of each chunk (+1 sentinel: n_entries)
+  DevBuf item_chunk;                        // first chunk of each work item (+1 sentinel: the chunk count)
   int64_t n_entries = 0, n_items = 0;
   int bt = 0, bw = 0, bp = 0;
   // corrections
@@ -282,6 +321,17 @@ template <typename R>
 int grid_build_corrections(Job* job, cudaStream_t st);
 template <typename R>
 int grid_entry_geometry(Job* job, cudaStream_t st);
+// gridder order and chunks of the job's entries (k_tiles_fp.cu), after
+// grid_entry_geometry
+template <typename R>
+int grid_work_order(Job* job, cudaStream_t st);
+// The FP32 w-stacked gridder with register-resident kernel footprints
+// (k_tiles_fp.cu): mode kGrid spreads w * vis into out_planes, kResid
+// degrids model_planes and spreads w * (vis - model visibility); planes
+// [n_wplanes][S][S] complex on the partition's uv window [win_lo, win_lo + S)
+// (out_planes zeroed by the caller).  Tile side 16.
+int launch_tiles_fp(const Job* job, int mode, int64_t item_begin, int64_t item_count, int win_lo, int S,
+                    const void* model_planes, void* out_planes, const void* vis, cudaStream_t st);
 template <typename R>
 int op_degrid(Job* job, int p, const R* image, cplx<R>* vis_out, cudaStream_t st);
 template <typename R>
