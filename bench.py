@@ -55,6 +55,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-phases", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 operator comparison")
     ap.add_argument("--serve-jobs", type=int, default=24, help="arrivals in the serving experiment (0 = skip)")
     ap.add_argument("--serve-rate", type=float, default=20.0, help="Poisson arrival rate, jobs/s")
     ap.add_argument("--json-out", default=None)
@@ -171,36 +172,90 @@ def reference_arm(a, rank, world):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": config_dict(a),
             "cpu_baseline": {"value": res["value"], "unit": UNIT, "cores": res["cores"], "kind": "oracle",
-                             "sample": res["sample"]},
+                             "sample": res["sample"], "cpu": res["cpu"], "nproc": res["nproc"]},
             "e2e": {"value": res["value"], "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
 
 
-def cpu_baseline(a, steps=1, warmup=0):
-    """FP64 oracle major cycle (degrid + residual + grid, Eq. 2) of partition 0
-    on a 1/64 row subset of the workload; Mvis/s = samples / seconds."""
-    from oracle import gridder, partition
+def _oracle_init(barrier):
+    global _ORACLE_BARRIER
+    _ORACLE_BARRIER = barrier
+
+
+def _oracle_major_cycle(job):
+    """One FP64 oracle major cycle (degrid + residual + grid, Eq. 2) of
+    partition 0 on a row subset of the medium recipe; runs in a spawned
+    process with one FFT thread.  Returns (samples, seconds)."""
+    n_times, n, repeats = job
+    from oracle import filters, gridder, partition
+    filters.FFT_WORKERS = 1
+    gridder.FFT_WORKERS = 1
     from paper_2507_22128_gb300 import synth
-    obs = synth.medium(seed=1, n_times=max(4, a.n_times // 64), n=a.n)
+    obs = synth.medium(seed=1, n_times=n_times, n=n)
     g = gridder.geometry(obs.uvw, obs.freq, obs.n, obs.cell_rad, W=8, nw=obs.n_wplanes)
     r = partition.radius_px(g)
     m = partition.masks(r, partition.ring_radii(r, 2), 1.0, 2, g.inside)
     gp = gridder.subset(g, (m & 1) == 1)
     w = obs.weight.reshape(-1).astype(np.float64)
     model = np.zeros((obs.n, obs.n))
-    nsamp = int(gp.inside.sum())
-    times = []
-    for i in range(warmup + steps):
+    out = []
+    for _ in range(repeats):
+        _ORACLE_BARRIER.wait()          # every process starts its cycle together
         t0 = time.perf_counter()
         gridder.residual(obs.vis.reshape(-1), w, model, gp)
-        dt = time.perf_counter() - t0
-        if i >= warmup:
-            times.append(dt)
-    t = statistics.median(times)
-    return {"value": nsamp / t / 1e6, "ms_per_step": t * 1e3, "cores": 1,
-            "sample": f"one FP64 major cycle of partition 0 over {obs.nrow} rows x {obs.nchan} channels "
-                      f"({nsamp} samples; 1/64 of the {a.n}^2 workload's rows), numpy, median of {steps}"}
+        out.append(time.perf_counter() - t0)
+    return int(gp.inside.sum()), out
+
+
+def cpu_model():
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.strip().lower().startswith("model name"):
+                return ln.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        with open("/proc/cpuinfo") as f:
+            for ln in f:
+                if ln.lower().startswith(("model name", "cpu part")):
+                    return ln.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
+def cpu_baseline(a, steps=1, warmup=0):
+    """The oracle on all host cores: one spawned process per core (bounded by
+    host memory, about 4 GB per process at 1024^2 with 16 w-planes), each
+    running the oracle's FP64 major cycle of partition 0 over 1/64 of the
+    workload's time samples with one FFT thread, all started together;
+    Mvis/s = the processes' samples / the slowest process's time (median
+    over `steps` rounds after `warmup`)."""
+    import multiprocessing as mp
+    ncpu = os.cpu_count() or 1
+    try:
+        with open("/proc/meminfo") as f:
+            avail_gb = next(int(ln.split()[1]) for ln in f if ln.startswith("MemAvailable")) / 2 ** 20
+    except (OSError, StopIteration):
+        avail_gb = 16.0
+    nproc = max(1, min(ncpu, int(avail_gb // 4)))
+    n_times = max(4, a.n_times // 64)
+    ctx = mp.get_context("spawn")           # the parent holds a CUDA context: never fork it
+    barrier = ctx.Barrier(nproc)
+    with ctx.Pool(nproc, initializer=_oracle_init, initargs=(barrier,)) as pool:
+        res = pool.map(_oracle_major_cycle, [(n_times, a.n, warmup + steps)] * nproc)
+    nsamp = sum(r[0] for r in res)
+    rounds = [max(r[1][i] for r in res) for i in range(warmup, warmup + steps)]
+    t = statistics.median(rounds)
+    return {"value": nsamp / t / 1e6, "ms_per_step": t * 1e3, "cores": nproc, "cpu": cpu_model(),
+            "nproc": ncpu,
+            "sample": f"{nproc} processes (one per host core, {ncpu} cores, {cpu_model()}), each one FP64 oracle "
+                      f"major cycle of partition 0 over {n_times} of the {a.n_times} time samples x 4 channels "
+                      f"({res[0][0]} samples each, 1/64 of the {a.n}^2 workload's rows; numpy, one FFT thread "
+                      f"per process), started together; median of {steps} rounds"}
 
 
 def config_dict(a):
@@ -309,15 +364,20 @@ def main():
                "h2d_bytes_per_step": int(uvw_h.numel() * 8 + vis_h.numel() * vis_h.element_size() + w_h.numel() * 4),
                "d2h_bytes_per_step": int(img_h.numel() * img_h.element_size())}
 
-    # the gridder runs once per partition per major cycle and once per
-    # partition for the PSF; the PSF launches carry (weights only) a fraction
-    # of the work, so the flop count below is a lower bound of the work timed
-    roof = roofline_tiles(tiles_busy, tiles_n, st, a, units * a.steps)
+    # ---- the survey's major-cycle metric, the gridder's roofline, the
+    # stated error, the FP64 comparator and cuFFT ----
+    mc = major_cycle_metric(rec, rix, meth, stream, vis_d, flush, st, obs.nchan)
+    roof = roofline_gridder(mc, st, a)
+    err = direct_dft_errors(rec, rix, obs, out, vis_d, w_d, 1)
+    fp64 = None if (a.fp64 or a.no_fp64) else fp64_comparator(ctx, rix, pipeline, obs, a, flush)
+    cufft = cufft_comparison(obs.n, obs.n_wplanes, st["window_size"][:2], flush)
+    cufft["library_fft_ms_per_cycle"] = sum(mc["per_partition_serial"][p]["fft_ms"] for p in (0, 1))
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
             "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64" if a.fp64 else "f32", "data": "synthetic",
             "config": config_dict(a), "clocks": clk.summary(), "e2e": e2e, "gpu_launches": int(launches),
-            "roofline": roof, "phases_ms": phases,
+            "roofline": roof, "major_cycle": mc, "operator_error": err, "fp64_operator": fp64, "cufft": cufft,
+            "phases_ms": phases,
             "kernel_ms_per_step": {"grid_tiles_busy": tiles_busy / a.steps, "grid_tiles_sum": tiles_ms / a.steps,
                                    "fft_passes_busy": fft_busy / a.steps,
                                    "minor_loop_busy": loop_busy / a.steps, "minor_loop_sum": loop_ms / a.steps},
@@ -327,7 +387,7 @@ def main():
     if rank == 0 and not a.no_cpu_baseline:
         cb = cpu_baseline(a)
         line["cpu_baseline"] = {"value": cb["value"], "unit": UNIT, "cores": cb["cores"], "kind": "oracle",
-                                "sample": cb["sample"]}
+                                "sample": cb["sample"], "cpu": cb["cpu"], "nproc": cb["nproc"]}
     rec.close()
     rix.destroy(ctx)
     if rank == 0:
@@ -397,61 +457,224 @@ def phase_split(rec, rix, a, meth, stream, uvw, vis, w, out, flush):
     return {"partition_sort": e0.elapsed_time(e1), "major_cycles": maj, "minor_cycles_incl_psf": mnr}
 
 
-# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per k_tiles_ws
-# launch at the default 1024^2 workload, from a one-pass ncu capture of one
-# timed job: residual launches of
-# partitions 0 and 1, PSF launches of partitions 0 and 1.  Reported only for
-# that workload and while k_grid.cu is the source the counters were taken on.
-TILES_TRAFFIC = {"k_grid_sha1": "dab75048113381c5baa1a22cc19111f811558f46",
-                 "resid": (162.13e6, 261.79e6), "psf": (115.38e6, 237.54e6)}
+def major_cycle_metric(rec, rix, meth, stream, vis, flush, st, nchan, n_cycles=7):
+    """The survey's metric on the fused major-cycle operator alone: samples
+    of both partitions (overlap counted in each) / the wall time of one major
+    cycle of both partitions (a4-a6: model -> planes, degrid, residual,
+    grid, planes -> residual image; each partition on its own stream as the
+    pipeline issues them), median over cycles after the first, L2 flushed
+    before each; %HBM against the survey's algorithmic bytes: per sample
+    uvw 24/nchan + visibility 8 + weight 4 + index 4 B, per partition and
+    w-plane 8 passes over the full (2N)^2 complex plane.  Then one more
+    cycle with the partitions on one stream for the per-launch times of the
+    gridder and the transforms."""
+    main = stream
+    ps = rec._pstreams if hasattr(rec, "_pstreams") else [torch.cuda.Stream() for _ in range(2)]
+    times = []
+    for c in range(n_cycles):
+        flush_l2(flush)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(main)
+        for p, s in enumerate(ps):
+            s.wait_event(e0)
+            rec.major(p, stream=s)
+        for s in ps:
+            j = torch.cuda.Event()
+            j.record(s)
+            main.wait_event(j)
+        e1.record(main)
+        rec.minor_all(meth, main)
+        torch.cuda.synchronize()
+        if c > 0:
+            times.append(e0.elapsed_time(e1))
+    ms = statistics.median(times)
+    units = sum(st["part_count"][:2])
+    ng = 2 * rec.n
+    nplanes = 16
+    byt = units * (24.0 / nchan + 16.0) + 2 * nplanes * 8 * ng * ng * 8.0
+    peaks, kind = measured_peaks()
+    hbm = byt / (ms * 1e-3) / 1e9
+    # serial pass: per-launch device times of the gridder and the transforms
+    per = {}
+    for p in range(2):
+        flush_l2(flush)
+        torch.cuda.synchronize()
+        for cls in (rix.TIME_TILES, rix.TIME_FFT):
+            rix.timing_read(cls)
+        rix.timing_enable(True)
+        rec.major(p, stream=main)
+        torch.cuda.synchronize()
+        rix.timing_enable(False)
+        tt, tb, tn = rix.timing_read(rix.TIME_TILES)
+        ft, fb, fn = rix.timing_read(rix.TIME_FFT)
+        per[p] = {"gridder_ms": tt, "fft_ms": ft, "fft_launches": fn}
+    rec.minor_all(meth, main)
+    torch.cuda.synchronize()
+    return {"value": units / (ms * 1e-3) / 1e6, "unit": UNIT, "ms_per_cycle": ms, "cycles_timed": len(times),
+            "samples_per_cycle": int(units),
+            "hbm": {"algorithmic_bytes_per_cycle": byt, "achieved_gbs": hbm, "peak_gbs": float(peaks["hbm_gbs"]),
+                    "frac": hbm / float(peaks["hbm_gbs"]), "peak_source": kind,
+                    "bytes": "survey 8(d): per sample 24/nchan + 16 B; per partition and w-plane 8 x (2N)^2 x 8 B"},
+            "per_partition_serial": per}
+
+
+def direct_dft_errors(rec, rix, obs, image, vis_d, wt_d, part, n_vis=256, n_pix=64, seed=7):
+    """Error of the library's operator against the exact measurement operator
+    (Eq. 1 direct sums in FP64 on the device, independent of the library):
+    degrid of `image` on n_vis sampled visibilities of partition `part`, and
+    the partition's dirty image (grid of the observed visibilities) on n_pix
+    sampled pixels; relative L2 over the samples."""
+    dev = vis_d.device
+    n, cell = obs.n, obs.cell_rad
+    f = torch.as_tensor(obs.freq, dtype=torch.float64, device=dev) / 299792458.0
+    uvw = torch.as_tensor(obs.uvw, dtype=torch.float64, device=dev)
+    u = (uvw[:, 0:1] * f[None, :]).reshape(-1)
+    v = (uvw[:, 1:2] * f[None, :]).reshape(-1)
+    w = (uvw[:, 2:3] * f[None, :]).reshape(-1)
+    mask = torch.zeros(obs.nvis, dtype=torch.uint8, device=dev)
+    rix.set_uv_partition(rec.job, rec.uvw, rec.weight, None, 1.0, mask)
+    sel = torch.nonzero(((mask >> part) & 1) == 1).reshape(-1)
+    g = torch.Generator(device="cpu").manual_seed(seed)
+    pick = sel[torch.randperm(sel.numel(), generator=g)[:n_vis].to(dev)]
+    cdt = rec.cdtype
+    # degrid
+    out = torch.zeros(obs.nvis, dtype=cdt, device=dev)
+    rix.degrid(rec.job, part, image.to(rec.rdtype).contiguous(), out)
+    off = (torch.arange(n, dtype=torch.float64, device=dev) - n // 2) * cell
+    mm, ll = torch.meshgrid(off, off, indexing="ij")
+    r2 = ll * ll + mm * mm
+    nn = torch.sqrt(1.0 - r2)
+    nm1 = -r2 / (1.0 + nn)
+    x = (image.to(torch.float64) / nn).reshape(-1)
+    want = torch.zeros(n_vis, dtype=torch.complex128, device=dev)
+    for c0 in range(0, n * n, 1 << 16):
+        c1 = min(n * n, c0 + (1 << 16))
+        ph = (torch.outer(u[pick], ll.reshape(-1)[c0:c1]) + torch.outer(v[pick], mm.reshape(-1)[c0:c1])
+              + torch.outer(w[pick], nm1.reshape(-1)[c0:c1]))
+        want += torch.exp(-2j * torch.pi * ph) @ x[c0:c1].to(torch.complex128)
+    got = out[pick].to(torch.complex128)
+    e_deg = float(torch.linalg.norm(got - want) / torch.linalg.norm(want))
+    # grid: dirty image of the observed visibilities on sampled pixels
+    img = torch.empty((n, n), dtype=rec.rdtype, device=dev)
+    rix.grid(rec.job, part, vis_d, img)
+    rows = torch.randint(0, n, (n_pix,), generator=g).to(dev)
+    cols = torch.randint(0, n, (n_pix,), generator=g).to(dev)
+    wt = wt_d.reshape(-1).to(torch.float64)[sel]
+    y = wt * vis_d.reshape(-1).to(torch.complex128)[sel]
+    lp, mp = off[cols], off[rows]
+    rp = lp * lp + mp * mp
+    np_ = torch.sqrt(1.0 - rp)
+    nm1p = -rp / (1.0 + np_)
+    acc = torch.zeros(n_pix, dtype=torch.float64, device=dev)
+    us, vs, ws = u[sel], v[sel], w[sel]
+    for s0 in range(0, sel.numel(), 1 << 18):
+        s1 = min(sel.numel(), s0 + (1 << 18))
+        ph = (torch.outer(us[s0:s1], lp) + torch.outer(vs[s0:s1], mp) + torch.outer(ws[s0:s1], nm1p))
+        acc += (y[s0:s1] @ torch.exp(2j * torch.pi * ph)).real
+    want_px = acc / np_ / wt.sum()
+    got_px = img[rows, cols].to(torch.float64)
+    e_grid = float(torch.linalg.norm(got_px - want_px) / torch.linalg.norm(want_px))
+    return {"degrid_rel_l2": e_deg, "grid_rel_l2": e_grid, "partition": part, "visibilities": n_vis,
+            "pixels": n_pix, "reference": "direct DFT of Eq. 1 in FP64 (sampled)"}
+
+
+def fp64_comparator(ctx, rix, pipeline, obs, a, flush, n_cycles=4):
+    """The plain FP64 GPU operator on the same workload: one FP64 job, the
+    fused major cycle of both partitions timed as in major_cycle_metric, and
+    its error against the direct DFT."""
+    rec = pipeline.Reconstruction(ctx, obs.n, obs.cell_rad, obs.n_wplanes, obs.freq, obs.nrow, 2, rix.FP64)
+    try:
+        rec.set_data(obs.uvw, obs.vis, obs.weight)
+        torch.cuda.synchronize()
+        st = rec.stats()
+        m = pipeline.Method("fista", lam_rel=1e-3, iters=2, levels=1)
+        s = torch.cuda.current_stream()
+        mc = major_cycle_metric(rec, rix, m, s, None, flush, st, obs.nchan, n_cycles=n_cycles)
+        model = torch.empty((obs.n, obs.n), dtype=torch.float64, device="cuda")
+        rix.get_model(rec.job, 1, model)
+        wt = torch.as_tensor(obs.weight, device="cuda")
+        err = direct_dft_errors(rec, rix, obs, model, rec.vis, wt, 1)
+        return {"value": mc["value"], "unit": UNIT, "ms_per_cycle": mc["ms_per_cycle"], "error": err,
+                "per_partition_serial": mc["per_partition_serial"]}
+    finally:
+        rec.close()
+
+
+def cufft_comparison(n, nplanes, window, flush, reps=5):
+    """cuFFT (through torch.fft) on the major cycle's plane transforms, as a
+    comparison for the library's own passes: the forward transform of the
+    zero-padded (2N)^2 planes of all w-planes and the inverse, full planes
+    (cuFFT has no pruned window), complex64, median of `reps`."""
+    ng = 2 * n
+    x = torch.zeros((nplanes, ng, ng), dtype=torch.complex64, device="cuda")
+    x[:, n // 2:n // 2 + n, n // 2:n // 2 + n] = 1.0
+    times = []
+    for _ in range(reps + 1):
+        flush_l2(flush)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        y = torch.fft.fft2(x)
+        z = torch.fft.ifft2(y)
+        e1.record()
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+    del x, y, z
+    return {"cufft_fwd_plus_inv_ms": statistics.median(times[1:]), "planes": nplanes, "grid": ng,
+            "note": "full (2N)^2 planes; the library transforms only each partition's uv window"}
+
+
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the
+# FP32 w-stacked gridder (k_tiles_fp<RESID>) at the default 1024^2 workload,
+# from a one-pass ncu capture of the major cycles of both partitions: (low,
+# high) partition.  Reported only for that workload and while the kernel's
+# source is the one the counters were taken on.
+TILES_TRAFFIC = {"src_sha1": None, "resid": (None, None)}
 
 
 def tiles_traffic(a):
     import hashlib
-    src = os.path.join(ROOT, "paper_2507_22128_gb300", "csrc", "k_grid.cu")
+    src = os.path.join(ROOT, "paper_2507_22128_gb300", "csrc", "k_tiles_fp.cu")
     with open(src, "rb") as f:
         sha = hashlib.sha1(f.read()).hexdigest()
-    if sha != TILES_TRAFFIC["k_grid_sha1"] or a.fp64 or a.n != 1024 or a.n_times != 1000:
+    if sha != TILES_TRAFFIC["src_sha1"] or a.fp64 or a.n != 1024 or a.n_times != 1000:
         return None
-    # a step: `cycles` residual launches per partition and one PSF launch each
-    tot = a.cycles * sum(TILES_TRAFFIC["resid"]) + sum(TILES_TRAFFIC["psf"])
-    return tot / (2 * a.cycles + 2)
+    return sum(TILES_TRAFFIC["resid"]) / 2
 
 
-def roofline_tiles(tiles_ms, tiles_n, st, a, entries_timed):
-    """Roofline of the tiled degrid/residual/grid kernel, the gridder of the
-    major cycle: FP32 (or FP64) arithmetic over its event-timed launches
-    (`tiles_ms` is their busy time: the two partitions' launches overlap).
-    Algorithmic work per (sample, partition) entry and major cycle: degrid
-    8 x 64 taps x 2 FMA (2048 flops) + grid 8 x 64 taps x (2 mul + 2 add)
-    (2048 flops) = 4096 flops; the PSF launches (weights only) are counted
-    at zero, so `achieved` is a lower bound."""
-    if not tiles_n or tiles_ms <= 0:
+def roofline_gridder(mc, st, a):
+    """Roofline of the major cycle's gridder (degrid + residual + grid), from
+    its per-launch device times with the partitions on one stream.  Bound:
+    FP32 issue (ALU): 4096 flops per (sample, partition) entry and major
+    cycle (degrid 512 taps x 2 complex-by-real FMAs, grid 512 taps x 2) over
+    152 SMs x 128 FP32 lanes x 2 flops x the maximum SM clock (a derived
+    peak: the measured peaks hold no FP32 SIMT figure).  `hbm` adds its
+    algorithmic bytes: per entry its geometry record and weighted visibility
+    (16 + 16 B), and per w-plane of the partition's uv window one model read
+    and one residual write (2 x 8 B per cell)."""
+    per = mc["per_partition_serial"]
+    ms = sum(per[p]["gridder_ms"] for p in (0, 1))
+    if ms <= 0:
         return None
     peaks, kind = measured_peaks()
     clk = float(peaks.get("sm_max_mhz", 2070.0))
     lanes = 2 if a.fp64 else 128        # FP64 / FP32 results per SM per clock (GB300 unit counts)
     peak = 152 * lanes * 2 * clk * 1e6 / 1e12
-    flops = 4096.0 * entries_timed
-    ach = flops / (tiles_ms * 1e-3) / 1e12
-    # secondary: HBM against the measured copy bandwidth, with the algorithmic
-    # bytes of the residual launches (per entry: uvw 24/nchan + visibility 8 +
-    # weight 4 + index 4 B; per w-plane of the partition's uv window: model
-    # read + residual write, 2 x 8 B per cell)
-    nchan = 4
-    ent_b = (24.0 / nchan + 8 + 4 + 4) * entries_timed
+    ent = float(sum(st["part_count"][:2]))
+    ach = 4096.0 * ent / (ms * 1e-3) / 1e12
     win = st["window_size"][:2]
-    plane_b = a.steps * a.cycles * sum(2 * 8.0 * 16 * w * w for w in win)
-    hbm = (ent_b + plane_b) / (tiles_ms * 1e-3) / 1e9
+    byt = ent * 32.0 + sum(2 * 8.0 * 16 * w * w for w in win)
+    hbm = byt / (ms * 1e-3) / 1e9
     hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
-    return {"bound": "alu", "kernel": "k_tiles (degrid + residual + grid, w-stacked, T=16)",
+    return {"bound": "alu",
+            "kernel": "k_tiles_ws (FP64, shared-memory staging)" if a.fp64 else
+                      "k_tiles_fp<RESID> (degrid + residual + grid, register-resident footprints, TMA tiles)",
             "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+            "ms_per_launch": {"low": per[0]["gridder_ms"], "high": per[1]["gridder_ms"]},
             "hbm": {"achieved_gbs": hbm, "peak_gbs": hbm_peak, "frac": hbm / hbm_peak,
-                    "algorithmic_bytes_per_launch": (ent_b + plane_b) / tiles_n, "peak_source": kind},
-            "traffic": tiles_traffic(a), "traffic_unit": "B per launch",
-            "launches_timed": tiles_n, "busy_ms_per_launch": tiles_ms / tiles_n,
-            "ncu_binding_unit": "shared memory: L1/shared throughput 86 % of peak, FMA pipe 20 % "
-                                "(ncu --set full of one launch at the medium recipe)",
+                    "algorithmic_bytes_per_launch": byt / 2, "peak_source": kind},
+            "traffic": tiles_traffic(a), "traffic_unit": "B per launch (ncu dram read + write)",
             "peak_source": f"152 SMs x {lanes} {'FP64' if a.fp64 else 'FP32'} lanes x 2 flop x {clk:.0f} MHz "
                            f"(max SM clock of {kind} peaks)"}
 

@@ -21,7 +21,11 @@ Gamma_H = 1 - Gamma_L.
 from __future__ import annotations
 
 import numpy as np
-import scipy.fft as _fft   # the 2D FFT primitive (all host threads)
+import scipy.fft as _fft   # the 2D FFT primitive
+
+# host threads of each 2D FFT (-1 = all); a caller running several oracle
+# processes side by side sets 1
+FFT_WORKERS = -1
 
 
 def radius_grid(n: int) -> np.ndarray:
@@ -54,11 +58,11 @@ def crop(z: np.ndarray) -> np.ndarray:
 
 def spectrum(z2n: np.ndarray) -> np.ndarray:
     """Centred FFT of a 2N x 2N array whose centre is at index (N, N)."""
-    return np.fft.fftshift(_fft.fft2(np.fft.ifftshift(z2n), workers=-1))
+    return np.fft.fftshift(_fft.fft2(np.fft.ifftshift(z2n), workers=FFT_WORKERS))
 
 
 def ispectrum(s: np.ndarray) -> np.ndarray:
-    return np.fft.fftshift(_fft.ifft2(np.fft.ifftshift(s), workers=-1))
+    return np.fft.fftshift(_fft.ifft2(np.fft.ifftshift(s), workers=FFT_WORKERS))
 
 
 def image_spectrum(x: np.ndarray) -> np.ndarray:

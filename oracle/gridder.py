@@ -33,7 +33,11 @@ import dataclasses
 import math
 
 import numpy as np
-import scipy.fft as _fft   # the 2D FFT primitive (all host threads)
+import scipy.fft as _fft   # the 2D FFT primitive
+
+# host threads of each 2D FFT (-1 = all); a caller running several oracle
+# processes side by side sets 1
+FFT_WORKERS = -1
 
 from . import es
 
@@ -159,7 +163,7 @@ def model_planes(image: np.ndarray, g: Geometry) -> np.ndarray:
         z = corr.astype(np.complex128)
         if g.nw > 0:
             z = z * np.exp(-2j * np.pi * plane_w(g, p) * nm1)
-        planes[p] = np.fft.fftshift(_fft.fft2(np.fft.ifftshift(_pad_center(z, g.ng)), workers=-1))
+        planes[p] = np.fft.fftshift(_fft.fft2(np.fft.ifftshift(_pad_center(z, g.ng)), workers=FFT_WORKERS))
     return planes
 
 
@@ -170,7 +174,7 @@ def planes_to_image(planes: np.ndarray, g: Geometry) -> np.ndarray:
     if g.nw > 0:
         _, nm1 = _lmn(g.n, g.cell)
     for p in range(g.nplanes):
-        z = np.fft.fftshift(_fft.ifft2(np.fft.ifftshift(planes[p]), workers=-1)) * (g.ng * g.ng)
+        z = np.fft.fftshift(_fft.ifft2(np.fft.ifftshift(planes[p]), workers=FFT_WORKERS)) * (g.ng * g.ng)
         z = z[o:o + g.n, o:o + g.n]
         if g.nw > 0:
             z = z * np.exp(2j * np.pi * plane_w(g, p) * nm1)

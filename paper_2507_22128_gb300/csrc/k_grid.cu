@@ -195,6 +195,7 @@ struct TileArgs {
   const float* weight;      // per sample or null
   const void* geom;         // EntryGeom<R> per sorted entry, from entry geom_off on
   int64_t geom_off;
+  int64_t ent_begin, ent_count;   // the partition's entries
 };
 
 // On the PSF's 2N grid (x_psf = 2 x exactly), an image-grid tile of side T
@@ -673,7 +674,8 @@ int launch_tiles(const Job* job, const TileArgs& a, cudaStream_t st) {
     // FP32 w-stacked gridding on the image grid: register-resident
     // footprints (k_tiles_fp.cu)
     if (ws && job->tile == 16)
-      return launch_tiles_fp(job, MODE, a.item_begin, a.item_count, a.win_lo, a.S, a.model, a.out, a.vis_in, st);
+      return launch_tiles_fp(job, MODE, a.item_begin, a.item_count, a.ent_begin, a.ent_count, a.win_lo, a.S, a.model,
+                             a.out, a.vis_in, st);
   }
   if constexpr (MODE != kDegrid) {
     // w-stacked gridding: plane-owned shared-memory sub-grid (tile 16 only)
@@ -709,6 +711,8 @@ TileArgs base_args(const Job* job, const Part& pt) {
   a.weight = job->weight.as<float>();
   a.geom = job->egeom.p;
   a.geom_off = 0;
+  a.ent_begin = pt.ent_begin;
+  a.ent_count = pt.ent_count;
   return a;
 }
 

@@ -6,14 +6,19 @@
 // footprint (same first tap in u, v and w).  At partition time the entries
 // of every work item (one 16 x 16 tile of one w-plane block) are reordered by
 // their first tap and cut into chunks: runs of at most 32 entries with one
-// footprint.  The kernel then gives each chunk to one warp, which
+// footprint.  Per call, k_gather_y writes every entry's weighted visibility
+// {w re v, w im v, w} in that order, so the gridder reads each chunk as two
+// contiguous 512-byte runs.  The kernel gives each chunk to one warp (warps
+// claim an item's chunks from a shared-memory queue, and each warp fetches
+// its next chunk by cp.async while it works on the current one), which
 //   * reads the footprint's 512 model cells from the staged tile once into
 //     registers (lane: v row = lane & 7, planes lane >> 3 and that + 4, all 8
-//     u taps: 16 complex cells),
-//   * per sample forms the 24 kernel weights (lanes 0-23, one
-//     exponential-of-semicircle evaluation each), degrids with 32 FMAs per
-//     lane and a shuffle reduction, forms the weighted residual and spreads
-//     it into 16 complex accumulators per lane, all in registers,
+//     u taps: 16 complex cells, held as FP32 pairs of adjacent u taps),
+//   * per pair of samples forms the 2 x 24 kernel weights (one
+//     exponential-of-semicircle evaluation per weight, spread over the
+//     lanes), degrids both with packed FP32x2 FMAs, reduces them with a
+//     transposed butterfly (10 shuffles for the pair), forms the weighted
+//     residuals and spreads them into 16 complex accumulators per lane,
 //   * adds its accumulators into the shared-memory grid tile once per chunk
 //     (shared-memory float reductions: warps of one item may share cells).
 // The model tile (8 planes x 23 x 24 complex cells, the tile plus the kernel
@@ -165,16 +170,74 @@ struct FpArgs {
   const uint32_t* items;       // entry offset of each work item (+ sentinel)
   const uint32_t* item_chunk;  // first chunk of each work item (+ sentinel)
   const uint32_t* chunks;      // entry offset of each chunk (+ sentinel)
-  const uint32_t* samples;     // sample index per entry, gridder order
   const float4* geom;          // EntryGeom<float> per entry, gridder order
-  const float2* vis;           // per sample
-  const float* weight;         // per sample, or null (= 1)
+  const float4* ysamp;         // per entry: {w re v, w im v, w, 0}, gridder order
   int64_t item_begin, item_count;
   int bt, bw, win_lo;
   int* status;                 // the job's status word
 };
 
 constexpr unsigned kFull = 0xffffffffu;
+constexpr int kGroup = 2;                     // samples degridded, reduced and gridded together
+constexpr int kCbMax = 1024;                  // chunk bounds of an item staged in shared memory
+
+// Exponential-of-semicircle weight of tap i (see es_weight) from the
+// hardware approximations: sqrt.approx and exp(x) = 2^(x log2 e) by
+// ex2.approx (relative errors near 2^-22, far below the FP32 operator's
+// 1e-5 bound).
+__device__ __forceinline__ float es_weight_fast(float d, int i) {
+  const float z = fmaf(d + (float)i, 2.0f / kW, -1.0f);
+  const float t = fmaxf(fmaf(-z, z, 1.0f), 0.0f);
+  float r, e;
+  asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(t));
+  const float x = (float)(kBeta * 1.4426950408889634) * (r - 1.0f);
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(e) : "f"(x));
+  return e;
+}
+
+// Packed FP32 pairs held as 64-bit register pairs (lo = first element) for
+// the f32x2 FMA: d = a * b + c element-wise.
+typedef unsigned long long f2x;
+__device__ __forceinline__ f2x ffma2(f2x a, f2x b, f2x c) {
+  f2x d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+__device__ __forceinline__ f2x pack2(float lo, float hi) {
+  f2x d;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(d) : "f"(lo), "f"(hi));
+  return d;
+}
+__device__ __forceinline__ float2 unpack2(f2x v) {
+  float2 r;
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(r.x), "=f"(r.y) : "l"(v));
+  return r;
+}
+__device__ __forceinline__ float hsum2(f2x v) {
+  const float2 r = unpack2(v);
+  return r.x + r.y;
+}
+
+// keep-or-send exchange of one butterfly stage: the lane keeps the half its
+// lane bit selects and adds the partner's copy of the same sample
+__device__ __forceinline__ float2 bfly(bool hi, float2 lo_v, float2 hi_v, int mask) {
+  const float2 keep = hi ? hi_v : lo_v;
+  const float2 send = hi ? lo_v : hi_v;
+  return make_float2(keep.x + __shfl_xor_sync(kFull, send.x, mask), keep.y + __shfl_xor_sync(kFull, send.y, mask));
+}
+
+// 16-byte asynchronous global -> shared copy (cp.async, cached at L2 only)
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+
+// per warp: two chunk slots ({du, dv, dw, tap} and {w re v, w im v, w, 0} of
+// up to 32 entries) and the weights of one group of samples
+struct WarpScratch {
+  float4 g[2][kChunkMax];
+  float4 y[2][kChunkMax];
+  float w[kGroup * 24];
+};
 
 template <int MODE>
 __global__ void __launch_bounds__(kFpThreads, 2)
@@ -182,14 +245,19 @@ __global__ void __launch_bounds__(kFpThreads, 2)
   constexpr bool kModel = (MODE == kResid);
   extern __shared__ unsigned char smem_raw[];
   unsigned char* base =
-      reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+      reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
   float* grid = reinterpret_cast<float*>(base);
   const float2* model = reinterpret_cast<const float2*>(base + kTileBytes);
-  uint64_t* bar = reinterpret_cast<uint64_t*>(base + (kModel ? 2 : 1) * kTileBytes);
-  float* wscr = reinterpret_cast<float*>(bar + 2);   // per warp: two slots of 32 weights
+  unsigned char* tail = base + (kModel ? 2 : 1) * kTileBytes;
+  WarpScratch* scratch = reinterpret_cast<WarpScratch*>(tail);
+  uint32_t* cb = reinterpret_cast<uint32_t*>(scratch + kFpWarps);   // chunk bounds of the item
+  uint32_t* queue = cb + kCbMax;                                     // next chunk to claim
+  uint64_t* bar = reinterpret_cast<uint64_t*>(queue + 2);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int vrow = lane & 7, pa = lane >> 3;         // this lane's v row and planes pa, pa + 4
+  const int mine = (lane >> 4) & 1;                  // the group sample whose degrid sum this lane ends with
+  const bool b4 = (lane >> 4) & 1;
   const uint32_t bar_a = smem_u32(bar);
   const uint32_t tmask = (1u << a.bt) - 1u;
   if (kModel && threadIdx.x == 0) {
@@ -199,7 +267,8 @@ __global__ void __launch_bounds__(kFpThreads, 2)
   }
   __syncthreads();
   uint32_t phase = 0;
-  float* ws = wscr + warp * 64;
+  WarpScratch& ws = scratch[warp];
+  float* wg = ws.w;
 
   for (int64_t it = blockIdx.x; it < a.item_count; it += gridDim.x) {
     const int64_t item = a.item_begin + it;
@@ -212,11 +281,20 @@ __global__ void __launch_bounds__(kFpThreads, 2)
       mbar_expect_tx(bar_a, kTileBytes);
       tma_load_3d(smem_u32(model), &tm_model, 2 * v0, u0, p0, bar_a);
     }
+    const uint32_t c0 = a.item_chunk[item];
+    const int nch = (int)(a.item_chunk[item + 1] - c0);
     float4* g4 = reinterpret_cast<float4*>(grid);
     for (int i = threadIdx.x; i < kTileFloats / 4; i += kFpThreads) g4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int i = threadIdx.x; i <= nch && i < kCbMax; i += kFpThreads) cb[i] = a.chunks[c0 + i];
+    if (threadIdx.x == 0) *queue = 0u;
     if (kModel) {
-      bool ok = false;
-      for (uint32_t k = 0; k < kWaitPolls && !ok; ++k) ok = mbar_try_wait(bar_a, phase);
+      // one thread polls (bounded) while the others wait at the barrier,
+      // leaving the issue slots to the SM's other CTA
+      bool ok = true;
+      if (threadIdx.x == 0) {
+        ok = false;
+        for (uint32_t k = 0; k < kWaitPolls && !ok; ++k) ok = mbar_try_wait(bar_a, phase);
+      }
       phase ^= 1u;
       if (!__syncthreads_and(ok)) {
         // the tile never arrived: report, give the copy a last bounded
@@ -232,92 +310,167 @@ __global__ void __launch_bounds__(kFpThreads, 2)
       __syncthreads();
     }
 
-    const uint32_t c0 = a.item_chunk[item], c1 = a.item_chunk[item + 1];
-    for (uint32_t c = c0 + warp; c < c1; c += kFpWarps) {
-      const uint32_t eb = a.chunks[c];
-      const int nb = (int)(a.chunks[c + 1] - eb);
-      float du = 0.f, dv = 0.f, dw = 0.f, vr = 0.f, vi = 0.f, wt = 0.f;
-      uint32_t ouv = 0;
+    // chunk bound i of the item (staged, or read from global past kCbMax)
+    auto bound = [&](int i) -> uint32_t { return i < kCbMax ? cb[i] : a.chunks[c0 + i]; };
+    // claim the next chunk of the item for this warp
+    auto claim = [&]() -> int {
+      int k = 0;
+      if (lane == 0) k = (int)atomicAdd(queue, 1u);
+      return __shfl_sync(kFull, k, 0);
+    };
+    // start the copies of chunk k's entries into slot `sl`; entries past the
+    // chunk's end are zero (zero weight and data)
+    auto fetch = [&](int k, int sl) {
+      const uint32_t eb = bound(k);
+      const int nb = (int)(bound(k + 1) - eb);
       if (lane < nb) {
-        const float4 g = a.geom[eb + lane];
-        du = g.x;
-        dv = g.y;
-        dw = g.z;
-        ouv = __float_as_uint(g.w);
-        const uint32_t s = a.samples[eb + lane];
-        const float2 v = a.vis[s];
-        wt = a.weight ? a.weight[s] : 1.0f;
-        vr = wt * v.x;
-        vi = wt * v.y;
+        cp_async16(&ws.g[sl][lane], a.geom + eb + lane);
+        cp_async16(&ws.y[sl][lane], a.ysamp + eb + lane);
+      } else {
+        ws.g[sl][lane] = make_float4(0.f, 0.f, 0.f, 0.f);
+        ws.y[sl][lane] = make_float4(0.f, 0.f, 0.f, 0.f);
       }
-      ouv = __shfl_sync(kFull, ouv, 0);
+      asm volatile("cp.async.commit_group;" ::: "memory");
+    };
+
+    int k = claim();
+    int sl = 0;
+    if (k < nch) fetch(k, sl);
+    while (k < nch) {
+      const int k2 = claim();
+      if (k2 < nch) {
+        fetch(k2, sl ^ 1);
+        asm volatile("cp.async.wait_group 1;" ::: "memory");
+      } else {
+        asm volatile("cp.async.wait_group 0;" ::: "memory");
+      }
+      __syncwarp();
+      const int nb = (int)(bound(k + 1) - bound(k));
+      const float4* sd = ws.g[sl];
+      const float4* sy = ws.y[sl];
+      const uint32_t ouv = __float_as_uint(sd[0].w);
       const int cell = (int)(ouv & 0xffu) * kRow + (int)(ouv >> 8) + vrow;   // complex cell in a plane
-      float2 m0[kW], m1[kW];
+      // the footprint's model cells as pairs of adjacent u taps (re, im separately)
+      f2x mar[4], mai[4], mbr[4], mbi[4];
       if (kModel) {
 #pragma unroll
-        for (int i = 0; i < kW; ++i) {
-          m0[i] = model[pa * kPlaneC + cell + i * kRow];
-          m1[i] = model[(pa + 4) * kPlaneC + cell + i * kRow];
+        for (int t = 0; t < 4; ++t) {
+          const float2 x0 = model[pa * kPlaneC + cell + (2 * t) * kRow];
+          const float2 x1 = model[pa * kPlaneC + cell + (2 * t + 1) * kRow];
+          const float2 y0 = model[(pa + 4) * kPlaneC + cell + (2 * t) * kRow];
+          const float2 y1 = model[(pa + 4) * kPlaneC + cell + (2 * t + 1) * kRow];
+          mar[t] = pack2(x0.x, x1.x);
+          mai[t] = pack2(x0.y, x1.y);
+          mbr[t] = pack2(y0.x, y1.x);
+          mbi[t] = pack2(y0.y, y1.y);
         }
       }
-      float a0r[kW], a0i[kW], a1r[kW], a1i[kW];
+      f2x aar[4], aai[4], abr[4], abi[4];   // accumulators, pairs of adjacent u taps
 #pragma unroll
-      for (int i = 0; i < kW; ++i) a0r[i] = a0i[i] = a1r[i] = a1i[i] = 0.f;
+      for (int t = 0; t < 4; ++t) aar[t] = aai[t] = abr[t] = abi[t] = 0ull;
 
-      for (int j = 0; j < nb; ++j) {
-        // kernel weights of sample j: lanes 0-7 u taps, 8-15 v taps, 16-23 w taps
-        const float kdu = __shfl_sync(kFull, du, j);
-        const float kdv = __shfl_sync(kFull, dv, j);
-        const float kdw = __shfl_sync(kFull, dw, j);
-        const float d = lane < 8 ? kdu : (lane < 16 ? kdv : kdw);
-        const float wgt = lane < 24 ? es_weight<float>(d, lane & 7) : 0.f;
-        float* slot = ws + (j & 1) * 32;
-        slot[lane] = wgt;
+      for (int j0 = 0; j0 < nb; j0 += kGroup) {
+        // ---- the group's kGroup x 24 kernel weights over the warp's lanes:
+        // entry e of sample e / 24, tap e % 24 (0-7 u, 8-15 v, 16-23 w)
+#pragma unroll
+        for (int r = 0; r < (kGroup * 24 + 31) / 32; ++r) {
+          const int e = lane + 32 * r;
+          if (e >= kGroup * 24) break;
+          const int kk = e / 24, tap = e - 24 * (e / 24);
+          const float* dk = reinterpret_cast<const float*>(&sd[j0 + kk]);
+          wg[e] = es_weight_fast(dk[tap >> 3], tap & 7);
+        }
         __syncwarp();
-        const float4 wlo = *reinterpret_cast<const float4*>(slot);
-        const float4 whi = *reinterpret_cast<const float4*>(slot + 4);
-        const float wu[kW] = {wlo.x, wlo.y, wlo.z, wlo.w, whi.x, whi.y, whi.z, whi.w};
-        const float wv = slot[8 + vrow];
-        const float fa = wv * slot[16 + pa], fb = wv * slot[20 + pa];
-        float yr = __shfl_sync(kFull, vr, j);
-        float yi = __shfl_sync(kFull, vi, j);
+        // per sample: the lane's v-row times w-plane weights (fa: plane pa,
+        // fb: plane pa + 4)
+        float fa[kGroup], fb[kGroup];
+#pragma unroll
+        for (int kk = 0; kk < kGroup; ++kk) {
+          const float wv = wg[kk * 24 + 8 + vrow];
+          fa[kk] = wv * wg[kk * 24 + 16 + pa];
+          fb[kk] = wv * wg[kk * 24 + 20 + pa];
+        }
+        float y0 = 0.f, y1 = 0.f;   // w (v - model) of sample `mine`
         if (kModel) {
-          float sar = 0.f, sai = 0.f, sbr = 0.f, sbi = 0.f;
+          // ---- degrid partials of the 4 samples over this lane's 16 cells
+          float2 part[kGroup];
 #pragma unroll
-          for (int i = 0; i < kW; ++i) {
-            sar = fmaf(wu[i], m0[i].x, sar);
-            sai = fmaf(wu[i], m0[i].y, sai);
-            sbr = fmaf(wu[i], m1[i].x, sbr);
-            sbi = fmaf(wu[i], m1[i].y, sbi);
+          for (int kk = 0; kk < kGroup; ++kk) {
+            const ulonglong2 wlo = *reinterpret_cast<const ulonglong2*>(wg + kk * 24);
+            const ulonglong2 whi = *reinterpret_cast<const ulonglong2*>(wg + kk * 24 + 4);
+            const f2x wu[4] = {wlo.x, wlo.y, whi.x, whi.y};
+            f2x sar = 0ull, sai = 0ull, sbr = 0ull, sbi = 0ull;
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+              sar = ffma2(wu[t], mar[t], sar);
+              sai = ffma2(wu[t], mai[t], sai);
+              sbr = ffma2(wu[t], mbr[t], sbr);
+              sbi = ffma2(wu[t], mbi[t], sbi);
+            }
+            part[kk] = make_float2(fmaf(fa[kk], hsum2(sar), fb[kk] * hsum2(sbr)),
+                                   fmaf(fa[kk], hsum2(sai), fb[kk] * hsum2(sbi)));
           }
-          float pr = fa * sar + fb * sbr, pi = fa * sai + fb * sbi;
+          // ---- transposed butterfly: the first stage exchanges half of the
+          // pair, so the lane ends with the sum over all 32 lanes of sample
+          // `mine` after 10 shuffles for the 2 samples
+          float2 tot = bfly(b4, part[0], part[1], 16);
+          tot.x += __shfl_xor_sync(kFull, tot.x, 8);
+          tot.y += __shfl_xor_sync(kFull, tot.y, 8);
+          tot.x += __shfl_xor_sync(kFull, tot.x, 4);
+          tot.y += __shfl_xor_sync(kFull, tot.y, 4);
+          tot.x += __shfl_xor_sync(kFull, tot.x, 2);
+          tot.y += __shfl_xor_sync(kFull, tot.y, 2);
+          tot.x += __shfl_xor_sync(kFull, tot.x, 1);
+          tot.y += __shfl_xor_sync(kFull, tot.y, 1);
+          const float4 ym = sy[j0 + mine];
+          y0 = fmaf(-ym.z, tot.x, ym.x);
+          y1 = fmaf(-ym.z, tot.y, ym.y);
+        }
+        // ---- grid the group's samples into the accumulators
 #pragma unroll
-          for (int o = 16; o; o >>= 1) {
-            pr += __shfl_xor_sync(kFull, pr, o);
-            pi += __shfl_xor_sync(kFull, pi, o);
+        for (int kk = 0; kk < kGroup; ++kk) {
+          const float fak = fa[kk], fbk = fb[kk];
+          float yrk, yik;
+          if (kModel) {
+            yrk = __shfl_sync(kFull, y0, 16 * kk);
+            yik = __shfl_sync(kFull, y1, 16 * kk);
+          } else {
+            const float4 yk = sy[j0 + kk];
+            yrk = yk.x;
+            yik = yk.y;
           }
-          const float kwt = __shfl_sync(kFull, wt, j);
-          yr = fmaf(-kwt, pr, yr);
-          yi = fmaf(-kwt, pi, yi);
-        }
-        const float car = yr * fa, cai = yi * fa, cbr = yr * fb, cbi = yi * fb;
+          const ulonglong2 wlo = *reinterpret_cast<const ulonglong2*>(wg + kk * 24);
+          const ulonglong2 whi = *reinterpret_cast<const ulonglong2*>(wg + kk * 24 + 4);
+          const f2x wu[4] = {wlo.x, wlo.y, whi.x, whi.y};
+          const float ar = yrk * fak, ai = yik * fak, br = yrk * fbk, bi = yik * fbk;
+          const f2x car = pack2(ar, ar), cai = pack2(ai, ai), cbr = pack2(br, br), cbi = pack2(bi, bi);
 #pragma unroll
-        for (int i = 0; i < kW; ++i) {
-          a0r[i] = fmaf(car, wu[i], a0r[i]);
-          a0i[i] = fmaf(cai, wu[i], a0i[i]);
-          a1r[i] = fmaf(cbr, wu[i], a1r[i]);
-          a1i[i] = fmaf(cbi, wu[i], a1i[i]);
+          for (int t = 0; t < 4; ++t) {
+            aar[t] = ffma2(car, wu[t], aar[t]);
+            aai[t] = ffma2(cai, wu[t], aai[t]);
+            abr[t] = ffma2(cbr, wu[t], abr[t]);
+            abi[t] = ffma2(cbi, wu[t], abi[t]);
+          }
         }
+        __syncwarp();   // the group's weights are read before the next group overwrites them
       }
       float* ga = grid + 2 * (pa * kPlaneC + cell);
       float* gb = grid + 2 * ((pa + 4) * kPlaneC + cell);
 #pragma unroll
-      for (int i = 0; i < kW; ++i) {
-        atomicAdd(ga + 2 * i * kRow, a0r[i]);
-        atomicAdd(ga + 2 * i * kRow + 1, a0i[i]);
-        atomicAdd(gb + 2 * i * kRow, a1r[i]);
-        atomicAdd(gb + 2 * i * kRow + 1, a1i[i]);
+      for (int t = 0; t < 4; ++t) {
+        const float2 ar = unpack2(aar[t]), ai = unpack2(aai[t]), br = unpack2(abr[t]), bi = unpack2(abi[t]);
+        atomicAdd(ga + 2 * (2 * t) * kRow, ar.x);
+        atomicAdd(ga + 2 * (2 * t) * kRow + 1, ai.x);
+        atomicAdd(ga + 2 * (2 * t + 1) * kRow, ar.y);
+        atomicAdd(ga + 2 * (2 * t + 1) * kRow + 1, ai.y);
+        atomicAdd(gb + 2 * (2 * t) * kRow, br.x);
+        atomicAdd(gb + 2 * (2 * t) * kRow + 1, bi.x);
+        atomicAdd(gb + 2 * (2 * t + 1) * kRow, br.y);
+        atomicAdd(gb + 2 * (2 * t + 1) * kRow + 1, bi.y);
       }
+      __syncwarp();   // the slot is read before its next fetch
+      sl ^= 1;
+      k = k2;
     }
     // the grid tile's shared-memory writes become visible to the TMA unit,
     // then one thread adds the tile into the residual planes
@@ -330,6 +483,20 @@ __global__ void __launch_bounds__(kFpThreads, 2)
     __syncthreads();
   }
   if (threadIdx.x == 0) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+}
+
+// per entry of [e_begin, e_begin + n): ysamp = {w re v, w im v, w, 0} of its
+// sample (gridder order)
+__global__ void k_gather_y(const uint32_t* __restrict__ samples, const float2* __restrict__ vis,
+                           const float* __restrict__ weight, int64_t e_begin, int64_t n,
+                           float4* __restrict__ ysamp) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t e = e_begin + i;
+    const uint32_t s = samples[e];
+    const float2 v = vis[s];
+    const float w = weight ? weight[s] : 1.0f;
+    ysamp[e] = make_float4(w * v.x, w * v.y, w, 0.f);
+  }
 }
 
 // ------------------------------------------------------------------ host ----
@@ -364,7 +531,8 @@ int plane_map(CUtensorMap* map, const void* planes, int S, int nplanes) {
 
 template <int MODE>
 size_t fp_smem() {
-  return 1024 + (size_t)(MODE == kResid ? 2 : 1) * kTileBytes + 16 + kFpWarps * 64 * sizeof(float);
+  return 128 + (size_t)(MODE == kResid ? 2 : 1) * kTileBytes + (size_t)kFpWarps * sizeof(WarpScratch) +
+         kCbMax * sizeof(uint32_t) + 8 + 16;
 }
 
 template <int MODE>
@@ -388,9 +556,10 @@ int launch_fp(const Job* job, const FpArgs& a, const CUtensorMap& tm_model, cons
 
 }  // namespace
 
-int launch_tiles_fp(const Job* job, int mode, int64_t item_begin, int64_t item_count, int win_lo, int S,
-                    const void* model_planes, void* out_planes, const void* vis, cudaStream_t st) {
-  if (item_count <= 0) return RIX_OK;
+int launch_tiles_fp(const Job* job, int mode, int64_t item_begin, int64_t item_count, int64_t ent_begin,
+                    int64_t ent_count, int win_lo, int S, const void* model_planes, void* out_planes, const void* vis,
+                    cudaStream_t st) {
+  if (item_count <= 0 || ent_count <= 0) return RIX_OK;
   if (job->tile != kT || job->nw < kW || job->fp64 || (mode != kGrid && mode != kResid) || (S & 1))
     return set_error(RIX_EINVAL, "k_tiles_fp: unsupported job (tile %d, planes %d)", job->tile, job->nw);
   FpArgs a{};
@@ -398,10 +567,8 @@ int launch_tiles_fp(const Job* job, int mode, int64_t item_begin, int64_t item_c
   a.items = job->items.as<uint32_t>();
   a.item_chunk = job->item_chunk.as<uint32_t>();
   a.chunks = job->chunks.as<uint32_t>();
-  a.samples = job->gsamples.as<uint32_t>();
   a.geom = job->egeom.as<float4>();
-  a.vis = static_cast<const float2*>(vis);
-  a.weight = job->weight.as<float>();
+  a.ysamp = job->ysamp.as<float4>();
   a.item_begin = item_begin;
   a.item_count = item_count;
   a.bt = job->bt;
@@ -410,6 +577,14 @@ int launch_tiles_fp(const Job* job, int mode, int64_t item_begin, int64_t item_c
   a.status = job->status.as<int>();
   CUtensorMap tm_out, tm_model;
   RIX_TRY(plane_map(&tm_out, out_planes, S, job->nw));
+  {
+    // the weighted visibilities of the partition's entries in gridder order
+    const int blocks = (int)std::min<int64_t>(ceil_div(ent_count, 256), (int64_t)job->ctx->num_sms * 8);
+    ::rix::note_launch();
+    k_gather_y<<<blocks, 256, 0, st>>>(job->gsamples.as<uint32_t>(), static_cast<const float2*>(vis),
+                                       job->weight.as<float>(), ent_begin, ent_count, job->ysamp.as<float4>());
+    RIX_LAUNCH_CHECK();
+  }
   if (mode == kResid) {
     RIX_TRY(plane_map(&tm_model, model_planes, S, job->nw));
     return launch_fp<kResid>(job, a, tm_model, tm_out, st);
@@ -421,6 +596,8 @@ template <typename R>
 int grid_work_order(Job* job, cudaStream_t st) {
   const int64_t n_ent = job->n_entries, n_items = job->n_items;
   RIX_TRY(job->gsamples.alloc(job->ctx, (size_t)std::max<int64_t>(n_ent, 1) * sizeof(uint32_t)));
+  if (!job->fp64 && job->nw > 0)   // the FP32 w-stacked gridder's per-entry weighted visibilities
+    RIX_TRY(job->ysamp.alloc(job->ctx, (size_t)std::max<int64_t>(n_ent, 1) * sizeof(float4)));
   RIX_TRY(job->chunks.alloc(job->ctx, (size_t)(n_ent + 1) * sizeof(uint32_t)));
   RIX_TRY(job->item_chunk.alloc(job->ctx, (size_t)(n_items + 1) * sizeof(uint32_t)));
   if (n_ent == 0 || n_items == 0) {

@@ -287,6 +287,7 @@ struct Job {
   // sorted order rix_get_sorted_entries reports.
   DevBuf egeom;                             // per entry: kernel offsets and tap origin (EntryGeom<R>)
   DevBuf gsamples;                          // per entry: sample index
+  DevBuf ysamp;                             // FP32 w-stacked: per entry {w re v, w im v, w, 0} of the last gridding call
   DevBuf chunks;                            // entry offset of each chunk (+1 sentinel: n_entries)
   DevBuf item_chunk;                        // first chunk of each work item (+1 sentinel: the chunk count)
   int64_t n_entries = 0, n_items = 0;
@@ -330,8 +331,9 @@ int grid_work_order(Job* job, cudaStream_t st);
 // degrids model_planes and spreads w * (vis - model visibility); planes
 // [n_wplanes][S][S] complex on the partition's uv window [win_lo, win_lo + S)
 // (out_planes zeroed by the caller).  Tile side 16.
-int launch_tiles_fp(const Job* job, int mode, int64_t item_begin, int64_t item_count, int win_lo, int S,
-                    const void* model_planes, void* out_planes, const void* vis, cudaStream_t st);
+int launch_tiles_fp(const Job* job, int mode, int64_t item_begin, int64_t item_count, int64_t ent_begin,
+                    int64_t ent_count, int win_lo, int S, const void* model_planes, void* out_planes, const void* vis,
+                    cudaStream_t st);
 template <typename R>
 int op_degrid(Job* job, int p, const R* image, cplx<R>* vis_out, cudaStream_t st);
 template <typename R>

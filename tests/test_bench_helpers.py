@@ -50,17 +50,16 @@ def _args(**kw):
 
 
 def test_tiles_traffic_only_for_the_measured_source_and_workload(bench):
-    src = os.path.join(ROOT, "paper_2507_22128_gb300", "csrc", "k_grid.cu")
+    src = os.path.join(ROOT, "paper_2507_22128_gb300", "csrc", "k_tiles_fp.cu")
     with open(src, "rb") as f:
         sha = hashlib.sha1(f.read()).hexdigest()
     t = bench.TILES_TRAFFIC
     got = bench.tiles_traffic(_args())
-    if sha != t["k_grid_sha1"]:
+    if sha != t["src_sha1"]:
         assert got is None
     else:
-        # ten residual launches per partition and one PSF launch each
-        want = (10 * sum(t["resid"]) + sum(t["psf"])) / 22
-        assert got == pytest.approx(want)
+        # the mean over the two partitions' launches
+        assert got == pytest.approx(sum(t["resid"]) / 2)
     assert bench.tiles_traffic(_args(fp64=True)) is None
     assert bench.tiles_traffic(_args(n=512)) is None
     assert bench.tiles_traffic(_args(n_times=300)) is None
@@ -68,19 +67,20 @@ def test_tiles_traffic_only_for_the_measured_source_and_workload(bench):
 
 def test_roofline_arithmetic(bench, monkeypatch):
     monkeypatch.setattr(bench, "measured_peaks", lambda: ({"sm_max_mhz": 2000.0, "hbm_gbs": 5000.0}, "measured"))
-    st = {"window_size": [100, 200]}
-    a = _args(steps=1, cycles=2)
-    r = bench.roofline_tiles(tiles_ms=4.0, tiles_n=4, st=st, a=a, entries_timed=1_000_000)
+    st = {"window_size": [100, 200], "part_count": [600_000, 400_000]}
+    a = _args()
+    mc = {"per_partition_serial": {0: {"gridder_ms": 1.5}, 1: {"gridder_ms": 2.5}}}
+    r = bench.roofline_gridder(mc, st, a)
     peak = 152 * 128 * 2 * 2000e6 / 1e12
     assert r["peak"] == pytest.approx(peak)
     assert r["achieved"] == pytest.approx(4096.0 * 1e6 / 4e-3 / 1e12)
     assert r["frac"] == pytest.approx(r["achieved"] / peak)
-    ent_b = (24.0 / 4 + 8 + 4 + 4) * 1e6
-    plane_b = 1 * 2 * (2 * 8.0 * 16 * (100 ** 2 + 200 ** 2))
-    assert r["hbm"]["algorithmic_bytes_per_launch"] == pytest.approx((ent_b + plane_b) / 4)
-    assert r["hbm"]["frac"] == pytest.approx((ent_b + plane_b) / 4e-3 / 1e9 / 5000.0)
-    assert bench.roofline_tiles(0.0, 4, st, a, 1) is None
-    assert bench.roofline_tiles(4.0, 0, st, a, 1) is None
+    byt = 32.0 * 1e6 + 2 * 8.0 * 16 * (100 ** 2 + 200 ** 2)
+    assert r["hbm"]["algorithmic_bytes_per_launch"] == pytest.approx(byt / 2)
+    assert r["hbm"]["frac"] == pytest.approx(byt / 4e-3 / 1e9 / 5000.0)
+    assert r["ms_per_launch"] == {"low": 1.5, "high": 2.5}
+    mc0 = {"per_partition_serial": {0: {"gridder_ms": 0.0}, 1: {"gridder_ms": 0.0}}}
+    assert bench.roofline_gridder(mc0, st, a) is None
 
 
 def test_whole_job_value_is_the_aggregate_over_ranks(bench):
