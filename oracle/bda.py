@@ -71,7 +71,7 @@ def windows(uvw_m: np.ndarray, n_times: int, n_bl: int, f_max: float, n: int, ce
     sb = uv_shift_cells(uvw_m, n_times, n_bl, f_max, n, cell)
     k = np.full(n_bl, n_times, dtype=np.int64)
     moving = sb > 0.0
-    k[moving] = np.minimum(n_times, np.maximum(1, np.floor(max_shift / sb[moving]).astype(np.int64)))
+    k[moving] = np.clip(np.floor(max_shift / sb[moving]), 1, n_times).astype(np.int64)
     return k
 
 
