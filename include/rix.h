@@ -76,7 +76,19 @@ typedef struct {
   int32_t n_part;         /* number of uv partitions: 1 .. RIX_MAX_PART */
   int32_t tile;           /* uv tile side for the sort and the gridder: 16 or 32; 0 = 16 */
   int32_t weighting;      /* RIX_WEIGHT_NATURAL (the given weights) or RIX_WEIGHT_UNIFORM */
+  int32_t exchange;       /* RIX_EXCHANGE_IMAGE (0) or RIX_EXCHANGE_SPECTRAL: the form of Phi_p^n */
 } rix_job_desc;
+
+/* How a partition's filtered deconvolved residual Phi_p^n = Gamma_p i_bar_p^n
+ * travels to the other partitions (Sec. 4.1).  IMAGE: the N x N image.
+ * SPECTRAL (the band-limited compression of Sec. 6.3 and Sec. 7 item a):
+ * the coefficients of Gamma_p F pad i_bar_p on the ring support of Gamma_p
+ * (where Gamma_p > 0) in the half plane k_u <= 0 (i_bar is real, so the
+ * spectrum is Hermitian), rix_phi_support of them; the receiver rebuilds the
+ * spectrum, its conjugate half, transforms and crops: the same Phi_p up to
+ * rounding, in fewer bytes for every partition but the outermost. */
+#define RIX_EXCHANGE_IMAGE 0
+#define RIX_EXCHANGE_SPECTRAL 1
 
 /* Visibility weighting.  Uniform (Sec. 5.1): each sample's weight is divided
  * by the sum of the weights in its cell of the N x N image's Fourier grid
@@ -278,6 +290,69 @@ int rix_get_model(rix_job_t job, int part, void* image_out, rix_stream_t stream)
 /* Final image: the equal-weight mean of the partitions' model images
  * (0.5 / 0.5 for two partitions), device N x N. */
 int rix_combine(rix_job_t job, void* image_out, rix_stream_t stream);
+
+/* ---- band-limited exchange (Sec. 6.3, Sec. 7 item a) ---------------------- */
+
+/* Number of complex coefficients of partition `part`'s band-limited
+ * message (valid after rix_set_uv_partition; fixed for the job): the points
+ * of the centred 2N x 2N frequency grid with Gamma_part > 0 and k_u <= 0. */
+int rix_phi_support(rix_job_t job, int part, int64_t* count_out);
+
+/* The band-limited message of partition `part`'s last minor cycle: the
+ * coefficients of Gamma_part F pad i_bar (i_bar the deconvolved residual of
+ * that cycle) at the rix_phi_support points, in ascending order of the
+ * u-major flat index ju * 2N + jv (ju, jv the centred indices of k_u, k_v),
+ * into packed_out (device, the job precision's complex type).  Needs a
+ * completed minor cycle of the partition (RIX_ESTATE otherwise). */
+int rix_phi_pack(rix_job_t job, int part, void* packed_out, rix_stream_t stream);
+
+/* Phi = crop F^-1 of the spectrum rebuilt from such coefficients of
+ * partition `part` (their conjugates completing the other half plane),
+ * normalised like the minor cycles' filtered images: into phi_out (device
+ * N x N real).  The round trip rix_phi_pack -> rix_phi_unpack gives
+ * Gamma_part i_bar without loss beyond rounding. */
+int rix_phi_unpack(rix_job_t job, int part, const void* packed, void* phi_out, rix_stream_t stream);
+
+/* ---- baseline-dependent averaging (Sec. 6.2, Sec. 7 item d) ---------------- */
+
+/* The remedy the paper names for unbalanced partitions: a dense uv centre
+ * (Sgr B2, Sec. 6.2) leaves the outer partition idle; averaging each
+ * baseline's consecutive time samples over a window that shrinks with its
+ * uv speed (after Wijnholds et al. 2018) thins the centre, so a ring radius
+ * splits the samples more evenly.  A preprocessing step before
+ * rix_set_uv_partition, on the context's device.
+ *   uvw_m    device [n_times][n_baselines][3] float64, rows time-major
+ *   vis      device [n_times * n_baselines][nchan] complex (float2 for
+ *            RIX_FP32, double2 for RIX_FP64)
+ *   weight   device [n_times * n_baselines][nchan] float32, or NULL (= 1)
+ *   freq_hz  host [nchan]
+ * Per baseline b: s_b = the largest (u, v) change between consecutive times
+ * at the highest frequency, in cells of the N x N image's Fourier grid
+ * (|du, dv|_lambda N cell_rad, the unit of the partition radius); window
+ * k_b = min(n_times, max(1, floor(max_shift_px / s_b))) time samples
+ * (n_times when s_b = 0); the times are cut into consecutive windows of k_b,
+ * the last shorter.  Each window gives one output row: the mean uvw, and per
+ * channel the weight sum and the weighted mean visibility (0 when the sum
+ * is 0).  Output rows are baseline-major (baseline 0's windows in time
+ * order, then baseline 1's, ...).  The window arithmetic is FP64 with every
+ * product, sum and quotient rounded separately; sums are FP64. */
+
+/* The number of averaged rows (host *nrow_out) and optionally the windows
+ * k_b (host [n_baselines] int32).  Synchronises `stream`. */
+int rix_bda_rows(rix_ctx_t ctx, const double* uvw_m, int64_t n_times, int64_t n_baselines, const double* freq_hz,
+                 int32_t nchan, int32_t n, double cell_rad, double max_shift_px, int32_t* window_out,
+                 int64_t* nrow_out, rix_stream_t stream);
+
+/* The averaged rows into uvw_out (device [rows][3] float64), vis_out (device
+ * [rows][nchan], the precision's complex type) and weight_out (device
+ * [rows][nchan] float32); RIX_EINVAL when they hold fewer than the rows
+ * rix_bda_rows reports (nrow_capacity).  *nrow_out (host, may be NULL)
+ * receives the row count.  Synchronises `stream` once (the row count is read
+ * back) before the averaging kernel is queued. */
+int rix_bda_average(rix_ctx_t ctx, const double* uvw_m, const void* vis, const float* weight, int64_t n_times,
+                    int64_t n_baselines, const double* freq_hz, int32_t nchan, int32_t precision, int32_t n,
+                    double cell_rad, double max_shift_px, double* uvw_out, void* vis_out, float* weight_out,
+                    int64_t nrow_capacity, int64_t* nrow_out, rix_stream_t stream);
 
 /* ---- gridding without device allocation ----------------------------------- */
 

@@ -76,3 +76,39 @@ def apply(x: np.ndarray, spec: np.ndarray) -> np.ndarray:
 
 def psf_spectrum(psf2n: np.ndarray) -> np.ndarray:
     return spectrum(psf2n.astype(np.complex128))
+
+
+# ---- band-limited exchange (Sec. 6.3, Sec. 7 item a) ------------------------
+# Phi_p = crop F^-1 [Gamma_p F pad i_bar_p] is the crop of an image whose
+# spectrum vanishes wherever Gamma_p does, and i_bar_p is real, so its
+# spectrum is Hermitian: the coefficients of Gamma_p F pad i_bar_p on the
+# ring support of Gamma_p in the half plane k_u <= 0 (centred index ju <= N,
+# both halves of the self-mirrored columns ju = 0 and ju = N) determine
+# Phi_p.  A receiver that scatters them back, completes the other half by
+# conjugation, transforms and crops recovers Phi_p without loss.
+
+def ring_support(gam_p: np.ndarray) -> np.ndarray:
+    """Flat u-major indices ju * 2N + jv, ascending, of the half plane
+    ju <= N where Gamma_p > 0."""
+    n2 = gam_p.shape[0]
+    mask = np.zeros_like(gam_p, dtype=bool)
+    mask[: n2 // 2 + 1] = gam_p[: n2 // 2 + 1] > 0.0
+    return np.nonzero(mask.reshape(-1))[0]
+
+
+def phi_pack(ibar: np.ndarray, gam_p: np.ndarray, idx: np.ndarray) -> np.ndarray:
+    """The exchanged coefficients: Gamma_p F pad i_bar at the support."""
+    return (gam_p * image_spectrum(ibar)).reshape(-1)[idx]
+
+
+def phi_unpack(coef: np.ndarray, idx: np.ndarray, n: int) -> np.ndarray:
+    """Phi = crop F^-1 of the spectrum rebuilt from the coefficients and
+    their conjugate mirrors k -> -k (centred index j -> 2N - j mod 2N)."""
+    n2 = 2 * n
+    spec = np.zeros(n2 * n2, dtype=np.complex128)
+    spec[idx] = coef
+    spec = spec.reshape(n2, n2)
+    ju, jv = np.divmod(idx, n2)
+    mirror = (ju > 0) & (ju < n)
+    spec[(n2 - ju[mirror]) % n2, (n2 - jv[mirror]) % n2] = np.conj(coef[mirror])
+    return crop(ispectrum(spec)).real

@@ -103,6 +103,46 @@ __global__ void k_axpy(R* __restrict__ y, const R* __restrict__ x, R alpha, int6
     y[i] += alpha * x[i];
 }
 
+// ---- band-limited exchange (Sec. 6.3, Sec. 7 item a) ----------------------
+// flags of the half plane ju <= N (k_u <= 0) of a partition's ring support,
+// Gamma_p > 0 (flat u-major index ju * 2N + jv)
+template <typename R>
+__global__ void k_ring_flags(const R* __restrict__ gam_p, int64_t nhalf, uint32_t* __restrict__ flags) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nhalf; i += (int64_t)gridDim.x * blockDim.x)
+    flags[i] = gam_p[i] > R(0) ? 1u : 0u;
+}
+__global__ void k_ring_index(const uint32_t* __restrict__ flags, const uint32_t* __restrict__ pos, int64_t nhalf,
+                             uint32_t* __restrict__ idx) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nhalf; i += (int64_t)gridDim.x * blockDim.x)
+    if (flags[i]) idx[pos[i]] = (uint32_t)i;
+}
+// the exchanged coefficients Gamma_p X at the support
+template <typename R>
+__global__ void k_phi_pack(const R* __restrict__ gam_p, const cplx<R>* __restrict__ spec,
+                           const uint32_t* __restrict__ idx, int64_t count, cplx<R>* __restrict__ out) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x) {
+    const uint32_t j = idx[i];
+    const R g = gam_p[j];
+    const cplx<R> x = spec[j];
+    out[i] = cmake<cplx<R>>(g * x.x, g * x.y);
+  }
+}
+// the spectrum rebuilt from the coefficients (zeroed by the caller) and
+// their conjugate mirrors k -> -k (index j -> 2N - j mod 2N) off the
+// self-mirrored columns ju = 0 and ju = N
+template <typename R>
+__global__ void k_phi_unpack(const cplx<R>* __restrict__ coef, const uint32_t* __restrict__ idx, int64_t count,
+                             int n, cplx<R>* __restrict__ spec) {
+  const int n2 = 2 * n;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x) {
+    const uint32_t j = idx[i];
+    const int ju = (int)(j / (uint32_t)n2), jv = (int)(j - (uint32_t)ju * n2);
+    const cplx<R> c = coef[i];
+    spec[j] = c;
+    if (ju > 0 && ju < n) spec[(int64_t)((n2 - ju) % n2) * n2 + (n2 - jv) % n2] = cmake<cplx<R>>(c.x, -c.y);
+  }
+}
+
 template <typename R>
 __global__ void k_mean(R* __restrict__ out, const R* const* __restrict__ imgs, int nimg, int64_t n) {
   const R inv = R(1) / (R)nimg;
@@ -407,11 +447,40 @@ int ensure(Job* job, DevBuf& b, size_t bytes) {
   return RIX_OK;
 }
 
-// rho_{q->p} += Phi_q^{n-1} for every other partition (cycle n >= 2)
+// Phi_p from its exchanged coefficients: out (+)= scale * crop F^-1[spectrum]
+// with the spectrum rebuilt in `spec` ((2N)^2) and `T` as the transpose
+// buffer ([2N][N] complex)
+template <typename R>
+int phi_from_coef(Job* job, int p, const cplx<R>* coef, cplx<R>* spec, cplx<R>* T, R* out, double scale,
+                  int accumulate, cudaStream_t st) {
+  const int n = job->desc.n;
+  const int64_t tot = (int64_t)4 * n * n;
+  const Part& pt = job->part[p];
+  RIX_CUDA(cudaMemsetAsync(spec, 0, tot * sizeof(cplx<R>), st));
+  ::rix::note_launch();
+  k_phi_unpack<R><<<blocks_for(job->ctx, pt.ring_count), 256, 0, st>>>(coef, pt.ring_idx.as<uint32_t>(),
+                                                                       pt.ring_count, n, spec);
+  RIX_LAUNCH_CHECK();
+  const XformGeom g = fill_geom(n);
+  RIX_TRY(inv_cols<R>(job->ctx, g, spec, kOpNone, nullptr, nullptr, T, st));
+  return inv_rows<R>(job->ctx, g, T, out, scale, accumulate, st);
+}
+
+// rho_{q->p} += Phi_q^{n-1} for every other partition (cycle n >= 2); with
+// the spectral exchange Phi_q arrives as its ring-support coefficients
 template <typename R>
 int ingest(Job* job, int p, int cycle, cudaStream_t st) {
   if (cycle < 2) return RIX_OK;
   const int64_t npix = (int64_t)job->desc.n * job->desc.n;
+  if (job->desc.exchange == RIX_EXCHANGE_SPECTRAL) {
+    Part& pt = job->part[p];
+    const double inv = 1.0 / (double)(4 * npix);
+    for (int q = 0; q < job->n_part; ++q)
+      if (q != p)
+        RIX_TRY(phi_from_coef<R>(job, q, job->part[q].outbox[(cycle - 1) & 1].as<cplx<R>>(), pt.fs_a.as<cplx<R>>(),
+                                 pt.ft_a.as<cplx<R>>(), pt.rho[q].as<R>(), inv, 1, st));
+    return RIX_OK;
+  }
   for (int q = 0; q < job->n_part; ++q) {
     if (q == p) continue;
     ::rix::note_launch(); k_axpy<R><<<blocks_for(job->ctx, npix), 256, 0, st>>>(job->part[p].rho[q].as<R>(),
@@ -461,7 +530,17 @@ int publish(Job* job, int p, int cycle, cudaStream_t st) {
   ::rix::note_launch(); k_axpy<R><<<blocks_for(job->ctx, npix), 256, 0, st>>>(pt.model.as<R>(), ibar, R(1), npix);
   RIX_LAUNCH_CHECK();
   const R* gam = job->gam.as<R>();
-  RIX_TRY(convolve<R>(job, pt, ibar, kOpMulReal, gam + p * tot, nullptr, pt.outbox[cycle & 1].as<R>(), inv, 0, st));
+  if (job->desc.exchange == RIX_EXCHANGE_SPECTRAL) {
+    // the message is Gamma_p F pad i_bar on the ring support (half plane)
+    RIX_TRY(img_spectrum<R>(job, pt, ibar, pt.fs_a.as<cplx<R>>(), st));
+    ::rix::note_launch();
+    k_phi_pack<R><<<blocks_for(job->ctx, pt.ring_count), 256, 0, st>>>(gam + p * tot, pt.fs_a.as<cplx<R>>(),
+                                                                       pt.ring_idx.as<uint32_t>(), pt.ring_count,
+                                                                       pt.outbox[cycle & 1].as<cplx<R>>());
+    RIX_LAUNCH_CHECK();
+  } else {
+    RIX_TRY(convolve<R>(job, pt, ibar, kOpMulReal, gam + p * tot, nullptr, pt.outbox[cycle & 1].as<R>(), inv, 0, st));
+  }
   for (int q = 0; q < job->n_part; ++q)
     if (q != p) RIX_TRY(convolve<R>(job, pt, ibar, kOpMulReal, gam + q * tot, nullptr, pt.rho[q].as<R>(), -inv, 1, st));
   return RIX_OK;
@@ -512,6 +591,39 @@ int fill_init(Job* job, cudaStream_t st) {
   ga.delta = job->stats.delta_px;
   ::rix::note_launch(); k_gamma<R><<<blocks_for(job->ctx, tot), 256, 0, st>>>(ga, job->gam.as<R>());
   RIX_LAUNCH_CHECK();
+  // ring support of every partition's filter on the half plane ju <= N
+  {
+    const int64_t nhalf = (int64_t)(n + 1) * 2 * n;
+    uint32_t *flags = nullptr, *pos = nullptr, *total = nullptr;
+    int rc = RIX_OK;
+    if (malloc_async(&flags, nhalf * sizeof(uint32_t), st) != cudaSuccess ||
+        malloc_async(&pos, nhalf * sizeof(uint32_t), st) != cudaSuccess ||
+        malloc_async(&total, sizeof(uint32_t), st) != cudaSuccess) {
+      cudaGetLastError();
+      rc = set_error(RIX_ENOMEM, "ring support scratch");
+    }
+    for (int p = 0; p < P && rc == RIX_OK; ++p) {
+      Part& pt = job->part[p];
+      ::rix::note_launch();
+      k_ring_flags<R><<<blocks_for(job->ctx, nhalf), 256, 0, st>>>(job->gam.as<R>() + p * tot, nhalf, flags);
+      if ((rc = scan_exclusive_u32(flags, pos, nhalf, total, st)) != RIX_OK) break;
+      uint32_t cnt = 0;
+      if (cudaMemcpyAsync(&cnt, total, sizeof(uint32_t), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+          cudaStreamSynchronize(st) != cudaSuccess) {
+        rc = set_error(RIX_ECUDA, "ring support count");
+        break;
+      }
+      pt.ring_count = cnt;
+      if ((rc = ensure<R>(job, pt.ring_idx, std::max<size_t>(cnt, 1) * sizeof(uint32_t))) != RIX_OK) break;
+      ::rix::note_launch();
+      k_ring_index<<<blocks_for(job->ctx, nhalf), 256, 0, st>>>(flags, pos, nhalf, pt.ring_idx.as<uint32_t>());
+      if (cudaGetLastError() != cudaSuccess) rc = set_error(RIX_ECUDA, "ring index launch");
+    }
+    if (flags) cudaFreeAsync(flags, st);
+    if (pos) cudaFreeAsync(pos, st);
+    if (total) cudaFreeAsync(total, st);
+    if (rc != RIX_OK) return rc;
+  }
   for (int p = 0; p < P; ++p) {
     Part& pt = job->part[p];
     RIX_TRY(ensure<R>(job, pt.fs_a, tot * sizeof(cplx<R>)));
@@ -520,8 +632,12 @@ int fill_init(Job* job, cudaStream_t st) {
     RIX_TRY(ensure<R>(job, pt.ft_b, (size_t)2 * n * n * sizeof(cplx<R>)));
     RIX_TRY(ensure<R>(job, pt.fimg, npix * sizeof(R)));
     RIX_TRY(ensure<R>(job, pt.fspec, (size_t)P * tot * sizeof(cplx<R>)));
-    RIX_TRY(alloc_zero<R>(job, pt.outbox[0], npix * sizeof(R), st));
-    RIX_TRY(alloc_zero<R>(job, pt.outbox[1], npix * sizeof(R), st));
+    // the exchanged message per cycle parity: the image, or its ring-support
+    // coefficients
+    const size_t ob = job->desc.exchange == RIX_EXCHANGE_SPECTRAL
+                          ? std::max<size_t>(pt.ring_count, 1) * sizeof(cplx<R>) : npix * sizeof(R);
+    RIX_TRY(alloc_zero<R>(job, pt.outbox[0], ob, st));
+    RIX_TRY(alloc_zero<R>(job, pt.outbox[1], ob, st));
     for (int q = 0; q < P; ++q)
       if (q != p) RIX_TRY(alloc_zero<R>(job, pt.rho[q], npix * sizeof(R), st));
     RIX_TRY(alloc_zero<R>(job, pt.fi_state, 4 * sizeof(R), st));
@@ -839,5 +955,61 @@ int get_components(Job* job, int part, int32_t* count, int32_t capacity, int32_t
   }
   return RIX_OK;
 }
+
+// ---- band-limited exchange calls ---------------------------------------------
+// Gamma_p F pad i_bar_p of the partition's last minor cycle on its ring
+// support (half plane), ring_count coefficients, into `out`
+template <typename R>
+int op_phi_pack(Job* job, int p, cplx<R>* out, cudaStream_t st) {
+  Part& pt = job->part[p];
+  const int n = job->desc.n;
+  const int64_t tot = (int64_t)4 * n * n;
+  cplx<R>* spec = nullptr;
+  cplx<R>* T = nullptr;
+  int rc = RIX_OK;
+  if (malloc_async(&spec, tot * sizeof(cplx<R>), st) != cudaSuccess ||
+      malloc_async(&T, (size_t)2 * n * n * sizeof(cplx<R>), st) != cudaSuccess) {
+    cudaGetLastError();
+    rc = set_error(RIX_ENOMEM, "pack scratch");
+  }
+  if (rc == RIX_OK) {
+    const XformGeom g = fill_geom(n);
+    rc = fwd_rows<R>(job->ctx, g, pt.delta.as<R>(), T, st);
+    if (rc == RIX_OK) rc = fwd_cols<R>(job->ctx, g, T, spec, st);
+  }
+  if (rc == RIX_OK) {
+    ::rix::note_launch();
+    k_phi_pack<R><<<blocks_for(job->ctx, pt.ring_count), 256, 0, st>>>(job->gam.as<R>() + p * tot, spec,
+                                                                       pt.ring_idx.as<uint32_t>(), pt.ring_count, out);
+    if (cudaGetLastError() != cudaSuccess) rc = set_error(RIX_ECUDA, "pack launch");
+  }
+  if (spec) cudaFreeAsync(spec, st);
+  if (T) cudaFreeAsync(T, st);
+  return rc;
+}
+
+// Phi_p = crop F^-1 of the spectrum rebuilt from partition p's coefficients
+template <typename R>
+int op_phi_unpack(Job* job, int p, const cplx<R>* coef, R* out, cudaStream_t st) {
+  const int n = job->desc.n;
+  const int64_t tot = (int64_t)4 * n * n;
+  cplx<R>* spec = nullptr;
+  cplx<R>* T = nullptr;
+  int rc = RIX_OK;
+  if (malloc_async(&spec, tot * sizeof(cplx<R>), st) != cudaSuccess ||
+      malloc_async(&T, (size_t)2 * n * n * sizeof(cplx<R>), st) != cudaSuccess) {
+    cudaGetLastError();
+    rc = set_error(RIX_ENOMEM, "unpack scratch");
+  }
+  if (rc == RIX_OK) rc = phi_from_coef<R>(job, p, coef, spec, T, out, 1.0 / (double)tot, 0, st);
+  if (spec) cudaFreeAsync(spec, st);
+  if (T) cudaFreeAsync(T, st);
+  return rc;
+}
+
+template int op_phi_pack<float>(Job*, int, float2*, cudaStream_t);
+template int op_phi_pack<double>(Job*, int, double2*, cudaStream_t);
+template int op_phi_unpack<float>(Job*, int, const float2*, float*, cudaStream_t);
+template int op_phi_unpack<double>(Job*, int, const double2*, double*, cudaStream_t);
 
 }  // namespace rix

@@ -158,6 +158,8 @@ static int check_desc(const rix_job_desc* d) {
   if (d->precision == RIX_FP64 && d->n > 2048) return set_error(RIX_EINVAL, "FP64 jobs support n <= 2048");
   if (d->weighting != RIX_WEIGHT_NATURAL && d->weighting != RIX_WEIGHT_UNIFORM)
     return set_error(RIX_EINVAL, "weighting must be RIX_WEIGHT_NATURAL or RIX_WEIGHT_UNIFORM");
+  if (d->exchange != RIX_EXCHANGE_IMAGE && d->exchange != RIX_EXCHANGE_SPECTRAL)
+    return set_error(RIX_EINVAL, "exchange must be RIX_EXCHANGE_IMAGE or RIX_EXCHANGE_SPECTRAL");
   return RIX_OK;
 }
 
@@ -670,6 +672,112 @@ static int rix_combine_impl(rix_job_t job, void* image_out, rix_stream_t stream)
   return op_combine<float>(&J, (float*)image_out, st);
 }
 
+// ---- band-limited exchange ------------------------------------------------
+int rix_phi_support(rix_job_t job, int part, int64_t* count_out) {
+  if (!job || !count_out) return set_error(RIX_EINVAL, "NULL argument");
+  RIX_TRY(check_part(&job->j, part));
+  *count_out = job->j.part[part].ring_count;
+  return RIX_OK;
+}
+
+static int rix_phi_pack_impl(rix_job_t job, int part, void* packed_out, rix_stream_t stream) {
+  if (!job || !packed_out) return set_error(RIX_EINVAL, "NULL argument");
+  Job& J = job->j;
+  RIX_TRY(check_part(&J, part));
+  Part& pt = J.part[part];
+  if (pt.minor_done < 1) return set_error(RIX_ESTATE, "partition %d has no completed minor cycle", part);
+  RIX_CUDA(cudaSetDevice(J.ctx->device));
+  cudaStream_t st = (cudaStream_t)stream;
+  RIX_CUDA(cudaStreamWaitEvent(st, pt.ev_minor[pt.minor_done & 1], 0));
+  if (J.fp64) return op_phi_pack<double>(&J, part, static_cast<double2*>(packed_out), st);
+  return op_phi_pack<float>(&J, part, static_cast<float2*>(packed_out), st);
+}
+
+static int rix_phi_unpack_impl(rix_job_t job, int part, const void* packed, void* phi_out, rix_stream_t stream) {
+  if (!job || !packed || !phi_out) return set_error(RIX_EINVAL, "NULL argument");
+  Job& J = job->j;
+  RIX_TRY(check_part(&J, part));
+  RIX_CUDA(cudaSetDevice(J.ctx->device));
+  cudaStream_t st = (cudaStream_t)stream;
+  if (J.fp64) return op_phi_unpack<double>(&J, part, static_cast<const double2*>(packed), static_cast<double*>(phi_out), st);
+  return op_phi_unpack<float>(&J, part, static_cast<const float2*>(packed), static_cast<float*>(phi_out), st);
+}
+
+// ---- baseline-dependent averaging (context-level preprocessing) ----------
+namespace {
+// windows, counts and output offsets on the device; the row total on the host
+struct BdaPlan {
+  int32_t* window = nullptr;
+  uint32_t* count = nullptr;
+  uint32_t* offset = nullptr;
+  uint32_t* total = nullptr;
+  cudaStream_t st = nullptr;
+  ~BdaPlan() {
+    if (window) cudaFreeAsync(window, st);
+    if (count) cudaFreeAsync(count, st);
+    if (offset) cudaFreeAsync(offset, st);
+    if (total) cudaFreeAsync(total, st);
+  }
+};
+
+int bda_plan(Ctx* ctx, const double* uvw, int64_t nt, int64_t nbl, const double* freq, int nchan, int n,
+             double cell, double max_shift, cudaStream_t st, BdaPlan& pl, int64_t* nrow) {
+  pl.st = st;
+  if (malloc_async(&pl.window, nbl * sizeof(int32_t), st) != cudaSuccess ||
+      malloc_async(&pl.count, nbl * sizeof(uint32_t), st) != cudaSuccess ||
+      malloc_async(&pl.offset, nbl * sizeof(uint32_t), st) != cudaSuccess ||
+      malloc_async(&pl.total, sizeof(uint32_t), st) != cudaSuccess) {
+    cudaGetLastError();
+    return set_error(RIX_ENOMEM, "averaging plan");
+  }
+  RIX_TRY(bda_windows(ctx, uvw, nt, nbl, freq, nchan, n, cell, max_shift, pl.window, pl.count, st));
+  RIX_TRY(scan_exclusive_u32(pl.count, pl.offset, nbl, pl.total, st));
+  uint32_t tot = 0;
+  RIX_CUDA(cudaMemcpyAsync(&tot, pl.total, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+  RIX_CUDA(cudaStreamSynchronize(st));
+  *nrow = tot;
+  return RIX_OK;
+}
+}  // namespace
+
+int rix_bda_rows(rix_ctx_t ctx, const double* uvw_m, int64_t n_times, int64_t n_baselines, const double* freq_hz,
+                 int32_t nchan, int32_t n, double cell_rad, double max_shift_px, int32_t* window_out,
+                 int64_t* nrow_out, rix_stream_t stream) {
+  if (!ctx || !uvw_m || !nrow_out) return set_error(RIX_EINVAL, "NULL argument");
+  RIX_CUDA(cudaSetDevice(ctx->c.device));
+  cudaStream_t st = (cudaStream_t)stream;
+  BdaPlan pl;
+  RIX_TRY(bda_plan(&ctx->c, uvw_m, n_times, n_baselines, freq_hz, nchan, n, cell_rad, max_shift_px, st, pl,
+                   nrow_out));
+  if (window_out) {
+    RIX_CUDA(cudaMemcpyAsync(window_out, pl.window, n_baselines * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    RIX_CUDA(cudaStreamSynchronize(st));
+  }
+  return RIX_OK;
+}
+
+int rix_bda_average(rix_ctx_t ctx, const double* uvw_m, const void* vis, const float* weight, int64_t n_times,
+                    int64_t n_baselines, const double* freq_hz, int32_t nchan, int32_t precision, int32_t n,
+                    double cell_rad, double max_shift_px, double* uvw_out, void* vis_out, float* weight_out,
+                    int64_t nrow_capacity, int64_t* nrow_out, rix_stream_t stream) {
+  if (!ctx || !uvw_m || !vis || !uvw_out || !vis_out || !weight_out) return set_error(RIX_EINVAL, "NULL argument");
+  if (precision != RIX_FP32 && precision != RIX_FP64) return set_error(RIX_EINVAL, "bad precision");
+  RIX_CUDA(cudaSetDevice(ctx->c.device));
+  cudaStream_t st = (cudaStream_t)stream;
+  BdaPlan pl;
+  int64_t nrow = 0;
+  RIX_TRY(bda_plan(&ctx->c, uvw_m, n_times, n_baselines, freq_hz, nchan, n, cell_rad, max_shift_px, st, pl, &nrow));
+  if (nrow > nrow_capacity)
+    return set_error(RIX_EINVAL, "averaging gives %lld rows, the output holds %lld", (long long)nrow,
+                     (long long)nrow_capacity);
+  if (nrow_out) *nrow_out = nrow;
+  if (precision == RIX_FP64)
+    return bda_average<double2>(&ctx->c, uvw_m, static_cast<const double2*>(vis), weight, n_times, n_baselines,
+                                nchan, pl.window, pl.offset, uvw_out, static_cast<double2*>(vis_out), weight_out, st);
+  return bda_average<float2>(&ctx->c, uvw_m, static_cast<const float2*>(vis), weight, n_times, n_baselines, nchan,
+                             pl.window, pl.offset, uvw_out, static_cast<float2*>(vis_out), weight_out, st);
+}
+
 // ---- public wrappers: run the call, then note the stream the job used ----
 #define RIX_NOTE(job, stream, call)                                           \
   do {                                                                        \
@@ -719,6 +827,13 @@ int rix_get_model(rix_job_t job, int part, void* image_out, rix_stream_t stream)
 int rix_combine(rix_job_t job, void* image_out, rix_stream_t stream) {
   RIX_NOTE(job, stream, rix_combine_impl(job, image_out, stream));
 }
+int rix_phi_pack(rix_job_t job, int part, void* packed_out, rix_stream_t stream) {
+  RIX_NOTE(job, stream, rix_phi_pack_impl(job, part, packed_out, stream));
+}
+int rix_phi_unpack(rix_job_t job, int part, const void* packed, void* phi_out, rix_stream_t stream) {
+  RIX_NOTE(job, stream, rix_phi_unpack_impl(job, part, packed, phi_out, stream));
+}
+
 
 }  // extern "C"
 

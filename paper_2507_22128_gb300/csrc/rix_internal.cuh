@@ -242,7 +242,9 @@ struct Part {
   DevBuf model_planes, resid_planes, tbuf;  // [nw][S][S], [nw][S][S], [nw][S][N]
   DevBuf groups;                            // plane-group images of the inverse row pass, [G][N][N]
   DevBuf model, resid, delta;               // N x N Real
-  DevBuf outbox[2];                         // Phi_p^n by cycle parity
+  DevBuf outbox[2];                         // Phi_p^n by cycle parity (image, or ring-support coefficients)
+  DevBuf ring_idx;                          // ring support of Gamma_p, half plane ju <= N (flat u-major indices)
+  int64_t ring_count = 0;
   DevBuf rho[kMaxPart];                     // rho_{q->p}, N x N
   DevBuf psf;                               // 2N x 2N Real
   DevBuf hspec;                             // centred spectrum of the PSF, (2N)^2 complex
@@ -346,6 +348,16 @@ int op_psf(Job* job, int p, cudaStream_t st);
 int op_grid_into_scratch(Job* job, int p, const float2* vis, float* image_out, float2* scratch,
                          size_t scratch_elems, cudaStream_t st);
 
+// baseline-dependent averaging (k_bda.cu): per baseline the window k_b and
+// its number of windows, then the averaged rows at the exclusive scan of the
+// counts
+int bda_windows(Ctx* ctx, const double* uvw, int64_t nt, int64_t nbl, const double* freq, int nchan, int n,
+                double cell, double max_shift, int32_t* window, uint32_t* count, cudaStream_t st);
+template <typename C>
+int bda_average(Ctx* ctx, const double* uvw, const C* vis, const float* weight, int64_t nt, int64_t nbl, int nchan,
+                const int32_t* window, const uint32_t* offset, double* uvw_out, C* vis_out, float* w_out,
+                cudaStream_t st);
+
 // partition entry point (k_partition.cu)
 int partition_job(Job* job, const double* uvw, int64_t nrow, const float* weight,
                   const double* ell_px, double delta, uint8_t* mask_out, cudaStream_t st);
@@ -365,6 +377,12 @@ int op_fista_batch(Job* job, int nb, const int* parts, const rix_fista_params* p
                    const cudaStream_t* ps);
 template <typename R>
 int op_combine(Job* job, R* out, cudaStream_t st);
+// band-limited exchange (k_minor.cu): the ring-support coefficients of
+// Gamma_p F pad i_bar_p, and Phi_p rebuilt from such coefficients
+template <typename R>
+int op_phi_pack(Job* job, int p, cplx<R>* out, cudaStream_t st);
+template <typename R>
+int op_phi_unpack(Job* job, int p, const cplx<R>* coef, R* out, cudaStream_t st);
 
 // persistent FISTA iteration loop (k_fista*.cu): all `iters` iterations of
 // the minor cycles of one or more partitions in one cooperative launch.

@@ -34,7 +34,7 @@ class Reconstruction:
     """One job on one device; partitions run on the caller's stream."""
 
     def __init__(self, ctx, n, cell_rad, n_wplanes, freq, nrow, n_part=2, precision=rix.FP32, tile=0,
-                 device="cuda", weighting=rix.WEIGHT_NATURAL):
+                 device="cuda", weighting=rix.WEIGHT_NATURAL, exchange=rix.EXCHANGE_IMAGE):
         self.ctx = ctx
         self.n = n
         self.n_part = n_part
@@ -42,7 +42,8 @@ class Reconstruction:
         self.rdtype = torch.float64 if precision == rix.FP64 else torch.float32
         self.cdtype = torch.complex128 if precision == rix.FP64 else torch.complex64
         self.device = torch.device(device)
-        self.job = rix.job_create(ctx, n, cell_rad, n_wplanes, list(freq), precision, n_part, nrow, tile, weighting)
+        self.job = rix.job_create(ctx, n, cell_rad, n_wplanes, list(freq), precision, n_part, nrow, tile, weighting,
+                                  exchange)
         self.vis = None
 
     def close(self):
@@ -171,9 +172,9 @@ class Reconstruction:
 
 
 def observation_job(ctx, obs, n_part=2, precision=rix.FP32, tile=0, ell_px=None, delta_px=1.0,
-                    weighting=rix.WEIGHT_NATURAL):
+                    weighting=rix.WEIGHT_NATURAL, exchange=rix.EXCHANGE_IMAGE):
     """Reconstruction set up from a synth.Observation."""
     r = Reconstruction(ctx, obs.n, obs.cell_rad, obs.n_wplanes, obs.freq, obs.nrow, n_part, precision, tile,
-                       weighting=weighting)
+                       weighting=weighting, exchange=exchange)
     r.set_data(obs.uvw, obs.vis, obs.weight, ell_px, delta_px)
     return r

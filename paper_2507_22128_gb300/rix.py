@@ -29,10 +29,11 @@ class RixError(RuntimeError):
 class JobDesc(C.Structure):
     _fields_ = [("n", C.c_int32), ("cell_rad", C.c_double), ("n_wplanes", C.c_int32),
                 ("nchan", C.c_int32), ("freq_hz", C.POINTER(C.c_double)), ("precision", C.c_int32),
-                ("n_part", C.c_int32), ("tile", C.c_int32), ("weighting", C.c_int32)]
+                ("n_part", C.c_int32), ("tile", C.c_int32), ("weighting", C.c_int32), ("exchange", C.c_int32)]
 
 
 WEIGHT_NATURAL, WEIGHT_UNIFORM = 0, 1
+EXCHANGE_IMAGE, EXCHANGE_SPECTRAL = 0, 1
 
 
 MAX_PART = 8
@@ -95,6 +96,12 @@ def _load() -> C.CDLL:
         "rix_timing_read": (C.c_int, [C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
         "rix_selftest_barrier_timeout": (C.c_int, [vp, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
         "rix_daubechies_lowpass": (C.c_int, [C.c_int, C.POINTER(C.c_double)]),
+        "rix_phi_support": (C.c_int, [vp, C.c_int, C.POINTER(i64)]),
+        "rix_phi_pack": (C.c_int, [vp, C.c_int, vp, vp]),
+        "rix_phi_unpack": (C.c_int, [vp, C.c_int, vp, vp, vp]),
+        "rix_bda_rows": (C.c_int, [vp, vp, i64, i64, C.POINTER(dbl), i32, i32, dbl, dbl, vp, C.POINTER(i64), vp]),
+        "rix_bda_average": (C.c_int, [vp, vp, vp, vp, i64, i64, C.POINTER(dbl), i32, i32, i32, dbl, dbl, vp, vp, vp,
+                                      i64, C.POINTER(i64), vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -111,7 +118,8 @@ EXPORTED = ("rix_create", "rix_destroy", "rix_job_workspace_bytes", "rix_job_cre
             "rix_minor_cycle_fista", "rix_get_components", "rix_get_model", "rix_combine", "rix_last_error",
             "rix_kernel_launches", "rix_timing_enable", "rix_timing_read", "rix_grid_noalloc",
             "rix_selftest_barrier_timeout", "rix_daubechies_lowpass", "rix_get_weights",
-            "rix_minor_cycle_fista_batch", "rix_device_allocations")
+            "rix_minor_cycle_fista_batch", "rix_device_allocations", "rix_bda_rows", "rix_bda_average",
+            "rix_phi_support", "rix_phi_pack", "rix_phi_unpack")
 
 
 def _check(rc: int):
@@ -152,22 +160,23 @@ def destroy(ctx: int):
     _check(_lib.rix_destroy(ctx))
 
 
-def _desc(n, cell_rad, n_wplanes, freq_hz, precision, n_part, tile, weighting=WEIGHT_NATURAL):
+def _desc(n, cell_rad, n_wplanes, freq_hz, precision, n_part, tile, weighting=WEIGHT_NATURAL,
+          exchange=EXCHANGE_IMAGE):
     f = (C.c_double * len(freq_hz))(*[float(x) for x in freq_hz])
     d = JobDesc(n, cell_rad, n_wplanes, len(freq_hz), C.cast(f, C.POINTER(C.c_double)), precision,
-                n_part, tile, weighting)
+                n_part, tile, weighting, exchange)
     return d, f
 
 
 def job_workspace_bytes(n, cell_rad, n_wplanes, freq_hz, precision, n_part, nrow, tile=0,
-                        weighting=WEIGHT_NATURAL) -> int:
-    d, _keep = _desc(n, cell_rad, n_wplanes, freq_hz, precision, n_part, tile, weighting)
+                        weighting=WEIGHT_NATURAL, exchange=EXCHANGE_IMAGE) -> int:
+    d, _keep = _desc(n, cell_rad, n_wplanes, freq_hz, precision, n_part, tile, weighting, exchange)
     return int(_lib.rix_job_workspace_bytes(C.byref(d), nrow))
 
 
 def job_create(ctx, n, cell_rad, n_wplanes, freq_hz, precision, n_part, max_rows, tile=0,
-               weighting=WEIGHT_NATURAL) -> int:
-    d, _keep = _desc(n, cell_rad, n_wplanes, freq_hz, precision, n_part, tile, weighting)
+               weighting=WEIGHT_NATURAL, exchange=EXCHANGE_IMAGE) -> int:
+    d, _keep = _desc(n, cell_rad, n_wplanes, freq_hz, precision, n_part, tile, weighting, exchange)
     h = C.c_void_p()
     _check(_lib.rix_job_create(ctx, C.byref(d), max_rows, C.byref(h)))
     return h.value
@@ -227,6 +236,56 @@ def degrid(job, part, image, vis_out, stream=None):
 def grid(job, part, vis, image_out, stream=None):
     _check(_lib.rix_grid(job, part, _ptr(vis, _CT, name="vis"), _ptr(image_out, _RT, name="image_out"),
                          _stream(stream)))
+
+
+# ------------------------------------------------- band-limited exchange --
+def phi_support(job, part) -> int:
+    c = C.c_int64()
+    _check(_lib.rix_phi_support(job, part, C.byref(c)))
+    return int(c.value)
+
+
+def phi_pack(job, part, packed_out, stream=None):
+    _check(_lib.rix_phi_pack(job, part, _ptr(packed_out, _CT, name="packed_out"), _stream(stream)))
+
+
+def phi_unpack(job, part, packed, phi_out, stream=None):
+    _check(_lib.rix_phi_unpack(job, part, _ptr(packed, _CT, name="packed"), _ptr(phi_out, _RT, name="phi_out"),
+                               _stream(stream)))
+
+
+# ------------------------------------------- baseline-dependent averaging --
+def bda_rows(ctx, uvw, n_times, n_baselines, freq_hz, n, cell_rad, max_shift_px, stream=None):
+    """(number of averaged rows, numpy int32 window per baseline)."""
+    import numpy as np
+    f = (C.c_double * len(freq_hz))(*[float(x) for x in freq_hz])
+    win = np.zeros(n_baselines, np.int32)
+    nrow = C.c_int64()
+    _check(_lib.rix_bda_rows(ctx, _ptr(uvw, torch.float64, n_times * n_baselines * 3, "uvw"), n_times, n_baselines,
+                             f, len(freq_hz), n, cell_rad, max_shift_px, win.ctypes.data_as(C.c_void_p),
+                             C.byref(nrow), _stream(stream)))
+    return int(nrow.value), win
+
+
+def bda_average(ctx, uvw, vis, weight, n_times, n_baselines, freq_hz, n, cell_rad, max_shift_px, stream=None):
+    """Averaged (uvw, vis, weight) as new device tensors: [rows][3] float64,
+    [rows][nchan] of vis's complex type, [rows][nchan] float32."""
+    nchan = len(freq_hz)
+    prec = FP64 if vis.dtype == torch.complex128 else FP32
+    nrow, _ = bda_rows(ctx, uvw, n_times, n_baselines, freq_hz, n, cell_rad, max_shift_px, stream)
+    dev = uvw.device
+    uvw_o = torch.empty((nrow, 3), dtype=torch.float64, device=dev)
+    vis_o = torch.empty((nrow, nchan), dtype=vis.dtype, device=dev)
+    w_o = torch.empty((nrow, nchan), dtype=torch.float32, device=dev)
+    f = (C.c_double * nchan)(*[float(x) for x in freq_hz])
+    got = C.c_int64()
+    nv = n_times * n_baselines * nchan
+    _check(_lib.rix_bda_average(ctx, _ptr(uvw, torch.float64, n_times * n_baselines * 3, "uvw"),
+                                _ptr(vis, (torch.complex64, torch.complex128), nv, "vis"),
+                                _ptr(weight, torch.float32, nv, "weight"), n_times, n_baselines, f, nchan, prec, n,
+                                cell_rad, max_shift_px, _ptr(uvw_o, name="uvw_out"), _ptr(vis_o, name="vis_out"),
+                                _ptr(w_o, name="weight_out"), nrow, C.byref(got), _stream(stream)))
+    return uvw_o, vis_o, w_o
 
 
 def grid_noalloc(job, part, vis, image_out, stream=None):
