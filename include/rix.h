@@ -62,6 +62,7 @@ extern "C" {
 
 typedef struct rix_ctx_s* rix_ctx_t;
 typedef struct rix_job_s* rix_job_t;
+typedef struct rix_batch_s* rix_batch_t;
 typedef void* rix_stream_t; /* cudaStream_t */
 
 /* One reconstruction job (Sec. 3: one set of visibilities split into n_part
@@ -290,6 +291,54 @@ int rix_get_model(rix_job_t job, int part, void* image_out, rix_stream_t stream)
 /* Final image: the equal-weight mean of the partitions' model images
  * (0.5 / 0.5 for two partitions), device N x N. */
 int rix_combine(rix_job_t job, void* image_out, rix_stream_t stream);
+
+/* ---- batched major cycles and gridder tuning ------------------------------ */
+
+/* Tuning of the FP32 w-stacked gridder of a job (a deployment knob; the paper
+ * has no counterpart): chunk_limit (1 .. 32) = the most samples with one
+ * kernel footprint a warp grids at a time (the work items' entries are
+ * regrouped on the spot when it changes; results are the same up to
+ * rounding), ctas_per_sm (0 .. 8, 0 = as many as fit) = resident gridder
+ * CTAs per SM.  Defaults 32 and 0.  Waits for the job's own work. */
+int rix_job_tune(rix_job_t job, int32_t chunk_limit, int32_t ctas_per_sm);
+
+/* A batch of (job, partition) pairs whose major cycles run together (the
+ * paper's independent partition jobs, Sec. 3, for many jobs at once): every
+ * pair's model -> w-planes transform, then ONE persistent gridder launch over
+ * all pairs' work items (degrid, residual, grid of Eq. 2), then every pair's
+ * planes -> residual transform.  jobs: host [n] (FP32 w-stacked, tile 16,
+ * partitioned, of this context); parts: host [n]; pairs distinct.  The batch
+ * records the pairs' buffers: create it after rix_set_uv_partition and
+ * rix_job_tune, and again after re-partitioning a job; the jobs outlive it.
+ * Allocates the pairs' plane buffers if needed and uploads the gridder's
+ * per-pair descriptors (synchronises the device). */
+int rix_batch_create(rix_ctx_t ctx, int32_t n, const rix_job_t* jobs, const int32_t* parts, rix_batch_t* batch);
+int rix_batch_destroy(rix_batch_t batch);
+
+/* One major cycle of every pair, as rix_major_cycle(jobs[i], parts[i],
+ * vis_obs[i], NULL, NULL) for each (the same call-order rules and result:
+ * the residual stays resident for the partition's minor cycle, the cycle
+ * counters advance).  vis_obs: host [n] of device pointers [nrow][nchan]
+ * float2.  residual_out: NULL, or host [n] of device pointers (N x N float,
+ * NULL entries skipped) that receive the pairs' residual images.  The
+ * pairs' transforms run on streams of the batch forked from
+ * and joined to `stream`; nothing is allocated or synchronised, so the
+ * call can be captured in a CUDA graph once the pairs have run one
+ * (uncaptured) major cycle.  A captured call is not an executed one: it
+ * waits on and records none of the jobs' events and leaves their cycle
+ * counters as they were, so a replayed graph repeats the captured cycle
+ * (on the models of the moment) and its ordering against other work is the
+ * caller's. */
+int rix_batch_major_cycle(rix_batch_t batch, const void* const* vis_obs, void* const* residual_out,
+                          rix_stream_t stream);
+
+/* Device time of the FP32 w-stacked gridder on one partition (a tuning
+ * diagnostic): the mean over `reps` launches of the residual mode (degrid,
+ * residual, grid) with the job's current tuning, on the partition's plane
+ * buffers, which hold nothing between major cycles; the job's results and
+ * cycle state are untouched.  vis_obs: device [nrow][nchan] float2.  Waits
+ * for the job's work and synchronises. */
+int rix_gridder_probe(rix_job_t job, int part, const void* vis_obs, int32_t reps, double* ms_out);
 
 /* ---- band-limited exchange (Sec. 6.3, Sec. 7 item a) ---------------------- */
 

@@ -945,6 +945,52 @@ int op_grid_into_scratch(Job* job, int p, const float2* vis, float* image_out, f
   return inv_rows<float>(job->ctx, g, tbuf, image_out, sc, 0, st, group_imgs, std::max(max_groups, 1));
 }
 
+int ensure_planes_f32(Job* job, int p) { return ensure_plane_buffers<float>(job, job->part[p]); }
+
+// The major cycles of the batch's pairs (each as op_major) with one gridder
+// launch: the caller's stream forks to the batch's streams for every pair's
+// model -> planes transform, residual-plane clearing and visibility gather,
+// joins for the gridder, and forks again for the planes -> residual
+// transforms.
+int op_major_batch(Batch* b, const float2* const* vis, cudaStream_t st) {
+  const int ns = Batch::kStreams;
+  auto fork = [&]() -> int {
+    RIX_CUDA(cudaEventRecord(b->ev_fork, st));
+    for (int k = 0; k < ns; ++k) RIX_CUDA(cudaStreamWaitEvent(b->streams[k], b->ev_fork, 0));
+    return RIX_OK;
+  };
+  auto join = [&]() -> int {
+    for (int k = 0; k < ns; ++k) {
+      RIX_CUDA(cudaEventRecord(b->ev_join[k], b->streams[k]));
+      RIX_CUDA(cudaStreamWaitEvent(st, b->ev_join[k], 0));
+    }
+    return RIX_OK;
+  };
+  RIX_TRY(fork());
+  for (int i = 0; i < b->n; ++i) {
+    Job* job = b->jobs[i];
+    Part& pt = job->part[b->parts[i]];
+    cudaStream_t s = b->streams[i % ns];
+    if (pt.ent_count == 0) {
+      RIX_CUDA(cudaMemsetAsync(pt.resid.p, 0, (size_t)job->desc.n * job->desc.n * sizeof(float), s));
+      continue;
+    }
+    RIX_TRY(image_to_planes<float>(job, pt, pt.model.as<float>(), s));
+    const size_t np = (size_t)job->nw;
+    RIX_CUDA(cudaMemsetAsync(pt.resid_planes.p, 0, np * pt.win_n * pt.win_n * sizeof(float2), s));
+    RIX_TRY(gather_y(job, pt.ent_begin, pt.ent_count, vis[i], s));
+  }
+  RIX_TRY(join());
+  RIX_TRY(batch_gridder(b, st));
+  RIX_TRY(fork());
+  for (int i = 0; i < b->n; ++i) {
+    Job* job = b->jobs[i];
+    Part& pt = job->part[b->parts[i]];
+    if (pt.ent_count > 0) RIX_TRY(planes_to_image<float>(job, pt, pt.resid.as<float>(), b->streams[i % ns]));
+  }
+  return join();
+}
+
 template <typename R>
 int grid_entry_geometry(Job* job, cudaStream_t st) {
   const int64_t n = job->n_entries;
@@ -952,6 +998,7 @@ int grid_entry_geometry(Job* job, cudaStream_t st) {
   if (n == 0) return RIX_OK;
   TileArgs a = base_args(job, job->part[0]);   // job-level fields only
   a.samples = job->samples.as<uint32_t>();      // the sorted order (grid_work_order reorders both after)
+  job->gorder = false;
   const int blocks = (int)std::min<int64_t>(ceil_div(n, 256), (int64_t)job->ctx->num_sms * 16);
   ::rix::note_launch();
   if (job->tile == 16) k_entry_geom<R, false, 16><<<blocks, 256, 0, st>>>(a, 0, n, job->egeom.as<EntryGeom<R>>());

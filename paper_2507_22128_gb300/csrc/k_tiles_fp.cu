@@ -53,16 +53,21 @@ static_assert(kTileBytes % 128 == 0, "tile alignment");
 
 // ------------------------------------------------------ partition time -----
 // Per work item: reorder its entries (at most 2048) by first tap, stably
-// (key = tap << 11 | position), write the sample index of each entry in that
-// order to gsamples and the geometry records in place, and flag the entries
-// that start a chunk (the first of a run of one tap, and every 32nd after).
+// (key = tap << 11 | position), the geometry records in place and the sample
+// indices (read from `samples`, in the geometry's current order: the sorted
+// order at partition time, the gridder order when the chunks are rebuilt)
+// into gsamples (which may be `samples`), and flag the entries
+// that start a chunk (the first of a run of one tap, and every limit-th
+// after; limit <= 32, the job's tuning).
 template <typename R>
 __global__ void __launch_bounds__(256) k_item_order(const uint32_t* __restrict__ items, int64_t n_items,
-                                                    const uint32_t* __restrict__ samples, EntryGeom<R>* geom,
-                                                    uint32_t* __restrict__ gsamples, uint32_t* __restrict__ cflag) {
+                                                    const uint32_t* samples, EntryGeom<R>* geom,
+                                                    uint32_t* gsamples, uint32_t* __restrict__ cflag,
+                                                    int limit) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   EntryGeom<R>* sg = reinterpret_cast<EntryGeom<R>*>(smem_raw);
   uint32_t* sk = reinterpret_cast<uint32_t*>(sg + kItemMax);
+  uint32_t* ss = sk + kItemMax;
   for (int64_t item = blockIdx.x; item < n_items; item += gridDim.x) {
     const uint32_t e0 = items[item];
     const int cnt = (int)(items[item + 1] - e0);
@@ -72,6 +77,7 @@ __global__ void __launch_bounds__(256) k_item_order(const uint32_t* __restrict__
       if (r < cnt) {
         const EntryGeom<R> g = geom[e0 + r];
         sg[r] = g;
+        ss[r] = samples[e0 + r];
         sk[r] = ((g.ouv & 0xffffu) << 11) | (uint32_t)r;
       } else {
         sk[r] = 0xffffffffu;
@@ -98,7 +104,7 @@ __global__ void __launch_bounds__(256) k_item_order(const uint32_t* __restrict__
     for (int r = threadIdx.x; r < cnt; r += blockDim.x) {
       const uint32_t key = sk[r];
       const int src = (int)(key & 2047u);
-      gsamples[e0 + r] = samples[e0 + src];
+      gsamples[e0 + r] = ss[src];
       geom[e0 + r] = sg[src];
       // position of the first entry with this tap (lower bound of tap << 11)
       const uint32_t lo_key = key & ~2047u;
@@ -108,7 +114,7 @@ __global__ void __launch_bounds__(256) k_item_order(const uint32_t* __restrict__
         if (sk[mid] < lo_key) lo = mid + 1;
         else hi = mid;
       }
-      cflag[e0 + r] = ((r - lo) % kChunkMax) == 0 ? 1u : 0u;
+      cflag[e0 + r] = ((r - lo) % limit) == 0 ? 1u : 0u;
     }
     __syncthreads();
   }
@@ -239,10 +245,25 @@ struct WarpScratch {
   float w[kGroup * 24];
 };
 
-template <int MODE>
+// Several partitions (of one or more jobs) in one launch: per pair its
+// arguments and its two tensor maps (model planes, residual planes; 64-byte
+// aligned device array), and the first global work item of every pair
+// (n + 1 values: item_start[n] = the total).
+struct FpBatch {
+  const FpArgs* descs;
+  const CUtensorMap* maps;
+  const int64_t* item_start;
+  int n;
+};
+
+template <int MODE, bool BATCH>
 __global__ void __launch_bounds__(kFpThreads, 2)
-    k_tiles_fp(FpArgs a, const __grid_constant__ CUtensorMap tm_model, const __grid_constant__ CUtensorMap tm_out) {
+    k_tiles_fp(FpArgs a0, const __grid_constant__ CUtensorMap tm_model0, const __grid_constant__ CUtensorMap tm_out0,
+               FpBatch bt) {
   constexpr bool kModel = (MODE == kResid);
+  __shared__ FpArgs sa;   // the arguments of the pair the CTA works on
+  if (!BATCH && threadIdx.x == 0) sa = a0;
+  const FpArgs& a = sa;
   extern __shared__ unsigned char smem_raw[];
   unsigned char* base =
       reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
@@ -259,7 +280,6 @@ __global__ void __launch_bounds__(kFpThreads, 2)
   const int mine = (lane >> 4) & 1;                  // the group sample whose degrid sum this lane ends with
   const bool b4 = (lane >> 4) & 1;
   const uint32_t bar_a = smem_u32(bar);
-  const uint32_t tmask = (1u << a.bt) - 1u;
   if (kModel && threadIdx.x == 0) {
     mbar_init(bar_a, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -270,8 +290,35 @@ __global__ void __launch_bounds__(kFpThreads, 2)
   WarpScratch& ws = scratch[warp];
   float* wg = ws.w;
 
-  for (int64_t it = blockIdx.x; it < a.item_count; it += gridDim.x) {
-    const int64_t item = a.item_begin + it;
+  const int64_t total = BATCH ? bt.item_start[bt.n] : a0.item_count;
+  int cur = -1;
+  for (int64_t it = blockIdx.x; it < total; it += gridDim.x) {
+    int64_t item;
+    const CUtensorMap* tm_model;
+    const CUtensorMap* tm_out;
+    if constexpr (BATCH) {
+      // the pair of global item `it`: the last i with item_start[i] <= it
+      int lo = 0, hi = bt.n - 1;
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (bt.item_start[mid] <= it) lo = mid;
+        else hi = mid - 1;
+      }
+      if (lo != cur) {
+        __syncthreads();
+        if (threadIdx.x == 0) sa = bt.descs[lo];
+        __syncthreads();
+        cur = lo;
+      }
+      item = a.item_begin + (it - bt.item_start[lo]);
+      tm_model = bt.maps + 2 * lo;
+      tm_out = bt.maps + 2 * lo + 1;
+    } else {
+      item = a0.item_begin + it;
+      tm_model = &tm_model0;
+      tm_out = &tm_out0;
+    }
+    const uint32_t tmask = (1u << a.bt) - 1u;
     const uint32_t e0 = a.items[item];
     const uint32_t key = a.keys[e0];
     const int tx = (int)(key & tmask), ty = (int)((key >> a.bt) & tmask);
@@ -279,7 +326,7 @@ __global__ void __launch_bounds__(kFpThreads, 2)
     const int u0 = tx * kT - a.win_lo, v0 = ty * kT - a.win_lo;   // >= 0: the window is tile-aligned
     if (kModel && threadIdx.x == 0) {
       mbar_expect_tx(bar_a, kTileBytes);
-      tma_load_3d(smem_u32(model), &tm_model, 2 * v0, u0, p0, bar_a);
+      tma_load_3d(smem_u32(model), tm_model, 2 * v0, u0, p0, bar_a);
     }
     const uint32_t c0 = a.item_chunk[item];
     const int nch = (int)(a.item_chunk[item + 1] - c0);
@@ -477,7 +524,7 @@ __global__ void __launch_bounds__(kFpThreads, 2)
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     __syncthreads();
     if (threadIdx.x == 0) {
-      tma_reduce_add_3d(&tm_out, 2 * v0, u0, p0, smem_u32(grid));
+      tma_reduce_add_3d(tm_out, 2 * v0, u0, p0, smem_u32(grid));
       asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
     }
     __syncthreads();
@@ -535,33 +582,36 @@ size_t fp_smem() {
          kCbMax * sizeof(uint32_t) + 8 + 16;
 }
 
-template <int MODE>
-int launch_fp(const Job* job, const FpArgs& a, const CUtensorMap& tm_model, const CUtensorMap& tm_out,
-              cudaStream_t st) {
-  const size_t sm = fp_smem<MODE>();
-  auto kern = k_tiles_fp<MODE>;
+// resident CTAs per SM of the gridder: the job's tuning (0: the occupancy
+// limit), never above it
+template <int MODE, bool BATCH>
+int gridder_blocks(const Ctx* ctx, int ctas_per_sm, int64_t items, size_t sm, int64_t* blocks) {
+  auto kern = k_tiles_fp<MODE, BATCH>;
   RIX_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
   int per_sm = 0;
   RIX_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kFpThreads, sm));
   per_sm = std::max(per_sm, 1);
-  const int64_t blocks = std::min<int64_t>(a.item_count, (int64_t)job->ctx->num_sms * per_sm);
+  if (ctas_per_sm > 0) per_sm = std::min(per_sm, ctas_per_sm);
+  *blocks = std::min<int64_t>(items, (int64_t)ctx->num_sms * per_sm);
+  return RIX_OK;
+}
+
+template <int MODE>
+int launch_fp(const Job* job, const FpArgs& a, const CUtensorMap& tm_model, const CUtensorMap& tm_out,
+              cudaStream_t st) {
+  const size_t sm = fp_smem<MODE>();
+  int64_t blocks = 0;
+  RIX_TRY((gridder_blocks<MODE, false>(job->ctx, job->fp_ctas_per_sm, a.item_count, sm, &blocks)));
   if (blocks <= 0) return RIX_OK;
   timing_mark(kTimeTiles, st, true);
   ::rix::note_launch();
-  kern<<<(unsigned)blocks, kFpThreads, sm, st>>>(a, tm_model, tm_out);
+  k_tiles_fp<MODE, false><<<(unsigned)blocks, kFpThreads, sm, st>>>(a, tm_model, tm_out, FpBatch{});
   timing_mark(kTimeTiles, st, false);
   RIX_LAUNCH_CHECK();
   return RIX_OK;
 }
 
-}  // namespace
-
-int launch_tiles_fp(const Job* job, int mode, int64_t item_begin, int64_t item_count, int64_t ent_begin,
-                    int64_t ent_count, int win_lo, int S, const void* model_planes, void* out_planes, const void* vis,
-                    cudaStream_t st) {
-  if (item_count <= 0 || ent_count <= 0) return RIX_OK;
-  if (job->tile != kT || job->nw < kW || job->fp64 || (mode != kGrid && mode != kResid) || (S & 1))
-    return set_error(RIX_EINVAL, "k_tiles_fp: unsupported job (tile %d, planes %d)", job->tile, job->nw);
+FpArgs fp_args(const Job* job, int64_t item_begin, int64_t item_count, int win_lo) {
   FpArgs a{};
   a.keys = job->keys.as<uint32_t>();
   a.items = job->items.as<uint32_t>();
@@ -575,21 +625,78 @@ int launch_tiles_fp(const Job* job, int mode, int64_t item_begin, int64_t item_c
   a.bw = job->bw;
   a.win_lo = win_lo;
   a.status = job->status.as<int>();
+  return a;
+}
+
+}  // namespace
+
+int gather_y(const Job* job, int64_t ent_begin, int64_t ent_count, const void* vis, cudaStream_t st) {
+  if (ent_count <= 0) return RIX_OK;
+  const int blocks = (int)std::min<int64_t>(ceil_div(ent_count, 256), (int64_t)job->ctx->num_sms * 8);
+  ::rix::note_launch();
+  k_gather_y<<<blocks, 256, 0, st>>>(job->gsamples.as<uint32_t>(), static_cast<const float2*>(vis),
+                                     job->weight.as<float>(), ent_begin, ent_count, job->ysamp.as<float4>());
+  RIX_LAUNCH_CHECK();
+  return RIX_OK;
+}
+
+int launch_tiles_fp(const Job* job, int mode, int64_t item_begin, int64_t item_count, int64_t ent_begin,
+                    int64_t ent_count, int win_lo, int S, const void* model_planes, void* out_planes, const void* vis,
+                    cudaStream_t st) {
+  if (item_count <= 0 || ent_count <= 0) return RIX_OK;
+  if (job->tile != kT || job->nw < kW || job->fp64 || (mode != kGrid && mode != kResid) || (S & 1))
+    return set_error(RIX_EINVAL, "k_tiles_fp: unsupported job (tile %d, planes %d)", job->tile, job->nw);
+  const FpArgs a = fp_args(job, item_begin, item_count, win_lo);
   CUtensorMap tm_out, tm_model;
   RIX_TRY(plane_map(&tm_out, out_planes, S, job->nw));
-  {
-    // the weighted visibilities of the partition's entries in gridder order
-    const int blocks = (int)std::min<int64_t>(ceil_div(ent_count, 256), (int64_t)job->ctx->num_sms * 8);
-    ::rix::note_launch();
-    k_gather_y<<<blocks, 256, 0, st>>>(job->gsamples.as<uint32_t>(), static_cast<const float2*>(vis),
-                                       job->weight.as<float>(), ent_begin, ent_count, job->ysamp.as<float4>());
-    RIX_LAUNCH_CHECK();
-  }
+  // the weighted visibilities of the partition's entries in gridder order
+  RIX_TRY(gather_y(job, ent_begin, ent_count, vis, st));
   if (mode == kResid) {
     RIX_TRY(plane_map(&tm_model, model_planes, S, job->nw));
     return launch_fp<kResid>(job, a, tm_model, tm_out, st);
   }
   return launch_fp<kGrid>(job, a, tm_out, tm_out, st);
+}
+
+// ---- several partitions in one launch ----------------------------------------
+int batch_build(Batch* b) {
+  const int n = b->n;
+  std::vector<FpArgs> descs(n);
+  std::vector<CUtensorMap> maps(2 * n);
+  std::vector<int64_t> start(n + 1, 0);
+  for (int i = 0; i < n; ++i) {
+    const Job* job = b->jobs[i];
+    const Part& pt = job->part[b->parts[i]];
+    if (job->tile != kT || job->nw < kW || job->fp64)
+      return set_error(RIX_EINVAL, "batched gridding needs FP32 w-stacked jobs with tile 16");
+    descs[i] = fp_args(job, pt.item_begin, pt.item_count, pt.win_lo);
+    RIX_TRY(plane_map(&maps[2 * i], pt.model_planes.p, pt.win_n, job->nw));
+    RIX_TRY(plane_map(&maps[2 * i + 1], pt.resid_planes.p, pt.win_n, job->nw));
+    start[i + 1] = start[i] + (pt.ent_count > 0 ? pt.item_count : 0);
+  }
+  b->total_items = start[n];
+  RIX_TRY(b->descs.alloc(b->ctx, n * sizeof(FpArgs)));
+  RIX_TRY(b->maps.alloc(b->ctx, 2 * n * sizeof(CUtensorMap)));
+  RIX_TRY(b->item_start.alloc(b->ctx, (n + 1) * sizeof(int64_t)));
+  RIX_CUDA(cudaMemcpy(b->descs.p, descs.data(), n * sizeof(FpArgs), cudaMemcpyHostToDevice));
+  RIX_CUDA(cudaMemcpy(b->maps.p, maps.data(), 2 * n * sizeof(CUtensorMap), cudaMemcpyHostToDevice));
+  RIX_CUDA(cudaMemcpy(b->item_start.p, start.data(), (n + 1) * sizeof(int64_t), cudaMemcpyHostToDevice));
+  return RIX_OK;
+}
+
+int batch_gridder(const Batch* b, cudaStream_t st) {
+  if (b->total_items <= 0) return RIX_OK;
+  const size_t sm = fp_smem<kResid>();
+  int64_t blocks = 0;
+  RIX_TRY((gridder_blocks<kResid, true>(b->ctx, b->ctas_per_sm, b->total_items, sm, &blocks)));
+  FpBatch bt{b->descs.as<FpArgs>(), b->maps.as<CUtensorMap>(), b->item_start.as<int64_t>(), b->n};
+  CUtensorMap unused{};
+  timing_mark(kTimeTiles, st, true);
+  ::rix::note_launch();
+  k_tiles_fp<kResid, true><<<(unsigned)blocks, kFpThreads, sm, st>>>(FpArgs{}, unused, unused, bt);
+  timing_mark(kTimeTiles, st, false);
+  RIX_LAUNCH_CHECK();
+  return RIX_OK;
 }
 
 template <typename R>
@@ -614,15 +721,19 @@ int grid_work_order(Job* job, cudaStream_t st) {
     rc = set_error(RIX_ENOMEM, "gridder order scratch");
   }
   if (rc == RIX_OK) {
-    const size_t sm = (size_t)kItemMax * (sizeof(EntryGeom<R>) + sizeof(uint32_t));
+    const size_t sm = (size_t)kItemMax * (sizeof(EntryGeom<R>) + 2 * sizeof(uint32_t));
     auto kern = k_item_order<R>;
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess) {
       rc = set_error(RIX_ECUDA, "k_item_order shared memory");
     } else {
       const int blocks = (int)std::min<int64_t>(n_items, (int64_t)job->ctx->num_sms * 4);
       ::rix::note_launch();
-      kern<<<blocks, 256, sm, st>>>(job->items.as<uint32_t>(), n_items, job->samples.as<uint32_t>(),
-                                    job->egeom.as<EntryGeom<R>>(), job->gsamples.as<uint32_t>(), cflag);
+      // the geometry is in the sorted order right after partitioning, in the
+      // gridder order (with gsamples) when the chunks are rebuilt
+      const uint32_t* in = job->gorder ? job->gsamples.as<uint32_t>() : job->samples.as<uint32_t>();
+      kern<<<blocks, 256, sm, st>>>(job->items.as<uint32_t>(), n_items, in,
+                                    job->egeom.as<EntryGeom<R>>(), job->gsamples.as<uint32_t>(), cflag,
+                                    std::min(std::max(job->chunk_limit, 1), kChunkMax));
       if (cudaGetLastError() != cudaSuccess) rc = set_error(RIX_ECUDA, "k_item_order launch");
     }
   }
@@ -637,6 +748,7 @@ int grid_work_order(Job* job, cudaStream_t st) {
   if (cflag) cudaFreeAsync(cflag, st);
   if (cidx) cudaFreeAsync(cidx, st);
   if (total) cudaFreeAsync(total, st);
+  if (rc == RIX_OK) job->gorder = true;
   return rc;
 }
 

@@ -19,6 +19,9 @@ struct rix_ctx_s {
 struct rix_job_s {
   rix::Job j;
 };
+struct rix_batch_s {
+  rix::Batch b;
+};
 
 namespace rix {
 
@@ -354,9 +357,11 @@ int rix_job_destroy(rix_job_t job) {
   if (!job) return RIX_OK;
   Job& J = job->j;
   cudaSetDevice(J.ctx->device);
-  // wait for this job's own work only (other jobs keep running)
+  // wait for this job's own work only (other jobs keep running); an error of
+  // the wait (an event last recorded in a stream capture) is not left behind
+  // for the next call's launch checks
   for (auto& pr : J.touched) {
-    cudaEventSynchronize(pr.second);
+    if (cudaEventSynchronize(pr.second) != cudaSuccess) cudaGetLastError();
     cudaEventDestroy(pr.second);
   }
   J.touched.clear();
@@ -670,6 +675,156 @@ static int rix_combine_impl(rix_job_t job, void* image_out, rix_stream_t stream)
     if (J.part[q].minor_done > 0) RIX_CUDA(cudaStreamWaitEvent(st, J.part[q].ev_minor[J.part[q].minor_done & 1], 0));
   if (J.fp64) return op_combine<double>(&J, (double*)image_out, st);
   return op_combine<float>(&J, (float*)image_out, st);
+}
+
+// ---- gridder tuning and batched major cycles ------------------------------
+int rix_job_tune(rix_job_t job, int32_t chunk_limit, int32_t ctas_per_sm) {
+  if (!job) return set_error(RIX_EINVAL, "job is NULL");
+  if (chunk_limit < 1 || chunk_limit > 32 || ctas_per_sm < 0 || ctas_per_sm > 8)
+    return set_error(RIX_EINVAL, "chunk_limit in [1, 32] and ctas_per_sm in [0, 8]");
+  Job& J = job->j;
+  RIX_CUDA(cudaSetDevice(J.ctx->device));
+  J.fp_ctas_per_sm = ctas_per_sm;
+  if (chunk_limit != J.chunk_limit) {
+    J.chunk_limit = chunk_limit;
+    if (J.partitioned) {
+      // the jobs' own work finishes before the chunk lists are rebuilt
+      for (auto& pr : J.touched) RIX_CUDA(cudaEventSynchronize(pr.second));
+      cudaStream_t st = J.ctx->mem_stream;
+      if (J.fp64) RIX_TRY(grid_work_order<double>(&J, st));
+      else RIX_TRY(grid_work_order<float>(&J, st));
+      RIX_CUDA(cudaStreamSynchronize(st));
+    }
+  }
+  return RIX_OK;
+}
+
+int rix_batch_create(rix_ctx_t ctx, int32_t n, const rix_job_t* jobs, const int32_t* parts, rix_batch_t* batch) {
+  if (!ctx || !jobs || !parts || !batch) return set_error(RIX_EINVAL, "NULL argument");
+  *batch = nullptr;
+  if (n < 1 || n > 4096) return set_error(RIX_EINVAL, "a batch holds 1 .. 4096 pairs");
+  RIX_CUDA(cudaSetDevice(ctx->c.device));
+  rix_batch_s* bs = new (std::nothrow) rix_batch_s();
+  if (!bs) return set_error(RIX_ENOMEM, "host allocation");
+  Batch& B = bs->b;
+  B.ctx = &ctx->c;
+  B.n = n;
+  int rc = RIX_OK;
+  for (int i = 0; i < n && rc == RIX_OK; ++i) {
+    if (!jobs[i]) { rc = set_error(RIX_EINVAL, "job %d is NULL", i); break; }
+    Job* J = &jobs[i]->j;
+    if (J->ctx != &ctx->c) rc = set_error(RIX_EINVAL, "job %d belongs to another context", i);
+    else if ((rc = check_part(J, parts[i])) != RIX_OK) break;
+    else if (J->fp64 || J->nw < kW || J->tile != 16)
+      rc = set_error(RIX_EINVAL, "job %d: batches hold FP32 w-stacked jobs with tile 16", i);
+    for (int k = 0; k < i && rc == RIX_OK; ++k)
+      if (B.jobs[k] == J && B.parts[k] == parts[i]) rc = set_error(RIX_EINVAL, "pair %d listed twice", i);
+    if (rc == RIX_OK) {
+      B.jobs.push_back(J);
+      B.parts.push_back(parts[i]);
+      rc = ensure_planes_f32(J, parts[i]);
+    }
+  }
+  if (rc == RIX_OK) B.ctas_per_sm = B.jobs[0]->fp_ctas_per_sm;
+  if (rc == RIX_OK) rc = batch_build(&B);
+  for (int k = 0; k < Batch::kStreams && rc == RIX_OK; ++k)
+    if (cudaStreamCreateWithFlags(&B.streams[k], cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&B.ev_join[k], cudaEventDisableTiming) != cudaSuccess)
+      rc = set_error(RIX_ECUDA, "batch streams");
+  if (rc == RIX_OK && cudaEventCreateWithFlags(&B.ev_fork, cudaEventDisableTiming) != cudaSuccess)
+    rc = set_error(RIX_ECUDA, "batch events");
+  if (rc != RIX_OK) {
+    rix_batch_destroy(bs);
+    return rc;
+  }
+  *batch = bs;
+  return RIX_OK;
+}
+
+int rix_batch_destroy(rix_batch_t batch) {
+  if (!batch) return RIX_OK;
+  Batch& B = batch->b;
+  cudaSetDevice(B.ctx->device);
+  for (int k = 0; k < Batch::kStreams; ++k) {
+    if (B.streams[k]) {
+      if (cudaStreamSynchronize(B.streams[k]) != cudaSuccess) cudaGetLastError();
+      cudaStreamDestroy(B.streams[k]);
+    }
+    if (B.ev_join[k]) cudaEventDestroy(B.ev_join[k]);
+  }
+  if (B.ev_fork) cudaEventDestroy(B.ev_fork);
+  delete batch;
+  return RIX_OK;
+}
+
+int rix_batch_major_cycle(rix_batch_t batch, const void* const* vis_obs, void* const* residual_out,
+                          rix_stream_t stream) {
+  if (!batch || !vis_obs) return set_error(RIX_EINVAL, "NULL argument");
+  Batch& B = batch->b;
+  RIX_CUDA(cudaSetDevice(B.ctx->device));
+  cudaStream_t st = (cudaStream_t)stream;
+  std::vector<const float2*> vis(B.n);
+  for (int i = 0; i < B.n; ++i) {
+    Job* J = B.jobs[i];
+    Part& pt = J->part[B.parts[i]];
+    if (!J->partitioned) return set_error(RIX_ESTATE, "pair %d: the job is not partitioned", i);
+    if (!vis_obs[i]) return set_error(RIX_EINVAL, "pair %d: vis_obs is NULL", i);
+    if (pt.minor_done < pt.cycle) return set_error(RIX_ESTATE, "pair %d: minor cycle %d not done", i, pt.cycle);
+    vis[i] = static_cast<const float2*>(vis_obs[i]);
+  }
+  // order after each pair's previous minor cycle; under stream capture the
+  // graph is replayed after work the caller has ordered itself (an event
+  // recorded before the capture cannot be waited on inside it)
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  RIX_CUDA(cudaStreamIsCapturing(st, &cap));
+  for (int i = 0; i < B.n && cap == cudaStreamCaptureStatusNone; ++i) {
+    Part& pt = B.jobs[i]->part[B.parts[i]];
+    if (pt.minor_done > 0) RIX_CUDA(cudaStreamWaitEvent(st, pt.ev_minor[pt.minor_done & 1], 0));
+  }
+  RIX_TRY(op_major_batch(&B, vis.data(), st));
+  for (int i = 0; i < B.n; ++i) {
+    Job* J = B.jobs[i];
+    Part& pt = J->part[B.parts[i]];
+    if (residual_out && residual_out[i])
+      RIX_CUDA(cudaMemcpyAsync(residual_out[i], pt.resid.p, (size_t)J->desc.n * J->desc.n * sizeof(float),
+                               cudaMemcpyDeviceToDevice, st));
+    // a captured cycle is not an executed one: the jobs' events and cycle
+    // counters stay as they were (an event recorded in a capture could not
+    // be waited on by later calls)
+    if (cap != cudaStreamCaptureStatusNone) continue;
+    RIX_CUDA(cudaEventRecord(pt.ev_major, st));
+    pt.cycle += 1;
+    RIX_TRY(note_stream(J, st));
+  }
+  return RIX_OK;
+}
+
+int rix_gridder_probe(rix_job_t job, int part, const void* vis_obs, int32_t reps, double* ms_out) {
+  if (!job || !vis_obs || !ms_out || reps < 1) return set_error(RIX_EINVAL, "bad argument");
+  Job& J = job->j;
+  RIX_TRY(check_part(&J, part));
+  if (J.fp64 || J.nw < kW || J.tile != 16) return set_error(RIX_EINVAL, "the probe times the FP32 w-stacked gridder");
+  RIX_CUDA(cudaSetDevice(J.ctx->device));
+  for (auto& pr : J.touched) RIX_CUDA(cudaEventSynchronize(pr.second));
+  RIX_TRY(ensure_planes_f32(&J, part));
+  Part& pt = J.part[part];
+  cudaStream_t st = J.ctx->mem_stream;
+  cudaEvent_t e0, e1;
+  RIX_CUDA(cudaEventCreate(&e0));
+  RIX_CUDA(cudaEventCreate(&e1));
+  int rc = gather_y(&J, pt.ent_begin, pt.ent_count, vis_obs, st);
+  if (rc == RIX_OK && cudaEventRecord(e0, st) != cudaSuccess) rc = set_error(RIX_ECUDA, "event");
+  for (int r = 0; r < reps && rc == RIX_OK; ++r)
+    rc = launch_tiles_fp(&J, kResid, pt.item_begin, pt.item_count, pt.ent_begin, pt.ent_count, pt.win_lo, pt.win_n,
+                         pt.model_planes.p, pt.resid_planes.p, vis_obs, st);
+  float ms = 0.f;
+  if (rc == RIX_OK && (cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+                       cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
+    rc = set_error(RIX_ECUDA, "probe timing");
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc == RIX_OK) *ms_out = ms / reps;
+  return rc;
 }
 
 // ---- band-limited exchange ------------------------------------------------

@@ -306,7 +306,40 @@ struct Job {
   DevBuf status;                            // int: 0, or the RIX_E* code a device-side wait raised
   // streams the job's calls ran on, each with an event recorded after the call
   std::vector<std::pair<cudaStream_t, cudaEvent_t>> touched;
+  // tuning of the FP32 w-stacked gridder (rix_job_tune): entries per chunk
+  // (at most 32) and resident CTAs per SM (0: as many as fit)
+  int chunk_limit = 32;
+  int fp_ctas_per_sm = 0;
+  bool gorder = false;   // egeom (and gsamples) in the gridder order
 };
+
+// The major cycles of several (job, partition) pairs with one gridder launch
+// (rix_batch_*): per pair the gridder's arguments and tensor maps, uploaded
+// once by batch_build.
+struct Batch {
+  Ctx* ctx = nullptr;
+  int n = 0;
+  std::vector<Job*> jobs;
+  std::vector<int> parts;
+  DevBuf descs, maps, item_start;
+  int64_t total_items = 0;
+  int ctas_per_sm = 0;
+  // the pairs' transforms run on these streams, forked from and joined to
+  // the caller's stream by events
+  static constexpr int kStreams = 4;
+  cudaStream_t streams[kStreams] = {};
+  cudaEvent_t ev_fork = nullptr;
+  cudaEvent_t ev_join[kStreams] = {};
+};
+// k_tiles_fp.cu: the descriptors (the pairs' plane buffers must exist), the
+// weighted visibilities of one partition, and the batch's gridder launch
+int batch_build(Batch* b);
+int gather_y(const Job* job, int64_t ent_begin, int64_t ent_count, const void* vis, cudaStream_t st);
+int batch_gridder(const Batch* b, cudaStream_t st);
+// k_grid.cu: the pairs' major cycles (image -> planes, one gridder launch,
+// planes -> residual images into each partition's resident residual)
+int op_major_batch(Batch* b, const float2* const* vis, cudaStream_t st);
+int ensure_planes_f32(Job* job, int p);
 
 // records that `st` carries work of `job` (for rix_job_destroy)
 int note_stream(Job* job, cudaStream_t st);

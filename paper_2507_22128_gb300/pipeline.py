@@ -37,6 +37,9 @@ class Reconstruction:
                  device="cuda", weighting=rix.WEIGHT_NATURAL, exchange=rix.EXCHANGE_IMAGE):
         self.ctx = ctx
         self.n = n
+        self.cell_rad = cell_rad
+        self.n_wplanes = n_wplanes
+        self.freq = list(freq)
         self.n_part = n_part
         self.precision = precision
         self.rdtype = torch.float64 if precision == rix.FP64 else torch.float32
@@ -169,6 +172,42 @@ class Reconstruction:
     def run(self, m: Method, n_major: int, stream=None):
         self.cycles(m, n_major, stream)
         return self.combine(stream=stream)
+
+
+class BatchedMajor:
+    """The major cycles of every partition of several FP32 w-stacked
+    reconstructions with one gridder launch (rix_batch_*), issued directly
+    or replayed from a captured CUDA graph.  Marshalling only."""
+
+    def __init__(self, ctx, recs):
+        self.recs = list(recs)
+        self.pairs = [(r, p) for r in self.recs for p in range(r.n_part)]
+        self.batch = rix.batch_create(ctx, [r.job for r, _ in self.pairs], [p for _, p in self.pairs])
+        self.graph = None
+
+    def close(self):
+        if self.batch:
+            rix.batch_destroy(self.batch)
+            self.batch = None
+        self.graph = None
+
+    def samples(self) -> int:
+        return sum(r.stats()["part_count"][p] for r, p in self.pairs)
+
+    def run(self, stream=None, residual_out=None):
+        rix.batch_major_cycle(self.batch, [r.vis.reshape(-1) for r, _ in self.pairs], residual_out, stream)
+
+    def capture(self, stream, residual_out=None):
+        """Capture one batched major cycle (after an uncaptured one has run:
+        the pairs' buffers exist) into a CUDA graph on `stream`."""
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=stream):
+            self.run(stream, residual_out)
+        self.graph = g
+        return g
+
+    def replay(self):
+        self.graph.replay()
 
 
 def observation_job(ctx, obs, n_part=2, precision=rix.FP32, tile=0, ell_px=None, delta_px=1.0,

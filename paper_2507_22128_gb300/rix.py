@@ -96,6 +96,11 @@ def _load() -> C.CDLL:
         "rix_timing_read": (C.c_int, [C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
         "rix_selftest_barrier_timeout": (C.c_int, [vp, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
         "rix_daubechies_lowpass": (C.c_int, [C.c_int, C.POINTER(C.c_double)]),
+        "rix_job_tune": (C.c_int, [vp, i32, i32]),
+        "rix_batch_create": (C.c_int, [vp, i32, C.POINTER(vp), C.POINTER(i32), C.POINTER(vp)]),
+        "rix_batch_destroy": (C.c_int, [vp]),
+        "rix_batch_major_cycle": (C.c_int, [vp, C.POINTER(vp), C.POINTER(vp), vp]),
+        "rix_gridder_probe": (C.c_int, [vp, C.c_int, vp, i32, C.POINTER(dbl)]),
         "rix_phi_support": (C.c_int, [vp, C.c_int, C.POINTER(i64)]),
         "rix_phi_pack": (C.c_int, [vp, C.c_int, vp, vp]),
         "rix_phi_unpack": (C.c_int, [vp, C.c_int, vp, vp, vp]),
@@ -119,7 +124,8 @@ EXPORTED = ("rix_create", "rix_destroy", "rix_job_workspace_bytes", "rix_job_cre
             "rix_kernel_launches", "rix_timing_enable", "rix_timing_read", "rix_grid_noalloc",
             "rix_selftest_barrier_timeout", "rix_daubechies_lowpass", "rix_get_weights",
             "rix_minor_cycle_fista_batch", "rix_device_allocations", "rix_bda_rows", "rix_bda_average",
-            "rix_phi_support", "rix_phi_pack", "rix_phi_unpack")
+            "rix_phi_support", "rix_phi_pack", "rix_phi_unpack", "rix_job_tune", "rix_batch_create",
+            "rix_batch_destroy", "rix_batch_major_cycle", "rix_gridder_probe")
 
 
 def _check(rc: int):
@@ -236,6 +242,41 @@ def degrid(job, part, image, vis_out, stream=None):
 def grid(job, part, vis, image_out, stream=None):
     _check(_lib.rix_grid(job, part, _ptr(vis, _CT, name="vis"), _ptr(image_out, _RT, name="image_out"),
                          _stream(stream)))
+
+
+# ------------------------------------------ tuning and batched major cycles --
+def job_tune(job, chunk_limit=32, ctas_per_sm=0):
+    _check(_lib.rix_job_tune(job, int(chunk_limit), int(ctas_per_sm)))
+
+
+def batch_create(ctx, jobs, parts) -> int:
+    n = len(jobs)
+    ja = (C.c_void_p * n)(*[C.c_void_p(j) for j in jobs])
+    pa = (C.c_int32 * n)(*[int(p) for p in parts])
+    h = C.c_void_p()
+    _check(_lib.rix_batch_create(ctx, n, ja, pa, C.byref(h)))
+    return h.value
+
+
+def batch_destroy(batch):
+    _check(_lib.rix_batch_destroy(batch))
+
+
+def batch_major_cycle(batch, vis_list, residual_out=None, stream=None):
+    """vis_list: one complex64 device tensor per pair; residual_out: None or
+    one float32 N x N device tensor (or None) per pair."""
+    arr = (C.c_void_p * len(vis_list))(*[_ptr(v, torch.complex64, name="vis_obs") for v in vis_list])
+    res = None
+    if residual_out is not None:
+        res = (C.c_void_p * len(residual_out))(*[_ptr(r, torch.float32, name="residual_out") for r in residual_out])
+    _check(_lib.rix_batch_major_cycle(batch, arr, res, _stream(stream)))
+
+
+def gridder_probe(job, part, vis, reps=3) -> float:
+    """Mean device ms per launch of the partition's FP32 w-stacked gridder."""
+    ms = C.c_double()
+    _check(_lib.rix_gridder_probe(job, part, _ptr(vis, torch.complex64, name="vis"), int(reps), C.byref(ms)))
+    return ms.value
 
 
 # ------------------------------------------------- band-limited exchange --

@@ -283,3 +283,22 @@ def large(seed: int = 3, n_times: int = 4000, n: int = 4096, n_wplanes: int = 32
     cell = 0.5
     return _observe(f"large_{n}", rl, rs, rn, enu, n_times, 4.0, freq, n, cell, n_wplanes,
                     2000, 100, "powerlaw", 5e-4)
+
+
+def batch_chunk_jobs(n_jobs: int = 64, base_seed: int = 1000, n_min: float = 0.5e6, n_max: float = 8e6,
+                     sizes=(256, 512, 1024, 2048), n_ant: int = 64, n_chan: int = 4,
+                     with_vis: bool = True) -> list[Observation]:
+    """The batching workload: n_jobs independent channel-chunk jobs, job j
+    the medium recipe's generator with its own seed base_seed + j, its
+    visibility count log-uniform in [n_min, n_max] (the time samples scaled
+    to reach it) and its image side drawn from `sizes` (1" cells, 16
+    w-planes)."""
+    out = []
+    nbl = n_ant * (n_ant - 1) // 2
+    for j in range(n_jobs):
+        rng = np.random.default_rng(base_seed + j)
+        nvis = math.exp(rng.uniform(math.log(n_min), math.log(n_max)))
+        n = int(rng.choice(np.asarray(sizes)))
+        n_times = max(2, int(round(nvis / (nbl * n_chan))))
+        out.append(medium(seed=base_seed + j, n_times=n_times, n=n, n_ant=n_ant, n_chan=n_chan, with_vis=with_vis))
+    return out
