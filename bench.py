@@ -57,6 +57,9 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-phases", action="store_true")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 operator comparison")
+    ap.add_argument("--job-only", action="store_true",
+                    help="time the jobs only: no major-cycle metric, roofline, error, FP64 or cuFFT measurement "
+                         "(for launch lists and profiles)")
     ap.add_argument("--serve-jobs", type=int, default=24, help="arrivals in the serving experiment (0 = skip)")
     ap.add_argument("--serve-rate", type=float, default=20.0, help="Poisson arrival rate, jobs/s")
     ap.add_argument("--json-out", default=None)
@@ -372,12 +375,14 @@ def main():
 
     # ---- the survey's major-cycle metric, the gridder's roofline, the
     # stated error, the FP64 comparator and cuFFT ----
-    mc = major_cycle_metric(rec, rix, meth, stream, vis_d, flush, st, obs.nchan)
-    roof = roofline_gridder(mc, st, a)
-    err = direct_dft_errors(rec, rix, obs, out, vis_d, w_d, 1)
-    fp64 = None if (a.fp64 or a.no_fp64) else fp64_comparator(ctx, rix, pipeline, obs, a, flush)
-    cufft = cufft_comparison(obs.n, obs.n_wplanes, st["window_size"][:2], flush)
-    cufft["library_fft_ms_per_cycle"] = sum(mc["per_partition_serial"][p]["fft_ms"] for p in (0, 1))
+    mc = roof = err = fp64 = cufft = None
+    if not a.job_only:
+        mc = major_cycle_metric(rec, rix, meth, stream, vis_d, flush, st, obs.nchan)
+        roof = roofline_gridder(mc, st, a)
+        err = direct_dft_errors(rec, rix, obs, out, vis_d, w_d, 1)
+        fp64 = None if (a.fp64 or a.no_fp64) else fp64_comparator(ctx, rix, pipeline, obs, a, flush)
+        cufft = cufft_comparison(obs.n, obs.n_wplanes, st["window_size"][:2], flush)
+        cufft["library_fft_ms_per_cycle"] = sum(mc["per_partition_serial"][p]["fft_ms"] for p in (0, 1))
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
             "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64" if a.fp64 else "f32", "data": "synthetic",
@@ -737,7 +742,7 @@ def cufft_comparison(n, nplanes, window, flush, reps=5):
 # from a one-pass ncu capture of the major cycles of both partitions: (low,
 # high) partition.  Reported only for that workload and while the kernel's
 # source is the one the counters were taken on.
-TILES_TRAFFIC = {"src_sha1": None, "resid": (None, None)}
+TILES_TRAFFIC = {"src_sha1": "93f45944f9c96b322e3a999ed695aac565257a3f", "resid": (139.818752e6, 203.810560e6)}
 
 
 def tiles_traffic(a):
