@@ -63,8 +63,10 @@ def parse():
     ap.add_argument("--serve-jobs", type=int, default=24, help="arrivals in the serving experiment (0 = skip)")
     ap.add_argument("--serve-rate", type=float, default=20.0, help="Poisson arrival rate, jobs/s")
     ap.add_argument("--json-out", default=None)
-    ap.add_argument("--workload", default="medium", choices=["medium", "batch"],
-                    help="medium: the whole-job benchmark; batch: the batching workload's batched major cycle")
+    ap.add_argument("--workload", default="medium", choices=["medium", "batch", "large"],
+                    help="medium: the whole-job benchmark; batch: the batching workload's batched major cycle; "
+                         "large: the 4096^2 workload's major cycle")
+    ap.add_argument("--parts", type=int, default=2, help="uv partitions of the large workload (2 or 4)")
     ap.add_argument("--batch-jobs", type=int, default=64)
     return ap.parse_args()
 
@@ -285,6 +287,8 @@ def main():
         return reference_arm(a, rank, world)
     if a.workload == "batch":
         return batch_workload(a, rank, world, local)
+    if a.workload == "large":
+        return large_workload(a, rank, world, local)
 
     from paper_2507_22128_gb300 import pipeline, rix, synth
 
@@ -501,6 +505,78 @@ def batch_workload(a, rank, world, local):
     bm.close()
     for r in recs:
         r.close()
+    rix.destroy(ctx)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+        if a.json_out:
+            with open(a.json_out, "w") as f:
+                json.dump(line, f, indent=1)
+    return 0
+
+
+def large_workload(a, rank, world, local):
+    """The large workload: 4096 x 4096 at 0.5", 128 antennas on a 10 km log
+    spiral x 4000 times x 8 channels (1.3-1.5 GHz) = 260 M visibilities, 32
+    w-planes, `--parts` uv partitions, FP32: partition and sort, then the
+    fused major-cycle operator of every partition timed by
+    rix_major_cycle_probe (its device time on the current model; the
+    partitions one after another, so the cycle time is their sum).
+    Visibilities are seeded complex Gaussian values drawn on the device (the
+    operator's cost does not depend on them; analytic visibilities of 2100
+    sources at 260 M samples take far longer to generate than to image)."""
+    from paper_2507_22128_gb300 import pipeline, rix, synth
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    t0 = time.perf_counter()
+    obs = synth.large(seed=3 + rank, with_vis=False)
+    gen_s = time.perf_counter() - t0
+    ctx = rix.create(local)
+    P = a.parts
+    rec = pipeline.Reconstruction(ctx, obs.n, obs.cell_rad, obs.n_wplanes, obs.freq, obs.nrow, P, rix.FP32)
+    gen = torch.Generator(device=dev).manual_seed(3 + rank)
+    vis = torch.complex(torch.randn(obs.nvis, generator=gen, device=dev),
+                        torch.randn(obs.nvis, generator=gen, device=dev)).reshape(obs.nrow, obs.nchan)
+    s = torch.cuda.current_stream(dev)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(s)
+    rec.set_data(obs.uvw, vis, obs.weight, stream=s)
+    e1.record(s)
+    torch.cuda.synchronize()
+    part_ms = e0.elapsed_time(e1)
+    st = rec.stats()
+    flat = rec.vis.reshape(-1)
+    with ClockSampler(local) as clk:
+        per = {}
+        for p in range(P):
+            per[p] = {"major_cycle_ms": rix.major_cycle_probe(rec.job, p, flat, max(a.steps, 3)),
+                      "gridder_ms": rix.gridder_probe(rec.job, p, flat, max(a.steps, 3)),
+                      "entries": int(st["part_count"][p]), "window": int(st["window_size"][p])}
+    units = sum(st["part_count"][:P])
+    ms = max_over_ranks(sum(per[p]["major_cycle_ms"] for p in range(P)), dev)
+    peaks, kind = measured_peaks()
+    ng = 2 * obs.n
+    byt = units * (24.0 / obs.nchan + 16.0) + P * obs.n_wplanes * 8 * ng * ng * 8.0
+    mc = {"value": units / (ms * 1e-3) / 1e6, "unit": UNIT, "ms_per_cycle": ms, "samples_per_cycle": int(units),
+          "cycles_timed": max(a.steps, 3),
+          "timing": "rix_major_cycle_probe per partition (one after another: the sum), mean of the timed runs",
+          "hbm": {"algorithmic_bytes_per_cycle": byt, "achieved_gbs": byt / (ms * 1e-3) / 1e9,
+                  "peak_gbs": float(peaks["hbm_gbs"]), "frac": byt / (ms * 1e-3) / 1e9 / float(peaks["hbm_gbs"]),
+                  "peak_source": kind},
+          "per_partition": per}
+    value = whole_job_value(mc["samples_per_cycle"], world, mc["ms_per_cycle"])
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": mc["cycles_timed"],
+            "warmup": 1, "ms_per_step": mc["ms_per_cycle"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (uvw of the large recipe; seeded Gaussian visibilities)",
+            "config": {"workload": f"large: 4096x4096 0.5as, 128 ant log-spiral 10 km x 4000 times x 8 ch "
+                                   f"(1.3-1.5 GHz) = {obs.nvis / 1e6:.1f} M visibilities, 32 w-planes, {P} uv "
+                                   f"partitions; one fused major cycle of every partition per step",
+                       "n": obs.n, "n_wplanes": obs.n_wplanes, "n_part": P, "entries": int(st["n_entries"]),
+                       "windows": st["window_size"][:P], "l2": "flushed before each cycle (512 MiB write)"},
+            "clocks": clk.summary(), "major_cycle": mc, "partition_ms": part_ms, "generate_uvw_s": gen_s,
+            "part_count": st["part_count"][:P], "n_outside": st["n_outside"]}
+    rec.close()
     rix.destroy(ctx)
     if rank == 0:
         print(json.dumps(line), flush=True)

@@ -340,6 +340,15 @@ int rix_batch_major_cycle(rix_batch_t batch, const void* const* vis_obs, void* c
  * for the job's work and synchronises. */
 int rix_gridder_probe(rix_job_t job, int part, const void* vis_obs, int32_t reps, double* ms_out);
 
+/* Device time of partition `part`'s fused major-cycle operator (a
+ * measurement diagnostic): model -> w-planes, degrid, residual and grid,
+ * planes -> residual image (Eq. 2), on the partition's current resident
+ * model, into a temporary image; the mean over `reps` runs after one
+ * untimed run.  The job's results and cycle state are untouched (no call
+ * order is needed); allocates one image; waits for the job's work and
+ * synchronises. */
+int rix_major_cycle_probe(rix_job_t job, int part, const void* vis_obs, int32_t reps, double* ms_out);
+
 /* ---- band-limited exchange (Sec. 6.3, Sec. 7 item a) ---------------------- */
 
 /* Number of complex coefficients of partition `part`'s band-limited

@@ -101,6 +101,7 @@ def _load() -> C.CDLL:
         "rix_batch_destroy": (C.c_int, [vp]),
         "rix_batch_major_cycle": (C.c_int, [vp, C.POINTER(vp), C.POINTER(vp), vp]),
         "rix_gridder_probe": (C.c_int, [vp, C.c_int, vp, i32, C.POINTER(dbl)]),
+        "rix_major_cycle_probe": (C.c_int, [vp, C.c_int, vp, i32, C.POINTER(dbl)]),
         "rix_phi_support": (C.c_int, [vp, C.c_int, C.POINTER(i64)]),
         "rix_phi_pack": (C.c_int, [vp, C.c_int, vp, vp]),
         "rix_phi_unpack": (C.c_int, [vp, C.c_int, vp, vp, vp]),
@@ -125,7 +126,8 @@ EXPORTED = ("rix_create", "rix_destroy", "rix_job_workspace_bytes", "rix_job_cre
             "rix_selftest_barrier_timeout", "rix_daubechies_lowpass", "rix_get_weights",
             "rix_minor_cycle_fista_batch", "rix_device_allocations", "rix_bda_rows", "rix_bda_average",
             "rix_phi_support", "rix_phi_pack", "rix_phi_unpack", "rix_job_tune", "rix_batch_create",
-            "rix_batch_destroy", "rix_batch_major_cycle", "rix_gridder_probe")
+            "rix_batch_destroy", "rix_batch_major_cycle", "rix_gridder_probe",
+            "rix_major_cycle_probe")
 
 
 def _check(rc: int):
@@ -270,6 +272,13 @@ def batch_major_cycle(batch, vis_list, residual_out=None, stream=None):
     if residual_out is not None:
         res = (C.c_void_p * len(residual_out))(*[_ptr(r, torch.float32, name="residual_out") for r in residual_out])
     _check(_lib.rix_batch_major_cycle(batch, arr, res, _stream(stream)))
+
+
+def major_cycle_probe(job, part, vis, reps=3) -> float:
+    """Mean device ms of the partition's fused major-cycle operator."""
+    ms = C.c_double()
+    _check(_lib.rix_major_cycle_probe(job, part, _ptr(vis, _CT, name="vis"), int(reps), C.byref(ms)))
+    return ms.value
 
 
 def gridder_probe(job, part, vis, reps=3) -> float:

@@ -273,7 +273,7 @@ def medium(seed: int = 1, n_times: int = 1000, n: int = 1024, n_wplanes: int = 1
 
 
 def large(seed: int = 3, n_times: int = 4000, n: int = 4096, n_wplanes: int = 32,
-          n_chan: int = 8) -> Observation:
+          n_chan: int = 8, with_vis: bool = True) -> Observation:
     """4096x4096 at 0.5", 128 antennas on a 10 km log spiral (8128
     baselines) x 4000 times x 8 channels = 260 M visibilities, 32 w-planes;
     2000 points + 100 Gaussians; noise sigma 5e-4 Jy."""
@@ -282,7 +282,7 @@ def large(seed: int = 3, n_times: int = 4000, n: int = 4096, n_wplanes: int = 32
     freq = np.linspace(1.3e9, 1.5e9, n_chan)
     cell = 0.5
     return _observe(f"large_{n}", rl, rs, rn, enu, n_times, 4.0, freq, n, cell, n_wplanes,
-                    2000, 100, "powerlaw", 5e-4)
+                    2000, 100, "powerlaw", 5e-4, with_vis=with_vis)
 
 
 def batch_chunk_jobs(n_jobs: int = 64, base_seed: int = 1000, n_min: float = 0.5e6, n_max: float = 8e6,
