@@ -56,6 +56,8 @@ extern "C" {
 #define RIX_ETIMEOUT (-4) /* a bounded device-side wait expired */
 #define RIX_ESTATE (-5)   /* calls made out of order (e.g. minor before major) */
 #define RIX_EBUSY (-6)    /* the context still owns live jobs */
+#define RIX_EINTERNAL (-7) /* a device-side consistency check failed (e.g. a kernel footprint
+                              outside the tile its sort key names); results are not trusted */
 
 #define RIX_FP32 0
 #define RIX_FP64 1
@@ -220,6 +222,26 @@ int rix_grid(rix_job_t job, int part, const void* vis, void* image_out, rix_stre
  * psf_out (device (2N)^2, may be NULL); *weight_sum_out (host, may be NULL)
  * receives W_part.  Computed once and kept by the job. */
 int rix_psf(rix_job_t job, int part, void* psf_out, double* weight_sum_out, rix_stream_t stream);
+
+/* How rix_psf forms the 2N x 2N PSF (both approximate Re A^H w / W_part of
+ * Sec. 2's measurement operator to the gridding kernel's accuracy):
+ *   RIX_PSF_DOUBLE_GRID  one gridding of the unit visibilities on the 2N
+ *                        image's own oversampled grid (side 2 Ng = 4N);
+ *   RIX_PSF_TILES        four N x N tiles on the image grid (side Ng): tile t
+ *                        is the dirty image of exp(2 pi i (u l_t + v m_t))
+ *                        with its image-domain factors taken at the sky
+ *                        positions of its pixels (shift theorem); the PSF
+ *                        grid is never formed, so it serves N = 4096 (FP32)
+ *                        and N = 2048 (FP64), whose 4N-long transforms exceed
+ *                        the transform passes' limit;
+ *   RIX_PSF_AUTO         (default) DOUBLE_GRID when 4N is within that limit,
+ *                        else TILES.
+ * Setting a method drops the job's PSFs (they are formed again, lazily).
+ * Host-only; RIX_EINVAL for an unknown method. */
+#define RIX_PSF_AUTO 0
+#define RIX_PSF_DOUBLE_GRID 1
+#define RIX_PSF_TILES 2
+int rix_job_set_psf_method(rix_job_t job, int32_t method);
 
 /* One major cycle of partition `part` (Eq. 2): residual
  * F^dagger G (v - G^dagger F model) / W_part of the partition's samples, with

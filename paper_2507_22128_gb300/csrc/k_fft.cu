@@ -151,6 +151,15 @@ int check_geom(const XformGeom& g) {
 
 }  // namespace
 
+template <typename R>
+int fft_max_len() {
+  int L = 1;
+  while (2 * L <= kTwMax && kFftThreads * Vpt<R>::kLarge >= 2 * L) L *= 2;
+  return L;
+}
+template int fft_max_len<float>();
+template int fft_max_len<double>();
+
 int fft_init_twiddles(Ctx* ctx) {
   std::vector<double2> t64(kTwMax);
   std::vector<float2> t32(kTwMax);

@@ -93,6 +93,7 @@ void chebyshev_fit(const EsFourier& phi, double lo, double hi, double* c) {
 
 struct CorrArgs {
   int M;
+  int ox, oy;           // pixel offset of the table's centre from the phase centre
   double cell;
   const double* p1;     // Phi((a - M/2) / Ng), [M]
   int wstack;
@@ -100,7 +101,9 @@ struct CorrArgs {
   double cheb[kCheb];
 };
 
-// corr[b][a] = 1 / (Phi(a'/Ng) Phi(b'/Ng) [n Phi(dw (n-1))]),  nm1[b][a] = n - 1
+// corr[b][a] = 1 / (Phi(a'/Ng) Phi(b'/Ng) [n Phi(dw (n-1))]),  nm1[b][a] = n - 1,
+// with a' = a - M/2, b' = b - M/2 the offsets from the table's centre and n at
+// the sky position (a' + ox, b' + oy) cells from the phase centre
 template <typename R>
 __global__ void k_corrections(CorrArgs a, R* __restrict__ corr, double* __restrict__ nm1) {
   const int64_t tot = (int64_t)a.M * a.M;
@@ -109,7 +112,7 @@ __global__ void k_corrections(CorrArgs a, R* __restrict__ corr, double* __restri
     const int b = (int)(i / a.M), c = (int)(i - (int64_t)b * a.M);
     double v = 1.0 / (a.p1[c] * a.p1[b]);
     if (a.wstack) {
-      const double l = (double)(c - h) * a.cell, m = (double)(b - h) * a.cell;
+      const double l = (double)(c - h + a.ox) * a.cell, m = (double)(b - h + a.oy) * a.cell;
       const double r2 = __dadd_rn(__dmul_rn(l, l), __dmul_rn(m, m));
       const double n = __dsqrt_rn(1.0 - r2);
       const double d = -r2 / (1.0 + n);
@@ -134,8 +137,11 @@ __global__ void k_corrections(CorrArgs a, R* __restrict__ corr, double* __restri
   }
 }
 
+// Fills the M x M tables corr and nm1 (w-stacked jobs) for grid side ng,
+// centred ox, oy cells from the phase centre; the w-correction's Chebyshev
+// fit covers a field of half side `half_px` cells about the phase centre.
 template <typename R>
-int build_correction(Job* job, int M, int ng, DevBuf& corr, DevBuf& nm1, cudaStream_t st) {
+int fill_correction(Job* job, int M, int ng, int ox, int oy, int half_px, R* corr, double* nm1, cudaStream_t st) {
   static const EsFourier phi;
   const bool ws = job->nw > 0;
   const double cell = job->desc.cell_rad, dw = job->stats.dw;
@@ -143,12 +149,14 @@ int build_correction(Job* job, int M, int ng, DevBuf& corr, DevBuf& nm1, cudaStr
   for (int a = 0; a < M; ++a) p1[a] = phi((double)(a - M / 2) / ng);
   CorrArgs ca{};
   ca.M = M;
+  ca.ox = ox;
+  ca.oy = oy;
   ca.cell = cell;
   ca.wstack = ws;
   ca.dw = dw;
   if (ws) {
-    // the most negative dw (n - 1) is at the image corner
-    const double l = (double)(-M / 2) * cell;
+    // the most negative dw (n - 1) is at the field's corner
+    const double l = (double)(-half_px) * cell;
     const double r2 = 2.0 * l * l;
     const double n = std::sqrt(1.0 - r2);
     const double dmin = dw * (-r2 / (1.0 + n));
@@ -158,19 +166,24 @@ int build_correction(Job* job, int M, int ng, DevBuf& corr, DevBuf& nm1, cudaStr
     else ca.cheb[0] = phi(0.0);
     job->stats.max_dw_nm1 = std::max(job->stats.max_dw_nm1, std::fabs(dmin));
   }
-  RIX_TRY(corr.alloc(job->ctx, (size_t)M * M * sizeof(R)));
-  if (ws) RIX_TRY(nm1.alloc(job->ctx, (size_t)M * M * sizeof(double)));
   double* p1d = nullptr;
   RIX_CUDA(::rix::malloc_async((void**)&p1d, M * sizeof(double), st));
   RIX_CUDA(cudaMemcpyAsync(p1d, p1.data(), M * sizeof(double), cudaMemcpyHostToDevice, st));
   ca.p1 = p1d;
   const int64_t tot = (int64_t)M * M;
   const int blocks = (int)std::min<int64_t>(ceil_div(tot, 256), (int64_t)job->ctx->num_sms * 16);
-  ::rix::note_launch(); k_corrections<R><<<blocks, 256, 0, st>>>(ca, corr.as<R>(), ws ? nm1.as<double>() : nullptr);
+  ::rix::note_launch(); k_corrections<R><<<blocks, 256, 0, st>>>(ca, corr, ws ? nm1 : nullptr);
   cudaFreeAsync(p1d, st);
   RIX_LAUNCH_CHECK();
   RIX_CUDA(cudaStreamSynchronize(st));   // p1 is a host temporary
   return RIX_OK;
+}
+
+template <typename R>
+int build_correction(Job* job, int M, int ng, DevBuf& corr, DevBuf& nm1, cudaStream_t st) {
+  RIX_TRY(corr.alloc(job->ctx, (size_t)M * M * sizeof(R)));
+  if (job->nw > 0) RIX_TRY(nm1.alloc(job->ctx, (size_t)M * M * sizeof(double)));
+  return fill_correction<R>(job, M, ng, 0, 0, M / 2, corr.as<R>(), job->nw > 0 ? nm1.as<double>() : nullptr, st);
 }
 
 // --------------------------------------------------------------- kernels ----
@@ -196,6 +209,7 @@ struct TileArgs {
   const void* geom;         // EntryGeom<R> per sorted entry, from entry geom_off on
   int64_t geom_off;
   int64_t ent_begin, ent_count;   // the partition's entries
+  int* status;              // the job's status word (RIX_EINTERNAL on a failed check)
 };
 
 // On the PSF's 2N grid (x_psf = 2 x exactly), an image-grid tile of side T
@@ -248,8 +262,14 @@ __global__ void k_entry_geom(TileArgs a, int64_t e_off, int64_t n, EntryGeom<R>*
       g.dw = (R)__dadd_rn(pc, -tw);
     }
     // the first tap lies in the entry's tile (staged region) by construction
-    // of the key
-    if (ou < 0 || ov < 0 || ou > kLim || ov > kLim) { ou = 0; ov = 0; }
+    // of the key; an entry that does not is flagged (RIX_EINTERNAL at the
+    // next rix_job_sync) and its offsets are kept in range so that no access
+    // leaves the staged tile
+    if (ou < 0 || ov < 0 || ou > kLim || ov > kLim) {
+      atomicCAS(a.status, 0, RIX_EINTERNAL);
+      ou = min(max(ou, 0), kLim);
+      ov = min(max(ov, 0), kLim);
+    }
     g.ouv = (uint32_t)ou | ((uint32_t)ov << 8);
     out[i] = g;
   }
@@ -713,6 +733,7 @@ TileArgs base_args(const Job* job, const Part& pt) {
   a.geom_off = 0;
   a.ent_begin = pt.ent_begin;
   a.ent_count = pt.ent_count;
+  a.status = job->status.as<int>();
   return a;
 }
 
@@ -841,6 +862,127 @@ int op_major(Job* job, int p, const cplx<R>* vis, R* residual, cudaStream_t st) 
   return planes_to_image<R>(job, pt, residual, st);
 }
 
+// pt.hspec = the centred spectrum of the 2N x 2N PSF on the 2N grid; `tt`
+// ([2N][2N] complex) is the transpose buffer, a temporary when null
+template <typename R>
+int psf_spectrum(Job* job, Part& pt, cudaStream_t st, cplx<R>* tt = nullptr) {
+  const int n = job->desc.n;
+  const size_t img2 = (size_t)4 * n * n;
+  cplx<R>* tmp = nullptr;
+  if (!tt) {
+    RIX_CUDA(::rix::malloc_async(&tmp, img2 * sizeof(cplx<R>), st));
+    tt = tmp;
+  }
+  XformGeom h{};
+  h.M = 2 * n; h.L = 2 * n; h.logL = ilog2(h.L); h.lo = 0; h.S = 2 * n; h.nplanes = 1; h.mode = kFacNone;
+  int rc = fwd_rows<R>(job->ctx, h, pt.psf.as<R>(), tt, st);
+  if (rc == RIX_OK) rc = fwd_cols<R>(job->ctx, h, tt, pt.hspec.as<cplx<R>>(), st);
+  if (tmp) cudaFreeAsync(tmp, st);
+  return rc;
+}
+
+// vis[s] = exp(2 pi i (u_s l0 + v_s m0)) for every sample s = row * nchan + ch
+// (u, v in wavelengths, FP64 argument): unit visibilities with the phase
+// centre moved to (l0, m0)
+template <typename R>
+__global__ void k_psf_phase(const double* __restrict__ uvw, const double* __restrict__ inv_lambda, int nchan,
+                            int64_t ns, double l0, double m0, cplx<R>* __restrict__ vis) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < ns; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t row = i / nchan;
+    const int ch = (int)(i - row * nchan);
+    const double sc = inv_lambda[ch];
+    const double u = __dmul_rn(uvw[row * 3 + 0], sc), v = __dmul_rn(uvw[row * 3 + 1], sc);
+    double sn, cs;
+    sincospi(2.0 * __dadd_rn(__dmul_rn(u, l0), __dmul_rn(v, m0)), &sn, &cs);
+    cplx<R> y;
+    y.x = (R)cs;
+    y.y = (R)sn;
+    vis[i] = y;
+  }
+}
+
+// The 2N x 2N PSF as four N x N tiles on the image grid (Ng = 2N), for jobs
+// whose PSF grid (2 Ng) is longer than the transforms support.  By the shift
+// theorem the tile whose centre sits (ox, oy) cells from the phase centre is
+// the dirty image of the unit visibilities exp(2 pi i (u l0 + v m0)),
+// (l0, m0) = (ox, oy) dl, with the image-domain factors (1/n, the w-screens
+// and the w-correction) taken at the sky position of each pixel:
+//   PSF(l0 + l', m0 + m') = Re sum_k w_k n^-1 exp(2 pi i (u_k (l0 + l')
+//                           + v_k (m0 + m') + w_k (n - 1))) / W_p.
+// The gridding kernel's correction is the image's own (it depends on l', m').
+template <typename R>
+int op_psf_tiled(Job* job, int p, cudaStream_t st) {
+  Part& pt = job->part[p];
+  const int n = job->desc.n;
+  const bool ws = job->nw > 0;
+  const int64_t ns = job->stats.n_samples;
+  const size_t npix = (size_t)n * n;
+  RIX_TRY(ensure_plane_buffers<R>(job, pt));
+  cplx<R>* vis = nullptr;
+  R* tile = nullptr;
+  R* corr = nullptr;
+  double* nm1 = nullptr;
+  int rc = RIX_OK;
+  if (::rix::malloc_async(&vis, (size_t)std::max<int64_t>(ns, 1) * sizeof(cplx<R>), st) != cudaSuccess ||
+      ::rix::malloc_async(&tile, npix * sizeof(R), st) != cudaSuccess ||
+      (ws && (::rix::malloc_async(&corr, npix * sizeof(R), st) != cudaSuccess ||
+              ::rix::malloc_async(&nm1, npix * sizeof(double), st) != cudaSuccess))) {
+    cudaGetLastError();
+    rc = set_error(RIX_ENOMEM, "PSF tiles");
+  }
+  const XformGeom g0 = plane_geom(job, pt, false);
+  const int G = inv_rows_groups<R>(job->ctx, g0, 16);
+  if (rc == RIX_OK && G < 0) rc = G;
+  if (rc == RIX_OK && G > 1 && pt.groups.bytes < (size_t)G * npix * sizeof(R))
+    rc = pt.groups.alloc(job->ctx, (size_t)G * npix * sizeof(R));
+  const double sc = pt.wsum > 0.0 ? 1.0 / pt.wsum : 0.0;
+  const int np = ws ? job->nw : 1;
+  for (int t = 0; t < 4 && rc == RIX_OK; ++t) {
+    const int tx = t & 1, ty = t >> 1;
+    const int ox = tx * n - n / 2, oy = ty * n - n / 2;
+    ::rix::note_launch();
+    k_psf_phase<R><<<(int)std::min<int64_t>(ceil_div(std::max<int64_t>(ns, 1), 256), (int64_t)job->ctx->num_sms * 16),
+                     256, 0, st>>>(job->uvw.as<double>(), job->inv_lambda.as<double>(), job->desc.nchan, ns,
+                                   ox * job->desc.cell_rad, oy * job->desc.cell_rad, vis);
+    if (cudaGetLastError() != cudaSuccess) { rc = set_error(RIX_ECUDA, "PSF phase launch"); break; }
+    XformGeom g = g0;
+    g.screen = nullptr;
+    if (ws) {
+      if ((rc = fill_correction<R>(job, n, job->ng, ox, oy, n, corr, nm1, st)) != RIX_OK) break;
+      g.corr = corr;
+      g.nm1 = nm1;
+    }
+    if (cudaMemsetAsync(pt.resid_planes.p, 0, (size_t)np * pt.win_n * pt.win_n * sizeof(cplx<R>), st) != cudaSuccess) {
+      rc = set_error(RIX_ECUDA, "memset");
+      break;
+    }
+    TileArgs a = base_args(job, pt);
+    a.out = pt.resid_planes.p;
+    a.vis_in = vis;
+    if ((rc = launch_tiles<R, kGrid>(job, a, st)) != RIX_OK) break;
+    if ((rc = inv_cols<R>(job->ctx, g, pt.resid_planes.as<cplx<R>>(), kOpNone, nullptr, nullptr,
+                          pt.tbuf.as<cplx<R>>(), st)) != RIX_OK)
+      break;
+    if ((rc = inv_rows<R>(job->ctx, g, pt.tbuf.as<cplx<R>>(), tile, sc, 0, st, pt.groups.as<R>(), G)) != RIX_OK) break;
+    if (cudaMemcpy2DAsync(pt.psf.as<R>() + (size_t)ty * n * 2 * n + (size_t)tx * n, 2 * n * sizeof(R), tile,
+                          n * sizeof(R), n * sizeof(R), n, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+      rc = set_error(RIX_ECUDA, "PSF tile copy");
+  }
+  if (vis) cudaFreeAsync(vis, st);
+  if (tile) cudaFreeAsync(tile, st);
+  if (corr) cudaFreeAsync(corr, st);
+  if (nm1) cudaFreeAsync(nm1, st);
+  return rc;
+}
+
+// whether partition PSFs of this job are formed by op_psf_tiled
+template <typename R>
+bool psf_uses_tiles(const Job* job) {
+  if (job->psf_method == RIX_PSF_TILES) return true;
+  if (job->psf_method == RIX_PSF_DOUBLE_GRID) return false;
+  return 2 * job->ng > fft_max_len<R>();
+}
+
 template <typename R>
 int op_psf(Job* job, int p, cudaStream_t st) {
   Part& pt = job->part[p];
@@ -852,6 +994,12 @@ int op_psf(Job* job, int p, cudaStream_t st) {
   if (pt.ent_count == 0) {
     RIX_CUDA(cudaMemsetAsync(pt.psf.p, 0, img2 * sizeof(R), st));
     RIX_CUDA(cudaMemsetAsync(pt.hspec.p, 0, img2 * sizeof(cplx<R>), st));
+    pt.psf_ready = true;
+    return RIX_OK;
+  }
+  if (psf_uses_tiles<R>(job)) {
+    RIX_TRY(op_psf_tiled<R>(job, p, st));
+    RIX_TRY(psf_spectrum<R>(job, pt, st));
     pt.psf_ready = true;
     return RIX_OK;
   }
@@ -897,10 +1045,7 @@ int op_psf(Job* job, int p, cudaStream_t st) {
     const double sc = pt.wsum > 0.0 ? 1.0 / pt.wsum : 0.0;
     if ((rc = inv_rows<R>(job->ctx, g, tt, pt.psf.as<R>(), sc, 0, st)) != RIX_OK) break;
     // centred spectrum of the 2N x 2N PSF on the 2N grid
-    XformGeom h{};
-    h.M = 2 * n; h.L = 2 * n; h.logL = ilog2(h.L); h.lo = 0; h.S = 2 * n; h.nplanes = 1; h.mode = kFacNone;
-    if ((rc = fwd_rows<R>(job->ctx, h, pt.psf.as<R>(), tt, st)) != RIX_OK) break;
-    if ((rc = fwd_cols<R>(job->ctx, h, tt, pt.hspec.as<cplx<R>>(), st)) != RIX_OK) break;
+    rc = psf_spectrum<R>(job, pt, st, tt);
   } while (0);
   cudaFreeAsync(pp, st);
   cudaFreeAsync(tt, st);

@@ -5,7 +5,6 @@
 //
 // All image-domain operators are applied on the 2N-padded grid through the
 // transforms of k_fft.cu; spectra are centred and stored u-major, (2N)^2.
-#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -15,8 +14,7 @@
 #include "rix_internal.cuh"
 #include "fft_device.cuh"
 #include "wavelet_device.cuh"
-
-namespace cg = cooperative_groups;
+#include "grid_sync.cuh"
 
 namespace rix {
 namespace {
@@ -342,15 +340,18 @@ struct CleanArgs {
   int* comp_pix;
   double* comp_amp;
   int* count;
+  unsigned int* barrier;       // arrival counter, zeroed before the launch
+  int* status;                 // the job's status word
 };
 
 // The whole minor cycle in one cooperative launch: each iteration subtracts
 // the previous component from every scale residual and, in the same sweep,
-// finds the next peak; one grid barrier per iteration separates the sweep
-// from the global reduction (double-buffered candidate slots).
+// finds the next peak; one bounded grid barrier per iteration separates the
+// sweep from the global reduction (double-buffered candidate slots).  A
+// barrier that gives up (RIX_ETIMEOUT in the status word) ends every CTA.
 template <typename R>
 __global__ void __launch_bounds__(256) k_msclean(CleanArgs a) {
-  cg::grid_group grid = cg::this_grid();
+  GridBarrier bar{a.barrier, a.status, 0u};
   __shared__ Cand<R> sh[32];
   const int n = a.n, n2 = 2 * a.n;
   const int64_t npix = (int64_t)n * n;
@@ -391,7 +392,7 @@ __global__ void __launch_bounds__(256) k_msclean(CleanArgs a) {
   if (threadIdx.x == 0) slots[blockIdx.x] = loc;
   int it = 0;
   for (;; ++it) {
-    grid.sync();
+    if (!grid_barrier(bar)) return;
     const Cand<R>* cur = slots + (int64_t)(it & 1) * gridDim.x;
     Cand<R> c{R(-1), R(0), 0x7fffffff, 0x7fffffff, R(0)};
     for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) c = merge(c, cur[b]);
@@ -761,6 +762,10 @@ int op_msclean(Job* job, int p, const rix_msclean_params* prm, R* delta_out, cud
   ca.comp_s = reinterpret_cast<int*>(cb + (size_t)cap * sizeof(double));
   ca.comp_pix = ca.comp_s + cap;
   ca.count = ca.comp_pix + cap;
+  RIX_TRY(ensure<R>(job, pt.sync, 16));
+  RIX_CUDA(cudaMemsetAsync(pt.sync.p, 0, sizeof(unsigned int), st));
+  ca.barrier = pt.sync.as<unsigned int>();
+  ca.status = job->status.as<int>();
   void* args[] = {&ca};
   ::rix::note_launch();
   timing_mark(kTimeMinorLoop, st, true);

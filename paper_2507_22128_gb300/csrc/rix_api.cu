@@ -677,6 +677,16 @@ static int rix_combine_impl(rix_job_t job, void* image_out, rix_stream_t stream)
   return op_combine<float>(&J, (float*)image_out, st);
 }
 
+int rix_job_set_psf_method(rix_job_t job, int32_t method) {
+  if (!job) return set_error(RIX_EINVAL, "job is NULL");
+  if (method != RIX_PSF_AUTO && method != RIX_PSF_DOUBLE_GRID && method != RIX_PSF_TILES)
+    return set_error(RIX_EINVAL, "PSF method must be RIX_PSF_AUTO, RIX_PSF_DOUBLE_GRID or RIX_PSF_TILES");
+  Job& J = job->j;
+  J.psf_method = method;
+  for (int p = 0; p < kMaxPart; ++p) J.part[p].psf_ready = false;
+  return RIX_OK;
+}
+
 // ---- gridder tuning and batched major cycles ------------------------------
 int rix_job_tune(rix_job_t job, int32_t chunk_limit, int32_t ctas_per_sm) {
   if (!job) return set_error(RIX_EINVAL, "job is NULL");

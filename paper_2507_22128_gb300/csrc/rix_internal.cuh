@@ -176,6 +176,9 @@ struct XformGeom {
 template <typename R>
 int build_screen_table(const Ctx* ctx, const XformGeom& g, cplx<R>* screen, cudaStream_t st);
 
+// the longest transform the row and column passes support (a power of two)
+template <typename R>
+int fft_max_len();
 template <typename R>
 int fwd_rows(const Ctx* ctx, const XformGeom& g, const R* img, cplx<R>* T, cudaStream_t st);
 template <typename R>
@@ -311,6 +314,7 @@ struct Job {
   int chunk_limit = 32;
   int fp_ctas_per_sm = 0;
   bool gorder = false;   // egeom (and gsamples) in the gridder order
+  int psf_method = 0;    // RIX_PSF_* (rix_job_set_psf_method)
 };
 
 // The major cycles of several (job, partition) pairs with one gridder launch

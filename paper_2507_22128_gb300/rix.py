@@ -16,8 +16,9 @@ import torch
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "librix.so")
 
-OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, ESTATE, EBUSY = 0, -1, -2, -3, -4, -5, -6
+OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, ESTATE, EBUSY, EINTERNAL = 0, -1, -2, -3, -4, -5, -6, -7
 FP32, FP64 = 0, 1
+PSF_AUTO, PSF_DOUBLE_GRID, PSF_TILES = 0, 1, 2
 
 
 class RixError(RuntimeError):
@@ -97,6 +98,7 @@ def _load() -> C.CDLL:
         "rix_selftest_barrier_timeout": (C.c_int, [vp, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
         "rix_daubechies_lowpass": (C.c_int, [C.c_int, C.POINTER(C.c_double)]),
         "rix_job_tune": (C.c_int, [vp, i32, i32]),
+        "rix_job_set_psf_method": (C.c_int, [vp, i32]),
         "rix_batch_create": (C.c_int, [vp, i32, C.POINTER(vp), C.POINTER(i32), C.POINTER(vp)]),
         "rix_batch_destroy": (C.c_int, [vp]),
         "rix_batch_major_cycle": (C.c_int, [vp, C.POINTER(vp), C.POINTER(vp), vp]),
@@ -125,7 +127,8 @@ EXPORTED = ("rix_create", "rix_destroy", "rix_job_workspace_bytes", "rix_job_cre
             "rix_kernel_launches", "rix_timing_enable", "rix_timing_read", "rix_grid_noalloc",
             "rix_selftest_barrier_timeout", "rix_daubechies_lowpass", "rix_get_weights",
             "rix_minor_cycle_fista_batch", "rix_device_allocations", "rix_bda_rows", "rix_bda_average",
-            "rix_phi_support", "rix_phi_pack", "rix_phi_unpack", "rix_job_tune", "rix_batch_create",
+            "rix_phi_support", "rix_phi_pack", "rix_phi_unpack", "rix_job_tune", "rix_job_set_psf_method",
+            "rix_batch_create",
             "rix_batch_destroy", "rix_batch_major_cycle", "rix_gridder_probe",
             "rix_major_cycle_probe")
 
@@ -249,6 +252,11 @@ def grid(job, part, vis, image_out, stream=None):
 # ------------------------------------------ tuning and batched major cycles --
 def job_tune(job, chunk_limit=32, ctas_per_sm=0):
     _check(_lib.rix_job_tune(job, int(chunk_limit), int(ctas_per_sm)))
+
+
+def job_set_psf_method(job, method=0):
+    """PSF_AUTO, PSF_DOUBLE_GRID or PSF_TILES (how rix_psf forms the PSF)."""
+    _check(_lib.rix_job_set_psf_method(job, int(method)))
 
 
 def batch_create(ctx, jobs, parts) -> int:

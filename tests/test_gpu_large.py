@@ -4,7 +4,15 @@ of its 4000 time samples (62 times: 4.03 M visibilities), FP32, 2 and 4 uv
 partitions: masks, ring radii and the sort bit-exact in full; degrid on 10^4
 sampled visibilities, grid and the fused major cycle on 64 sampled pixels
 per partition against the direct DFT within the FP32 operator's 1e-4; the
-major-cycle probe reproduces the major cycle's residual."""
+major-cycle probe reproduces the major cycle's residual.
+
+The PSF of a 4096^2 job is formed as four N x N tiles on the image grid (its
+own 2N grid would need 16384-long transforms): the peak and 96 sampled pixels
+(the centre, the tile seams, anywhere) against Re A^H w / W_p by direct DFT.
+The minor cycles at this size (ms-CLEAN with the recipe's scales, FISTA with
+2N = 8192 transforms) have no oracle run here; two full cycles of each are
+checked for what holds at any size: components from the scales allowed in
+cycle 1, a finite model, and a residual peak that falls from cycle 1 to 2."""
 import numpy as np
 import pytest
 
@@ -95,3 +103,85 @@ def test_operator_sampled_vs_direct_dft(large):
         ms = rix.major_cycle_probe(job, part, y_d, 2)
         assert ms > 0.0
         assert rix.job_get_stats(job)["cycle"][part] == 1
+
+
+def test_psf_tiles_sampled_vs_direct_dft(large):
+    from oracle import dft
+    obs, rix, job, mask, g, ells, want_mask, P = large
+    n = obs.n
+    n2 = 2 * n
+    u, v, w = dft.uvw_lambda(obs.uvw, obs.freq)
+    wt_all = obs.weight.reshape(-1).astype(np.float64)
+    for part in (0, P - 1):
+        psf = torch.empty((n2, n2), dtype=torch.float32, device="cuda")
+        wsum = rix.psf(job, part, psf)
+        torch.cuda.synchronize()
+        sel = ((mask >> part) & 1) == 1
+        wt = wt_all[sel]
+        assert wsum == pytest.approx(wt.sum(), rel=1e-12)
+        assert float(psf[n, n]) == pytest.approx(1.0, abs=1e-5)
+        rng = np.random.default_rng(201 + 10 * P + part)
+        k = 24
+        rows = np.concatenate([rng.integers(0, n2, k), n + rng.integers(-48, 48, k),
+                               rng.choice([n - 1, n, 0, n2 - 1], k), rng.integers(0, n2, k)])
+        cols = np.concatenate([rng.integers(0, n2, k), n + rng.integers(-48, 48, k),
+                               rng.integers(0, n2, k), rng.choice([n - 1, n, 0, n2 - 1], k)])
+        got = psf[torch.as_tensor(rows, device="cuda"), torch.as_tensor(cols, device="cuda")].cpu().numpy()
+        want = dft.adjoint_at(wt.astype(np.complex128), u[sel], v[sel], w[sel], n2, obs.cell_rad, True,
+                              rows, cols) / wt.sum()
+        assert rel_l2(got, want) < 1e-4
+
+
+@pytest.mark.parametrize("kind", ["msclean", "fista"])
+def test_minor_cycles_at_size(kind):
+    """Two major+minor cycles of a 4096^2 FP32 job (P = 2, 1/64 of the rows,
+    visibilities of 25 point sources by direct DFT)."""
+    need_gpu()
+    from oracle import dft
+    from paper_2507_22128_gb300 import pipeline, rix, synth
+    obs = synth.large(seed=3, n_times=62, with_vis=False)
+    n = obs.n
+    x = sparse_model(n, 25, seed=303)
+    u, v, w = dft.uvw_lambda(obs.uvw, obs.freq)
+    ch = 1 << 18
+    vis = np.concatenate([dft.degrid_pixels_sparse(x, u[i:i + ch], v[i:i + ch], w[i:i + ch], obs.cell_rad, True)
+                          for i in range(0, u.shape[0], ch)]).reshape(obs.nrow, obs.nchan)
+    ctx = rix.create(0)
+    rec = pipeline.Reconstruction(ctx, n, obs.cell_rad, obs.n_wplanes, obs.freq, obs.nrow, 2, rix.FP32)
+    try:
+        rec.set_data(obs.uvw, vis, obs.weight)
+        if kind == "msclean":
+            m = pipeline.Method("msclean", (0.0, 4.0, 16.0, 32.0), 0.1, 200, 1e-4)
+        else:
+            m = pipeline.Method("fista", lam_rel=1e-3, iters=20, levels=4)
+        peaks = []
+        for c in range(2):
+            res = [torch.empty((n, n), dtype=torch.float32, device="cuda") for _ in range(2)]
+            for p in range(2):
+                rec.major(p, res[p])
+            torch.cuda.synchronize()
+            peaks.append([float(r.abs().max()) for r in res])
+            if kind == "fista":
+                rec.minor_all(m, torch.cuda.current_stream())
+            else:
+                for p in range(2):
+                    rec.minor(p, m)
+            rix.job_sync(rec.job)
+            if kind == "msclean" and c == 0:
+                ell = rix.job_get_stats(rec.job)["ell_px"][0]
+                for p in range(2):
+                    sc, _, _ = rix.get_components(rec.job, p)
+                    assert 0 < len(sc) <= 200
+                    used = set(int(s) for s in sc)
+                    # scales present in cycle 1: partition 0 all; partition 1
+                    # s = 0 and those with N / (2 s) >= ell - delta
+                    allowed = {0} | {i for i, s in enumerate(m.scales) if s > 0 and (p == 0 or n / (2 * s) >= ell - 1.0)}
+                    assert used <= allowed
+        img = rec.combine()
+        torch.cuda.synchronize()
+        assert bool(torch.isfinite(img).all())
+        for p in range(2):
+            assert peaks[1][p] < peaks[0][p]
+    finally:
+        rec.close()
+        rix.destroy(ctx)

@@ -136,6 +136,47 @@ def test_psf_matches_oracle(ctx, obs_small, obs_wstack, name, prec, nparts):
         rix.job_destroy(job)
 
 
+# The tiled PSF grids on the image grid instead of the 2N image's own grid,
+# so it matches the oracle's PSF to the gridding kernel's accuracy (the
+# oracle's PSF is within 6e-8 of the direct DFT on these cases), not to
+# rounding: 1e-6 in FP64, 1e-5 in FP32.
+TOL_TILES = {0: 1e-5, 1: 1e-6}
+
+
+@pytest.mark.parametrize("name,prec,nparts", CASES[:4])
+def test_tiled_psf_matches_oracle(ctx, obs_small, obs_wstack, name, prec, nparts):
+    """rix_psf with RIX_PSF_TILES (four N x N tiles on the image grid, the form
+    N = 4096 jobs take): the whole 2N x 2N PSF, seams included, against the
+    oracle's; then RIX_PSF_DOUBLE_GRID forms the PSF again, to the oracle's
+    own tolerance."""
+    from paper_2507_22128_gb300 import rix
+    obs = _obs(name, obs_small, obs_wstack)
+    job, _ = _job(ctx, obs, prec, nparts)
+    try:
+        st = _oracle(obs, nparts)
+        rix.job_set_psf_method(job, rix.PSF_TILES)
+        n = obs.n
+        for p in range(nparts):
+            out = torch.empty((2 * n, 2 * n), dtype=real_dtype(prec), device="cuda")
+            wsum = rix.psf(job, p, out)
+            torch.cuda.synchronize()
+            got = out.cpu().numpy().astype(np.float64)
+            assert wsum == pytest.approx(st.wsum[p], rel=1e-12)
+            assert rel_l2(got, st.psf[p]) < TOL_TILES[prec]
+            assert got[n, n] == pytest.approx(1.0, abs=TOL_TILES[prec])
+            # the rows and columns on both sides of the tile seams
+            for sl in (np.s_[n - 1:n + 1, :], np.s_[:, n - 1:n + 1], np.s_[0:1, :], np.s_[:, 0:1]):
+                assert rel_l2(got[sl], st.psf[p][sl]) < 10 * TOL_TILES[prec]
+        rix.job_set_psf_method(job, rix.PSF_DOUBLE_GRID)
+        for p in range(nparts):
+            out = torch.empty((2 * n, 2 * n), dtype=real_dtype(prec), device="cuda")
+            rix.psf(job, p, out)
+            torch.cuda.synchronize()
+            assert rel_l2(out.cpu().numpy(), st.psf[p]) < TOL[prec]
+    finally:
+        rix.job_destroy(job)
+
+
 @pytest.mark.parametrize("name,prec,nparts", CASES)
 def test_major_cycle_matches_oracle(ctx, obs_small, obs_wstack, name, prec, nparts):
     from oracle import gridder
