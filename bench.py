@@ -63,9 +63,14 @@ def parse():
     ap.add_argument("--serve-jobs", type=int, default=24, help="arrivals in the serving experiment (0 = skip)")
     ap.add_argument("--serve-rate", type=float, default=20.0, help="Poisson arrival rate, jobs/s")
     ap.add_argument("--json-out", default=None)
-    ap.add_argument("--workload", default="medium", choices=["medium", "batch", "large"],
+    ap.add_argument("--workload", default="medium", choices=["medium", "batch", "large", "serve"],
                     help="medium: the whole-job benchmark; batch: the batching workload's batched major cycle; "
-                         "large: the 4096^2 workload's major cycle")
+                         "large: the 4096^2 workload's major cycle; serve: the serving workload (Poisson "
+                         "arrivals of the recipe mix under a memory budget)")
+    ap.add_argument("--serve-budget-gb", type=float, default=150.0, help="device-memory budget of the serving runs")
+    ap.add_argument("--serve-slots", type=int, default=16, help="streams (concurrent jobs at most) when serving")
+    ap.add_argument("--serve-compare-jobs", type=int, default=100,
+                    help="arrivals of the sustained-rate run and of the FP32-vs-FP64 runs (0 = skip them)")
     ap.add_argument("--parts", type=int, default=2, help="uv partitions of the large workload (2 or 4)")
     ap.add_argument("--batch-jobs", type=int, default=64)
     return ap.parse_args()
@@ -289,6 +294,8 @@ def main():
         return batch_workload(a, rank, world, local)
     if a.workload == "large":
         return large_workload(a, rank, world, local)
+    if a.workload == "serve":
+        return serve_workload(a, rank, world, local)
 
     from paper_2507_22128_gb300 import pipeline, rix, synth
 
@@ -578,6 +585,149 @@ def large_workload(a, rank, world, local):
             "part_count": st["part_count"][:P], "n_outside": st["n_outside"]}
     rec.close()
     rix.destroy(ctx)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+        if a.json_out:
+            with open(a.json_out, "w") as f:
+                json.dump(line, f, indent=1)
+    return 0
+
+
+def serve_pools(rank: int):
+    """The serving workload's observations: four of the small recipe (seeds
+    100-103), the medium recipe (seed 1: 8.06 M visibilities), four
+    channel-chunk jobs of the batching recipe (seeds 1000-1003) and the large
+    recipe's uvw (seed 3: 260 M visibilities) with seeded complex Gaussian
+    visibilities (analytic visibilities of its 2100 sources at 260 M samples
+    take far longer to make than to image).  Kind -> (share, [observations],
+    major cycles, ms-CLEAN scales, FISTA levels)."""
+    from paper_2507_22128_gb300 import synth
+    small = [synth.plain_small(seed=100 + k + 10 * rank) for k in range(4)]
+    medium = [synth.medium(seed=1 + rank)]
+    chunk = synth.batch_chunk_jobs(n_jobs=4, base_seed=1000 + 100 * rank)
+    large = synth.large(seed=3 + rank, with_vis=False)
+    rng = np.random.default_rng(3 + rank)
+    v = np.empty((large.nrow, large.nchan), np.complex64)
+    v.real = rng.standard_normal(v.shape, dtype=np.float32)
+    v.imag = rng.standard_normal(v.shape, dtype=np.float32)
+    large.vis = v
+    return {"small": (0.50, small, 5, (0.0, 3.0, 9.0), 3),
+            "medium": (0.30, medium, 10, (0.0, 4.0, 16.0), 4),
+            "chunk": (0.15, chunk, 5, (0.0, 4.0, 16.0), 4),
+            "large": (0.05, [large], 8, (0.0, 4.0, 16.0, 32.0), 4)}
+
+
+def serve_requests(pools, arrivals, rng, precision, only=None):
+    """One request per arrival: kind by the pools' shares, observation
+    uniform in its pool, ms-CLEAN or FISTA with probability 1/2 each
+    (ms-CLEAN: gain 0.1, 2000 iterations, threshold 1e-4; FISTA: Db4, 50
+    iterations, lambda = 1e-3 max |residual of cycle 1|)."""
+    from paper_2507_22128_gb300 import pipeline, serve
+    names = list(pools)
+    probs = np.array([pools[k][0] for k in names])
+    picks = rng.choice(len(names), arrivals.shape[0], p=probs / probs.sum())
+    obs_pick = rng.random(arrivals.shape[0])
+    meth_pick = rng.random(arrivals.shape[0]) < 0.5
+    reqs = []
+    for i, t in enumerate(arrivals):
+        kind = names[picks[i]]
+        _, obs_list, n_major, scales, levels = pools[kind]
+        if only is not None and kind not in only:
+            continue
+        obs = obs_list[int(obs_pick[i] * len(obs_list))]
+        if meth_pick[i]:
+            m = pipeline.Method("msclean", scales, 0.1, 2000, 1e-4)
+        else:
+            m = pipeline.Method("fista", lam_rel=1e-3, iters=50, levels=levels)
+        reqs.append(serve.Request(i, obs, m, n_major, arrival=float(t), precision=precision,
+                                  kind=f"{kind} {m.kind}"))
+    return reqs
+
+
+def serve_workload(a, rank, world, local):
+    """The serving workload (one process per GPU, each its own arrival
+    stream): Poisson arrivals (seed 4) at --serve-rate jobs/s of jobs drawn
+    50/30/15/5 % from the small, medium, channel-chunk and large recipes,
+    half ms-CLEAN and half FISTA, admitted in arrival order under a
+    --serve-budget-gb device-memory budget (the library's reservation per
+    job) with each job's state resident until its combined image is read
+    back, --serve-slots concurrent jobs at most.  Runs:
+      offered:   --serve-jobs arrivals at --serve-rate, FP32;
+      sustained: --serve-compare-jobs arrivals at 0.8 x the achieved rate of
+                 the first run, FP32;
+      fp32/fp64: the first --serve-compare-jobs arrivals of the first run's
+                 stream whose jobs FP64 supports (N <= 2048: the large
+                 recipe's are left out), at the same arrival times, served
+                 in FP32 and then in FP64; per job the relative L2 distance
+                 between the two combined images.
+    Latency runs from a job's arrival to the read-back of its combined image;
+    its inputs are copied from page-locked host memory when it is admitted."""
+    from paper_2507_22128_gb300 import rix, serve
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    t0 = time.perf_counter()
+    pools = serve_pools(rank)
+    gen_s = time.perf_counter() - t0
+    ctx = rix.create(local, int(a.serve_budget_gb * 1e9))
+    peak = {"bytes": 0}
+
+    def probe():
+        free, total = torch.cuda.mem_get_info(dev)
+        peak["bytes"] = max(peak["bytes"], total - free)
+
+    def run(reqs, label):
+        t1 = time.perf_counter()
+        serve.prepare_host(reqs)
+        prep = time.perf_counter() - t1
+        torch.cuda.synchronize()
+        peak["bytes"] = 0
+        with ClockSampler(local) as clk:
+            serve.serve(ctx, reqs, n_slots=a.serve_slots, mem_probe=probe)
+        torch.cuda.synchronize()
+        out = serve.summary(reqs)
+        out.update({"run": label, "clocks": clk.summary(), "device_bytes_in_use_peak": int(peak["bytes"]),
+                    "host_prepare_s": prep})
+        serve.clear_host()
+        return out
+
+    rng = np.random.default_rng(4 + rank)
+    arrivals = serve.poisson_arrivals(rng, a.serve_jobs, a.serve_rate)
+    reqs = serve_requests(pools, arrivals, np.random.default_rng(40 + rank), rix.FP32)
+    runs = {"offered": run(reqs, f"{a.serve_jobs} arrivals at {a.serve_rate} jobs/s, FP32")}
+    runs["offered"]["arrival_rate_per_s"] = a.serve_rate
+    k = a.serve_compare_jobs
+    if k > 0:
+        rate = max(0.8 * runs["offered"]["achieved_jobs_per_s"], 0.1)
+        arr2 = serve.poisson_arrivals(np.random.default_rng(44 + rank), k, rate)
+        runs["sustained"] = run(serve_requests(pools, arr2, np.random.default_rng(41 + rank), rix.FP32),
+                                f"{k} arrivals at {rate:.2f} jobs/s (0.8 x the achieved rate), FP32")
+        runs["sustained"]["arrival_rate_per_s"] = rate
+        sub = [q for q in serve_requests(pools, arrivals, np.random.default_rng(40 + rank), rix.FP32)
+               if not q.kind.startswith("large")][:k]
+        r32 = run(sub, f"first {len(sub)} arrivals without the large recipe, FP32")
+        img32 = {q.rid: q.image for q in sub}
+        sub64 = [q for q in serve_requests(pools, arrivals, np.random.default_rng(40 + rank), rix.FP64)
+                 if not q.kind.startswith("large")][:k]
+        r64 = run(sub64, f"the same {len(sub64)} arrivals, FP64")
+        diffs = {}
+        for q in sub64:
+            d = float(np.linalg.norm(img32[q.rid] - q.image) / max(np.linalg.norm(q.image), 1e-300))
+            diffs.setdefault(q.kind, []).append(d)
+        r64["fp32_vs_fp64_image_rel_l2"] = {kk: {"median": float(np.median(v)), "max": float(np.max(v)),
+                                                 "jobs": len(v)} for kk, v in sorted(diffs.items())}
+        runs["fp32"] = r32
+        runs["fp64"] = r64
+    rix.destroy(ctx)
+    off = runs["offered"]
+    line = {"metric": "p99 job latency", "value": off["p99_latency_s"], "unit": "s", "n_gpus": world,
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (analytic visibilities of the small, medium and chunk recipes; the large recipe's "
+                    "uvw with seeded Gaussian visibilities)",
+            "config": {"workload": f"serving: Poisson arrivals at {a.serve_rate} jobs/s, {a.serve_jobs} arrivals, "
+                                   "mix 50/30/15/5 % small/medium/chunk/large, half ms-CLEAN half FISTA",
+                       "budget_gb": a.serve_budget_gb, "slots": a.serve_slots,
+                       "pools": {kk: len(v[1]) for kk, v in pools.items()}},
+            "generate_s": gen_s, "runs": runs}
     if rank == 0:
         print(json.dumps(line), flush=True)
         if a.json_out:

@@ -146,7 +146,7 @@ def _stream(stream):
     return C.c_void_p(int(stream))
 
 
-def _ptr(t, dtype=None, numel=None, name="tensor"):
+def _ptr(t, dtype=None, numel=None, name="tensor", min_numel=None):
     if t is None:
         return None
     if not isinstance(t, torch.Tensor) or not t.is_cuda:
@@ -157,7 +157,36 @@ def _ptr(t, dtype=None, numel=None, name="tensor"):
         raise TypeError(f"{name} has dtype {t.dtype}, expected {dtype}")
     if numel is not None and t.numel() != numel:
         raise ValueError(f"{name} has {t.numel()} elements, expected {numel}")
+    if min_numel is not None and t.numel() < min_numel:
+        raise ValueError(f"{name} has {t.numel()} elements, at least {min_numel} needed")
     return C.c_void_p(t.data_ptr())
+
+
+# The library takes untyped device pointers; the binding checks each buffer
+# against the job it is passed with: element type by the job's precision,
+# images by their size, visibility arrays by the rows of the current
+# partitioning.
+_JOBS: dict = {}      # job handle -> [precision, n, nchan, rows partitioned (0 before)]
+
+
+def _real_t(job):
+    j = _JOBS.get(job)
+    return _RT if j is None else (torch.float64 if j[0] == FP64 else torch.float32)
+
+
+def _cplx_t(job):
+    j = _JOBS.get(job)
+    return _CT if j is None else (torch.complex128 if j[0] == FP64 else torch.complex64)
+
+
+def _img(job, t, name, side=1):
+    j = _JOBS.get(job)
+    return _ptr(t, _real_t(job), None if j is None else (side * j[1]) ** 2, name)
+
+
+def _visp(job, t, name):
+    j = _JOBS.get(job)
+    return _ptr(t, _cplx_t(job), name=name, min_numel=None if j is None else j[2] * j[3])
 
 
 # ---------------------------------------------------------------- lifetime --
@@ -190,11 +219,13 @@ def job_create(ctx, n, cell_rad, n_wplanes, freq_hz, precision, n_part, max_rows
     d, _keep = _desc(n, cell_rad, n_wplanes, freq_hz, precision, n_part, tile, weighting, exchange)
     h = C.c_void_p()
     _check(_lib.rix_job_create(ctx, C.byref(d), max_rows, C.byref(h)))
+    _JOBS[h.value] = [int(precision), int(n), len(freq_hz), 0]
     return h.value
 
 
 def job_destroy(job: int):
     _check(_lib.rix_job_destroy(job))
+    _JOBS.pop(job, None)
 
 
 def job_sync(job: int):
@@ -222,6 +253,8 @@ def set_uv_partition(job, uvw, weight=None, ell_px=None, delta_px=1.0, mask_out=
                                      C.cast(ells, C.POINTER(C.c_double)) if ells is not None else None,
                                      float(delta_px), _ptr(mask_out, torch.uint8, name="mask_out"),
                                      _stream(stream)))
+    if job in _JOBS:
+        _JOBS[job][3] = int(nrow)
 
 
 def get_sorted_entries(job, keys_out, samples_out, stream=None):
@@ -240,12 +273,12 @@ _CT = (torch.complex64, torch.complex128)
 
 
 def degrid(job, part, image, vis_out, stream=None):
-    _check(_lib.rix_degrid(job, part, _ptr(image, _RT, name="image"), _ptr(vis_out, _CT, name="vis_out"),
+    _check(_lib.rix_degrid(job, part, _img(job, image, "image"), _visp(job, vis_out, "vis_out"),
                            _stream(stream)))
 
 
 def grid(job, part, vis, image_out, stream=None):
-    _check(_lib.rix_grid(job, part, _ptr(vis, _CT, name="vis"), _ptr(image_out, _RT, name="image_out"),
+    _check(_lib.rix_grid(job, part, _visp(job, vis, "vis"), _img(job, image_out, "image_out"),
                          _stream(stream)))
 
 
@@ -265,34 +298,46 @@ def batch_create(ctx, jobs, parts) -> int:
     pa = (C.c_int32 * n)(*[int(p) for p in parts])
     h = C.c_void_p()
     _check(_lib.rix_batch_create(ctx, n, ja, pa, C.byref(h)))
+    _BATCHES[h.value] = list(jobs)
     return h.value
+
+
+_BATCHES: dict = {}   # batch handle -> the job of each pair
 
 
 def batch_destroy(batch):
     _check(_lib.rix_batch_destroy(batch))
+    _BATCHES.pop(batch, None)
 
 
 def batch_major_cycle(batch, vis_list, residual_out=None, stream=None):
     """vis_list: one complex64 device tensor per pair; residual_out: None or
     one float32 N x N device tensor (or None) per pair."""
-    arr = (C.c_void_p * len(vis_list))(*[_ptr(v, torch.complex64, name="vis_obs") for v in vis_list])
+    jobs = _BATCHES.get(batch)
+    if jobs is not None and (len(vis_list) != len(jobs) or (residual_out is not None and len(residual_out) != len(jobs))):
+        raise ValueError(f"the batch has {len(jobs)} pairs")
+    pick = (lambda i: jobs[i]) if jobs is not None else (lambda i: None)
+    arr = (C.c_void_p * len(vis_list))(*[_visp(pick(i), v, "vis_obs") if jobs else
+                                         _ptr(v, torch.complex64, name="vis_obs") for i, v in enumerate(vis_list)])
     res = None
     if residual_out is not None:
-        res = (C.c_void_p * len(residual_out))(*[_ptr(r, torch.float32, name="residual_out") for r in residual_out])
+        res = (C.c_void_p * len(residual_out))(*[_img(pick(i), r, "residual_out") if jobs else
+                                                 _ptr(r, torch.float32, name="residual_out")
+                                                 for i, r in enumerate(residual_out)])
     _check(_lib.rix_batch_major_cycle(batch, arr, res, _stream(stream)))
 
 
 def major_cycle_probe(job, part, vis, reps=3) -> float:
     """Mean device ms of the partition's fused major-cycle operator."""
     ms = C.c_double()
-    _check(_lib.rix_major_cycle_probe(job, part, _ptr(vis, _CT, name="vis"), int(reps), C.byref(ms)))
+    _check(_lib.rix_major_cycle_probe(job, part, _visp(job, vis, "vis"), int(reps), C.byref(ms)))
     return ms.value
 
 
 def gridder_probe(job, part, vis, reps=3) -> float:
     """Mean device ms per launch of the partition's FP32 w-stacked gridder."""
     ms = C.c_double()
-    _check(_lib.rix_gridder_probe(job, part, _ptr(vis, torch.complex64, name="vis"), int(reps), C.byref(ms)))
+    _check(_lib.rix_gridder_probe(job, part, _visp(job, vis, "vis"), int(reps), C.byref(ms)))
     return ms.value
 
 
@@ -304,12 +349,15 @@ def phi_support(job, part) -> int:
 
 
 def phi_pack(job, part, packed_out, stream=None):
-    _check(_lib.rix_phi_pack(job, part, _ptr(packed_out, _CT, name="packed_out"), _stream(stream)))
+    cnt = phi_support(job, part)
+    _check(_lib.rix_phi_pack(job, part, _ptr(packed_out, _cplx_t(job), name="packed_out", min_numel=cnt),
+                             _stream(stream)))
 
 
 def phi_unpack(job, part, packed, phi_out, stream=None):
-    _check(_lib.rix_phi_unpack(job, part, _ptr(packed, _CT, name="packed"), _ptr(phi_out, _RT, name="phi_out"),
-                               _stream(stream)))
+    cnt = phi_support(job, part)
+    _check(_lib.rix_phi_unpack(job, part, _ptr(packed, _cplx_t(job), name="packed", min_numel=cnt),
+                               _img(job, phi_out, "phi_out"), _stream(stream)))
 
 
 # ------------------------------------------- baseline-dependent averaging --
@@ -355,20 +403,20 @@ def grid_noalloc(job, part, vis, image_out, stream=None):
 
 def psf(job, part, psf_out=None, stream=None) -> float:
     w = C.c_double()
-    _check(_lib.rix_psf(job, part, _ptr(psf_out, _RT, name="psf_out"), C.byref(w), _stream(stream)))
+    _check(_lib.rix_psf(job, part, _img(job, psf_out, "psf_out", 2), C.byref(w), _stream(stream)))
     return w.value
 
 
 def major_cycle(job, part, vis_obs, model=None, residual_out=None, stream=None):
-    _check(_lib.rix_major_cycle(job, part, _ptr(vis_obs, _CT, name="vis_obs"), _ptr(model, _RT, name="model"),
-                                _ptr(residual_out, _RT, name="residual_out"), _stream(stream)))
+    _check(_lib.rix_major_cycle(job, part, _visp(job, vis_obs, "vis_obs"), _img(job, model, "model"),
+                                _img(job, residual_out, "residual_out"), _stream(stream)))
 
 
 # -------------------------------------------------------------- a8 - a11 --
 def minor_cycle_msclean(job, part, scales, gain, niter, threshold, delta_out=None, stream=None):
     sc = (C.c_float * len(scales))(*[float(s) for s in scales])
     p = MscleanParams(C.cast(sc, C.POINTER(C.c_float)), len(scales), float(gain), int(niter), float(threshold))
-    _check(_lib.rix_minor_cycle_msclean(job, part, C.byref(p), _ptr(delta_out, _RT, name="delta_out"),
+    _check(_lib.rix_minor_cycle_msclean(job, part, C.byref(p), _img(job, delta_out, "delta_out"),
                                         _stream(stream)))
 
 
@@ -377,7 +425,7 @@ def minor_cycle_fista(job, part, lam=0.0, lam_rel=1e-3, iters=50, levels=4, delt
     """schedule: (a, b) for lambda_n = a ||residual_n||_2 b^n, or None."""
     a, b = schedule if schedule is not None else (0.0, 0.0)
     p = FistaParams(float(lam), float(lam_rel), int(iters), int(levels), int(dictionary), 0, float(a), float(b))
-    _check(_lib.rix_minor_cycle_fista(job, part, C.byref(p), _ptr(delta_out, _RT, name="delta_out"),
+    _check(_lib.rix_minor_cycle_fista(job, part, C.byref(p), _img(job, delta_out, "delta_out"),
                                       _stream(stream)))
 
 
@@ -403,7 +451,7 @@ def get_components(job, part, capacity=1 << 16, stream=None):
 
 
 def get_model(job, part, image_out, stream=None):
-    _check(_lib.rix_get_model(job, part, _ptr(image_out, _RT, name="image_out"), _stream(stream)))
+    _check(_lib.rix_get_model(job, part, _img(job, image_out, "image_out"), _stream(stream)))
 
 
 def kernel_launches() -> int:
@@ -433,7 +481,7 @@ def timing_read(kernel_class: int):
 
 
 def combine(job, image_out, stream=None):
-    _check(_lib.rix_combine(job, _ptr(image_out, _RT, name="image_out"), _stream(stream)))
+    _check(_lib.rix_combine(job, _img(job, image_out, "image_out"), _stream(stream)))
 
 
 def selftest_barrier_timeout(ctx):

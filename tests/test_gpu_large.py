@@ -10,9 +10,10 @@ The PSF of a 4096^2 job is formed as four N x N tiles on the image grid (its
 own 2N grid would need 16384-long transforms): the peak and 96 sampled pixels
 (the centre, the tile seams, anywhere) against Re A^H w / W_p by direct DFT.
 The minor cycles at this size (ms-CLEAN with the recipe's scales, FISTA with
-2N = 8192 transforms) have no oracle run here; two full cycles of each are
-checked for what holds at any size: components from the scales allowed in
-cycle 1, a finite model, and a residual peak that falls from cycle 1 to 2."""
+2N = 8192 transforms), and those of the largest FP64 job (2048^2), have no
+oracle run here; two full cycles of each are checked for what holds at any
+size: components from the scales allowed in cycle 1, a finite non-zero
+image, and a residual peak that falls from cycle 1 to 2."""
 import numpy as np
 import pytest
 
@@ -132,31 +133,68 @@ def test_psf_tiles_sampled_vs_direct_dft(large):
         assert rel_l2(got, want) < 1e-4
 
 
-@pytest.mark.parametrize("kind", ["msclean", "fista"])
-def test_minor_cycles_at_size(kind):
-    """Two major+minor cycles of a 4096^2 FP32 job (P = 2, 1/64 of the rows,
-    visibilities of 25 point sources by direct DFT)."""
+def _point_source_vis(obs, seed):
+    from oracle import dft
+    x = sparse_model(obs.n, 25, seed=seed)
+    u, v, w = dft.uvw_lambda(obs.uvw, obs.freq)
+    ch = 1 << 18
+    return np.concatenate([dft.degrid_pixels_sparse(x, u[i:i + ch], v[i:i + ch], w[i:i + ch], obs.cell_rad, True)
+                           for i in range(0, u.shape[0], ch)]).reshape(obs.nrow, obs.nchan)
+
+
+@pytest.mark.parametrize("kind,prec", [("msclean", 0), ("fista", 0), ("msclean", 1), ("fista", 1)])
+def test_minor_cycles_at_size(kind, prec):
+    """Two major+minor cycles of the largest job of each precision (P = 2,
+    visibilities of 25 point sources by direct DFT): FP32 at 4096^2 (the
+    large recipe on 1/64 of its rows: FISTA with 8192-point transforms, the
+    ms-CLEAN scales {0, 4, 16, 32}), FP64 at 2048^2 (the medium recipe's
+    antennas, 100 times: FISTA with 4096-point transforms, scales {0, 4,
+    16}); both PSFs are tiled.  The FP64 PSF also matches the direct DFT on
+    sampled pixels: within 1e-6 near the centre, 1e-4 over the field."""
     need_gpu()
     from oracle import dft
     from paper_2507_22128_gb300 import pipeline, rix, synth
-    obs = synth.large(seed=3, n_times=62, with_vis=False)
+    if prec == 0:
+        obs = synth.large(seed=3, n_times=62, with_vis=False)
+        scales = (0.0, 4.0, 16.0, 32.0)
+    else:
+        obs = synth.medium(seed=5, n_times=100, n=2048, with_vis=False)
+        scales = (0.0, 4.0, 16.0)
     n = obs.n
-    x = sparse_model(n, 25, seed=303)
-    u, v, w = dft.uvw_lambda(obs.uvw, obs.freq)
-    ch = 1 << 18
-    vis = np.concatenate([dft.degrid_pixels_sparse(x, u[i:i + ch], v[i:i + ch], w[i:i + ch], obs.cell_rad, True)
-                          for i in range(0, u.shape[0], ch)]).reshape(obs.nrow, obs.nchan)
+    vis = _point_source_vis(obs, 303)
     ctx = rix.create(0)
-    rec = pipeline.Reconstruction(ctx, n, obs.cell_rad, obs.n_wplanes, obs.freq, obs.nrow, 2, rix.FP32)
+    rec = pipeline.Reconstruction(ctx, n, obs.cell_rad, obs.n_wplanes, obs.freq, obs.nrow, 2,
+                                  rix.FP32 if prec == 0 else rix.FP64)
     try:
         rec.set_data(obs.uvw, vis, obs.weight)
         if kind == "msclean":
-            m = pipeline.Method("msclean", (0.0, 4.0, 16.0, 32.0), 0.1, 200, 1e-4)
+            m = pipeline.Method("msclean", scales, 0.1, 200, 1e-4)
         else:
             m = pipeline.Method("fista", lam_rel=1e-3, iters=20, levels=4)
+        if prec == 1 and kind == "fista":
+            mask = torch.zeros(obs.nvis, dtype=torch.uint8, device="cuda")
+            rix.set_uv_partition(rec.job, rec.uvw, rec.weight, None, 1.0, mask)
+            sel = ((mask.cpu().numpy() >> 1) & 1) == 1
+            psf = torch.empty((2 * n, 2 * n), dtype=torch.float64, device="cuda")
+            rix.psf(rec.job, 1, psf)
+            torch.cuda.synchronize()
+            rng = np.random.default_rng(17)
+            rows = np.concatenate([n + rng.integers(-32, 32, 32), rng.integers(0, 2 * n, 32)])
+            cols = np.concatenate([n + rng.integers(-32, 32, 32), rng.choice([n - 1, n, 0], 32)])
+            u, v, w = dft.uvw_lambda(obs.uvw, obs.freq)
+            wt = obs.weight.reshape(-1).astype(np.float64)[sel]
+            want = dft.adjoint_at(wt.astype(np.complex128), u[sel], v[sel], w[sel], 2 * n, obs.cell_rad, True,
+                                  rows, cols) / wt.sum()
+            got = psf[torch.as_tensor(rows, device="cuda"), torch.as_tensor(cols, device="cuda")].cpu().numpy()
+            # near the centre the kernel's accuracy; over the 2N field the
+            # w-planes' spacing (set for the N field: dw |n - 1| reaches 0.36
+            # at the PSF's corners, 0.09 at the image's) bounds it, as it
+            # would on the PSF's own grid
+            assert rel_l2(got[:32], want[:32]) < 1e-6
+            assert rel_l2(got, want) < 1e-4
         peaks = []
         for c in range(2):
-            res = [torch.empty((n, n), dtype=torch.float32, device="cuda") for _ in range(2)]
+            res = [torch.empty((n, n), dtype=rec.rdtype, device="cuda") for _ in range(2)]
             for p in range(2):
                 rec.major(p, res[p])
             torch.cuda.synchronize()
@@ -180,6 +218,7 @@ def test_minor_cycles_at_size(kind):
         img = rec.combine()
         torch.cuda.synchronize()
         assert bool(torch.isfinite(img).all())
+        assert float(img.abs().max()) > 0.0
         for p in range(2):
             assert peaks[1][p] < peaks[0][p]
     finally:
