@@ -20,6 +20,8 @@ constexpr int kFftThreads = 256;
 template <typename R> struct Vpt;
 template <> struct Vpt<float> { static constexpr int kSmall = 16, kLarge = 32; };
 template <> struct Vpt<double> { static constexpr int kSmall = 8, kLarge = 16; };
+// Ping-pong CTAs hold kFftThreads * kPingPongVals complex values per buffer.
+template <typename R> constexpr int kPingPongVals = std::is_same<R, float>::value ? 16 : 8;
 
 __host__ __device__ constexpr int padi(int i) { return i + (i >> 4); }
 __host__ __device__ constexpr int padded_len(int L) { return L + (L >> 4); }
@@ -363,6 +365,13 @@ __device__ __forceinline__ void inv_rows_block(KArgs a, const cplx<R>* __restric
   const int pb = a.pg > 0 ? by * a.pg : 0;
   const int pe = a.pg > 0 ? pb + a.pg : a.nplanes;
   if (a.pg > 0) img += (int64_t)by * M * M;
+  // with several planes and at most KO outputs per thread, the sum over the
+  // planes is kept in registers and the image written once
+  constexpr int KO = VPT == 0 ? kPingPongVals<R> : 1;
+  const bool regacc = VPT == 0 && pe - pb > 1 && nout <= kFftThreads * KO;
+  R acc[KO];
+#pragma unroll
+  for (int k = 0; k < KO; ++k) acc[k] = R(0);
   for (int p = pb; p < pe; ++p) {
     const C* Tp = T + (int64_t)p * a.S * M;
   #pragma unroll 4
@@ -394,12 +403,11 @@ __device__ __forceinline__ void inv_rows_block(KArgs a, const cplx<R>* __restric
     const C* res = fft_any<R, VPT, +1>(s, s2, a.B, a.logL, a.stride, tw);
     const double wp = a.w0 + p * a.dw;
     const C* scr = a.mode == kFacPhase && a.screen ? static_cast<const C*>(a.screen) + (int64_t)p * M * M : nullptr;
-    // the output image accumulates the planes; the first plane initialises it
-    for (int idx = threadIdx.x; idx < nout; idx += kFftThreads) {
+    // plane p's contribution to output value idx of the CTA's rows
+    auto plane_value = [&](int idx, int64_t& pix) -> R {
       const int r = idx / M, aa = idx - r * M;
       const int b = b0 + r;
-      if (b >= M) continue;
-      const int64_t pix = (int64_t)b * M + aa;
+      pix = (int64_t)b * M + aa;
       const C z = res[r * a.stride + padi((aa - half) & (L - 1))];
       R v;
       if (scr) {
@@ -415,9 +423,39 @@ __device__ __forceinline__ void inv_rows_block(KArgs a, const cplx<R>* __restric
       v *= rscale;
       if ((aa + b) & 1) v = -v;
       if (a.mode != kFacNone && !scr) v *= corr[pix];
-      img[pix] = (p == pb && !accumulate) ? v : img[pix] + v;
+      return v;
+    };
+    if (regacc) {
+      // the planes' sum stays in registers (thread-owned outputs)
+#pragma unroll
+      for (int k = 0; k < KO; ++k) {
+        const int idx = threadIdx.x + k * kFftThreads;
+        if (idx < nout && b0 + idx / M < M) {
+          int64_t pix;
+          acc[k] += plane_value(idx, pix);
+        }
+      }
+    } else {
+      // the output image accumulates the planes; the first plane initialises it
+      for (int idx = threadIdx.x; idx < nout; idx += kFftThreads) {
+        if (b0 + idx / M >= M) continue;
+        int64_t pix;
+        const R v = plane_value(idx, pix);
+        img[pix] = (p == pb && !accumulate) ? v : img[pix] + v;
+      }
     }
     __syncthreads();
+  }
+  if (regacc) {
+#pragma unroll
+    for (int k = 0; k < KO; ++k) {
+      const int idx = threadIdx.x + k * kFftThreads;
+      const int r = idx / M, b = b0 + r;
+      if (idx < nout && b < M) {
+        const int64_t pix = (int64_t)b * M + (idx - r * M);
+        img[pix] = accumulate ? img[pix] + acc[k] : acc[k];
+      }
+    }
   }
   __syncthreads();
 }
@@ -562,8 +600,6 @@ KArgs make_args(const XformGeom& g, int B) {
   return a;
 }
 
-// Ping-pong CTAs hold kFftThreads * kPingPongVals complex values per buffer.
-template <typename R> constexpr int kPingPongVals = std::is_same<R, float>::value ? 16 : 8;
 
 // Ping-pong (VPT = 0) whenever two buffers of one row fit; otherwise in place
 // with the large values-per-thread setting.

@@ -35,8 +35,10 @@ __global__ void __launch_bounds__(kFftThreads, (VPT == 0 && sizeof(R) == 4) ? 4 
   fwd_rows_block<R, VPT>(a, img, T, tw, s, s2, blockIdx.x, blockIdx.y);
 }
 
+// three CTAs per SM: the shared memory of two 2048-point rows allows no more,
+// and the register accumulators of the plane sum need the room
 template <typename R, int VPT>
-__global__ void __launch_bounds__(kFftThreads, (VPT == 0 && sizeof(R) == 4) ? 4 : 1) k_inv_rows(KArgs a, const cplx<R>* __restrict__ T,
+__global__ void __launch_bounds__(kFftThreads, (VPT == 0 && sizeof(R) == 4) ? 3 : 1) k_inv_rows(KArgs a, const cplx<R>* __restrict__ T,
                                                           R* __restrict__ img, double scale, int accumulate,
                                                           const cplx<R>* __restrict__ tw) {
   using C = cplx<R>;

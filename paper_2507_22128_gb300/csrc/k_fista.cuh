@@ -856,8 +856,9 @@ int launch_fista_loop(const Ctx* ctx, const FistaLoop<R>* f, int nb, cudaStream_
       const int64_t nctl = 1 + (int64_t)nb * (2 + (int64_t)f[0].iters * nph);
       unsigned int* ctl = nullptr;
       R* mom = nullptr;
-      RIX_CUDA(cudaMallocAsync((void**)&ctl, (size_t)nctl * sizeof(unsigned int), st));
-      if (cudaMallocAsync((void**)&mom, (size_t)std::max(f[0].iters, 1) * sizeof(R), st) != cudaSuccess) {
+      RIX_CUDA(::rix::malloc_async(&ctl, (size_t)nctl * sizeof(unsigned int), st));
+      if (::rix::malloc_async(&mom, (size_t)std::max(f[0].iters, 1) * sizeof(R), st) != cudaSuccess) {
+        cudaGetLastError();
         cudaFreeAsync(ctl, st);
         return set_error(RIX_ENOMEM, "FISTA schedule tables");
       }

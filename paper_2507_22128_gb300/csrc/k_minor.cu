@@ -95,6 +95,13 @@ __global__ void k_gamma(GammaArgs a, R* __restrict__ gam) {
   }
 }
 
+// rho += phi - ibar
+template <typename R>
+__global__ void k_rho_sub(R* __restrict__ rho, const R* __restrict__ phi, const R* __restrict__ ibar, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    rho[i] += phi[i] - ibar[i];
+}
+
 template <typename R>
 __global__ void k_axpy(R* __restrict__ y, const R* __restrict__ x, R alpha, int64_t n) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
@@ -541,6 +548,16 @@ int publish(Job* job, int p, int cycle, cudaStream_t st) {
     RIX_LAUNCH_CHECK();
   } else {
     RIX_TRY(convolve<R>(job, pt, ibar, kOpMulReal, gam + p * tot, nullptr, pt.outbox[cycle & 1].as<R>(), inv, 0, st));
+    if (job->n_part == 2) {
+      // Gamma_q = 1 - Gamma_p and crop F^-1 F pad = identity, so
+      // Gamma_q i_bar = i_bar - Phi_p: rho_{q->p} += Phi_p - i_bar
+      const int q = 1 - p;
+      ::rix::note_launch();
+      k_rho_sub<R><<<blocks_for(job->ctx, npix), 256, 0, st>>>(pt.rho[q].as<R>(), pt.outbox[cycle & 1].as<R>(), ibar,
+                                                               npix);
+      RIX_LAUNCH_CHECK();
+      return RIX_OK;
+    }
   }
   for (int q = 0; q < job->n_part; ++q)
     if (q != p) RIX_TRY(convolve<R>(job, pt, ibar, kOpMulReal, gam + q * tot, nullptr, pt.rho[q].as<R>(), -inv, 1, st));
