@@ -356,39 +356,64 @@ struct CleanArgs {
 // finds the next peak; one bounded grid barrier per iteration separates the
 // sweep from the global reduction (double-buffered candidate slots).  A
 // barrier that gives up (RIX_ETIMEOUT in the status word) ends every CTA.
-template <typename R>
+// NS = the number of scales, fixed at compile time so that a sweep issues
+// the loads of every scale of a pixel together.
+template <typename R, int NS>
 __global__ void __launch_bounds__(256) k_msclean(CleanArgs a) {
   GridBarrier bar{a.barrier, a.status, 0u};
   __shared__ Cand<R> sh[32];
   const int n = a.n, n2 = 2 * a.n;
   const int64_t npix = (int64_t)n * n;
-  R* Rs = static_cast<R*>(a.R);
-  const R* P = static_cast<const R*>(a.P);
+  R* __restrict__ Rs = static_cast<R*>(a.R);
+  const R* __restrict__ P = static_cast<const R*>(a.P);
   Cand<R>* slots = static_cast<Cand<R>*>(a.slots);
-  R peak[kMaxScales], bias[kMaxScales];
-  for (int s = 0; s < a.ns; ++s) {
-    peak[s] = P[((int64_t)(s * a.ns + s) * n2 + n) * n2 + n];
-    bias[s] = (R)a.bias[s];
+  __shared__ R peak[kMaxScales], scl[kMaxScales];
+  if (threadIdx.x < NS) {
+    const int s = threadIdx.x;
+    peak[s] = P[((int64_t)(s * NS + s) * n2 + n) * n2 + n];
+    // the candidate value b_s |R_s| / P_ss(0) as |R_s| times b_s / P_ss(0)
+    // (a scale whose peak is 0 never wins: 0; the loop stops if it is chosen)
+    scl[s] = peak[s] != R(0) ? (R)a.bias[s] / peak[s] : R(0);
   }
+  __syncthreads();
   const int64_t gtid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t gstride = (int64_t)gridDim.x * blockDim.x;
+  const int logn = 31 - __clz(n);   // n is a power of two
+  const int64_t n2sq = (int64_t)n2 * n2;
 
   // sweep with the subtraction of component (sc, py, px, amp) (amp = 0: none)
   auto sweep = [&](int sc, int py, int px, R amp) {
     Cand<R> c{R(-1), R(0), 0x7fffffff, 0x7fffffff, R(0)};
+    const R* __restrict__ psc = P + (int64_t)sc * n2sq;   // P_{s, sc} = psc + s NS (2n)^2
     for (int64_t i = gtid; i < npix; i += gstride) {
-      const int y = (int)(i / n), x = (int)(i - (int64_t)y * n);
-      for (int s = 0; s < a.ns; ++s) {
-        R v = Rs[s * npix + i];
-        if (amp != R(0)) {
-          v -= amp * P[((int64_t)(s * a.ns + sc) * n2 + (n + y - py)) * n2 + (n + x - px)];
-          Rs[s * npix + i] = v;
+      const int y = (int)(i >> logn), x = (int)(i & (n - 1));
+      // P_{s,sc}(y - py, x - px) on the centred 2n grid
+      const int64_t pp = (int64_t)(n + y - py) * n2 + (n + x - px);
+      R v[NS];
+#pragma unroll
+      for (int s = 0; s < NS; ++s) v[s] = Rs[s * npix + i];
+      if (amp != R(0)) {
+        R q[NS];
+#pragma unroll
+        for (int s = 0; s < NS; ++s) q[s] = psc[(int64_t)s * NS * n2sq + pp];
+#pragma unroll
+        for (int s = 0; s < NS; ++s) {
+          v[s] -= amp * q[s];
+          Rs[s * npix + i] = v[s];
         }
-        if (s == 0) c.r0max = fmax(c.r0max, fabs(v));
+      }
+#pragma unroll
+      for (int s = 0; s < NS; ++s) {
+        const R av = fabs(v[s]);
+        if (s == 0) c.r0max = fmax(c.r0max, av);
         if ((a.allowed >> s) & 1) {
-          const R val = bias[s] * fabs(v) / peak[s];
-          Cand<R> t{val, v, s, (int)i, R(0)};
-          if (better(t, c)) { c.val = t.val; c.rval = t.rval; c.s = t.s; c.pix = t.pix; }
+          const R val = av * scl[s];
+          if (val > c.val || (val == c.val && (s < c.s || (s == c.s && (int)i < c.pix)))) {
+            c.val = val;
+            c.rval = v[s];
+            c.s = s;
+            c.pix = (int)i;
+          }
         }
       }
     }
@@ -699,10 +724,16 @@ int op_msclean(Job* job, int p, const rix_msclean_params* prm, R* delta_out, cud
     ca.st_rad[s] = rad;
     stn_all.insert(stn_all.end(), stn.begin(), stn.end());
   }
+  // the composite PSF of cycles >= 2 is the same: reuse the scale spectra
+  // and cross PSFs of an earlier such cycle with the same scales
+  const std::vector<float> scales(prm->scales, prm->scales + ns);
+  const bool reuse = cycle >= 3 && pt.ms_p_cycle >= 2 && pt.ms_p_scales == scales &&
+                     pt.ms_P.bytes >= (size_t)ns * ns * tot * sizeof(R);
+  if (!reuse) pt.ms_p_cycle = 0;
   RIX_TRY(ensure<R>(job, pt.ms_B, (size_t)ns * tot * sizeof(cplx<R>) + stn_all.size() * sizeof(R) + 64));
   cplx<R>* bspec = pt.ms_B.as<cplx<R>>();
   R* stn_dev = reinterpret_cast<R*>(bspec + ns * tot);
-  {
+  if (!reuse) {
     std::vector<R> tmp(stn_all.begin(), stn_all.end());
     RIX_CUDA(cudaMemcpyAsync(stn_dev, tmp.data(), tmp.size() * sizeof(R), cudaMemcpyHostToDevice, st));
     RIX_CUDA(cudaStreamSynchronize(st));   // tmp is a host temporary
@@ -718,7 +749,7 @@ int op_msclean(Job* job, int p, const rix_msclean_params* prm, R* delta_out, cud
   int rc = RIX_OK;
   XformGeom g2{};
   g2.M = 2 * n; g2.L = 2 * n; g2.logL = ilog2(g2.L); g2.lo = 0; g2.S = 2 * n; g2.nplanes = 1; g2.mode = kFacNone;
-  for (int s = 0; s < ns && rc == RIX_OK; ++s) {
+  for (int s = 0; s < ns && rc == RIX_OK && !reuse; ++s) {
     if (cudaMemsetAsync(img2, 0, tot * sizeof(R), st) != cudaSuccess) { rc = set_error(RIX_ECUDA, "memset"); break; }
     ::rix::note_launch(); k_place_stencil<R><<<4, 256, 0, st>>>(stn_dev + ca.st_off[s], ca.st_rad[s], img2, 2 * n);
     if ((rc = fwd_rows<R>(ctx, g2, img2, t2, st)) != RIX_OK) break;
@@ -729,15 +760,25 @@ int op_msclean(Job* job, int p, const rix_msclean_params* prm, R* delta_out, cud
   if (rc == RIX_OK) rc = ensure<R>(job, pt.ms_P, (size_t)ns * ns * tot * sizeof(R));
   for (int s = 0; s < ns && rc == RIX_OK; ++s)
     rc = spec_to_img<R>(job, pt, dspec, kOpMulCplx, bspec + s * tot, pt.ms_R.as<R>() + s * npix, inv, 0, st);
-  for (int s = 0; s < ns && rc == RIX_OK; ++s)
-    for (int t = 0; t < ns && rc == RIX_OK; ++t) {
+  // P_ts = P_st (B_s B_t = B_t B_s): the upper triangle is transformed, the
+  // lower one copied
+  for (int s = 0; s < ns && rc == RIX_OK && !reuse; ++s)
+    for (int t = s; t < ns && rc == RIX_OK; ++t) {
+      R* pst = pt.ms_P.as<R>() + (int64_t)(s * ns + t) * tot;
       ::rix::note_launch(); k_cmul3<R><<<blocks_for(ctx, tot), 256, 0, st>>>(bspec + s * tot, bspec + t * tot, pspec, dspec, tot);
       if ((rc = inv_cols<R>(ctx, g2, dspec, kOpNone, nullptr, nullptr, t2, st)) != RIX_OK) break;
-      rc = inv_rows<R>(ctx, g2, t2, pt.ms_P.as<R>() + (int64_t)(s * ns + t) * tot, inv, 0, st);
+      if ((rc = inv_rows<R>(ctx, g2, t2, pst, inv, 0, st)) != RIX_OK) break;
+      if (t != s && cudaMemcpyAsync(pt.ms_P.as<R>() + (int64_t)(t * ns + s) * tot, pst, tot * sizeof(R),
+                                    cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+        rc = set_error(RIX_ECUDA, "cross PSF copy");
     }
   cudaFreeAsync(img2, st);
   cudaFreeAsync(t2, st);
   if (rc != RIX_OK) return rc;
+  if (!reuse && cycle >= 2) {
+    pt.ms_p_cycle = cycle;
+    pt.ms_p_scales = scales;
+  }
 
   // scales present at cycle 1 (psi^1 of Eq. 7): partition 0 keeps all; p > 0
   // keeps s = 0 and the scales with N / (2 s) >= ell_p - delta
@@ -754,8 +795,22 @@ int op_msclean(Job* job, int p, const rix_msclean_params* prm, R* delta_out, cud
   // state: delta image, components, slots
   const int cap = std::max(prm->niter, 1);
   int per_sm = 0;
-  RIX_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_msclean<R>, 256, 0));
-  const int nblk = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)ctx->num_sms * std::max(per_sm, 1),
+  void (*kern)(CleanArgs) = nullptr;
+  switch (ns) {
+    case 1: kern = k_msclean<R, 1>; break;
+    case 2: kern = k_msclean<R, 2>; break;
+    case 3: kern = k_msclean<R, 3>; break;
+    case 4: kern = k_msclean<R, 4>; break;
+    case 5: kern = k_msclean<R, 5>; break;
+    case 6: kern = k_msclean<R, 6>; break;
+    case 7: kern = k_msclean<R, 7>; break;
+    case 8: kern = k_msclean<R, 8>; break;
+    default: return set_error(RIX_EINVAL, "%d scales", ns);
+  }
+  RIX_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, 0));
+  // at most four CTAs per SM: enough loads in flight for the sweeps, and
+  // every CTA reads every CTA's candidate at each iteration
+  const int nblk = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)ctx->num_sms * std::min(std::max(per_sm, 1), 4),
                                                                  ceil_div(npix, 256)));
   const size_t comp_bytes = (size_t)cap * (2 * sizeof(int) + sizeof(double)) + 16;
   RIX_TRY(ensure<R>(job, pt.ms_comp, comp_bytes));
@@ -786,7 +841,7 @@ int op_msclean(Job* job, int p, const rix_msclean_params* prm, R* delta_out, cud
   void* args[] = {&ca};
   ::rix::note_launch();
   timing_mark(kTimeMinorLoop, st, true);
-  RIX_CUDA(cudaLaunchCooperativeKernel((const void*)k_msclean<R>, dim3(nblk), dim3(256), args, 0, st));
+  RIX_CUDA(cudaLaunchCooperativeKernel((const void*)kern, dim3(nblk), dim3(256), args, 0, st));
   timing_mark(kTimeMinorLoop, st, false);
   RIX_TRY(publish<R>(job, p, cycle, st));
   if (delta_out) RIX_CUDA(cudaMemcpyAsync(delta_out, pt.delta.p, npix * sizeof(R), cudaMemcpyDeviceToDevice, st));

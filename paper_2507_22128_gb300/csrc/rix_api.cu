@@ -190,6 +190,7 @@ static void reset_partitions(Job* job) {
     pt.psf_ready = false;
     pt.lambda_set = false;
     pt.ms_ncomp_cap = 0;
+    pt.ms_p_cycle = 0;
   }
 }
 
@@ -683,7 +684,10 @@ int rix_job_set_psf_method(rix_job_t job, int32_t method) {
     return set_error(RIX_EINVAL, "PSF method must be RIX_PSF_AUTO, RIX_PSF_DOUBLE_GRID or RIX_PSF_TILES");
   Job& J = job->j;
   J.psf_method = method;
-  for (int p = 0; p < kMaxPart; ++p) J.part[p].psf_ready = false;
+  for (int p = 0; p < kMaxPart; ++p) {
+    J.part[p].psf_ready = false;
+    J.part[p].ms_p_cycle = 0;
+  }
   return RIX_OK;
 }
 

@@ -260,6 +260,11 @@ struct Part {
   DevBuf ms_R, ms_P, ms_B, ms_comp, ms_state;   // ms-CLEAN
   DevBuf fi_alpha, fi_alpha_prev, fi_y, fi_mx, fi_c, fi_x, fi_d;   // FISTA
   int ms_ncomp_cap = 0;
+  // the cycle whose composite PSF ms_P holds (0: none) and its scales: from
+  // cycle 2 on the composite PSF of Eq. 7 no longer changes, so later cycles
+  // with the same scales reuse ms_P and the scale spectra in ms_B
+  int ms_p_cycle = 0;
+  std::vector<float> ms_p_scales;
   // recorded after the minor cycle of each cycle parity (cycle n -> [n % 2])
   cudaEvent_t ev_minor[2] = {nullptr, nullptr};
   cudaEvent_t ev_psf = nullptr;             // recorded after the PSF is computed
