@@ -51,6 +51,10 @@ def parse():
                     help="run each partition's FISTA minor cycle as its own loop launch instead of one batched launch")
     ap.add_argument("--dictionary", default="db4", choices=["db4", "db1-8"],
                     help="FISTA dictionary: Db4 alone, or the concatenation of db1..db8")
+    ap.add_argument("--method", default="fista", choices=["fista", "msclean"],
+                    help="minor cycle of the medium workload: FISTA (the benchmark) or multi-scale CLEAN")
+    ap.add_argument("--scales", default="0,4,16", help="ms-CLEAN scale radii in pixels")
+    ap.add_argument("--clean-iters", type=int, default=2000, help="ms-CLEAN iterations per minor cycle")
     ap.add_argument("--schedule", default=None,
                     help="a,b: lambda_n = a ||residual_n||_2 b^n instead of 1e-3 max |residual_1|")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -273,12 +277,17 @@ def cpu_baseline(a, steps=1, warmup=0):
 
 
 def config_dict(a):
+    if a.method == "msclean":
+        minor = f"ms-CLEAN scales {{{a.scales}}} gain 0.1 {a.clean_iters} it"
+    else:
+        minor = (f"FISTA {'Db4' if a.dictionary == 'db4' else 'db1..db8'} "
+                 f"{a.iters} it{'' if a.schedule is None else ', lambda schedule ' + a.schedule}")
     return {"workload": f"medium: {a.n}x{a.n} 1as, 64 ant log-spiral x {a.n_times} times x 4 ch "
-                        f"(1.3-1.5 GHz), 16 w-planes, 2 uv partitions, FISTA {'Db4' if a.dictionary == 'db4' else 'db1..db8'} "
-                        f"{a.iters} it{'' if a.schedule is None else ', lambda schedule ' + a.schedule}, "
+                        f"(1.3-1.5 GHz), 16 w-planes, 2 uv partitions, {minor}, "
                         f"{a.cycles} major cycles",
-            "n": a.n, "n_wplanes": 16, "n_part": 2, "major_cycles": a.cycles, "fista_iters": a.iters,
-            "fista_dictionary": a.dictionary, "fista_batched": not a.no_batch_minor,
+            "n": a.n, "n_wplanes": 16, "n_part": 2, "major_cycles": a.cycles, "minor_cycle": a.method,
+            **({"clean_scales": a.scales, "clean_iters": a.clean_iters} if a.method == "msclean" else
+               {"fista_iters": a.iters, "fista_dictionary": a.dictionary, "fista_batched": not a.no_batch_minor}),
             "l2": "flushed between steps (512 MiB write)", "precision": "fp64" if a.fp64 else "fp32"}
 
 
@@ -315,7 +324,11 @@ def main():
     ctx = rix.create(local)
     rec = pipeline.Reconstruction(ctx, obs.n, obs.cell_rad, obs.n_wplanes, obs.freq, obs.nrow, 2, prec)
     sched = None if a.schedule is None else tuple(float(v) for v in a.schedule.split(","))
-    meth = pipeline.Method("fista", lam_rel=1e-3, iters=a.iters, levels=4, dictionary=a.dictionary, schedule=sched)
+    if a.method == "msclean":
+        meth = pipeline.Method("msclean", tuple(float(v) for v in a.scales.split(",")), 0.1, a.clean_iters, 1e-4)
+    else:
+        meth = pipeline.Method("fista", lam_rel=1e-3, iters=a.iters, levels=4, dictionary=a.dictionary,
+                               schedule=sched)
     stream = torch.cuda.current_stream(dev)
     flush = torch.empty(128 * 1024 * 1024, dtype=torch.float32, device=dev)
     out = torch.empty((obs.n, obs.n), dtype=rdt, device=dev)
