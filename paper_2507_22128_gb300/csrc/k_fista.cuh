@@ -34,6 +34,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cmath>
 
 #include "fft_ct.cuh"
 #include "grid_sync.cuh"
@@ -422,6 +423,9 @@ __device__ __noinline__ void ana_member(const R* src, int n, R* dst, int N, int 
   dwt_tile<R, kTB, true>(src, N, n, nullptr, dst, N, last, sm, bx, by, dsm, RefTaps<R, 2 * (MM + 1)>{taps});
 }
 
+// iterations whose FISTA momentum travels in the launch arguments
+constexpr int kMomTab = 256;
+
 template <typename R>
 struct FistaArgs {
   FistaLoop<R> f[kMaxPart];   // the batch's loops, [0, nb)
@@ -433,7 +437,8 @@ struct FistaArgs {
   // iteration
   unsigned int* ticket;
   unsigned int* done;
-  const R* mom;
+  const R* mom;           // device table, or null: mom_tab holds the iterations
+  R mom_tab[kMomTab];
 };
 
 // units of one wavelet level of one loop: tiles of side `tile` over an n x n
@@ -793,7 +798,7 @@ __global__ void __launch_bounds__(kFftThreads, sizeof(R) == 4 && LOGL <= 12 ? 2 
     } else if (kind == kFlowRowsInv) {
       rows_inv_unit<R, LOGL, true>(f.tb, f.g, a.gscale, f.d, f.tw, s, s2, stage, u);
     } else {
-      const StepArgs<R> sa{f.alpha, f.y, s_inv_l[b], s_thr[b], s_inv_l[b] != R(0), a.mom[it]};
+      const StepArgs<R> sa{f.alpha, f.y, s_inv_l[b], s_thr[b], s_inv_l[b] != R(0), a.mom ? a.mom[it] : a.mom_tab[it]};
       analysis_unit<R, RIX_DICT_DB4, N>(f, lev, u, sa, smem_raw, a.taps);
     }
     flow_done(done_b + stg);
@@ -810,6 +815,25 @@ __global__ void k_mom_table(int iters, R* mom) {
   for (int it = 0; it < iters; ++it) {
     const double tn = __dmul_rn(0.5, __dadd_rn(1.0, __dsqrt_rn(__dadd_rn(1.0, __dmul_rn(__dmul_rn(4.0, t), t)))));
     mom[it] = (R)__ddiv_rn(__dadd_rn(t, -1.0), tn);
+    t = tn;
+  }
+}
+
+// the same sequence on the host, each operation rounded on its own
+// (volatile temporaries keep the compiler from contracting them)
+template <typename R>
+void mom_host(int iters, R* mom) {
+  double t = 1.0;
+  for (int it = 0; it < iters; ++it) {
+    volatile double a = 4.0 * t;
+    volatile double b = a * t;
+    volatile double c = 1.0 + b;
+    volatile double q = std::sqrt((double)c);
+    volatile double e = 1.0 + q;
+    volatile double tn = 0.5 * e;
+    volatile double num = t - 1.0;
+    volatile double m = num / tn;
+    mom[it] = (R)m;
     t = tn;
   }
 }
@@ -866,11 +890,16 @@ int launch_fista_loop(const Ctx* ctx, const FistaLoop<R>* f, int nb, cudaStream_
       if (cudaMemsetAsync(ctl, 0, (size_t)nctl * sizeof(unsigned int), st) != cudaSuccess) {
         rc = set_error(RIX_ECUDA, "FISTA schedule reset");
       } else {
-        ::rix::note_launch();
-        k_mom_table<R><<<1, 1, 0, st>>>(f[0].iters, mom);
         args.ticket = ctl;
         args.done = ctl + 1;
-        args.mom = mom;
+        if (f[0].iters <= kMomTab) {
+          mom_host<R>(f[0].iters, args.mom_tab);
+          args.mom = nullptr;
+        } else {
+          ::rix::note_launch();
+          k_mom_table<R><<<1, 1, 0, st>>>(f[0].iters, mom);
+          args.mom = mom;
+        }
         void* params[] = {&args};
         ::rix::note_launch();
         timing_mark(kTimeMinorLoop, st, true);

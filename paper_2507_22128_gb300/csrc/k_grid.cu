@@ -137,6 +137,58 @@ __global__ void k_corrections(CorrArgs a, R* __restrict__ corr, double* __restri
   }
 }
 
+// dw (n - 1) -> n Phi(dw (n - 1)) and n - 1 at squared radius r2 (a Clenshaw
+// sum of the Chebyshev fit of Phi)
+__device__ __forceinline__ double wfactor(const CorrArgs& a, double r2, double* nm1_out) {
+  const double n = __dsqrt_rn(1.0 - r2);
+  const double d = -r2 / (1.0 + n);
+  double phw;
+  if (a.hi > a.lo) {
+    const double x = (2.0 * a.dw * d - (a.lo + a.hi)) / (a.hi - a.lo);
+    double b1 = 0.0, b2 = 0.0;
+    for (int j = kCheb - 1; j >= 1; --j) {
+      const double t = 2.0 * x * b1 - b2 + a.cheb[j];
+      b2 = b1;
+      b1 = t;
+    }
+    phw = x * b1 - b2 + a.cheb[0];
+  } else {
+    phw = a.cheb[0];
+  }
+  *nm1_out = d;
+  return n * phw;
+}
+
+// k_corrections for a table centred on the phase centre (ox = oy = 0): the
+// w-factor depends on l^2 + m^2 only, so one thread per pixel of the quadrant
+// [0, M/2]^2 evaluates it once and writes the up to four pixels (b, c),
+// (b, M - c), (M - b, c), (M - b, M - c) that share it
+template <typename R>
+__global__ void k_corrections_sym(CorrArgs a, R* __restrict__ corr, double* __restrict__ nm1) {
+  const int h = a.M / 2;
+  const int64_t q = (int64_t)(h + 1) * (h + 1);
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < q; i += (int64_t)gridDim.x * blockDim.x) {
+    const int b = (int)(i / (h + 1)), c = (int)(i - (int64_t)b * (h + 1));
+    double wf = 1.0, d = 0.0;
+    if (a.wstack) {
+      const double l = (double)(c - h) * a.cell, m = (double)(b - h) * a.cell;
+      wf = wfactor(a, __dadd_rn(__dmul_rn(l, l), __dmul_rn(m, m)), &d);
+    }
+    const int bs[2] = {b, 2 * h - b}, cs[2] = {c, 2 * h - c};
+    for (int u = 0; u < 2; ++u) {
+      const int bb = bs[u];
+      if (bb >= a.M || (u == 1 && bb == b)) continue;
+      for (int w = 0; w < 2; ++w) {
+        const int cc = cs[w];
+        if (cc >= a.M || (w == 1 && cc == c)) continue;
+        const int64_t pix = (int64_t)bb * a.M + cc;
+        corr[pix] = (R)(1.0 / (a.p1[cc] * a.p1[bb] * wf));
+        if (a.wstack) nm1[pix] = d;
+      }
+    }
+  }
+}
+
 // Fills the M x M tables corr and nm1 (w-stacked jobs) for grid side ng,
 // centred ox, oy cells from the phase centre; the w-correction's Chebyshev
 // fit covers a field of half side `half_px` cells about the phase centre.
@@ -172,7 +224,9 @@ int fill_correction(Job* job, int M, int ng, int ox, int oy, int half_px, R* cor
   ca.p1 = p1d;
   const int64_t tot = (int64_t)M * M;
   const int blocks = (int)std::min<int64_t>(ceil_div(tot, 256), (int64_t)job->ctx->num_sms * 16);
-  ::rix::note_launch(); k_corrections<R><<<blocks, 256, 0, st>>>(ca, corr, ws ? nm1 : nullptr);
+  ::rix::note_launch();
+  if (ox == 0 && oy == 0) k_corrections_sym<R><<<blocks, 256, 0, st>>>(ca, corr, ws ? nm1 : nullptr);
+  else k_corrections<R><<<blocks, 256, 0, st>>>(ca, corr, ws ? nm1 : nullptr);
   cudaFreeAsync(p1d, st);
   RIX_LAUNCH_CHECK();
   RIX_CUDA(cudaStreamSynchronize(st));   // p1 is a host temporary
