@@ -89,3 +89,34 @@ def test_whole_job_value_is_the_aggregate_over_ranks(bench):
     # scales with the ranks over the slowest rank's time
     assert bench.whole_job_value(82_466_880, 1, 140.0) == pytest.approx(82_466_880 / 0.140 / 1e6)
     assert bench.whole_job_value(1e6, 4, 10.0) == pytest.approx(4 * 1e6 / 0.010 / 1e6)
+
+
+def test_serving_requests_follow_the_mix(bench):
+    """The serving workload's requests: kinds drawn by the pools' shares
+    (50/30/15/5 %), ms-CLEAN or FISTA with probability 1/2, each kind's cycle
+    count and scale set, arrival times kept; the FP64 comparison subset
+    leaves out the large recipe and keeps the order of the stream."""
+    import numpy as np
+    if not os.path.exists(os.path.join(ROOT, "paper_2507_22128_gb300", "librix.so")):
+        from paper_2507_22128_gb300 import build
+        build.build()
+    from paper_2507_22128_gb300 import rix, serve
+    obs = [types.SimpleNamespace(name=f"o{i}") for i in range(5)]
+    pools = {"small": (0.50, obs[:2], 5, (0.0, 3.0, 9.0), 3), "medium": (0.30, obs[2:3], 10, (0.0, 4.0, 16.0), 4),
+             "chunk": (0.15, obs[3:4], 5, (0.0, 4.0, 16.0), 4), "large": (0.05, obs[4:], 8, (0.0, 4.0, 16.0, 32.0), 4)}
+    arr = serve.poisson_arrivals(np.random.default_rng(4), 4000, 20.0)
+    reqs = bench.serve_requests(pools, arr, np.random.default_rng(40), rix.FP32)
+    assert len(reqs) == 4000 and [q.arrival for q in reqs] == list(arr)
+    for kind, (share, olist, n_major, scales, levels) in pools.items():
+        mine = [q for q in reqs if q.kind.startswith(kind + " ")]
+        assert abs(len(mine) / 4000 - share) < 0.02
+        assert all(q.n_major == n_major and q.obs in olist for q in mine)
+        assert all(tuple(q.method.scales) == scales for q in mine if q.method.kind == "msclean")
+        assert all(q.method.levels == levels for q in mine if q.method.kind == "fista")
+    assert abs(np.mean([q.method.kind == "msclean" for q in reqs]) - 0.5) < 0.03
+    sub = [q for q in bench.serve_requests(pools, arr, np.random.default_rng(40), rix.FP64)
+           if not q.kind.startswith("large")][:100]
+    assert all(q.precision == rix.FP64 for q in sub)
+    assert [q.rid for q in sub] == sorted(q.rid for q in sub)
+    same = {q.rid: q.kind for q in reqs}
+    assert all(same[q.rid] == q.kind for q in sub)
