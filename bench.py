@@ -985,8 +985,8 @@ def cufft_comparison(n, nplanes, window, flush, reps=5):
 # launches of the medium job's first major cycle (low, high partition), with
 # the sha1 of the sources the kernel was built from (k_tiles_fp.cu,
 # rix_internal.cuh): a changed source voids them
-TILES_TRAFFIC = {"src_sha1": ("93f45944f9c96b322e3a999ed695aac565257a3f", "45f1cbffe5f747db8cef33c42215f3751bfb66e7"),
-                 "resid": (139.848448e6, 204.659200e6)}
+TILES_TRAFFIC = {"src_sha1": ("03afda2e8b324c09c64e6ce3ac102a779b58d481", "46c6ab7c0cf76cc6afff00fcfb847231dc6f1a3a"),
+                 "resid": (139.747840e6, 203.521024e6)}
 
 
 def tiles_traffic(a):

@@ -317,11 +317,12 @@ int rix_combine(rix_job_t job, void* image_out, rix_stream_t stream);
 /* ---- batched major cycles and gridder tuning ------------------------------ */
 
 /* Tuning of the FP32 w-stacked gridder of a job (a deployment knob; the paper
- * has no counterpart): chunk_limit (1 .. 32) = the most samples with one
- * kernel footprint a warp grids at a time (the work items' entries are
- * regrouped on the spot when it changes; results are the same up to
- * rounding), ctas_per_sm (0 .. 8, 0 = as many as fit) = resident gridder
- * CTAs per SM.  Defaults 32 and 0.  Waits for the job's own work. */
+ * has no counterpart): chunk_limit (1 .. 256) = the most samples with one
+ * kernel footprint a warp grids between two flushes of its accumulators
+ * (the work items' entries are regrouped on the spot when it changes;
+ * results are the same up to rounding), ctas_per_sm (0 .. 8, 0 = as many as
+ * fit) = resident gridder CTAs per SM.  Defaults 64 and 0.  Waits for the
+ * job's own work. */
 int rix_job_tune(rix_job_t job, int32_t chunk_limit, int32_t ctas_per_sm);
 
 /* A batch of (job, partition) pairs whose major cycles run together (the

@@ -1,7 +1,7 @@
 """Autotuner of the FP32 w-stacked gridder's per-job tuning.
 
 Two knobs (rix_job_tune): the most samples with one kernel footprint a warp
-grids at a time (chunk_limit) and the resident gridder CTAs per SM.  For a
+grids between two flushes of its accumulators (chunk_limit) and the resident gridder CTAs per SM.  For a
 job shape (GPU, image side, w-planes, channels, partitions, and the sample
 count in powers of two) every candidate is applied and the partitions'
 gridder is timed with rix_gridder_probe (device time, no change to the job's
@@ -19,7 +19,7 @@ import torch
 from . import rix
 
 # (chunk_limit, ctas_per_sm); ctas_per_sm 0 = as many as fit (two at 128 registers)
-CANDIDATES = ((32, 0), (16, 0), (8, 0), (32, 1))
+CANDIDATES = ((64, 0), (128, 0), (32, 0), (16, 0), (64, 1))
 
 
 def default_cache_path() -> str:

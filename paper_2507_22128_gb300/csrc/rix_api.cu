@@ -694,8 +694,8 @@ int rix_job_set_psf_method(rix_job_t job, int32_t method) {
 // ---- gridder tuning and batched major cycles ------------------------------
 int rix_job_tune(rix_job_t job, int32_t chunk_limit, int32_t ctas_per_sm) {
   if (!job) return set_error(RIX_EINVAL, "job is NULL");
-  if (chunk_limit < 1 || chunk_limit > 32 || ctas_per_sm < 0 || ctas_per_sm > 8)
-    return set_error(RIX_EINVAL, "chunk_limit in [1, 32] and ctas_per_sm in [0, 8]");
+  if (chunk_limit < 1 || chunk_limit > 256 || ctas_per_sm < 0 || ctas_per_sm > 8)
+    return set_error(RIX_EINVAL, "chunk_limit in [1, 256] and ctas_per_sm in [0, 8]");
   Job& J = job->j;
   RIX_CUDA(cudaSetDevice(J.ctx->device));
   J.fp_ctas_per_sm = ctas_per_sm;

@@ -342,7 +342,7 @@ struct Job {
   std::vector<std::pair<cudaStream_t, cudaEvent_t>> touched;
   // tuning of the FP32 w-stacked gridder (rix_job_tune): entries per chunk
   // (at most 32) and resident CTAs per SM (0: as many as fit)
-  int chunk_limit = 32;
+  int chunk_limit = 64;
   int fp_ctas_per_sm = 0;
   bool gorder = false;   // egeom (and gsamples) in the gridder order
   int psf_method = 0;    // RIX_PSF_* (rix_job_set_psf_method)

@@ -283,7 +283,7 @@ def grid(job, part, vis, image_out, stream=None):
 
 
 # ------------------------------------------ tuning and batched major cycles --
-def job_tune(job, chunk_limit=32, ctas_per_sm=0):
+def job_tune(job, chunk_limit=64, ctas_per_sm=0):
     _check(_lib.rix_job_tune(job, int(chunk_limit), int(ctas_per_sm)))
 
 

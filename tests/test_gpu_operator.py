@@ -280,3 +280,69 @@ def test_samples_outside_the_grid(ctx, obs_outside, prec):
             assert rel_l2(res.cpu().numpy(), gridder.residual(obs.vis.reshape(-1), w, x, g)) < TOL[prec]
     finally:
         rix.job_destroy(job)
+
+
+@pytest.fixture(scope="module")
+def obs_dense():
+    """The medium recipe's 1" cell on a 128 x 128 field: 32 antennas x 100
+    times x 2 channels (99,200 visibilities) land on a few hundred kernel
+    footprints of the low partition (up to 3,440 samples share one), so the
+    FP32 gridder's chunks span several batches of 32 and one footprint spans
+    several chunks and work items."""
+    from paper_2507_22128_gb300 import synth
+    return synth.medium(seed=21, n_times=100, n=128, n_ant=32, n_chan=2)
+
+
+@pytest.fixture(scope="module")
+def dense_oracle(obs_dense):
+    from oracle import gridder
+    obs = obs_dense
+    st = _oracle(obs, 2)
+    w = obs.weight.reshape(-1).astype(np.float64)
+    model = sparse_model(obs.n, 20, seed=9)
+    vis = obs.vis.reshape(-1)
+    res = [gridder.residual(vis, w, model, st.gparts[p]) for p in range(2)]
+    dirty = [gridder.dirty(vis, w, st.gparts[p]) for p in range(2)]
+    return st, model, res, dirty
+
+
+@pytest.mark.parametrize("limit", [1, 7, 32, 33, 64, 256])
+def test_fp32_gridder_at_every_chunk_limit(ctx, obs_dense, dense_oracle, limit):
+    """The FP32 w-stacked gridder regrouped at chunk limits below, at and
+    above its 32-entry batch (rix_job_tune): fused major cycle and grid of
+    both partitions within 1e-5 of the oracle gridder."""
+    from paper_2507_22128_gb300 import rix
+    obs = obs_dense
+    st, model, want_res, want_dirty = dense_oracle
+    # the workload does put more samples than every tested limit on one footprint
+    g = st.geom
+    sel = np.nonzero(st.mask & 1)[0]
+    _, per_tap = np.unique((g.p0[sel] * 4096 + g.j0u[sel]) * 4096 + g.j0v[sel], return_counts=True)
+    assert per_tap.max() > 2048 and per_tap.max() > limit
+    job, _ = _job(ctx, obs, rix.FP32, 2)
+    try:
+        rix.job_tune(job, limit, 0)
+        vis = to_dev(obs.vis.reshape(-1), torch.complex64)
+        for p in range(2):
+            res = torch.empty((obs.n, obs.n), dtype=torch.float32, device="cuda")
+            rix.major_cycle(job, p, vis, to_dev(model, torch.float32), res)
+            img = torch.empty((obs.n, obs.n), dtype=torch.float32, device="cuda")
+            rix.grid(job, p, vis, img)
+            torch.cuda.synchronize()
+            assert rel_l2(res.cpu().numpy(), want_res[p]) < TOL[rix.FP32]
+            assert rel_l2(img.cpu().numpy(), want_dirty[p]) < TOL[rix.FP32]
+        rix.job_sync(job)
+    finally:
+        rix.job_destroy(job)
+
+
+def test_chunk_limit_range(ctx, obs_small):
+    from paper_2507_22128_gb300 import rix
+    job, _ = _job(ctx, obs_small, rix.FP32, 2)
+    try:
+        for bad in (0, 257):
+            with pytest.raises(rix.RixError):
+                rix.job_tune(job, bad, 0)
+        rix.job_tune(job, 256, 0)
+    finally:
+        rix.job_destroy(job)
