@@ -1078,22 +1078,28 @@ int op_psf(Job* job, int p, cudaStream_t st) {
     a.win_lo = pt.pwin_lo;
     a.S = pt.pwin_n;
     a.out = pp;
-    // the partition's entries' geometry on the 2N grid, in FP64 (one thread
-    // per entry), for the one PSF launch
-    if (::rix::malloc_async(&pg, (size_t)pt.ent_count * sizeof(EntryGeom<R>), st) != cudaSuccess) {
-      rc = set_error(RIX_ENOMEM, "PSF entry geometry");
-      break;
+    if (std::is_same<R, float>::value && job->nw > 0 && job->tile == 16) {
+      // FP32 w-stacked: the register-resident gridder on 16 x 16 tiles of the
+      // PSF grid (k_tiles_fp.cu)
+      if ((rc = launch_psf_fp(job, p, a.scale, a.half, pp, st)) != RIX_OK) break;
+    } else {
+      // the partition's entries' geometry on the 2N grid, in FP64 (one thread
+      // per entry), for the one PSF launch
+      if (::rix::malloc_async(&pg, (size_t)pt.ent_count * sizeof(EntryGeom<R>), st) != cudaSuccess) {
+        rc = set_error(RIX_ENOMEM, "PSF entry geometry");
+        break;
+      }
+      {
+        const int blocks = (int)std::min<int64_t>(ceil_div(pt.ent_count, 256), (int64_t)job->ctx->num_sms * 16);
+        ::rix::note_launch();
+        if (job->tile == 16) k_entry_geom<R, true, 16><<<blocks, 256, 0, st>>>(a, pt.ent_begin, pt.ent_count, pg);
+        else k_entry_geom<R, true, 32><<<blocks, 256, 0, st>>>(a, pt.ent_begin, pt.ent_count, pg);
+        RIX_LAUNCH_CHECK();
+      }
+      a.geom = pg;
+      a.geom_off = pt.ent_begin;
+      if ((rc = launch_tiles<R, kPsf>(job, a, st)) != RIX_OK) break;
     }
-    {
-      const int blocks = (int)std::min<int64_t>(ceil_div(pt.ent_count, 256), (int64_t)job->ctx->num_sms * 16);
-      ::rix::note_launch();
-      if (job->tile == 16) k_entry_geom<R, true, 16><<<blocks, 256, 0, st>>>(a, pt.ent_begin, pt.ent_count, pg);
-      else k_entry_geom<R, true, 32><<<blocks, 256, 0, st>>>(a, pt.ent_begin, pt.ent_count, pg);
-      RIX_LAUNCH_CHECK();
-    }
-    a.geom = pg;
-    a.geom_off = pt.ent_begin;
-    if ((rc = launch_tiles<R, kPsf>(job, a, st)) != RIX_OK) break;
     const XformGeom g = plane_geom(job, pt, true);
     if ((rc = inv_cols<R>(job->ctx, g, pp, kOpNone, nullptr, nullptr, tt, st)) != RIX_OK) break;
     const double sc = pt.wsum > 0.0 ? 1.0 / pt.wsum : 0.0;

@@ -142,6 +142,163 @@ __global__ void k_chunk_lists(const uint32_t* __restrict__ cflag, const uint32_t
   }
 }
 
+// ------------------------------------------------------- the PSF's grid ----
+// The PSF (H of Eq. 4-7) is the dirty image of unit visibilities on the 2N x
+// 2N field, gridded on that field's own oversampled grid (side 4N).  Its
+// entries are the partition's, regrouped once per job into 16 x 16 tiles of
+// the PSF grid counted from the partition's PSF window.
+struct PsfArgs {
+  const uint32_t* keys;      // image-grid sort keys (the plane block)
+  const uint32_t* samples;   // sample index per entry (image gridder order)
+  const double* uvw;
+  const double* inv_lambda;
+  int nchan;
+  double scale, half;        // PSF grid coordinate x = u_lambda * scale + half
+  int nw, ww;
+  double w_min, dw;
+  int bt_img, bt, bw;        // key bits per tile coordinate (image grid, PSF window), plane bits
+  int win_lo, win_n;         // the partition's PSF window [win_lo, win_lo + win_n)^2
+  int64_t e_begin, n;        // the partition's entries
+  int* status;
+};
+
+// Per entry (local index i = entry - e_begin): the geometry record on the PSF
+// grid {du, dv, dw, first tap's offsets in its PSF tile} and the PSF key
+// (plane block, tile row, tile column), FP64 coordinates as k_entry_geom.
+__global__ void k_psf_geom(PsfArgs a, float4* __restrict__ geom, uint32_t* __restrict__ pkey) {
+  const uint32_t pmask = (1u << a.bw) - 1u;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < a.n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t e = a.e_begin + i;
+    const uint32_t p0 = (a.keys[e] >> (2 * a.bt_img)) & pmask;
+    const uint32_t s = a.samples[e];
+    const int64_t row = s / (uint32_t)a.nchan;
+    const int ch = (int)(s - row * a.nchan);
+    const double sc = a.inv_lambda[ch];
+    const double ul = __dmul_rn(a.uvw[row * 3 + 0], sc);
+    const double vl = __dmul_rn(a.uvw[row * 3 + 1], sc);
+    const double x = __dadd_rn(__dmul_rn(ul, a.scale), a.half);
+    const double y = __dadd_rn(__dmul_rn(vl, a.scale), a.half);
+    const double xs = __dadd_rn(x, -0.5 * kW), ys = __dadd_rn(y, -0.5 * kW);
+    const double cx = ceil(xs), cy = ceil(ys);
+    int ju = (int)cx - a.win_lo, jv = (int)cy - a.win_lo;
+    float dw = 0.f;
+    if (a.nw > 0) {
+      const double wl = __dmul_rn(a.uvw[row * 3 + 2], sc);
+      const double tw = __ddiv_rn(__dadd_rn(wl, -a.w_min), a.dw);
+      const double pc = fmin(fmax(ceil(tw), 0.0), (double)(a.nw - a.ww));
+      dw = (float)__dadd_rn(pc, -tw);
+    }
+    // the window holds every footprint of the partition by construction; an
+    // entry outside it is flagged (RIX_EINTERNAL) and kept in range
+    if (ju < 0 || jv < 0 || ju > a.win_n - kW || jv > a.win_n - kW) {
+      atomicCAS(a.status, 0, RIX_EINTERNAL);
+      ju = min(max(ju, 0), a.win_n - kW);
+      jv = min(max(jv, 0), a.win_n - kW);
+    }
+    const uint32_t ouv = (uint32_t)(ju & (kT - 1)) | ((uint32_t)(jv & (kT - 1)) << 8);
+    geom[i] = make_float4((float)__dadd_rn(cx, -xs), (float)__dadd_rn(cy, -ys), dw, __uint_as_float(ouv));
+    pkey[i] = (p0 << (2 * a.bt)) | ((uint32_t)(jv / kT) << a.bt) | (uint32_t)(ju / kT);
+  }
+}
+
+// Per image-grid work item of the partition (its entries lie in 3 x 3 PSF
+// tiles at most: an image tile of 16 cells maps to first taps in a run of 32
+// PSF cells): the entries reordered stably by (PSF tile, first tap), their
+// unit visibilities {w, 0, w, 0} written in that order, the entries that
+// start a segment (a new PSF tile: one work item of the PSF gridding)
+// flagged in sflag, those that start a chunk (a new first tap, and every
+// limit-th after) in cflag.  Local entry indices.
+__global__ void __launch_bounds__(256) k_psf_order(const uint32_t* __restrict__ items, int64_t item_begin,
+                                                   int64_t n_items, int64_t e_begin,
+                                                   const uint32_t* __restrict__ samples,
+                                                   const float* __restrict__ weight, float4* geom, uint32_t* pkey,
+                                                   float4* __restrict__ ysamp, uint32_t* __restrict__ cflag,
+                                                   uint32_t* __restrict__ sflag, int bt, int limit) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float4* sg = reinterpret_cast<float4*>(smem_raw);
+  uint32_t* sk = reinterpret_cast<uint32_t*>(sg + kItemMax);
+  uint32_t* sp = sk + kItemMax;
+  float* sw = reinterpret_cast<float*>(sp + kItemMax);
+  for (int64_t it = blockIdx.x; it < n_items; it += gridDim.x) {
+    const uint32_t g0 = items[item_begin + it];
+    const int cnt = (int)(items[item_begin + it + 1] - g0);
+    const int64_t e0 = (int64_t)g0 - e_begin;
+    int p2 = 2;
+    while (p2 < cnt) p2 <<= 1;
+    for (int r = threadIdx.x; r < p2; r += blockDim.x) {
+      if (r < cnt) {
+        const float4 g = geom[e0 + r];
+        const uint32_t k = pkey[e0 + r];
+        sg[r] = g;
+        sp[r] = k;
+        sw[r] = weight ? weight[samples[g0 + r]] : 1.0f;
+        const uint32_t ouv = __float_as_uint(g.w);
+        const uint32_t tap = ((ouv >> 8) << 4) | (ouv & 0xffu);          // 8 bits
+        const uint32_t sub = (((k >> bt) & 3u) << 2) | (k & 3u);          // the tile among 3 x 3
+        sk[r] = (((sub << 8) | tap) << 11) | (uint32_t)r;
+      } else {
+        sk[r] = 0xffffffffu;
+      }
+    }
+    __syncthreads();
+    for (int k = 2; k <= p2; k <<= 1) {
+      for (int j = k >> 1; j > 0; j >>= 1) {
+        for (int i = threadIdx.x; i < p2; i += blockDim.x) {
+          const int ixj = i ^ j;
+          if (ixj > i) {
+            const uint32_t x = sk[i], y = sk[ixj];
+            const bool up = (i & k) == 0;
+            if ((x > y) == up) {
+              sk[i] = y;
+              sk[ixj] = x;
+            }
+          }
+        }
+        __syncthreads();
+      }
+    }
+    for (int r = threadIdx.x; r < cnt; r += blockDim.x) {
+      const uint32_t key = sk[r];
+      const int src = (int)(key & 2047u);
+      geom[e0 + r] = sg[src];
+      pkey[e0 + r] = sp[src];
+      ysamp[e0 + r] = make_float4(sw[src], 0.f, sw[src], 0.f);
+      const uint32_t lo_key = key & ~2047u;
+      int lo = 0, hi = r;
+      while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (sk[mid] < lo_key) lo = mid + 1;
+        else hi = mid;
+      }
+      cflag[e0 + r] = ((r - lo) % limit) == 0 ? 1u : 0u;
+      sflag[e0 + r] = (r == 0 || (key >> 19) != (sk[r - 1] >> 19)) ? 1u : 0u;
+    }
+    __syncthreads();
+  }
+}
+
+// chunk and segment lists of the PSF's entries: chunks[cidx[e]] = e,
+// segs[sidx[e]] = e and seg_chunk[sidx[e]] = cidx[e] at the flagged
+// entries; sentinels at the ends
+__global__ void k_psf_lists(const uint32_t* __restrict__ cflag, const uint32_t* __restrict__ cidx,
+                            const uint32_t* __restrict__ sflag, const uint32_t* __restrict__ sidx, int64_t n,
+                            const uint32_t* __restrict__ totals, uint32_t* __restrict__ chunks,
+                            uint32_t* __restrict__ segs, uint32_t* __restrict__ seg_chunk) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += stride) {
+    if (cflag[e]) chunks[cidx[e]] = (uint32_t)e;
+    if (sflag[e]) {
+      segs[sidx[e]] = (uint32_t)e;
+      seg_chunk[sidx[e]] = cidx[e];
+    }
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    chunks[totals[0]] = (uint32_t)n;
+    segs[totals[1]] = (uint32_t)n;
+    seg_chunk[totals[1]] = totals[0];
+  }
+}
+
 // ------------------------------------------------------------- PTX glue ----
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -185,6 +342,7 @@ struct FpArgs {
   const float4* geom;          // EntryGeom<float> per entry, gridder order
   const float4* ysamp;         // per entry: {w re v, w im v, w, 0}, gridder order
   int64_t item_begin, item_count;
+  const uint32_t* dev_items;   // grid mode: null, or the number of work items in device memory (item_count bounds it)
   int bt, bw, win_lo;
   int* status;                 // the job's status word
 };
@@ -298,7 +456,10 @@ __global__ void __launch_bounds__(kFpThreads, 2)
   WarpScratch& ws = scratch[warp];
   float* wg = ws.w;
 
-  const int64_t total = BATCH ? bt.item_start[bt.n] : a0.item_count;
+  int64_t total = BATCH ? bt.item_start[bt.n] : a0.item_count;
+  if constexpr (MODE == kGrid && !BATCH) {
+    if (a0.dev_items) total = min(total, (int64_t)*a0.dev_items);
+  }
   int cur = -1;
   for (int64_t it = blockIdx.x; it < total; it += gridDim.x) {
     int64_t item;
@@ -719,6 +880,108 @@ int launch_tiles_fp(const Job* job, int mode, int64_t item_begin, int64_t item_c
     return launch_fp<kResid>(job, a, tm_model, tm_out, st);
   }
   return launch_fp<kGrid>(job, a, tm_out, tm_out, st);
+}
+
+int launch_psf_fp(const Job* job, int p, double scale, double half, void* planes, cudaStream_t st) {
+  const Part& pt = job->part[p];
+  const int64_t n = pt.ent_count;
+  if (n <= 0 || pt.item_count <= 0) return RIX_OK;
+  if (job->tile != kT || job->nw < kW || job->fp64)
+    return set_error(RIX_EINVAL, "PSF gridding on k_tiles_fp: unsupported job (tile %d, planes %d)", job->tile,
+                     job->nw);
+  const int ntile = (pt.pwin_n + kT - 1) / kT;
+  int bt = 1;
+  while ((1 << bt) < ntile) ++bt;
+  if (2 * bt + job->bw > 32) return set_error(RIX_EINVAL, "PSF window too large for the tile keys");
+  // scratch: geometry and unit visibilities (16 B per entry), keys, flags and
+  // their scans (4 B each), chunk and segment lists (n + 1 each), two totals
+  const size_t nn = (size_t)n;
+  const size_t bytes = nn * 32 + nn * 4 * 5 + (nn + 1) * 4 * 3 + 16;
+  unsigned char* buf = nullptr;
+  if (malloc_async(&buf, bytes, st) != cudaSuccess) {
+    cudaGetLastError();
+    return set_error(RIX_ENOMEM, "PSF gridder scratch (%zu bytes)", bytes);
+  }
+  float4* geom = reinterpret_cast<float4*>(buf);
+  float4* ys = geom + nn;
+  uint32_t* pkey = reinterpret_cast<uint32_t*>(ys + nn);
+  uint32_t* cflag = pkey + nn;
+  uint32_t* sflag = cflag + nn;
+  uint32_t* cidx = sflag + nn;
+  uint32_t* sidx = cidx + nn;
+  uint32_t* chunks = sidx + nn;
+  uint32_t* segs = chunks + nn + 1;
+  uint32_t* seg_chunk = segs + nn + 1;
+  uint32_t* totals = seg_chunk + nn + 1;
+  int rc = RIX_OK;
+  do {
+    PsfArgs a{};
+    a.keys = job->keys.as<uint32_t>();
+    a.samples = job->gsamples.as<uint32_t>();
+    a.uvw = job->uvw.as<double>();
+    a.inv_lambda = job->inv_lambda.as<double>();
+    a.nchan = job->desc.nchan;
+    a.scale = scale;
+    a.half = half;
+    a.nw = job->nw;
+    a.ww = job->ww;
+    a.w_min = job->stats.w_min;
+    a.dw = job->stats.dw;
+    a.bt_img = job->bt;
+    a.bt = bt;
+    a.bw = job->bw;
+    a.win_lo = pt.pwin_lo;
+    a.win_n = pt.pwin_n;
+    a.e_begin = pt.ent_begin;
+    a.n = n;
+    a.status = job->status.as<int>();
+    {
+      const int blocks = (int)std::min<int64_t>(ceil_div(n, 256), (int64_t)job->ctx->num_sms * 16);
+      ::rix::note_launch();
+      k_psf_geom<<<blocks, 256, 0, st>>>(a, geom, pkey);
+      if (cudaGetLastError() != cudaSuccess) { rc = set_error(RIX_ECUDA, "k_psf_geom launch"); break; }
+    }
+    {
+      const size_t sm = (size_t)kItemMax * (sizeof(float4) + 3 * sizeof(uint32_t));
+      if (cudaFuncSetAttribute(k_psf_order, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess) {
+        rc = set_error(RIX_ECUDA, "k_psf_order shared memory");
+        break;
+      }
+      const int blocks = (int)std::min<int64_t>(pt.item_count, (int64_t)job->ctx->num_sms * 4);
+      ::rix::note_launch();
+      k_psf_order<<<blocks, 256, sm, st>>>(job->items.as<uint32_t>(), pt.item_begin, pt.item_count, pt.ent_begin,
+                                           job->gsamples.as<uint32_t>(), job->weight.as<float>(), geom, pkey, ys,
+                                           cflag, sflag, bt, std::min(std::max(job->chunk_limit, 1), kChunkLimitMax));
+      if (cudaGetLastError() != cudaSuccess) { rc = set_error(RIX_ECUDA, "k_psf_order launch"); break; }
+    }
+    if ((rc = scan_exclusive_u32(cflag, cidx, n, totals, st)) != RIX_OK) break;
+    if ((rc = scan_exclusive_u32(sflag, sidx, n, totals + 1, st)) != RIX_OK) break;
+    {
+      const int blocks = (int)std::min<int64_t>(ceil_div(n, 256), (int64_t)job->ctx->num_sms * 8);
+      ::rix::note_launch();
+      k_psf_lists<<<blocks, 256, 0, st>>>(cflag, cidx, sflag, sidx, n, totals, chunks, segs, seg_chunk);
+      if (cudaGetLastError() != cudaSuccess) { rc = set_error(RIX_ECUDA, "k_psf_lists launch"); break; }
+    }
+    FpArgs f{};
+    f.keys = pkey;
+    f.items = segs;
+    f.item_chunk = seg_chunk;
+    f.chunks = chunks;
+    f.geom = geom;
+    f.ysamp = ys;
+    f.item_begin = 0;
+    f.item_count = std::min<int64_t>(n, 9 * pt.item_count);   // every image item spans 3 x 3 PSF tiles at most
+    f.dev_items = totals + 1;
+    f.bt = bt;
+    f.bw = job->bw;
+    f.win_lo = 0;   // the keys count tiles from the window
+    f.status = job->status.as<int>();
+    CUtensorMap tm{};
+    if ((rc = plane_map(&tm, planes, pt.pwin_n, job->nw)) != RIX_OK) break;
+    rc = launch_fp<kGrid>(job, f, tm, tm, st);
+  } while (0);
+  cudaFreeAsync(buf, st);
+  return rc;
 }
 
 // ---- several partitions in one launch ----------------------------------------

@@ -404,6 +404,11 @@ int grid_work_order(Job* job, cudaStream_t st);
 int launch_tiles_fp(const Job* job, int mode, int64_t item_begin, int64_t item_count, int64_t ent_begin,
                     int64_t ent_count, int win_lo, int S, const void* model_planes, void* out_planes, const void* vis,
                     cudaStream_t st);
+// The PSF gridding of partition p on the same gridder (FP32 w-stacked jobs
+// with tile 16): unit visibilities times the weights spread on the PSF grid
+// (coordinate x = u_lambda * scale + half) into planes [n_wplanes][S][S]
+// complex on the partition's PSF window (S = its side; zeroed by the caller).
+int launch_psf_fp(const Job* job, int p, double scale, double half, void* planes, cudaStream_t st);
 template <typename R>
 int op_degrid(Job* job, int p, const R* image, cplx<R>* vis_out, cudaStream_t st);
 template <typename R>

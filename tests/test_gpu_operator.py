@@ -309,8 +309,9 @@ def dense_oracle(obs_dense):
 @pytest.mark.parametrize("limit", [1, 7, 32, 33, 64, 256])
 def test_fp32_gridder_at_every_chunk_limit(ctx, obs_dense, dense_oracle, limit):
     """The FP32 w-stacked gridder regrouped at chunk limits below, at and
-    above its 32-entry batch (rix_job_tune): fused major cycle and grid of
-    both partitions within 1e-5 of the oracle gridder."""
+    above its 32-entry batch (rix_job_tune): fused major cycle, grid and PSF
+    (the same kernel on the PSF's grid) of both partitions within 1e-5 of the
+    oracle."""
     from paper_2507_22128_gb300 import rix
     obs = obs_dense
     st, model, want_res, want_dirty = dense_oracle
@@ -331,6 +332,11 @@ def test_fp32_gridder_at_every_chunk_limit(ctx, obs_dense, dense_oracle, limit):
             torch.cuda.synchronize()
             assert rel_l2(res.cpu().numpy(), want_res[p]) < TOL[rix.FP32]
             assert rel_l2(img.cpu().numpy(), want_dirty[p]) < TOL[rix.FP32]
+            psf = torch.empty((2 * obs.n, 2 * obs.n), dtype=torch.float32, device="cuda")
+            wsum = rix.psf(job, p, psf)
+            torch.cuda.synchronize()
+            assert abs(wsum - st.wsum[p]) <= 1e-9 * st.wsum[p]
+            assert rel_l2(psf.cpu().numpy(), st.psf[p]) < TOL[rix.FP32]
         rix.job_sync(job)
     finally:
         rix.job_destroy(job)
