@@ -985,8 +985,8 @@ def cufft_comparison(n, nplanes, window, flush, reps=5):
 # launches of the medium job's first major cycle (low, high partition), with
 # the sha1 of the sources the kernel was built from (k_tiles_fp.cu,
 # rix_internal.cuh): a changed source voids them
-TILES_TRAFFIC = {"src_sha1": ("03afda2e8b324c09c64e6ce3ac102a779b58d481", "46c6ab7c0cf76cc6afff00fcfb847231dc6f1a3a"),
-                 "resid": (139.747840e6, 203.521024e6)}
+TILES_TRAFFIC = {"src_sha1": ("26627dc6d95a2554aad224fbd0f5828f69ef81e6", "f3856a35dfa300bce2539f3ed838fef54aba3c6c"),
+                 "resid": (139.825408e6, 203.583488e6)}
 
 
 def tiles_traffic(a):

@@ -148,7 +148,12 @@ typedef struct {
 /* ---- context and job lifetime --------------------------------------------- */
 
 /* Creates a context on CUDA device `device` that admits jobs while their
- * summed workspace stays within mem_budget_bytes (0 = no budget). */
+ * summed workspace stays within mem_budget_bytes (0 = no budget).  The
+ * library's device memory (job buffers and the temporaries of its calls)
+ * comes from one stream-ordered pool per device, owned by the library for
+ * the life of the process, which keeps up to 8 GiB of freed memory reserved
+ * for later calls instead of returning it to the system at every
+ * synchronisation. */
 int rix_create(rix_ctx_t* ctx, int device, size_t mem_budget_bytes);
 /* Destroys a context; RIX_EBUSY while it still owns jobs. */
 int rix_destroy(rix_ctx_t ctx);

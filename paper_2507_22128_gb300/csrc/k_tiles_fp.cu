@@ -145,8 +145,9 @@ __global__ void k_chunk_lists(const uint32_t* __restrict__ cflag, const uint32_t
 // ------------------------------------------------------- the PSF's grid ----
 // The PSF (H of Eq. 4-7) is the dirty image of unit visibilities on the 2N x
 // 2N field, gridded on that field's own oversampled grid (side 4N).  Its
-// entries are the partition's, regrouped once per job into 16 x 16 tiles of
-// the PSF grid counted from the partition's PSF window.
+// entries are the partition's, sorted once per job by their 16 x 16 tile of
+// the PSF grid (tiles counted from the partition's PSF window) and w-plane
+// block, cut into work items and chunks as on the image grid.
 struct PsfArgs {
   const uint32_t* keys;      // image-grid sort keys (the plane block)
   const uint32_t* samples;   // sample index per entry (image gridder order)
@@ -163,9 +164,11 @@ struct PsfArgs {
 };
 
 // Per entry (local index i = entry - e_begin): the geometry record on the PSF
-// grid {du, dv, dw, first tap's offsets in its PSF tile} and the PSF key
-// (plane block, tile row, tile column), FP64 coordinates as k_entry_geom.
-__global__ void k_psf_geom(PsfArgs a, float4* __restrict__ geom, uint32_t* __restrict__ pkey) {
+// grid {du, dv, dw, first tap's offsets in its PSF tile}, the PSF key (plane
+// block, tile row, tile column) and i itself (the sort's payload); FP64
+// coordinates as k_entry_geom.
+__global__ void k_psf_geom(PsfArgs a, float4* __restrict__ geom, uint32_t* __restrict__ pkey,
+                           uint32_t* __restrict__ idx) {
   const uint32_t pmask = (1u << a.bw) - 1u;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < a.n; i += (int64_t)gridDim.x * blockDim.x) {
     const int64_t e = a.e_begin + i;
@@ -198,44 +201,73 @@ __global__ void k_psf_geom(PsfArgs a, float4* __restrict__ geom, uint32_t* __res
     const uint32_t ouv = (uint32_t)(ju & (kT - 1)) | ((uint32_t)(jv & (kT - 1)) << 8);
     geom[i] = make_float4((float)__dadd_rn(cx, -xs), (float)__dadd_rn(cy, -ys), dw, __uint_as_float(ouv));
     pkey[i] = (p0 << (2 * a.bt)) | ((uint32_t)(jv / kT) << a.bt) | (uint32_t)(ju / kT);
+    idx[i] = (uint32_t)i;
   }
 }
 
-// Per image-grid work item of the partition (its entries lie in 3 x 3 PSF
-// tiles at most: an image tile of 16 cells maps to first taps in a run of 32
-// PSF cells): the entries reordered stably by (PSF tile, first tap), their
-// unit visibilities {w, 0, w, 0} written in that order, the entries that
-// start a segment (a new PSF tile: one work item of the PSF gridding)
-// flagged in sflag, those that start a chunk (a new first tap, and every
-// limit-th after) in cflag.  Local entry indices.
-__global__ void __launch_bounds__(256) k_psf_order(const uint32_t* __restrict__ items, int64_t item_begin,
-                                                   int64_t n_items, int64_t e_begin,
-                                                   const uint32_t* __restrict__ samples,
-                                                   const float* __restrict__ weight, float4* geom, uint32_t* pkey,
-                                                   float4* __restrict__ ysamp, uint32_t* __restrict__ cflag,
-                                                   uint32_t* __restrict__ sflag, int bt, int limit) {
+// After the stable sort of the PSF keys (sk, with the local entry indices
+// sv): f[i] = 1 where a run of equal keys starts.
+__global__ void k_psf_runs(const uint32_t* __restrict__ sk, int64_t n, uint32_t* __restrict__ f) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    f[i] = (i == 0 || sk[i] != sk[i - 1]) ? 1u : 0u;
+}
+
+// first entry of every run (ex: exclusive scan of the run flags)
+__global__ void k_psf_run_starts(const uint32_t* __restrict__ f, const uint32_t* __restrict__ ex, int64_t n,
+                                 uint32_t* __restrict__ starts) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    if (f[i]) starts[ex[i]] = (uint32_t)i;
+}
+
+// The geometry and weight of every entry in key order, and the entries that
+// start a work item (the first of a run, and every kItemMax-th after it).
+__global__ void k_psf_gather(const uint32_t* __restrict__ sv, const float4* __restrict__ geom_in,
+                             const uint32_t* __restrict__ samples, const float* __restrict__ weight, int64_t e_begin,
+                             const uint32_t* __restrict__ f, const uint32_t* __restrict__ ex,
+                             const uint32_t* __restrict__ starts, int64_t n, float4* __restrict__ geom,
+                             float* __restrict__ w, uint32_t* __restrict__ iflag) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const uint32_t src = sv[i];
+    geom[i] = geom_in[src];
+    w[i] = weight ? weight[samples[e_begin + src]] : 1.0f;
+    const uint32_t run = ex[i] + f[i] - 1u;
+    iflag[i] = (((uint32_t)i - starts[run]) % (uint32_t)kItemMax) == 0u ? 1u : 0u;
+  }
+}
+
+// work-item start offsets (iex: exclusive scan of the item flags; sentinel n)
+__global__ void k_psf_items(const uint32_t* __restrict__ iflag, const uint32_t* __restrict__ iex, int64_t n,
+                            const uint32_t* __restrict__ n_items, uint32_t* __restrict__ items) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    if (iflag[i]) items[iex[i]] = (uint32_t)i;
+  if (blockIdx.x == 0 && threadIdx.x == 0) items[*n_items] = (uint32_t)n;
+}
+
+// Per work item (one PSF tile of one w-plane block, at most kItemMax entries;
+// *n_items of them): the entries reordered stably by first tap, their unit
+// visibilities {w, 0, w, 0} written in that order, and the entries that
+// start a chunk (a new first tap, and every limit-th after) flagged.
+__global__ void __launch_bounds__(256) k_psf_order(const uint32_t* __restrict__ items,
+                                                   const uint32_t* __restrict__ n_items, const float* __restrict__ w,
+                                                   float4* geom, float4* __restrict__ ysamp,
+                                                   uint32_t* __restrict__ cflag, int limit) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float4* sg = reinterpret_cast<float4*>(smem_raw);
   uint32_t* sk = reinterpret_cast<uint32_t*>(sg + kItemMax);
-  uint32_t* sp = sk + kItemMax;
-  float* sw = reinterpret_cast<float*>(sp + kItemMax);
-  for (int64_t it = blockIdx.x; it < n_items; it += gridDim.x) {
-    const uint32_t g0 = items[item_begin + it];
-    const int cnt = (int)(items[item_begin + it + 1] - g0);
-    const int64_t e0 = (int64_t)g0 - e_begin;
+  float* sw = reinterpret_cast<float*>(sk + kItemMax);
+  const int64_t ni = *n_items;
+  for (int64_t it = blockIdx.x; it < ni; it += gridDim.x) {
+    const uint32_t e0 = items[it];
+    const int cnt = (int)(items[it + 1] - e0);
     int p2 = 2;
     while (p2 < cnt) p2 <<= 1;
     for (int r = threadIdx.x; r < p2; r += blockDim.x) {
       if (r < cnt) {
         const float4 g = geom[e0 + r];
-        const uint32_t k = pkey[e0 + r];
         sg[r] = g;
-        sp[r] = k;
-        sw[r] = weight ? weight[samples[g0 + r]] : 1.0f;
+        sw[r] = w[e0 + r];
         const uint32_t ouv = __float_as_uint(g.w);
-        const uint32_t tap = ((ouv >> 8) << 4) | (ouv & 0xffu);          // 8 bits
-        const uint32_t sub = (((k >> bt) & 3u) << 2) | (k & 3u);          // the tile among 3 x 3
-        sk[r] = (((sub << 8) | tap) << 11) | (uint32_t)r;
+        sk[r] = ((((ouv >> 8) << 4) | (ouv & 0xffu)) << 11) | (uint32_t)r;   // 8-bit tap, position
       } else {
         sk[r] = 0xffffffffu;
       }
@@ -261,7 +293,6 @@ __global__ void __launch_bounds__(256) k_psf_order(const uint32_t* __restrict__ 
       const uint32_t key = sk[r];
       const int src = (int)(key & 2047u);
       geom[e0 + r] = sg[src];
-      pkey[e0 + r] = sp[src];
       ysamp[e0 + r] = make_float4(sw[src], 0.f, sw[src], 0.f);
       const uint32_t lo_key = key & ~2047u;
       int lo = 0, hi = r;
@@ -271,31 +302,26 @@ __global__ void __launch_bounds__(256) k_psf_order(const uint32_t* __restrict__ 
         else hi = mid;
       }
       cflag[e0 + r] = ((r - lo) % limit) == 0 ? 1u : 0u;
-      sflag[e0 + r] = (r == 0 || (key >> 19) != (sk[r - 1] >> 19)) ? 1u : 0u;
     }
     __syncthreads();
   }
 }
 
-// chunk and segment lists of the PSF's entries: chunks[cidx[e]] = e,
-// segs[sidx[e]] = e and seg_chunk[sidx[e]] = cidx[e] at the flagged
-// entries; sentinels at the ends
-__global__ void k_psf_lists(const uint32_t* __restrict__ cflag, const uint32_t* __restrict__ cidx,
-                            const uint32_t* __restrict__ sflag, const uint32_t* __restrict__ sidx, int64_t n,
-                            const uint32_t* __restrict__ totals, uint32_t* __restrict__ chunks,
-                            uint32_t* __restrict__ segs, uint32_t* __restrict__ seg_chunk) {
+// chunk lists of the PSF's entries: chunks[cidx[e]] = e at the flagged
+// entries, item_chunk[i] = cidx[items[i]]; sentinels at the ends
+__global__ void k_psf_lists(const uint32_t* __restrict__ cflag, const uint32_t* __restrict__ cidx, int64_t n,
+                            const uint32_t* __restrict__ items, const uint32_t* __restrict__ n_items,
+                            const uint32_t* __restrict__ n_chunks, uint32_t* __restrict__ chunks,
+                            uint32_t* __restrict__ item_chunk) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += stride) {
+  const int64_t ni = *n_items;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += stride)
     if (cflag[e]) chunks[cidx[e]] = (uint32_t)e;
-    if (sflag[e]) {
-      segs[sidx[e]] = (uint32_t)e;
-      seg_chunk[sidx[e]] = cidx[e];
-    }
-  }
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < ni; i += stride)
+    item_chunk[i] = cidx[items[i]];
   if (blockIdx.x == 0 && threadIdx.x == 0) {
-    chunks[totals[0]] = (uint32_t)n;
-    segs[totals[1]] = (uint32_t)n;
-    seg_chunk[totals[1]] = totals[0];
+    chunks[*n_chunks] = (uint32_t)n;
+    item_chunk[ni] = *n_chunks;
   }
 }
 
@@ -892,27 +918,34 @@ int launch_psf_fp(const Job* job, int p, double scale, double half, void* planes
   const int ntile = (pt.pwin_n + kT - 1) / kT;
   int bt = 1;
   while ((1 << bt) < ntile) ++bt;
-  if (2 * bt + job->bw > 32) return set_error(RIX_EINVAL, "PSF window too large for the tile keys");
-  // scratch: geometry and unit visibilities (16 B per entry), keys, flags and
-  // their scans (4 B each), chunk and segment lists (n + 1 each), two totals
+  const int key_bits = 2 * bt + job->bw;
+  if (key_bits > 32) return set_error(RIX_EINVAL, "PSF window too large for the tile keys");
+  // scratch: two geometry-sized arrays (16 B per entry), ten of 4 B, three
+  // lists of n + 1, four totals
   const size_t nn = (size_t)n;
-  const size_t bytes = nn * 32 + nn * 4 * 5 + (nn + 1) * 4 * 3 + 16;
+  const size_t bytes = nn * 16 * 2 + nn * 4 * 10 + (nn + 1) * 4 * 3 + 16;
   unsigned char* buf = nullptr;
   if (malloc_async(&buf, bytes, st) != cudaSuccess) {
     cudaGetLastError();
     return set_error(RIX_ENOMEM, "PSF gridder scratch (%zu bytes)", bytes);
   }
-  float4* geom = reinterpret_cast<float4*>(buf);
-  float4* ys = geom + nn;
-  uint32_t* pkey = reinterpret_cast<uint32_t*>(ys + nn);
-  uint32_t* cflag = pkey + nn;
-  uint32_t* sflag = cflag + nn;
-  uint32_t* cidx = sflag + nn;
-  uint32_t* sidx = cidx + nn;
-  uint32_t* chunks = sidx + nn;
-  uint32_t* segs = chunks + nn + 1;
-  uint32_t* seg_chunk = segs + nn + 1;
-  uint32_t* totals = seg_chunk + nn + 1;
+  float4* geom0 = reinterpret_cast<float4*>(buf);   // image order
+  float4* geom = geom0 + nn;                         // key order, then gridder order
+  float4* ys = geom0;                                // unit visibilities, once geom0 is gathered
+  uint32_t* key = reinterpret_cast<uint32_t*>(geom + nn);
+  uint32_t* keyt = key + nn;
+  uint32_t* val = keyt + nn;
+  uint32_t* valt = val + nn;
+  uint32_t* f = valt + nn;        // run flags, then chunk flags
+  uint32_t* ex = f + nn;          // their scans
+  uint32_t* starts = ex + nn;     // run starts
+  float* w = reinterpret_cast<float*>(starts + nn);
+  uint32_t* iflag = reinterpret_cast<uint32_t*>(w + nn);
+  uint32_t* iex = iflag + nn;
+  uint32_t* items = iex + nn;
+  uint32_t* chunks = items + nn + 1;
+  uint32_t* item_chunk = chunks + nn + 1;
+  uint32_t* totals = item_chunk + nn + 1;   // runs, items, chunks
   int rc = RIX_OK;
   do {
     PsfArgs a{};
@@ -935,50 +968,59 @@ int launch_psf_fp(const Job* job, int p, double scale, double half, void* planes
     a.e_begin = pt.ent_begin;
     a.n = n;
     a.status = job->status.as<int>();
+    const int eb = (int)std::min<int64_t>(ceil_div(n, 256), (int64_t)job->ctx->num_sms * 16);
+    ::rix::note_launch();
+    k_psf_geom<<<eb, 256, 0, st>>>(a, geom0, key, val);
+    if (cudaGetLastError() != cudaSuccess) { rc = set_error(RIX_ECUDA, "k_psf_geom launch"); break; }
+    // stable sort by (w-plane block, tile row, tile column)
+    bool in_tmp = false;
+    if ((rc = radix_sort_u32(key, val, keyt, valt, n, key_bits, st, &in_tmp)) != RIX_OK) break;
+    const uint32_t* sk = in_tmp ? keyt : key;
+    const uint32_t* sv = in_tmp ? valt : val;
+    ::rix::note_launch();
+    k_psf_runs<<<eb, 256, 0, st>>>(sk, n, f);
+    if ((rc = scan_exclusive_u32(f, ex, n, totals, st)) != RIX_OK) break;
+    ::rix::note_launch();
+    k_psf_run_starts<<<eb, 256, 0, st>>>(f, ex, n, starts);
+    ::rix::note_launch();
+    k_psf_gather<<<eb, 256, 0, st>>>(sv, geom0, job->gsamples.as<uint32_t>(), job->weight.as<float>(),
+                                     pt.ent_begin, f, ex, starts, n, geom, w, iflag);
+    if ((rc = scan_exclusive_u32(iflag, iex, n, totals + 1, st)) != RIX_OK) break;
+    ::rix::note_launch();
+    k_psf_items<<<eb, 256, 0, st>>>(iflag, iex, n, totals + 1, items);
+    if (cudaGetLastError() != cudaSuccess) { rc = set_error(RIX_ECUDA, "PSF work-item launches"); break; }
     {
-      const int blocks = (int)std::min<int64_t>(ceil_div(n, 256), (int64_t)job->ctx->num_sms * 16);
-      ::rix::note_launch();
-      k_psf_geom<<<blocks, 256, 0, st>>>(a, geom, pkey);
-      if (cudaGetLastError() != cudaSuccess) { rc = set_error(RIX_ECUDA, "k_psf_geom launch"); break; }
-    }
-    {
-      const size_t sm = (size_t)kItemMax * (sizeof(float4) + 3 * sizeof(uint32_t));
+      const size_t sm = (size_t)kItemMax * (sizeof(float4) + 2 * sizeof(uint32_t));
       if (cudaFuncSetAttribute(k_psf_order, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess) {
         rc = set_error(RIX_ECUDA, "k_psf_order shared memory");
         break;
       }
-      const int blocks = (int)std::min<int64_t>(pt.item_count, (int64_t)job->ctx->num_sms * 4);
       ::rix::note_launch();
-      k_psf_order<<<blocks, 256, sm, st>>>(job->items.as<uint32_t>(), pt.item_begin, pt.item_count, pt.ent_begin,
-                                           job->gsamples.as<uint32_t>(), job->weight.as<float>(), geom, pkey, ys,
-                                           cflag, sflag, bt, std::min(std::max(job->chunk_limit, 1), kChunkLimitMax));
+      k_psf_order<<<job->ctx->num_sms * 4, 256, sm, st>>>(items, totals + 1, w, geom, ys, f,
+                                                         std::min(std::max(job->chunk_limit, 1), kChunkLimitMax));
       if (cudaGetLastError() != cudaSuccess) { rc = set_error(RIX_ECUDA, "k_psf_order launch"); break; }
     }
-    if ((rc = scan_exclusive_u32(cflag, cidx, n, totals, st)) != RIX_OK) break;
-    if ((rc = scan_exclusive_u32(sflag, sidx, n, totals + 1, st)) != RIX_OK) break;
-    {
-      const int blocks = (int)std::min<int64_t>(ceil_div(n, 256), (int64_t)job->ctx->num_sms * 8);
-      ::rix::note_launch();
-      k_psf_lists<<<blocks, 256, 0, st>>>(cflag, cidx, sflag, sidx, n, totals, chunks, segs, seg_chunk);
-      if (cudaGetLastError() != cudaSuccess) { rc = set_error(RIX_ECUDA, "k_psf_lists launch"); break; }
-    }
-    FpArgs f{};
-    f.keys = pkey;
-    f.items = segs;
-    f.item_chunk = seg_chunk;
-    f.chunks = chunks;
-    f.geom = geom;
-    f.ysamp = ys;
-    f.item_begin = 0;
-    f.item_count = std::min<int64_t>(n, 9 * pt.item_count);   // every image item spans 3 x 3 PSF tiles at most
-    f.dev_items = totals + 1;
-    f.bt = bt;
-    f.bw = job->bw;
-    f.win_lo = 0;   // the keys count tiles from the window
-    f.status = job->status.as<int>();
+    if ((rc = scan_exclusive_u32(f, ex, n, totals + 2, st)) != RIX_OK) break;
+    ::rix::note_launch();
+    k_psf_lists<<<eb, 256, 0, st>>>(f, ex, n, items, totals + 1, totals + 2, chunks, item_chunk);
+    if (cudaGetLastError() != cudaSuccess) { rc = set_error(RIX_ECUDA, "k_psf_lists launch"); break; }
+    FpArgs fa{};
+    fa.keys = sk;
+    fa.items = items;
+    fa.item_chunk = item_chunk;
+    fa.chunks = chunks;
+    fa.geom = geom;
+    fa.ysamp = ys;
+    fa.item_begin = 0;
+    fa.item_count = n;              // bounds the work items, counted on the device
+    fa.dev_items = totals + 1;
+    fa.bt = bt;
+    fa.bw = job->bw;
+    fa.win_lo = 0;                  // the keys count tiles from the window
+    fa.status = job->status.as<int>();
     CUtensorMap tm{};
     if ((rc = plane_map(&tm, planes, pt.pwin_n, job->nw)) != RIX_OK) break;
-    rc = launch_fp<kGrid>(job, f, tm, tm, st);
+    rc = launch_fp<kGrid>(job, fa, tm, tm, st);
   } while (0);
   cudaFreeAsync(buf, st);
   return rc;

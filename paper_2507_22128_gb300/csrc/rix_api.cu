@@ -41,10 +41,44 @@ static std::atomic<unsigned long long> g_launches{0};
 void note_launch(long long n) { g_launches.fetch_add((unsigned long long)n, std::memory_order_relaxed); }
 unsigned long long launch_count() { return g_launches.load(); }
 
+// Device memory comes from one stream-ordered pool per device that the
+// library owns: it keeps up to kPoolKeep bytes of freed memory reserved
+// across synchronisations, so that the temporaries of the next calls (the
+// PSF's regrouping, the partition's sort) reuse them instead of mapping new
+// memory; the device's default pool (release threshold 0) would return them
+// to the system at every synchronisation.  The pools live until the process
+// exits.
+constexpr uint64_t kPoolKeep = 8ull << 30;
+constexpr int kMaxDevices = 64;
+static cudaMemPool_t g_pool[kMaxDevices] = {};
+static std::mutex g_pool_mu;
+
+static cudaMemPool_t device_pool() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return nullptr;
+  std::lock_guard<std::mutex> lk(g_pool_mu);
+  if (!g_pool[dev]) {
+    cudaMemPoolProps props{};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    cudaMemPool_t pool = nullptr;
+    if (cudaMemPoolCreate(&pool, &props) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    uint64_t keep = kPoolKeep;
+    if (cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep) != cudaSuccess) cudaGetLastError();
+    g_pool[dev] = pool;
+  }
+  return g_pool[dev];
+}
+
 static std::atomic<unsigned long long> g_allocs{0};
 cudaError_t malloc_async(void** p, size_t bytes, cudaStream_t st) {
   g_allocs.fetch_add(1, std::memory_order_relaxed);
-  return cudaMallocAsync(p, bytes, st);
+  cudaMemPool_t pool = device_pool();
+  return pool ? cudaMallocFromPoolAsync(p, bytes, pool, st) : cudaMallocAsync(p, bytes, st);
 }
 
 // ---- opt-in kernel timing ----
